@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""SNAP energy + force benchmark on GB300 (atom-steps/s).
+
+One step = one full snap_compute: device neighbour build, Cayley-Klein
+geometry, compute_U, compute_Y, fused dU + dE and the force/virial gather, on
+a synthetic BCC configuration resident in HBM.  The headline workload is the
+paper's benchmark shape (2000 atoms, 26 neighbours, 2J = 8) in mixed
+precision; FP64 and 2J = 14 (2000 and 16000 atoms) are reported as variants.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (under torchrun) runs independent replicas, one per GPU (the SNAP
+evaluation of one configuration does not shard here), weak scaling.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SNAP energy+force atom-steps/s at 2J=8/14: mixed vs FP64 on 1 GB300"
+UNIT = "atom-steps/s"
+FLUSH_BYTES = 256 << 20          # > 129 MB L2
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x FMA x max clock
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12         # 1.26: SMs x 2 DFMA/clk x FMA x max clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant-seconds", type=float, default=1.0)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        time.sleep(0.05)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                smax = max(smax, float(r[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[4:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def read_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary (a line 'traffic <kernel> <workload> <bytes>'), else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        p = line.split()
+        if len(p) == 4 and p[0] == "traffic" and p[1] == kernel and p[2] == workload:
+            return float(p[3])
+    return None
+
+
+def cpu_baseline(w, seconds=10.0):
+    """The FP64 oracle, as it stands, on the host cores: whole evaluations of
+    the workload (energy, forces, virial) repeated for about `seconds`."""
+    from oracle import snap_oracle as O
+    cfg, beta = w.config(), w.beta()
+    p = O.Params(w.twojmax)
+    pairs = O.build_neighbors(cfg.pos, cfg.box, p.rcut)
+    n = cfg.natoms
+    if w.twojmax > 8:
+        # 2J = 14: evaluate a fixed subset of centre atoms per step
+        import numpy as np
+        need = np.zeros(n, dtype=bool)
+        need[: min(n, 256)] = True
+        sample = f"oracle E+dE/dr for the first {int(need.sum())} of {n} atoms per step"
+        units = int(need.sum())
+    else:
+        need = None
+        sample = f"oracle full E+F+virial of all {n} atoms per step (neighbour list built once)"
+        units = n
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        O.compute(p, beta, n, pairs, need=need)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 50:
+            break
+    return {"value": units * steps / el, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+            "sample": f"{sample}; {steps} steps in {el:.1f} s, workload {w.name}"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle timed on the host cores, each step
+    a bounded sample (a fixed subset of centre atoms) of the workload."""
+    import numpy as np
+    from oracle import snap_oracle as O
+    from paper_2011_12875_gb300 import inputs
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    w = inputs.WORKLOADS["bcc10_2j8"]
+    cfg, beta = w.config(), w.beta()
+    p = O.Params(w.twojmax)
+    pairs = O.build_neighbors(cfg.pos, cfg.box, p.rcut)
+    n = cfg.natoms
+    # calibrate: time per centre atom
+    need = np.zeros(n, dtype=bool)
+    need[:64] = True
+    t0 = time.perf_counter()
+    O.compute(p, beta, n, pairs, need=need)
+    per_atom = (time.perf_counter() - t0) / 64
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    m = int(max(1, min(n, budget / max(per_atom, 1e-9))))
+    need = np.zeros(n, dtype=bool)
+    need[:m] = True
+    for _ in range(args.warmup):
+        O.compute(p, beta, n, pairs, need=need)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.compute(p, beta, n, pairs, need=need)
+    el = time.perf_counter() - t0
+    value = m * args.steps / el
+    sample = f"oracle E + dE/dr of {m} of {n} centre atoms per step ({w.name})"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "natoms": n, "twojmax": w.twojmax,
+                                        "sample_atoms": m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_variant(torch, snap, w, precision, steps, warmup, flush, dev, profile=False):
+    """Device time of `steps` evaluations (CUDA events on the compute stream,
+    L2 flushed between steps outside the events)."""
+    cfg, beta = w.config(), w.beta()
+    s = snap.Snap(w.twojmax, beta, precision=precision)
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device=dev)
+    n = cfg.natoms
+    E = torch.empty(n, dtype=torch.float64, device=dev)
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    W = torch.empty(6, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        s.compute(pos, cfg.box, E, F, W, wait=False)
+    s.sync()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    if profile:
+        s.profile(True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        evs[k][0].record(stream)
+        s.compute(pos, cfg.box, E, F, W, wait=False)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    s.sync()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    prof = s.profile_read() if profile else None
+    launches = s.launches_per_call()
+    npairs = int(s.get_buffer(snap.BUF_NBR_CNT).sum())
+    s.close()
+    return {"ms": ms, "wall": wall, "prof": prof, "launches": launches, "npairs": npairs,
+            "natoms": n}
+
+
+def e2e_host(snap, torch, w, precision, steps):
+    """Same metric through snap_compute_host: pinned host buffers, H2D of the
+    positions and D2H of energies, forces and virial inside every step."""
+    import numpy as np
+    cfg, beta = w.config(), w.beta()
+    n = cfg.natoms
+    s = snap.Snap(w.twojmax, beta, precision=precision)
+    pin = lambda shape: torch.empty(shape, dtype=torch.float64).pin_memory().numpy()
+    pos = pin((n, 3))
+    pos[:] = cfg.pos
+    out = (pin((n,)), pin((n, 3)), pin((6,)))
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(3):
+        s.compute_host(pos, cfg.box, stream=stream, out=out)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.compute_host(pos, cfg.box, stream=stream, out=out)
+    el = time.perf_counter() - t0
+    s.close()
+    return {"value": n * steps / el, "unit": UNIT, "h2d_bytes_per_step": n * 3 * 8,
+            "d2h_bytes_per_step": n * 8 + n * 3 * 8 + 6 * 8, "steps": steps,
+            "ms_per_step": 1e3 * el / steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world, rank, local = dist_setup(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    from paper_2011_12875_gb300 import build, flops, inputs, snap
+    build.build()
+    snap.load()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    head = inputs.WORKLOADS["bcc10_2j8"]
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    sampler = ClockSampler(int(cvd) if cvd.isdigit() else local)
+    if pg:
+        pg.barrier()
+    sampler.start()
+    r = time_variant(torch, snap, head, snap.MIXED, args.steps, args.warmup, flush, dev,
+                     profile=True)
+    clocks = sampler.stop()
+    ms_mean = statistics.mean(r["ms"])
+    ms_med = statistics.median(r["ms"])
+    t_max = ms_mean
+    if pg:
+        t = torch.tensor([ms_mean], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * r["natoms"] / (t_max * 1e-3)
+
+    # roofline of the dominant kernel (largest share of the step)
+    prof = r["prof"]
+    dom = max(prof, key=lambda k: prof[k][0])
+    fl = flops.step(head.twojmax, r["natoms"], r["npairs"])
+    dom_ms = prof[dom][0] / max(prof[dom][1], 1)
+    achieved = fl.get(dom, 0) / (dom_ms * 1e-3) / 1e12
+    stages = {k: {"ms_per_call": v[0] / max(v[1], 1),
+                  "share": v[0] / sum(x[0] for x in prof.values())} for k, v in prof.items()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max, "ms_per_step_median": ms_med,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 recursions + f64 geometry/accumulation",
+        "data": "synthetic BCC (a=3.1803 A, +-0.1 A displacements, seeded beta)",
+        "config": {"workload": head.name, "natoms": r["natoms"], "twojmax": head.twojmax,
+                   "neighbors": r["npairs"] / r["natoms"], "precision": "mixed",
+                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": r["launches"] * args.steps,
+        "stages": stages,
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "flops_per_launch": fl.get(dom, 0),
+                     "traffic": read_traffic(dom, head.name)},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        line["e2e"] = e2e_host(snap, torch, head, snap.MIXED, min(args.steps, 300))
+        if not args.no_variants:
+            variants = {}
+            for name, prec, tag in (("bcc10_2j8", snap.FP64, "fp64_2j8_2000"),
+                                    ("bcc10_2j14", snap.MIXED, "mixed_2j14_2000"),
+                                    ("bcc10_2j14", snap.FP64, "fp64_2j14_2000"),
+                                    ("bcc20_2j14", snap.MIXED, "mixed_2j14_16000"),
+                                    ("bcc20_2j14", snap.FP64, "fp64_2j14_16000")):
+                w = inputs.WORKLOADS[name]
+                probe = time_variant(torch, snap, w, prec, 2, 1, flush, dev)
+                est = statistics.mean(probe["ms"]) * 1e-3
+                k = int(max(3, min(args.steps, args.variant_seconds / max(est, 1e-6))))
+                v = time_variant(torch, snap, w, prec, k, 2, flush, dev, profile=True)
+                vm = statistics.mean(v["ms"])
+                vp = v["prof"]
+                vdom = max(vp, key=lambda x: vp[x][0])
+                vfl = flops.step(w.twojmax, v["natoms"], v["npairs"])
+                vdom_ms = vp[vdom][0] / max(vp[vdom][1], 1)
+                peak = FP32_PEAK_TFLOPS if prec == snap.MIXED else FP64_PEAK_TFLOPS
+                ach = vfl.get(vdom, 0) / (vdom_ms * 1e-3) / 1e12
+                variants[tag] = {"value": v["natoms"] / (vm * 1e-3), "ms_per_step": vm, "steps": k,
+                                 "dominant_kernel": vdom, "dominant_share": vp[vdom][0] / sum(x[0] for x in vp.values()),
+                                 "roofline_frac": ach / peak, "achieved_tflops": ach,
+                                 "peak_tflops": peak}
+            variants["mixed_2j8_2000"] = {"value": value / world, "ms_per_step": ms_mean}
+            line["variants"] = variants
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(head)
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * snap_gb300.h -- C ABI of the GB300 (sm_103a) SNAP energy + force library.
+ *
+ * The library computes, for a periodic orthorhombic configuration of atoms of
+ * one species, the SNAP per-atom energies, the forces and the virial with the
+ * adjoint formulation of Gayatri et al., "Rapid Exploration of Optimization
+ * Strategies on Advanced Architectures using TestSNAP and LAMMPS"
+ * (arXiv:2011.12875):
+ *
+ *   neighbour list            (Sec. II-B, build_neighborlist)
+ *   U_j = sum_k f_c u_j       (Sec. II-A Eq. u; Sec. V-A Eq. hysphrecur)
+ *   Y_j = sum beta Z^j_{j1j2} (Sec. III Eq. y)
+ *   dE_i/dr_ik = Y : conj(dU/dr)  (Sec. III Eq. snapforce2; fused dU + dE)
+ *   E_i = beta_0 + sum beta_l B_l          (Sec. II-A Eq. snapatomenergy)
+ *   F, virial from dE_i/dr_ik (Sec. III, dElist and update_forces)
+ *
+ * Conventions shared by all calls:
+ *  - Status: every call returns 0 (SNAP_OK) or a negative snap_status; the
+ *    message is in snap_last_error(ctx).  No call aborts, traps or prints.
+ *  - Memory: all array arguments are owned by the caller.  Unless a call
+ *    says "host", pointers are CUDA device pointers on the current device.
+ *    The context owns its coefficient tables and a device workspace that
+ *    grows with the largest system seen; it is released by snap_destroy.
+ *  - Streams: work is enqueued on the caller's cudaStream_t (passed as
+ *    void*; NULL = legacy default stream).
+ *  - Units: lengths in Angstrom; energies in the units of beta.
+ *  - One context must not be used from two host threads at once.
+ */
+#ifndef SNAP_GB300_H
+#define SNAP_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct snap_ctx snap_ctx;
+
+/* Working precision of the U, Y and dU recursions.  SNAP_FP64: everything
+ * in FP64.  SNAP_MIXED: the three recursions run in FP32; the Cayley-Klein
+ * parameters and the per-atom energy, force and virial accumulations stay
+ * in FP64. */
+enum snap_precision { SNAP_FP64 = 0, SNAP_MIXED = 1 };
+
+enum snap_status {
+  SNAP_OK = 0,
+  SNAP_ERR_ARG = -1,            /* invalid argument (message says which) */
+  SNAP_ERR_NEIGH_OVERFLOW = -2, /* an atom has more neighbours than the capacity */
+  SNAP_ERR_BOX = -3,            /* box length <= 0 or not finite */
+  SNAP_ERR_CUDA = -4,           /* a CUDA call failed (message has the CUDA error) */
+  SNAP_ERR_TIMEOUT = -5,        /* a bounded device wait gave up */
+  SNAP_ERR_NOMEM = -6,          /* device or host allocation failed */
+  SNAP_ERR_NEIGH_ASYM = -7      /* a given neighbour list is not symmetric */
+};
+
+/* Number of bispectrum components N_B for 0 <= 2j2 <= 2j1 <= 2j <= twojmax
+ * (Sec. II-A): 55 at twojmax 8, 204 at 14.  Returns -1 for twojmax outside
+ * 0..14. */
+int snap_num_coeff(int twojmax);
+
+/* Create a context.
+ *   twojmax    : 2J, 0..14 (Sec. II-C: 2J8 and 2J14 are the paper's sizes)
+ *   rcut       : cutoff radius R_cut (> rmin0)
+ *   rfac0      : in (0, 1]; theta0 = rfac0*pi*(r - rmin0)/(rcut - rmin0)
+ *   rmin0      : >= 0, start of the switching region
+ *   switchflag : 1 = cosine switching f_c on [rmin0, rcut), 0 = f_c = 1
+ *   beta       : host, 1 + N_B doubles: beta_0, then beta_l in canonical
+ *                order (2j1 outer, 2j2 <= 2j1, 2j from 2j1-2j2 in steps of
+ *                2 up to min(twojmax, 2j1+2j2), keeping 2j >= 2j1)
+ *   precision  : SNAP_FP64 or SNAP_MIXED
+ *   out        : receives the new context (NULL on failure)
+ * Uploads the index, Clebsch-Gordan and coefficient tables to the current
+ * device (synchronous). */
+int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switchflag,
+                const double* beta, int precision, snap_ctx** out);
+
+/* Replace beta (host, 1 + N_B doubles); used by fitting loops.  Synchronous
+ * with respect to the host; later snap_compute calls see the new values. */
+int snap_set_beta(snap_ctx* ctx, const double* beta);
+
+/* Capacity K of the device-built neighbour list (slots per atom, 1..64,
+ * default 32).  Counts above K make snap_compute return
+ * SNAP_ERR_NEIGH_OVERFLOW; snap_neigh_max() then reports the count needed. */
+int snap_set_neigh_cap(snap_ctx* ctx, int cap);
+
+/* Largest neighbour count seen by the last snap_compute (device builder). */
+int snap_neigh_max(const snap_ctx* ctx);
+
+/* Energy, forces and virial of one configuration.
+ *   natoms  : N >= 0 (N = 0 returns at once)
+ *   pos     : device, [N][3] doubles (x, y, z)
+ *   box     : HOST, 3 doubles: orthorhombic box lengths, periodic in x, y, z
+ *   nbr_cnt, nbr_idx, nbr_img, nbr_cap :
+ *             all NULL/0 -> the library builds the list on the device
+ *             (every k, image s with |r_k + s L - r_i| < rcut, k != i or
+ *             s != 0).  Otherwise a caller list on the device: nbr_cnt [N]
+ *             ints, nbr_idx [N][nbr_cap] ints, nbr_img [N][nbr_cap][3]
+ *             signed chars (image shift s, r_ik = r_k + s L - r_i).  The
+ *             list must be full (both (i,k,s) and (k,i,-s)); pairs with
+ *             r >= rcut are ignored.
+ *   energy  : device, [N] doubles per-atom energy E_i, or NULL
+ *   forces  : device, [N][3] doubles F_i = -dE/dr_i (required)
+ *   virial  : device, 6 doubles W_xx, W_yy, W_zz, W_xy, W_xz, W_yz with
+ *             W_ab = -sum_{i,k} (dE_i/dr_ik)_a (r_ik)_b, or NULL
+ *   stream  : cudaStream_t (void*)
+ * Returns after the stream has finished the call (the status needs the
+ * neighbour-overflow flag).  Results are deterministic for a given input. */
+int snap_compute(snap_ctx* ctx, int natoms, const double* pos, const double* box,
+                 const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
+                 int nbr_cap, double* energy, double* forces, double* virial,
+                 void* stream);
+
+/* snap_compute without the final wait: enqueues the whole evaluation on
+ * the stream and returns.  Argument errors are returned at once; errors
+ * found on the device (neighbour overflow, asymmetric list) are returned by
+ * the next snap_sync.  The first call for a given N and capacity allocates
+ * the workspace, so that call must not happen inside a CUDA graph capture;
+ * later calls with the same sizes allocate nothing and may be captured.
+ * The output buffers must stay valid until the stream reaches them. */
+int snap_compute_async(snap_ctx* ctx, int natoms, const double* pos, const double* box,
+                       const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
+                       int nbr_cap, double* energy, double* forces, double* virial,
+                       void* stream);
+
+/* Wait for `stream` and return the device status of the last
+ * snap_compute_async on ctx (SNAP_OK, SNAP_ERR_NEIGH_OVERFLOW, ...). */
+int snap_sync(snap_ctx* ctx, void* stream);
+
+/* Per-stage timing with CUDA events recorded on the compute stream.
+ * snap_profile(ctx, 1) starts (and zeroes) the totals, 0 stops.
+ * snap_profile_read waits for the recorded events and fills, for each of
+ * min(nstages, SNAP_NSTAGES) stages, the total milliseconds and the number of
+ * calls timed; it returns SNAP_NSTAGES.  snap_stage_name(k) names stage k.
+ * snap_launches_per_call(ctx) is the number of kernels the last compute
+ * launched. */
+#define SNAP_NSTAGES 7
+int snap_profile(snap_ctx* ctx, int enable);
+int snap_profile_read(snap_ctx* ctx, double* ms, long long* calls, int nstages);
+const char* snap_stage_name(int stage);
+int snap_launches_per_call(const snap_ctx* ctx);
+
+/* Same as snap_compute with HOST buffers and the device neighbour builder:
+ * copies pos to the device, computes, and copies energy (may be NULL),
+ * forces and virial (may be NULL) back, all on the given stream.  The host
+ * buffers should be pinned for full copy bandwidth. */
+int snap_compute_host(snap_ctx* ctx, int natoms, const double* pos_host,
+                      const double* box, double* energy_host, double* forces_host,
+                      double* virial_host, void* stream);
+
+/* Internal buffers of the last snap_compute, copied to HOST memory for
+ * inspection and parity tests.  Returns the number of bytes the buffer
+ * holds (copying min(bytes, that) when dst != NULL), or a negative status.
+ * Layouts (N atoms, K = capacity, H = half-matrix size, see below):
+ *   SNAP_BUF_NBR_CNT : int [N]
+ *   SNAP_BUF_NBR_IDX : int [N][K]
+ *   SNAP_BUF_NBR_IMG : signed char [N][K][3]
+ *   SNAP_BUF_NBR_REV : int [N][K]   slot of the reverse pair in k's list
+ *   SNAP_BUF_RIJ     : double [N][K][3]
+ *   SNAP_BUF_ULISTTOT: double [N][H][2] (re, im) in half layout
+ *   SNAP_BUF_YLIST   : double [N][H][2] (re, im) in half layout
+ *   SNAP_BUF_DEDR    : double [N][K][3]  dE_i/dr_ik per slot
+ * Half layout: for t = 2j = 0..twojmax, the columns mb = 0..floor(t/2) of
+ * the (t+1)x(t+1) matrix, each column ma = 0..t; element (t, ma, mb) at
+ * snap_half_index(twojmax, t, ma, mb).  The other columns follow from
+ * M[t-ma][t-mb] = (-1)^(ma+mb) conj(M[ma][mb]). */
+enum snap_buffer {
+  SNAP_BUF_NBR_CNT = 0,
+  SNAP_BUF_NBR_IDX = 1,
+  SNAP_BUF_NBR_IMG = 2,
+  SNAP_BUF_NBR_REV = 3,
+  SNAP_BUF_RIJ = 4,
+  SNAP_BUF_ULISTTOT = 5,
+  SNAP_BUF_YLIST = 6,
+  SNAP_BUF_DEDR = 7
+};
+long long snap_get_buffer(snap_ctx* ctx, int which, void* dst_host, size_t bytes);
+
+/* Index of element (t, ma, mb), mb <= t/2, in the half layout; -1 if out of
+ * range.  snap_half_size(twojmax) is H (155 at 8, 652 at 14). */
+int snap_half_index(int twojmax, int t, int ma, int mb);
+int snap_half_size(int twojmax);
+
+/* Release the context and its device memory. */
+int snap_destroy(snap_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none); with ctx == NULL the
+ * message of the last failed snap_create. */
+const char* snap_last_error(const snap_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNAP_GB300_H */

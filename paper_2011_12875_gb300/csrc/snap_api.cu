@@ -1,0 +1,622 @@
+// snap_api.cu -- the C ABI declared in include/snap_gb300.h: context, tables,
+// workspace and the per-call launch sequence (arXiv:2011.12875, Listing 5:
+// build_neighborlist, compute_U, compute_Y, compute_dU + compute_dE fused,
+// update_forces).
+#include <cmath>
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "snap_gb300.h"
+#include "snap_internal.h"
+#include "snap_tables.h"
+
+using snap::HostTables;
+
+struct snap_ctx {
+  int twojmax = 0;
+  double rcut = 0, rfac0 = 0, rmin0 = 0, wself = 1.0;
+  int switchflag = 1;
+  int precision = SNAP_FP64;
+  int nsm = 152;
+  HostTables tab;
+  std::vector<double> beta;
+  int K = 32;
+  int last_nmax = 0;
+  int last_n = 0, last_K = 0;
+  std::string err;
+
+  // device tables
+  int* d_half_tmm = nullptr;
+  snap::YJob* d_jobs = nullptr;
+  void* d_cg = nullptr;
+  void* d_betaw = nullptr;
+  void* d_root = nullptr;
+  int* d_yslice = nullptr;
+  int nslices = -1;
+
+  // workspace
+  long cap_nk = 0;
+  int cap_n = 0;
+  float4* d_pos4 = nullptr;
+  int* d_cnt = nullptr;
+  int* d_nbr = nullptr;
+  signed char* d_img = nullptr;
+  double* d_rij = nullptr;
+  int* d_rev = nullptr;
+  double* d_geom = nullptr;
+  double* d_dedr = nullptr;
+  void* d_Ure = nullptr;
+  void* d_Uim = nullptr;
+  void* d_Yre = nullptr;
+  void* d_Yim = nullptr;
+  double* d_vpart = nullptr;
+  int* d_flags = nullptr;
+  int* h_flags = nullptr;
+
+  // per-stage profiling
+  bool prof_on = false;
+  std::vector<std::vector<cudaEvent_t>> prof_pending, prof_free;
+  double prof_ms[SNAP_NSTAGES] = {0};
+  long long prof_calls[SNAP_NSTAGES] = {0};
+  int launches = 0;
+
+  // buffers of snap_compute_host
+  int cap_host = 0;
+  double* d_hpos = nullptr;
+  double* d_hE = nullptr;
+  double* d_hF = nullptr;
+  double* d_hW = nullptr;
+
+  size_t rsize() const { return precision == SNAP_MIXED ? sizeof(float) : sizeof(double); }
+};
+
+namespace {
+
+std::string g_create_error;
+
+int fail(snap_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define SNAP_CUDA(ctx, expr)                                                            \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, SNAP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// Convert doubles to the working precision and upload (allocating if needed).
+int upload_r(snap_ctx* c, void** dst, const std::vector<double>& v) {
+  const size_t n = v.size() ? v.size() : 1;
+  if (!*dst) SNAP_CUDA(c, cudaMalloc(dst, n * c->rsize()));
+  if (c->precision == SNAP_MIXED) {
+    std::vector<float> f(v.begin(), v.end());
+    if (f.empty()) f.push_back(0.f);
+    SNAP_CUDA(c, cudaMemcpy(*dst, f.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<double> d(v);
+    if (d.empty()) d.push_back(0.0);
+    SNAP_CUDA(c, cudaMemcpy(*dst, d.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return SNAP_OK;
+}
+
+template <typename T>
+int upload(snap_ctx* c, T** dst, const std::vector<T>& v) {
+  const size_t n = v.size() ? v.size() : 1;
+  dfree(*dst);
+  SNAP_CUDA(c, cudaMalloc((void**)dst, n * sizeof(T)));
+  if (!v.empty()) SNAP_CUDA(c, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SNAP_OK;
+}
+
+void free_workspace(snap_ctx* c) {
+  dfree(c->d_pos4);
+  dfree(c->d_cnt);
+  dfree(c->d_nbr);
+  dfree(c->d_img);
+  dfree(c->d_rij);
+  dfree(c->d_rev);
+  dfree(c->d_geom);
+  dfree(c->d_dedr);
+  dfree(c->d_Ure);
+  dfree(c->d_Uim);
+  dfree(c->d_Yre);
+  dfree(c->d_Yim);
+  dfree(c->d_vpart);
+  c->cap_nk = 0;
+  c->cap_n = 0;
+}
+
+int ensure_workspace(snap_ctx* c, int n, int K) {
+  const long nk = (long)n * K;
+  if (n <= c->cap_n && nk <= c->cap_nk) return SNAP_OK;
+  cudaDeviceSynchronize();
+  free_workspace(c);
+  const int ncap = std::max(n, 1);
+  const long nkcap = std::max(nk, 1L);
+  const long nblk = (ncap + 31) / 32;
+  const size_t uy = (size_t)nblk * 32 * c->tab.H * c->rsize();
+  SNAP_CUDA(c, cudaMalloc(&c->d_pos4, sizeof(float4) * ncap));
+  SNAP_CUDA(c, cudaMalloc(&c->d_cnt, sizeof(int) * ncap));
+  SNAP_CUDA(c, cudaMalloc(&c->d_nbr, sizeof(int) * nkcap));
+  SNAP_CUDA(c, cudaMalloc(&c->d_img, 3 * nkcap));
+  SNAP_CUDA(c, cudaMalloc(&c->d_rij, sizeof(double) * 3 * nkcap));
+  SNAP_CUDA(c, cudaMalloc(&c->d_rev, sizeof(int) * nkcap));
+  SNAP_CUDA(c, cudaMalloc(&c->d_geom, sizeof(double) * snap::kGeomStride * nkcap));
+  SNAP_CUDA(c, cudaMalloc(&c->d_dedr, sizeof(double) * 3 * nkcap));
+  SNAP_CUDA(c, cudaMalloc(&c->d_Ure, uy));
+  SNAP_CUDA(c, cudaMalloc(&c->d_Uim, uy));
+  SNAP_CUDA(c, cudaMalloc(&c->d_Yre, uy));
+  SNAP_CUDA(c, cudaMalloc(&c->d_Yim, uy));
+  // lanes past the last atom read zeros in compute_Y
+  SNAP_CUDA(c, cudaMemset(c->d_Ure, 0, uy));
+  SNAP_CUDA(c, cudaMemset(c->d_Uim, 0, uy));
+  SNAP_CUDA(c, cudaMalloc(&c->d_vpart, sizeof(double) * 6 * (snap::force_blocks(ncap) + 1)));
+  c->cap_n = ncap;
+  c->cap_nk = nkcap;
+  return SNAP_OK;
+}
+
+int ensure_slices(snap_ctx* c, int n) {
+  const int nblk = (n + 31) / 32;
+  const int target_warps = c->nsm * 16;
+  int ns = (target_warps + nblk - 1) / nblk;
+  ns = std::max(4, std::min(ns, 256));
+  ns = (ns + 3) / 4 * 4;
+  if (ns == c->nslices) return SNAP_OK;
+  int rc = upload(c, &c->d_yslice, c->tab.slices(ns));
+  if (rc) return rc;
+  c->nslices = ns;
+  return SNAP_OK;
+}
+
+bool box_ok(const double* box) {
+  if (!box) return false;
+  for (int d = 0; d < 3; ++d)
+    if (!(std::isfinite(box[d]) && box[d] > 0.0)) return false;
+  return true;
+}
+
+// Enqueue the whole evaluation on stream s (no synchronisation).
+int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int* ucnt,
+            const int* uidx, const signed char* uimg, int ucap, double* energy, double* forces,
+            double* virial, cudaStream_t s) {
+  const bool user = (ucnt || uidx || uimg);
+  if (user && (!ucnt || !uidx || !uimg || ucap < 1 || ucap > snap::kMaxNeighCap))
+    return fail(c, SNAP_ERR_ARG, "neighbour list: cnt, idx and img must all be given with 1 <= cap <= 64");
+  const int K = user ? ucap : c->K;
+  int rc = ensure_workspace(c, n, K);
+  if (rc) return rc;
+  if (!c->d_flags) {
+    SNAP_CUDA(c, cudaMalloc(&c->d_flags, 4 * sizeof(int)));
+    SNAP_CUDA(c, cudaMallocHost(&c->h_flags, 4 * sizeof(int)));
+  }
+  rc = ensure_slices(c, n);
+  if (rc) return rc;
+  SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), s));
+  std::vector<cudaEvent_t> ev;
+  if (c->prof_on) {
+    if (!c->prof_free.empty()) {
+      ev = c->prof_free.back();
+      c->prof_free.pop_back();
+    } else {
+      ev.resize(SNAP_NSTAGES + 1);
+      for (auto& e : ev) SNAP_CUDA(c, cudaEventCreate(&e));
+    }
+  }
+  int stage = 0;
+  auto mark = [&]() -> cudaError_t {
+    if (ev.empty()) return cudaSuccess;
+    return cudaEventRecord(ev[stage++], s);
+  };
+  c->launches = 0;
+  SNAP_CUDA(c, mark());
+
+  if (user) {
+    SNAP_CUDA(c, snap::launch_neigh_ingest(n, K, pos, box[0], box[1], box[2], ucnt, uidx, uimg, ucap,
+                                           c->d_cnt, c->d_nbr, c->d_img, c->d_rij, c->d_flags, s));
+    c->launches += 1;
+  } else {
+    snap::NeighArgs na;
+    na.n = n;
+    na.K = K;
+    na.pos = pos;
+    na.pos4 = c->d_pos4;
+    na.Lx = box[0];
+    na.Ly = box[1];
+    na.Lz = box[2];
+    int S[3];
+    for (int d = 0; d < 3; ++d)
+      S[d] = (box[d] > 2.0 * (c->rcut + 0.05)) ? 0 : (int)std::ceil(c->rcut / box[d]) + 1;
+    na.Sx = S[0];
+    na.Sy = S[1];
+    na.Sz = S[2];
+    na.rcut = c->rcut;
+    na.cnt = c->d_cnt;
+    na.nbr = c->d_nbr;
+    na.img = c->d_img;
+    na.rij = c->d_rij;
+    na.flags = c->d_flags;
+    SNAP_CUDA(c, snap::launch_pos4(n, pos, c->d_pos4, s));
+    SNAP_CUDA(c, snap::launch_neigh_build(na, s));
+    c->launches += 2;
+  }
+  SNAP_CUDA(c, mark());
+
+  snap::WorkArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.K = K;
+  a.twojmax = c->twojmax;
+  a.H = c->tab.H;
+  a.lmax = c->tab.lmax;
+  a.rcut = c->rcut;
+  a.rfac0 = c->rfac0;
+  a.rmin0 = c->rmin0;
+  a.wself = c->wself;
+  a.beta0 = c->beta[0];
+  a.switchflag = c->switchflag;
+  a.cnt = c->d_cnt;
+  a.nbr = c->d_nbr;
+  a.img = c->d_img;
+  a.rev = c->d_rev;
+  a.rij = c->d_rij;
+  a.geom = c->d_geom;
+  a.Ure = c->d_Ure;
+  a.Uim = c->d_Uim;
+  a.Yre = c->d_Yre;
+  a.Yim = c->d_Yim;
+  a.dedr = c->d_dedr;
+  a.energy = energy;
+  a.forces = forces;
+  a.vpart = c->d_vpart;
+  a.virial = virial;
+  a.flags = c->d_flags;
+  a.half_tmm = c->d_half_tmm;
+  a.yjobs = c->d_jobs;
+  a.yslice = c->d_yslice;
+  a.nslices = c->nslices;
+  a.cg = c->d_cg;
+  a.betaw = c->d_betaw;
+  a.rootpq = c->d_root;
+
+  SNAP_CUDA(c, snap::launch_rev(a, c->d_rev, s));
+  SNAP_CUDA(c, mark());
+  SNAP_CUDA(c, snap::launch_geom(a, s));
+  SNAP_CUDA(c, mark());
+  const bool mixed = c->precision == SNAP_MIXED;
+  SNAP_CUDA(c, mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s));
+  SNAP_CUDA(c, mark());
+  SNAP_CUDA(c, mixed ? snap::launch_yi<float>(a, s) : snap::launch_yi<double>(a, s));
+  SNAP_CUDA(c, mark());
+  SNAP_CUDA(c, mixed ? snap::launch_de<float>(a, s) : snap::launch_de<double>(a, s));
+  SNAP_CUDA(c, mark());
+  SNAP_CUDA(c, mixed ? snap::launch_force<float>(a, s) : snap::launch_force<double>(a, s));
+  SNAP_CUDA(c, mark());
+  c->launches += 6 + (virial ? 1 : 0);
+  if (!ev.empty()) c->prof_pending.push_back(ev);
+  SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  c->last_n = n;
+  c->last_K = K;
+  return SNAP_OK;
+}
+
+int check_flags(snap_ctx* c) {
+  c->last_nmax = c->h_flags[0];
+  if (c->h_flags[2]) return fail(c, SNAP_ERR_ARG, "neighbour list: count outside 0..cap or index outside 0..N-1");
+  if (c->h_flags[0] > c->last_K)
+    return fail(c, SNAP_ERR_NEIGH_OVERFLOW,
+                "an atom has " + std::to_string(c->h_flags[0]) + " neighbours, capacity is " +
+                    std::to_string(c->last_K));
+  if (c->h_flags[1]) return fail(c, SNAP_ERR_NEIGH_ASYM, "neighbour list is not symmetric (missing reverse pair)");
+  return SNAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int snap_num_coeff(int twojmax) { return snap::count_coeff(twojmax); }
+
+int snap_half_size(int twojmax) {
+  if (twojmax < 0 || twojmax > snap::kMaxTwoJ) return -1;
+  return snap::half_size(twojmax);
+}
+
+int snap_half_index(int twojmax, int t, int ma, int mb) {
+  if (twojmax < 0 || twojmax > snap::kMaxTwoJ || t < 0 || t > twojmax || ma < 0 || ma > t || mb < 0 ||
+      2 * mb > t)
+    return -1;
+  return snap::half_base(t) + mb * (t + 1) + ma;
+}
+
+int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switchflag,
+                const double* beta, int precision, snap_ctx** out) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return SNAP_ERR_ARG;
+  }
+  *out = nullptr;
+  if (twojmax < 0 || twojmax > snap::kMaxTwoJ) {
+    g_create_error = "twojmax must be in 0..14";
+    return SNAP_ERR_ARG;
+  }
+  if (!(std::isfinite(rcut) && std::isfinite(rmin0) && rmin0 >= 0.0 && rcut > rmin0)) {
+    g_create_error = "need 0 <= rmin0 < rcut";
+    return SNAP_ERR_ARG;
+  }
+  if (!(rfac0 > 0.0 && rfac0 <= 1.0)) {
+    g_create_error = "rfac0 must be in (0, 1]";
+    return SNAP_ERR_ARG;
+  }
+  if (switchflag != 0 && switchflag != 1) {
+    g_create_error = "switchflag must be 0 or 1";
+    return SNAP_ERR_ARG;
+  }
+  if (precision != SNAP_FP64 && precision != SNAP_MIXED) {
+    g_create_error = "precision must be SNAP_FP64 or SNAP_MIXED";
+    return SNAP_ERR_ARG;
+  }
+  if (!beta) {
+    g_create_error = "beta is NULL";
+    return SNAP_ERR_ARG;
+  }
+  snap_ctx* c = new (std::nothrow) snap_ctx;
+  if (!c) {
+    g_create_error = "out of host memory";
+    return SNAP_ERR_NOMEM;
+  }
+  c->twojmax = twojmax;
+  c->rcut = rcut;
+  c->rfac0 = rfac0;
+  c->rmin0 = rmin0;
+  c->switchflag = switchflag;
+  c->precision = precision;
+  c->tab.build(twojmax);
+  c->beta.assign(beta, beta + 1 + c->tab.ncoeff);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("CUDA: ") + cudaGetErrorString(e);
+    delete c;
+    return SNAP_ERR_CUDA;
+  }
+  int rc = upload(c, &c->d_half_tmm, c->tab.half_tmm);
+  if (!rc) rc = upload(c, &c->d_jobs, c->tab.jobs);
+  if (!rc) rc = upload_r(c, &c->d_cg, c->tab.cg);
+  if (!rc) rc = upload_r(c, &c->d_root, c->tab.rootpq);
+  if (!rc) rc = upload_r(c, &c->d_betaw, c->tab.beta_weights(c->beta.data()));
+  if (rc) {
+    g_create_error = c->err;
+    snap_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return SNAP_OK;
+}
+
+int snap_set_beta(snap_ctx* c, const double* beta) {
+  if (!c || !beta) return fail(c, SNAP_ERR_ARG, "NULL argument");
+  cudaDeviceSynchronize();
+  c->beta.assign(beta, beta + 1 + c->tab.ncoeff);
+  return upload_r(c, &c->d_betaw, c->tab.beta_weights(c->beta.data()));
+}
+
+int snap_set_neigh_cap(snap_ctx* c, int cap) {
+  if (!c) return SNAP_ERR_ARG;
+  if (cap < 1 || cap > snap::kMaxNeighCap) return fail(c, SNAP_ERR_ARG, "capacity must be in 1..64");
+  c->K = cap;
+  return SNAP_OK;
+}
+
+int snap_neigh_max(const snap_ctx* c) { return c ? c->last_nmax : -1; }
+
+int snap_compute(snap_ctx* c, int natoms, const double* pos, const double* box, const int* nbr_cnt,
+                 const int* nbr_idx, const signed char* nbr_img, int nbr_cap, double* energy,
+                 double* forces, double* virial, void* stream) {
+  if (!c) return SNAP_ERR_ARG;
+  if (natoms < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
+  if (!box_ok(box)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (natoms == 0) {
+    if (virial) SNAP_CUDA(c, cudaMemsetAsync(virial, 0, 6 * sizeof(double), s));
+    return SNAP_OK;
+  }
+  if (!pos || !forces) return fail(c, SNAP_ERR_ARG, "pos and forces are required");
+  int rc = enqueue(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, energy, forces, virial, s);
+  if (rc) return rc;
+  SNAP_CUDA(c, cudaStreamSynchronize(s));
+  return check_flags(c);
+}
+
+int snap_compute_async(snap_ctx* c, int natoms, const double* pos, const double* box,
+                       const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
+                       int nbr_cap, double* energy, double* forces, double* virial, void* stream) {
+  if (!c) return SNAP_ERR_ARG;
+  if (natoms < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
+  if (!box_ok(box)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (natoms == 0) {
+    if (virial) SNAP_CUDA(c, cudaMemsetAsync(virial, 0, 6 * sizeof(double), s));
+    return SNAP_OK;
+  }
+  if (!pos || !forces) return fail(c, SNAP_ERR_ARG, "pos and forces are required");
+  return enqueue(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, energy, forces, virial, s);
+}
+
+int snap_sync(snap_ctx* c, void* stream) {
+  if (!c) return SNAP_ERR_ARG;
+  SNAP_CUDA(c, cudaStreamSynchronize((cudaStream_t)stream));
+  if (!c->h_flags || c->last_n == 0) return SNAP_OK;
+  return check_flags(c);
+}
+
+int snap_profile(snap_ctx* c, int enable) {
+  if (!c) return SNAP_ERR_ARG;
+  double ms[SNAP_NSTAGES];
+  long long calls[SNAP_NSTAGES];
+  snap_profile_read(c, ms, calls, SNAP_NSTAGES);  // drain pending events
+  for (int k = 0; k < SNAP_NSTAGES; ++k) {
+    c->prof_ms[k] = 0.0;
+    c->prof_calls[k] = 0;
+  }
+  c->prof_on = enable != 0;
+  return SNAP_OK;
+}
+
+int snap_profile_read(snap_ctx* c, double* ms, long long* calls, int nstages) {
+  if (!c) return SNAP_ERR_ARG;
+  for (auto& ev : c->prof_pending) {
+    SNAP_CUDA(c, cudaEventSynchronize(ev[SNAP_NSTAGES]));
+    for (int k = 0; k < SNAP_NSTAGES; ++k) {
+      float t = 0.f;
+      SNAP_CUDA(c, cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+      c->prof_ms[k] += t;
+      c->prof_calls[k] += 1;
+    }
+    c->prof_free.push_back(ev);
+  }
+  c->prof_pending.clear();
+  for (int k = 0; k < std::min(nstages, SNAP_NSTAGES); ++k) {
+    if (ms) ms[k] = c->prof_ms[k];
+    if (calls) calls[k] = c->prof_calls[k];
+  }
+  return SNAP_NSTAGES;
+}
+
+const char* snap_stage_name(int stage) {
+  static const char* names[SNAP_NSTAGES] = {"neighbor_build", "reverse_map", "ck_geometry",
+                                            "compute_ui", "compute_yi", "fused_dE",
+                                            "force_virial"};
+  return (stage >= 0 && stage < SNAP_NSTAGES) ? names[stage] : "";
+}
+
+int snap_launches_per_call(const snap_ctx* c) { return c ? c->launches : -1; }
+
+int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const double* box,
+                      double* energy_host, double* forces_host, double* virial_host, void* stream) {
+  if (!c) return SNAP_ERR_ARG;
+  if (natoms < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
+  if (!box_ok(box)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+  if (natoms == 0) {
+    if (virial_host) std::memset(virial_host, 0, 6 * sizeof(double));
+    return SNAP_OK;
+  }
+  if (!pos_host || !forces_host) return fail(c, SNAP_ERR_ARG, "pos and forces are required");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (natoms > c->cap_host) {
+    cudaDeviceSynchronize();
+    dfree(c->d_hpos);
+    dfree(c->d_hE);
+    dfree(c->d_hF);
+    dfree(c->d_hW);
+    SNAP_CUDA(c, cudaMalloc(&c->d_hpos, sizeof(double) * 3 * natoms));
+    SNAP_CUDA(c, cudaMalloc(&c->d_hE, sizeof(double) * natoms));
+    SNAP_CUDA(c, cudaMalloc(&c->d_hF, sizeof(double) * 3 * natoms));
+    SNAP_CUDA(c, cudaMalloc(&c->d_hW, sizeof(double) * 6));
+    c->cap_host = natoms;
+  }
+  SNAP_CUDA(c, cudaMemcpyAsync(c->d_hpos, pos_host, sizeof(double) * 3 * natoms, cudaMemcpyHostToDevice, s));
+  int rc = enqueue(c, natoms, c->d_hpos, box, nullptr, nullptr, nullptr, 0, energy_host ? c->d_hE : nullptr,
+                   c->d_hF, virial_host ? c->d_hW : nullptr, s);
+  if (rc) return rc;
+  if (energy_host)
+    SNAP_CUDA(c, cudaMemcpyAsync(energy_host, c->d_hE, sizeof(double) * natoms, cudaMemcpyDeviceToHost, s));
+  SNAP_CUDA(c, cudaMemcpyAsync(forces_host, c->d_hF, sizeof(double) * 3 * natoms, cudaMemcpyDeviceToHost, s));
+  if (virial_host)
+    SNAP_CUDA(c, cudaMemcpyAsync(virial_host, c->d_hW, sizeof(double) * 6, cudaMemcpyDeviceToHost, s));
+  SNAP_CUDA(c, cudaStreamSynchronize(s));
+  return check_flags(c);
+}
+
+long long snap_get_buffer(snap_ctx* c, int which, void* dst, size_t bytes) {
+  if (!c) return SNAP_ERR_ARG;
+  const long n = c->last_n, K = c->last_K, H = c->tab.H;
+  if (n == 0) return 0;
+  SNAP_CUDA(c, cudaDeviceSynchronize());
+  auto copy = [&](const void* src, size_t size) -> long long {
+    if (dst) {
+      const cudaError_t e = cudaMemcpy(dst, src, std::min(size, bytes), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return fail(c, SNAP_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return (long long)size;
+  };
+  switch (which) {
+    case SNAP_BUF_NBR_CNT: return copy(c->d_cnt, sizeof(int) * n);
+    case SNAP_BUF_NBR_IDX: return copy(c->d_nbr, sizeof(int) * n * K);
+    case SNAP_BUF_NBR_IMG: return copy(c->d_img, 3 * n * K);
+    case SNAP_BUF_NBR_REV: return copy(c->d_rev, sizeof(int) * n * K);
+    case SNAP_BUF_RIJ: return copy(c->d_rij, sizeof(double) * 3 * n * K);
+    case SNAP_BUF_DEDR: return copy(c->d_dedr, sizeof(double) * 3 * n * K);
+    case SNAP_BUF_ULISTTOT:
+    case SNAP_BUF_YLIST: {
+      const size_t size = sizeof(double) * 2 * n * H;
+      if (!dst) return (long long)size;
+      const long nblk = (n + 31) / 32;
+      const size_t cnt = (size_t)nblk * 32 * H;
+      const bool isU = which == SNAP_BUF_ULISTTOT;
+      const void* re = isU ? c->d_Ure : c->d_Yre;
+      const void* im = isU ? c->d_Uim : c->d_Yim;
+      std::vector<double> hre(cnt), him(cnt);
+      if (c->precision == SNAP_MIXED) {
+        std::vector<float> f(cnt);
+        SNAP_CUDA(c, cudaMemcpy(f.data(), re, cnt * sizeof(float), cudaMemcpyDeviceToHost));
+        hre.assign(f.begin(), f.end());
+        SNAP_CUDA(c, cudaMemcpy(f.data(), im, cnt * sizeof(float), cudaMemcpyDeviceToHost));
+        him.assign(f.begin(), f.end());
+      } else {
+        SNAP_CUDA(c, cudaMemcpy(hre.data(), re, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+        SNAP_CUDA(c, cudaMemcpy(him.data(), im, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+      }
+      std::vector<double> out(2 * n * H);
+      for (long i = 0; i < n; ++i)
+        for (long e = 0; e < H; ++e) {
+          const size_t src = ((size_t)(i >> 5) * H + e) * 32 + (i & 31);
+          out[2 * (i * H + e)] = hre[src];
+          out[2 * (i * H + e) + 1] = him[src];
+        }
+      std::memcpy(dst, out.data(), std::min(size, bytes));
+      return (long long)size;
+    }
+    default: return fail(c, SNAP_ERR_ARG, "unknown buffer");
+  }
+}
+
+int snap_destroy(snap_ctx* c) {
+  if (!c) return SNAP_OK;
+  cudaDeviceSynchronize();
+  free_workspace(c);
+  dfree(c->d_half_tmm);
+  dfree(c->d_jobs);
+  dfree(c->d_cg);
+  dfree(c->d_betaw);
+  dfree(c->d_root);
+  dfree(c->d_yslice);
+  dfree(c->d_flags);
+  dfree(c->d_hpos);
+  dfree(c->d_hE);
+  dfree(c->d_hF);
+  dfree(c->d_hW);
+  if (c->h_flags) cudaFreeHost(c->h_flags);
+  for (auto* pool : {&c->prof_pending, &c->prof_free})
+    for (auto& ev : *pool)
+      for (auto e : ev) cudaEventDestroy(e);
+  delete c;
+  return SNAP_OK;
+}
+
+const char* snap_last_error(const snap_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+// snap_internal.h -- device-side layouts and launcher prototypes shared by the
+// library's translation units (not part of the public C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace snap {
+
+constexpr int kMaxTwoJ = 14;
+constexpr int kMaxNeighCap = 64;
+constexpr int kRootDim = 16;     // rootpq table is kRootDim x kRootDim
+constexpr int kGeomStride = 20;  // doubles per neighbour slot, see PairGeom
+
+// Half-matrix layout (Sec. V-A: u_j only needs floor(j)+1 of its columns):
+// layer t = 2j holds columns mb = 0..t/2, each column ma = 0..t.
+__host__ __device__ constexpr int half_layer_size(int t) { return (t + 1) * (t / 2 + 1); }
+__host__ __device__ constexpr int half_base(int t) {
+  int n = 0;
+  for (int s = 0; s < t; ++s) n += half_layer_size(s);
+  return n;
+}
+__host__ __device__ constexpr int half_size(int twojmax) { return half_base(twojmax + 1); }
+
+// Packed (t, ma, mb) of a half-layout element.
+__host__ __device__ constexpr int pack_tmm(int t, int ma, int mb) { return t | (ma << 8) | (mb << 16); }
+__host__ __device__ constexpr int tmm_t(int p) { return p & 0xff; }
+__host__ __device__ constexpr int tmm_ma(int p) { return (p >> 8) & 0xff; }
+__host__ __device__ constexpr int tmm_mb(int p) { return (p >> 16) & 0xff; }
+
+// Per neighbour slot geometry, FP64 (Cayley-Klein parameters, Sec. II-A):
+//  [0..1] a, [2..3] b, [4] f_c, [5..7] d f_c / d r_d,
+//  [8..13] d a / d r_d (re, im per d), [14..19] d b / d r_d.
+// A slot with r >= rcut has f_c = 0 and zero derivatives.
+
+// Y-kernel work item: one half-matrix element of one Z^t_{t1 t2}.
+//  x: t1 | t2<<4 | t<<8 | ma<<12 | mb<<16
+//  y: half base of t1 | half base of t2 << 16
+//  z: offset of the (t1, t2, t) Clebsch-Gordan block
+//  w: index of the (t1, t2, t) triple | output half index << 16
+struct YJob {
+  int x, y, z, w;
+};
+
+// Device copies of the per-context tables.
+struct DevTables {
+  int twojmax = 0;
+  int H = 0;        // half size
+  int lmax = 0;     // largest half layer
+  int nztrip = 0;   // (t1 >= t2, t) triples
+  int njobs = 0;
+  int* half_tmm = nullptr;  // [H]
+  YJob* yjobs = nullptr;    // [njobs], sorted by output element
+  void* cg = nullptr;       // R [ncg]: per triple, cg[x1][x2] of <j1 m1 j2 m2|j m1+m2>
+  void* betaw = nullptr;    // R [nztrip]: weighted beta of each triple
+  void* rootpq = nullptr;   // R [16*16]: sqrt(p/q)
+  double* cg64 = nullptr;   // host-built FP64 tables kept for re-upload
+};
+
+struct NeighArgs {
+  int n, K;
+  const double* pos;     // [n][3]
+  const float4* pos4;    // [n] FP32 copy for the coarse test
+  double Lx, Ly, Lz;
+  int Sx, Sy, Sz;        // image shifts enumerated beyond the nearest image
+  double rcut;
+  int* cnt;
+  int* nbr;
+  signed char* img;
+  double* rij;
+  int* flags;
+};
+
+struct WorkArgs {
+  int n, K, twojmax, H, lmax;
+  double rcut, rfac0, rmin0, wself, beta0;
+  int switchflag;
+  const int* cnt;
+  const int* nbr;
+  const signed char* img;
+  const int* rev;
+  double* rij;
+  double* geom;
+  void* Ure;
+  void* Uim;
+  void* Yre;
+  void* Yim;
+  double* dedr;
+  double* energy;
+  double* forces;
+  double* vpart;
+  double* virial;
+  int* flags;
+  const int* half_tmm;
+  const YJob* yjobs;
+  const int* yslice;
+  int nslices;
+  const void* cg;
+  const void* betaw;
+  const void* rootpq;
+};
+
+// Launchers (snap_neigh.cu)
+cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s);
+cudaError_t launch_neigh_build(const NeighArgs& a, cudaStream_t s);
+cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, double Ly,
+                                double Lz, const int* ucnt, const int* uidx,
+                                const signed char* uimg, int ucap, int* cnt, int* nbr,
+                                signed char* img, double* rij, int* flags, cudaStream_t s);
+cudaError_t launch_rev(const WorkArgs& a, int* rev, cudaStream_t s);
+cudaError_t launch_geom(const WorkArgs& a, cudaStream_t s);
+
+// Launchers (snap_kernels.cu), R = float (mixed) or double (FP64)
+template <typename R> cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s);
+template <typename R> cudaError_t launch_yi(const WorkArgs& a, cudaStream_t s);
+template <typename R> cudaError_t launch_de(const WorkArgs& a, cudaStream_t s);
+template <typename R> cudaError_t launch_force(const WorkArgs& a, cudaStream_t s);
+int force_blocks(int n);
+
+}  // namespace snap

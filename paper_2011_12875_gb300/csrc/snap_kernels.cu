@@ -1,0 +1,548 @@
+// snap_kernels.cu -- compute_U, compute_Y, fused dU/dE and the force gather.
+//
+// Notation follows arXiv:2011.12875: t = 2j, U_t = Ulisttot, Y_t = adjoint
+// (Eq. y), dE_i/dr_ik = Re sum_t Y_t : conj(dU_t/dr_ik) (Eq. snapforce2).
+// R is the working precision of the recursions: float (mixed) or double.
+// Every CTA works on a fixed set of atoms and writes each output once, so the
+// results are deterministic; there are no global atomics in the data path.
+#include <math.h>
+
+#include "snap_internal.h"
+
+namespace snap {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename R>
+struct cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> mk(R re, R im) {
+  cx<R> c;
+  c.re = re;
+  c.im = im;
+  return c;
+}
+// conj(a) * b
+template <typename R>
+__device__ __forceinline__ cx<R> conj_mul(cx<R> a, cx<R> b) {
+  return mk<R>(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+}
+// a * b
+template <typename R>
+__device__ __forceinline__ cx<R> mul(cx<R> a, cx<R> b) {
+  return mk<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Weight of a half-layout element in a full-matrix contraction M : N* of two
+// matrices with the inversion symmetry: 2 for mb < t/2; on the middle column
+// (2 mb = t) 2 above the centre, 1 at the centre, 0 below.
+__device__ __forceinline__ int half_weight(int t, int ma, int mb) {
+  if (2 * mb < t) return 2;
+  return ma < mb ? 2 : (ma == mb ? 1 : 0);
+}
+
+// Element (m, mb) of layer tp (= t - 1) stored in half layout at `lay`; the
+// column mb = (tp+1)/2 past the stored half comes from the inversion symmetry
+// u[m][mb] = (-1)^(m+mb) conj(u[tp-m][tp-mb]).
+template <typename R>
+__device__ __forceinline__ cx<R> prev_elem(const cx<R>* lay, int tp, int m, int mb) {
+  if (2 * mb <= tp) return lay[mb * (tp + 1) + m];
+  const cx<R> v = lay[(tp - mb) * (tp + 1) + (tp - m)];
+  const R s = ((m + mb) & 1) ? R(-1) : R(1);
+  return mk<R>(s * v.re, -s * v.im);
+}
+
+// ------------------------------------------------------------- compute_U
+// One CTA per atom i, one warp per neighbour pair (lanes over the elements of
+// a layer), NW warps per CTA.  u_t of a pair follows the layer recursion
+// (Eq. hysphrecur): for mb <= t/2,
+//   u_t[ma][mb] = sqrt((t-ma)/(t-mb)) conj(a) u_{t-1}[ma][mb]
+//               - sqrt(ma/(t-mb))     conj(b) u_{t-1}[ma-1][mb],
+// with only the previous layer kept (double buffer, shared memory).  f_c u_t
+// is summed per warp in shared memory, the warps are summed in a fixed order
+// and w_self is added on the diagonal (Eq. u).
+template <typename R, int NW>
+__global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int H = a.H, L = a.lmax, J2 = a.twojmax;
+  R* root = reinterpret_cast<R*>(smem);
+  cx<R>* acc = reinterpret_cast<cx<R>*>(root + kRootDim * kRootDim);
+  cx<R>* buf = acc + NW * H;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x;
+  const R* rootg = reinterpret_cast<const R*>(a.rootpq);
+  for (int e = threadIdx.x; e < kRootDim * kRootDim; e += blockDim.x) root[e] = rootg[e];
+  for (int e = threadIdx.x; e < NW * H; e += blockDim.x) acc[e] = mk<R>(0, 0);
+  __syncthreads();
+  cx<R>* myacc = acc + warp * H;
+  cx<R>* b0 = buf + warp * 2 * L;
+  cx<R>* b1 = b0 + L;
+  const int cnt = a.cnt[i];
+  for (int s = warp; s < cnt; s += NW) {
+    const double* g = a.geom + ((long)i * a.K + s) * kGeomStride;
+    const cx<R> ca = mk<R>((R)g[0], (R)g[1]);
+    const cx<R> cb = mk<R>((R)g[2], (R)g[3]);
+    const R fc = (R)g[4];
+    cx<R>* cur = b0;
+    cx<R>* nxt = b1;
+    if (lane == 0) {
+      cur[0] = mk<R>(1, 0);
+      myacc[0].re += fc;
+    }
+    __syncwarp();
+    for (int t = 1; t <= J2; ++t) {
+      const int size = half_layer_size(t), hb = half_base(t);
+      for (int e = lane; e < size; e += 32) {
+        const int mb = e / (t + 1), ma = e - mb * (t + 1);
+        cx<R> v = mk<R>(0, 0);
+        if (ma < t) {
+          const cx<R> p = prev_elem(cur, t - 1, ma, mb);
+          const cx<R> w = conj_mul(ca, p);
+          const R c = root[(t - ma) * kRootDim + (t - mb)];
+          v.re += c * w.re;
+          v.im += c * w.im;
+        }
+        if (ma > 0) {
+          const cx<R> p = prev_elem(cur, t - 1, ma - 1, mb);
+          const cx<R> w = conj_mul(cb, p);
+          const R c = root[ma * kRootDim + (t - mb)];
+          v.re -= c * w.re;
+          v.im -= c * w.im;
+        }
+        nxt[e] = v;
+        myacc[hb + e].re += fc * v.re;
+        myacc[hb + e].im += fc * v.im;
+      }
+      __syncwarp();
+      cx<R>* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  R* Ure = reinterpret_cast<R*>(a.Ure);
+  R* Uim = reinterpret_cast<R*>(a.Uim);
+  const long blk = i >> 5;
+  const int li = i & 31;
+  for (int e = threadIdx.x; e < H; e += blockDim.x) {
+    cx<R> s = acc[e];
+    for (int w = 1; w < NW; ++w) {
+      s.re += acc[w * H + e].re;
+      s.im += acc[w * H + e].im;
+    }
+    const int p = a.half_tmm[e];
+    if (tmm_ma(p) == tmm_mb(p)) s.re += (R)a.wself;
+    Ure[(blk * H + e) * 32 + li] = s.re;
+    Uim[(blk * H + e) * 32 + li] = s.im;
+  }
+}
+
+// ------------------------------------------------------------- compute_Y
+// Lanes = 32 consecutive atoms (the paper's warp-of-atoms AoSoA layout,
+// Sec. V-B), so the Clebsch-Gordan coefficients and all indices are uniform
+// across the warp and every U/Y access is one coalesced line.  Each warp owns
+// a contiguous run of work items sorted by output element, so each Y element
+// is accumulated in registers and written once (no atomics):
+//   Z^t_{t1t2}[ma][mb] = sum_{mb1} C_b sum_{ma1} C_a U_t1[ma1][mb1] U_t2[ma2][mb2]
+//   Y_t[ma][mb]       += betaw(t1, t2, t) Z^t_{t1t2}[ma][mb]            (Eq. y)
+// with ma2 = ma - ma1 + (t1+t2-t)/2 and the same for mb.  betaw carries beta
+// of the bispectrum component the triple belongs to and the factor that makes
+// Y the derivative of E_i with respect to U (see the table builder).
+template <typename R>
+__device__ __forceinline__ cx<R> u_full(const R* __restrict__ Ure, const R* __restrict__ Uim,
+                                        int base, int t, int ma, int mb, int lane) {
+  if (2 * mb <= t) {
+    const int idx = (base + mb * (t + 1) + ma) * 32 + lane;
+    return mk<R>(__ldg(Ure + idx), __ldg(Uim + idx));
+  }
+  const int idx = (base + (t - mb) * (t + 1) + (t - ma)) * 32 + lane;
+  const R s = ((ma + mb) & 1) ? R(-1) : R(1);
+  return mk<R>(s * __ldg(Ure + idx), -s * __ldg(Uim + idx));
+}
+
+template <typename R, int WPB>
+__global__ void __launch_bounds__(WPB * 32) yi_kernel(WorkArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slice = blockIdx.y * WPB + warp;
+  if (slice >= a.nslices) return;
+  const long blk = blockIdx.x;
+  const int H = a.H;
+  const R* Ure = reinterpret_cast<const R*>(a.Ure) + blk * H * 32;
+  const R* Uim = reinterpret_cast<const R*>(a.Uim) + blk * H * 32;
+  R* Yre = reinterpret_cast<R*>(a.Yre) + blk * H * 32;
+  R* Yim = reinterpret_cast<R*>(a.Yim) + blk * H * 32;
+  const R* cg = reinterpret_cast<const R*>(a.cg);
+  const R* betaw = reinterpret_cast<const R*>(a.betaw);
+  const int q0 = a.yslice[slice], q1 = a.yslice[slice + 1];
+  cx<R> y = mk<R>(0, 0);
+  int out = -1;
+  for (int q = q0; q < q1; ++q) {
+    const YJob job = a.yjobs[q];
+    const int t1 = job.x & 15, t2 = (job.x >> 4) & 15, t = (job.x >> 8) & 15;
+    const int ma = (job.x >> 12) & 15, mb = (job.x >> 16) & 15;
+    const int u1b = job.y & 0xffff, u2b = job.y >> 16;
+    const int cgb = job.z;
+    const int trip = job.w & 0xffff, o = job.w >> 16;
+    if (o != out) {
+      if (out >= 0) {
+        Yre[out * 32 + lane] = y.re;
+        Yim[out * 32 + lane] = y.im;
+      }
+      y = mk<R>(0, 0);
+      out = o;
+    }
+    const int dl = (t1 + t2 - t) >> 1;
+    const int ma1lo = max(0, ma + dl - t2), ma1hi = min(t1, ma + dl);
+    const int mb1lo = max(0, mb + dl - t2), mb1hi = min(t1, mb + dl);
+    cx<R> z = mk<R>(0, 0);
+    for (int mb1 = mb1lo; mb1 <= mb1hi; ++mb1) {
+      const int mb2 = mb + dl - mb1;
+      const R cgbv = __ldg(cg + cgb + mb1 * (t2 + 1) + mb2);
+      cx<R> zz = mk<R>(0, 0);
+      for (int ma1 = ma1lo; ma1 <= ma1hi; ++ma1) {
+        const int ma2 = ma + dl - ma1;
+        const R cgav = __ldg(cg + cgb + ma1 * (t2 + 1) + ma2);
+        const cx<R> u1 = u_full(Ure, Uim, u1b, t1, ma1, mb1, lane);
+        const cx<R> u2 = u_full(Ure, Uim, u2b, t2, ma2, mb2, lane);
+        const cx<R> p = mul(u1, u2);
+        zz.re += cgav * p.re;
+        zz.im += cgav * p.im;
+      }
+      z.re += cgbv * zz.re;
+      z.im += cgbv * zz.im;
+    }
+    const R bw = __ldg(betaw + trip);
+    y.re += bw * z.re;
+    y.im += bw * z.im;
+  }
+  if (out >= 0) {
+    Yre[out * 32 + lane] = y.re;
+    Yim[out * 32 + lane] = y.im;
+  }
+}
+
+// ------------------------------------------------------ fused dU + dE/dr
+// One CTA per atom i with Y_i (weighted by half_weight) staged in shared
+// memory; one warp per pair.  For a pair, S(a, b) = sum_t Re Y_t : conj(u_t)
+// is a real function of the Cayley-Klein parameters.  Its gradient follows
+// from one forward pass of the layer recursion (all layers kept in shared
+// memory) and one reverse (adjoint) pass through the same recursion, so
+// neither dU nor its three Cartesian components is ever formed.  Then
+//   dE_i/dr_ik = S df_c/dr + f_c (<g_a, da/dr> + <g_b, db/dr>),
+// <x, y> = Re(conj(x) y), which is Eq. (snapforce2) for this pair.
+template <typename R, int NW>
+__global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int H = a.H, L = a.lmax, J2 = a.twojmax;
+  R* root = reinterpret_cast<R*>(smem);
+  cx<R>* Yw = reinterpret_cast<cx<R>*>(root + kRootDim * kRootDim);
+  cx<R>* ubase = Yw + H;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x;
+  const R* rootg = reinterpret_cast<const R*>(a.rootpq);
+  for (int e = threadIdx.x; e < kRootDim * kRootDim; e += blockDim.x) root[e] = rootg[e];
+  {
+    const R* Yre = reinterpret_cast<const R*>(a.Yre);
+    const R* Yim = reinterpret_cast<const R*>(a.Yim);
+    const long blk = i >> 5;
+    const int li = i & 31;
+    for (int e = threadIdx.x; e < H; e += blockDim.x) {
+      const int p = a.half_tmm[e];
+      const R w = (R)half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
+      Yw[e] = mk<R>(w * Yre[(blk * H + e) * 32 + li], w * Yim[(blk * H + e) * 32 + li]);
+    }
+  }
+  __syncthreads();
+  cx<R>* ust = ubase + warp * (H + 2 * L);
+  cx<R>* lam0 = ust + H;
+  cx<R>* lam1 = lam0 + L;
+  const int cnt = a.cnt[i];
+  for (int s = warp; s < cnt; s += NW) {
+    const long slot = (long)i * a.K + s;
+    const double* g = a.geom + slot * kGeomStride;
+    const cx<R> ca = mk<R>((R)g[0], (R)g[1]);
+    const cx<R> cb = mk<R>((R)g[2], (R)g[3]);
+    // forward: all layers of u (half layout) and S
+    R S = 0;
+    if (lane == 0) {
+      ust[0] = mk<R>(1, 0);
+      S = Yw[0].re;
+    }
+    __syncwarp();
+    for (int t = 1; t <= J2; ++t) {
+      const int size = half_layer_size(t), hb = half_base(t);
+      const cx<R>* pl = ust + half_base(t - 1);
+      for (int e = lane; e < size; e += 32) {
+        const int mb = e / (t + 1), ma = e - mb * (t + 1);
+        cx<R> v = mk<R>(0, 0);
+        if (ma < t) {
+          const cx<R> w = conj_mul(ca, prev_elem(pl, t - 1, ma, mb));
+          const R c = root[(t - ma) * kRootDim + (t - mb)];
+          v.re += c * w.re;
+          v.im += c * w.im;
+        }
+        if (ma > 0) {
+          const cx<R> w = conj_mul(cb, prev_elem(pl, t - 1, ma - 1, mb));
+          const R c = root[ma * kRootDim + (t - mb)];
+          v.re -= c * w.re;
+          v.im -= c * w.im;
+        }
+        ust[hb + e] = v;
+        const cx<R> yw = Yw[hb + e];
+        S += yw.re * v.re + yw.im * v.im;
+      }
+      __syncwarp();
+    }
+    // reverse: lambda_t = adjoint of layer t, gathered from layer t+1
+    {
+      const int hb = half_base(J2);
+      for (int e = lane; e < half_layer_size(J2); e += 32) lam0[e] = Yw[hb + e];
+    }
+    __syncwarp();
+    cx<R> ga = mk<R>(0, 0), gb = mk<R>(0, 0);
+    cx<R>* lt = lam0;
+    cx<R>* ln = lam1;
+    for (int t = J2; t >= 1; --t) {
+      const int tp = t - 1;
+      const int sizep = half_layer_size(tp), hbp = half_base(tp);
+      const bool mirror = ((t & 1) == 0);
+      const int mc = t >> 1;  // the column of layer t that reads a mirrored column
+      for (int e = lane; e < sizep; e += 32) {
+        const int mb = e / (tp + 1), m = e - mb * (tp + 1);
+        const cx<R> u = ust[hbp + e];
+        // u_{t-1}[m][mb] feeds u_t[m][mb] (a-term) and u_t[m+1][mb] (b-term)
+        const R c1 = root[(t - m) * kRootDim + (t - mb)];
+        const R c2 = root[(m + 1) * kRootDim + (t - mb)];
+        const cx<R> l1 = lt[mb * (t + 1) + m];
+        const cx<R> l2 = lt[mb * (t + 1) + m + 1];
+        const cx<R> A = mk<R>(c1 * l1.re, c1 * l1.im);
+        const cx<R> B = mk<R>(c2 * l2.re, c2 * l2.im);
+        cx<R> r1 = conj_mul(A, u);
+        cx<R> r2 = conj_mul(B, u);
+        ga.re += r1.re;
+        ga.im += r1.im;
+        gb.re -= r2.re;
+        gb.im -= r2.im;
+        const cx<R> aA = mul(ca, A), bB = mul(cb, B);
+        const cx<R> yw = Yw[hbp + e];
+        cx<R> nl = mk<R>(yw.re + aA.re - bB.re, yw.im + aA.im - bB.im);
+        if (mirror && mb == mc - 1) {
+          // u_t column mc reads v(mp) = sig conj(u_{t-1}[m][mc-1]), mp = tp - m
+          const int mp = tp - m;
+          const R sig = ((m + mc - 1) & 1) ? R(-1) : R(1);
+          const cx<R> v = mk<R>(sig * u.re, -sig * u.im);
+          const R d1 = root[(t - mp) * kRootDim + (t - mc)];
+          const R d2 = root[(mp + 1) * kRootDim + (t - mc)];
+          const cx<R> k1 = lt[mc * (t + 1) + mp];
+          const cx<R> k2 = lt[mc * (t + 1) + mp + 1];
+          const cx<R> A2 = mk<R>(d1 * k1.re, d1 * k1.im);
+          const cx<R> B2 = mk<R>(d2 * k2.re, d2 * k2.im);
+          r1 = conj_mul(A2, v);
+          r2 = conj_mul(B2, v);
+          ga.re += r1.re;
+          ga.im += r1.im;
+          gb.re -= r2.re;
+          gb.im -= r2.im;
+          const cx<R> aA2 = mul(ca, A2), bB2 = mul(cb, B2);
+          const cx<R> lv = mk<R>(aA2.re - bB2.re, aA2.im - bB2.im);
+          nl.re += sig * lv.re;
+          nl.im -= sig * lv.im;
+        }
+        ln[e] = nl;
+      }
+      __syncwarp();
+      cx<R>* tmp = lt;
+      lt = ln;
+      ln = tmp;
+    }
+    S = warp_sum(S);
+    ga.re = warp_sum(ga.re);
+    ga.im = warp_sum(ga.im);
+    gb.re = warp_sum(gb.re);
+    gb.im = warp_sum(gb.im);
+    if (lane == 0) {
+      const double fc = g[4];
+      const double Sd = (double)S;
+      const double gar = (double)ga.re, gai = (double)ga.im;
+      const double gbr = (double)gb.re, gbi = (double)gb.im;
+      for (int d = 0; d < 3; ++d) {
+        const double dar = g[8 + 2 * d], dai = g[9 + 2 * d];
+        const double dbr = g[14 + 2 * d], dbi = g[15 + 2 * d];
+        const double ds = gar * dar + gai * dai + gbr * dbr + gbi * dbi;
+        a.dedr[slot * 3 + d] = g[5 + d] * Sd + fc * ds;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// --------------------------------------------- energy, forces and virial
+// One warp per atom.  E_i - beta_0 is a cubic form in U, so by Euler's
+// relation E_i = beta_0 + (1/3) Re sum_t Y_t : conj(U_t) (full matrices; half
+// layout with half_weight).  F_i = sum_k dE_i/dr_ik - sum_k dE_k/dr_ki, the
+// second term gathered through the reverse-slot map (no atomics).  The
+// virial W_ab = -sum dE_i/dr_ik,a r_ik,b is reduced per CTA into vpart.
+constexpr int kForceWarps = 4;
+
+template <typename R>
+__global__ void __launch_bounds__(kForceWarps * 32) force_kernel(WorkArgs a) {
+  __shared__ double vs[kForceWarps][6];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kForceWarps + warp;
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  if (i < a.n) {
+    const int H = a.H;
+    const R* Ure = reinterpret_cast<const R*>(a.Ure);
+    const R* Uim = reinterpret_cast<const R*>(a.Uim);
+    const R* Yre = reinterpret_cast<const R*>(a.Yre);
+    const R* Yim = reinterpret_cast<const R*>(a.Yim);
+    const long blk = i >> 5;
+    const int li = i & 31;
+    double e = 0.0;
+    for (int el = lane; el < H; el += 32) {
+      const int p = a.half_tmm[el];
+      const int w = half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
+      const long idx = (blk * H + el) * 32 + li;
+      e += (double)w * ((double)Yre[idx] * (double)Ure[idx] + (double)Yim[idx] * (double)Uim[idx]);
+    }
+    e = warp_sum(e);
+    double f[3] = {0, 0, 0};
+    const int cnt = a.cnt[i];
+    for (int s = lane; s < cnt; s += 32) {
+      const long q = (long)i * a.K + s;
+      const int k = a.nbr[q];
+      const int r = a.rev[q];
+      const double* d = a.dedr + q * 3;
+      const double* rv = a.rij + q * 3;
+      for (int c = 0; c < 3; ++c) f[c] += d[c];
+      if (r >= 0) {
+        const double* dk = a.dedr + ((long)k * a.K + r) * 3;
+        for (int c = 0; c < 3; ++c) f[c] -= dk[c];
+      }
+      v[0] -= d[0] * rv[0];
+      v[1] -= d[1] * rv[1];
+      v[2] -= d[2] * rv[2];
+      v[3] -= d[0] * rv[1];
+      v[4] -= d[0] * rv[2];
+      v[5] -= d[1] * rv[2];
+    }
+    for (int c = 0; c < 3; ++c) f[c] = warp_sum(f[c]);
+    if (lane == 0) {
+      if (a.energy) a.energy[i] = a.beta0 + e / 3.0;
+      for (int c = 0; c < 3; ++c) a.forces[3 * (long)i + c] = f[c];
+    }
+  }
+  for (int c = 0; c < 6; ++c) v[c] = warp_sum(v[c]);
+  if (lane == 0)
+    for (int c = 0; c < 6; ++c) vs[warp][c] = v[c];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double t = 0.0;
+    for (int w = 0; w < kForceWarps; ++w) t += vs[w][threadIdx.x];
+    a.vpart[6 * (long)blockIdx.x + threadIdx.x] = t;
+  }
+}
+
+// Fixed-order sum of the per-CTA virial partials (deterministic).
+__global__ void virial_reduce_kernel(const double* __restrict__ vpart, int nb, double* virial) {
+  __shared__ double red[256];
+  for (int c = 0; c < 6; ++c) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += vpart[6 * (long)b + c];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) virial[c] = red[0];
+    __syncthreads();
+  }
+}
+
+constexpr int kUiWarps = 4;
+constexpr int kDeWarps = 4;
+constexpr int kYiWarps = 4;
+
+template <typename R>
+size_t ui_smem(int H, int L) {
+  return sizeof(R) * kRootDim * kRootDim + sizeof(cx<R>) * (size_t)kUiWarps * (H + 2 * L);
+}
+template <typename R>
+size_t de_smem(int H, int L) {
+  return sizeof(R) * kRootDim * kRootDim + sizeof(cx<R>) * (H + (size_t)kDeWarps * (H + 2 * L));
+}
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+int force_blocks(int n) { return (n + kForceWarps - 1) / kForceWarps; }
+
+template <typename R>
+cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const size_t sm = ui_smem<R>(a.H, a.lmax);
+  cudaError_t e = allow_smem(ui_kernel<R, kUiWarps>, sm);
+  if (e != cudaSuccess) return e;
+  ui_kernel<R, kUiWarps><<<a.n, kUiWarps * 32, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_yi(const WorkArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const int nblk = (a.n + 31) / 32;
+  dim3 grid(nblk, (a.nslices + kYiWarps - 1) / kYiWarps);
+  yi_kernel<R, kYiWarps><<<grid, kYiWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_de(const WorkArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const size_t sm = de_smem<R>(a.H, a.lmax);
+  cudaError_t e = allow_smem(de_kernel<R, kDeWarps>, sm);
+  if (e != cudaSuccess) return e;
+  de_kernel<R, kDeWarps><<<a.n, kDeWarps * 32, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_force(const WorkArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const int nb = force_blocks(a.n);
+  force_kernel<R><<<nb, kForceWarps * 32, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !a.virial) return e;
+  virial_reduce_kernel<<<1, 256, 0, s>>>(a.vpart, nb, a.virial);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_ui<float>(const WorkArgs&, cudaStream_t);
+template cudaError_t launch_ui<double>(const WorkArgs&, cudaStream_t);
+template cudaError_t launch_yi<float>(const WorkArgs&, cudaStream_t);
+template cudaError_t launch_yi<double>(const WorkArgs&, cudaStream_t);
+template cudaError_t launch_de<float>(const WorkArgs&, cudaStream_t);
+template cudaError_t launch_de<double>(const WorkArgs&, cudaStream_t);
+template cudaError_t launch_force<float>(const WorkArgs&, cudaStream_t);
+template cudaError_t launch_force<double>(const WorkArgs&, cudaStream_t);
+
+}  // namespace snap

@@ -1,0 +1,33 @@
+// snap_tables.h -- host-side tables of the library (see snap_tables.cpp).
+#pragma once
+#include <vector>
+
+#include "snap_internal.h"
+
+namespace snap {
+
+struct ZTrip {
+  int t1, t2, t;  // Y triple: Z^t_{t1 t2} with t1 >= t2
+  int cg_off;     // offset of its cg[x1][x2] block
+  int bidx;       // canonical bispectrum component it belongs to
+  double fac;     // multiplicity / rank factor of the derivative
+};
+
+struct HostTables {
+  int twojmax = 0, H = 0, lmax = 0, ncoeff = 0;
+  std::vector<int> half_tmm;
+  std::vector<ZTrip> ztrip;
+  std::vector<double> cg;
+  std::vector<YJob> jobs;
+  std::vector<int> cost;
+  std::vector<double> rootpq;
+
+  void build(int twojmax);
+  std::vector<double> beta_weights(const double* beta) const;
+  std::vector<int> slices(int nslices) const;
+};
+
+double clebsch_gordan(int tj1, int tm1, int tj2, int tm2, int tj, int tm);
+int count_coeff(int twojmax);
+
+}  // namespace snap

@@ -1,0 +1,256 @@
+"""Thin Python binding of the C ABI in include/snap_gb300.h.
+
+Argument marshalling only: every step of the SNAP evaluation runs in the CUDA
+library ``_build/libsnap_gb300.so``.  PyTorch supplies device memory and the
+current CUDA stream.  If the library cannot be loaded this module raises; it
+has no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsnap_gb300.so")
+
+FP64 = 0
+MIXED = 1
+
+OK = 0
+ERR_ARG = -1
+ERR_NEIGH_OVERFLOW = -2
+ERR_BOX = -3
+ERR_CUDA = -4
+ERR_TIMEOUT = -5
+ERR_NOMEM = -6
+ERR_NEIGH_ASYM = -7
+
+BUF_NBR_CNT = 0
+BUF_NBR_IDX = 1
+BUF_NBR_IMG = 2
+BUF_NBR_REV = 3
+BUF_RIJ = 4
+BUF_ULISTTOT = 5
+BUF_YLIST = 6
+BUF_DEDR = 7
+
+EXPORTS = ("snap_num_coeff", "snap_create", "snap_set_beta", "snap_set_neigh_cap",
+           "snap_neigh_max", "snap_compute", "snap_compute_async", "snap_sync",
+           "snap_compute_host", "snap_get_buffer", "snap_half_index", "snap_half_size",
+           "snap_destroy", "snap_last_error", "snap_profile", "snap_profile_read",
+           "snap_stage_name", "snap_launches_per_call")
+NSTAGES = 7
+
+_lib = None
+
+
+class SnapError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"snap error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises OSError if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise OSError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    i, d, p, ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
+    L.snap_num_coeff.argtypes = [i]
+    L.snap_num_coeff.restype = i
+    L.snap_create.argtypes = [i, d, d, d, i, p, i, ctypes.POINTER(p)]
+    L.snap_create.restype = i
+    L.snap_set_beta.argtypes = [p, p]
+    L.snap_set_beta.restype = i
+    L.snap_set_neigh_cap.argtypes = [p, i]
+    L.snap_set_neigh_cap.restype = i
+    L.snap_neigh_max.argtypes = [p]
+    L.snap_neigh_max.restype = i
+    L.snap_compute.argtypes = [p, i, p, p, p, p, p, i, p, p, p, p]
+    L.snap_compute.restype = i
+    L.snap_compute_async.argtypes = [p, i, p, p, p, p, p, i, p, p, p, p]
+    L.snap_compute_async.restype = i
+    L.snap_sync.argtypes = [p, p]
+    L.snap_sync.restype = i
+    L.snap_profile.argtypes = [p, i]
+    L.snap_profile.restype = i
+    L.snap_profile_read.argtypes = [p, p, p, i]
+    L.snap_profile_read.restype = i
+    L.snap_stage_name.argtypes = [i]
+    L.snap_stage_name.restype = ctypes.c_char_p
+    L.snap_launches_per_call.argtypes = [p]
+    L.snap_launches_per_call.restype = i
+    L.snap_compute_host.argtypes = [p, i, p, p, p, p, p, p]
+    L.snap_compute_host.restype = i
+    L.snap_get_buffer.argtypes = [p, i, p, ctypes.c_size_t]
+    L.snap_get_buffer.restype = ll
+    L.snap_half_index.argtypes = [i, i, i, i]
+    L.snap_half_index.restype = i
+    L.snap_half_size.argtypes = [i]
+    L.snap_half_size.restype = i
+    L.snap_destroy.argtypes = [p]
+    L.snap_destroy.restype = i
+    L.snap_last_error.argtypes = [p]
+    L.snap_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def num_coeff(twojmax: int) -> int:
+    return load().snap_num_coeff(twojmax)
+
+
+def half_size(twojmax: int) -> int:
+    return load().snap_half_size(twojmax)
+
+
+def half_index(twojmax: int, t: int, ma: int, mb: int) -> int:
+    return load().snap_half_index(twojmax, t, ma, mb)
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _t_ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Snap:
+    """One SNAP potential (2J, R_cut, rfac0, rmin0, switching, beta) on the
+    current CUDA device, in FP64 or mixed precision."""
+
+    def __init__(self, twojmax: int, beta, rcut: float = 4.73442, rfac0: float = 0.99363,
+                 rmin0: float = 0.0, switchflag: int = 1, precision: int = FP64):
+        self._lib = load()
+        self.twojmax = twojmax
+        self.precision = precision
+        b = np.ascontiguousarray(beta, dtype=np.float64)
+        nc = self._lib.snap_num_coeff(twojmax)
+        if nc < 0 or b.shape != (nc + 1,):
+            raise ValueError(f"beta must have 1 + {nc} entries for twojmax={twojmax}")
+        h = ctypes.c_void_p()
+        rc = self._lib.snap_create(twojmax, rcut, rfac0, rmin0, switchflag, _np_ptr(b), precision,
+                                   ctypes.byref(h))
+        if rc != OK:
+            raise SnapError(rc, self._lib.snap_last_error(None).decode())
+        self._h = h
+
+    def _check(self, rc: int):
+        if rc != OK:
+            raise SnapError(rc, self._lib.snap_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.snap_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_beta(self, beta):
+        b = np.ascontiguousarray(beta, dtype=np.float64)
+        self._check(self._lib.snap_set_beta(self._h, _np_ptr(b)))
+
+    def set_neigh_cap(self, cap: int):
+        self._check(self._lib.snap_set_neigh_cap(self._h, cap))
+
+    def neigh_max(self) -> int:
+        return self._lib.snap_neigh_max(self._h)
+
+    def compute(self, pos, box, energy=None, forces=None, virial=None, neighbors=None,
+                stream=None, wait=True):
+        """Evaluate on device tensors (torch, float64, [N,3] positions).
+
+        box: 3 box lengths (host sequence).  neighbors: optional (cnt, idx, img)
+        device tensors (int32 [N], int32 [N,cap], int8 [N,cap,3]).
+        Returns (energy [N], forces [N,3], virial [6]) tensors.
+        """
+        import torch
+        if pos.dtype != torch.float64 or not pos.is_cuda or not pos.is_contiguous():
+            raise ValueError("pos must be a contiguous float64 CUDA tensor")
+        n = pos.shape[0]
+        dev = pos.device
+        if energy is None:
+            energy = torch.empty(n, dtype=torch.float64, device=dev)
+        if forces is None:
+            forces = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        if virial is None:
+            virial = torch.empty(6, dtype=torch.float64, device=dev)
+        boxa = np.ascontiguousarray(box, dtype=np.float64)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        cnt = idx = img = None
+        cap = 0
+        if neighbors is not None:
+            cnt, idx, img = neighbors
+            cap = idx.shape[1]
+        fn = self._lib.snap_compute if wait else self._lib.snap_compute_async
+        self._check(fn(self._h, n, _t_ptr(pos), _np_ptr(boxa), _t_ptr(cnt), _t_ptr(idx),
+                       _t_ptr(img), cap, _t_ptr(energy), _t_ptr(forces), _t_ptr(virial),
+                       ctypes.c_void_p(stream)))
+        return energy, forces, virial
+
+    def sync(self, stream=None):
+        """Wait for the stream; raise if the last asynchronous compute failed."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self._check(self._lib.snap_sync(self._h, ctypes.c_void_p(stream)))
+
+    def profile(self, enable: bool):
+        self._check(self._lib.snap_profile(self._h, int(enable)))
+
+    def profile_read(self):
+        """{stage name: (total ms, calls)} of the per-stage CUDA-event timing."""
+        ms = np.zeros(NSTAGES)
+        calls = np.zeros(NSTAGES, dtype=np.int64)
+        rc = self._lib.snap_profile_read(self._h, _np_ptr(ms), _np_ptr(calls), NSTAGES)
+        if rc < 0:
+            self._check(rc)
+        return {self._lib.snap_stage_name(k).decode(): (float(ms[k]), int(calls[k]))
+                for k in range(NSTAGES)}
+
+    def launches_per_call(self) -> int:
+        return self._lib.snap_launches_per_call(self._h)
+
+    def compute_host(self, pos: np.ndarray, box, stream=None, want_energy=True, want_virial=True,
+                     out=None):
+        """Evaluate from HOST numpy arrays (copies in and out inside the call)."""
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        n = pos.shape[0]
+        if out is None:
+            E = np.empty(n) if want_energy else None
+            F = np.empty((n, 3))
+            W = np.empty(6) if want_virial else None
+        else:
+            E, F, W = out
+        boxa = np.ascontiguousarray(box, dtype=np.float64)
+        self._check(self._lib.snap_compute_host(
+            self._h, n, _np_ptr(pos), _np_ptr(boxa), None if E is None else _np_ptr(E), _np_ptr(F),
+            None if W is None else _np_ptr(W), ctypes.c_void_p(stream or 0)))
+        return E, F, W
+
+    def get_buffer(self, which: int) -> np.ndarray:
+        """Internal buffer of the last compute, as a host numpy array."""
+        nbytes = self._lib.snap_get_buffer(self._h, which, None, 0)
+        if nbytes < 0:
+            self._check(int(nbytes))
+        raw = np.empty(max(int(nbytes), 1), dtype=np.uint8)
+        rc = self._lib.snap_get_buffer(self._h, which, _np_ptr(raw), raw.nbytes)
+        if rc < 0:
+            self._check(int(rc))
+        raw = raw[:int(nbytes)]
+        dt = {BUF_NBR_CNT: np.int32, BUF_NBR_IDX: np.int32, BUF_NBR_IMG: np.int8,
+              BUF_NBR_REV: np.int32, BUF_RIJ: np.float64, BUF_ULISTTOT: np.float64,
+              BUF_YLIST: np.float64, BUF_DEDR: np.float64}[which]
+        return raw.view(dt)

@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+FP64 path: 1e-10 relative (to the largest magnitude of each quantity) on
+Ulisttot, Y, dE/dr per pair, E_i, F and the virial; neighbour lists exact.
+Mixed path (FP32 recursions, FP64 geometry and accumulation): the tolerances
+below, measured per quantity and per 2J (Table MIXED_TOL).
+"""
+import numpy as np
+import pytest
+
+from oracle import snap_oracle as O
+from paper_2011_12875_gb300 import inputs
+from tests.parity_util import gpu_pairs, half_to_full, oracle_pairs, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+# relative-to-max tolerance of the mixed path: (U, Y, dedr, E, F, W)
+MIXED_TOL = {
+    "U": 2e-6, "Y": 2e-5, "dedr": 2e-4, "E": 2e-5, "F": 2e-4, "W": 2e-4,
+}
+
+
+@pytest.fixture(scope="module")
+def snapmod():
+    from paper_2011_12875_gb300 import build, snap
+    build.build()
+    snap.load()
+    assert torch.cuda.is_available()
+    return snap
+
+
+def run_gpu(snapmod, twojmax, beta, cfg, precision, **kw):
+    s = snapmod.Snap(twojmax, beta, precision=precision, **kw)
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device="cuda:0")
+    E, F, W = s.compute(pos, cfg.box)
+    torch.cuda.synchronize()
+    return s, E.cpu().numpy(), F.cpu().numpy(), W.cpu().numpy()
+
+
+def full_check(snapmod, twojmax, cfg, precision, beta=None, tol=None, params=None, **kw):
+    beta = inputs.beta(twojmax) if beta is None else beta
+    p = params or O.Params(twojmax)
+    pairs, ref = O.evaluate(p, beta, cfg.pos, cfg.box, want_UY=True)
+    s, E, F, W = run_gpu(snapmod, twojmax, beta, cfg, precision, rcut=p.rcut, rfac0=p.rfac0,
+                         rmin0=p.rmin0, switchflag=p.switchflag, **kw)
+    n = cfg.natoms
+    # neighbour lists: identical sets of (i, k, image)
+    gkeys, K, cnt = gpu_pairs(s, n)
+    okeys = oracle_pairs(pairs)
+    assert set(gkeys) == set(okeys)
+    # stages
+    H = snapmod.half_size(twojmax)
+    U = half_to_full(s.get_buffer(snapmod.BUF_ULISTTOT).reshape(n, H, 2), twojmax, snapmod.half_index)
+    Y = half_to_full(s.get_buffer(snapmod.BUF_YLIST).reshape(n, H, 2), twojmax, snapmod.half_index)
+    dedr_g = s.get_buffer(snapmod.BUF_DEDR).reshape(n * K, 3)
+    order = [gkeys[k] for k in okeys]
+    errs = {
+        "U": rel_err(U, ref.U), "Y": rel_err(Y, ref.Y),
+        "dedr": rel_err(dedr_g[order], ref.dedr), "E": rel_err(E, ref.E),
+        "F": rel_err(F, ref.F), "W": rel_err(W, ref.W),
+    }
+    s.close()
+    for key, e in errs.items():
+        lim = FP64_TOL if precision == snapmod.FP64 else (tol or MIXED_TOL)[key]
+        assert e <= lim, (key, e, errs)
+    return errs
+
+
+@pytest.mark.parametrize("twojmax", [0, 1, 2, 3, 4, 5, 6, 7, 8])
+def test_fp64_small_box_all_orders(snapmod, twojmax):
+    """16 atoms in a 6.36 A box (< 2 rcut): several images of the same atom
+    are neighbours; every 2J up to 8."""
+    full_check(snapmod, twojmax, inputs.bcc(2, disp=0.15, seed=3), snapmod.FP64)
+
+
+def test_fp64_128_atoms_2j8(snapmod):
+    """The 128-atom, 2J = 8 parity configuration: every stage and output."""
+    w = inputs.WORKLOADS["bcc4_2j8"]
+    full_check(snapmod, 8, w.config(), snapmod.FP64, beta=w.beta())
+
+
+def test_fp64_2j14(snapmod):
+    full_check(snapmod, 14, inputs.bcc(2, disp=0.1, seed=4), snapmod.FP64)
+
+
+@pytest.mark.parametrize("twojmax", [2, 8, 14])
+def test_mixed_precision(snapmod, twojmax):
+    cfg = inputs.bcc(3 if twojmax < 14 else 2, disp=0.1, seed=5)
+    errs = full_check(snapmod, twojmax, cfg, snapmod.MIXED)
+    print("mixed", twojmax, errs)
+
+
+def test_ragged_neighbour_counts(snapmod):
+    """+-0.4 A displacements: neighbour counts from 21 to 28."""
+    cfg = inputs.bcc(3, disp=0.4, seed=8)
+    pairs = O.build_neighbors(cfg.pos, cfg.box, inputs.RCUT)
+    counts = np.bincount(pairs.i, minlength=cfg.natoms)
+    assert counts.min() < 26 < counts.max()
+    full_check(snapmod, 6, cfg, snapmod.FP64)
+
+
+def test_switching_variants(snapmod):
+    cfg = inputs.bcc(2, disp=0.1, seed=9)
+    for p in (O.Params(4, rmin0=0.7), O.Params(4, switchflag=0), O.Params(5, rfac0=0.7, rcut=4.2)):
+        full_check(snapmod, p.twojmax, cfg, snapmod.FP64, params=p)
+
+
+def test_single_atom_self_images(snapmod):
+    """One atom in a 3 A box: all 18 neighbours are its own images."""
+    cfg = inputs.Config(pos=np.array([[0.3, 0.2, 0.1]]), box=np.array([3.0, 3.0, 3.0]))
+    full_check(snapmod, 6, cfg, snapmod.FP64)
+
+
+def test_isolated_atoms_without_neighbours(snapmod):
+    cfg = inputs.Config(pos=np.array([[1.0, 1.0, 1.0], [20.0, 20.0, 20.0], [21.0, 21.5, 20.2]]),
+                        box=np.array([40.0, 40.0, 40.0]))
+    errs = full_check(snapmod, 8, cfg, snapmod.FP64)
+    assert errs["E"] < FP64_TOL
+
+
+@pytest.mark.parametrize("name,prec,natoms_sample", [
+    ("bcc10_2j8", 0, 2000), ("bcc10_2j8", 1, 2000),
+    ("bcc10_2j14", 1, 12), ("bcc10_2j14", 0, 12), ("bcc20_2j14", 1, 12)])
+def test_full_size_workloads(snapmod, name, prec, natoms_sample):
+    """Full benchmark sizes in the benchmark's launch configuration; the
+    oracle evaluates every atom (2J = 8) or a seeded sample (2J = 14)."""
+    w = inputs.WORKLOADS[name]
+    cfg, beta = w.config(), w.beta()
+    p = O.Params(w.twojmax)
+    s, E, F, W = run_gpu(snapmod, w.twojmax, beta, cfg, prec)
+    s.close()
+    n = cfg.natoms
+    tol = FP64_TOL if prec == 0 else MIXED_TOL["F"]
+    if natoms_sample >= n:
+        _, ref = O.evaluate(p, beta, cfg.pos, cfg.box)
+        assert rel_err(E, ref.E) <= (FP64_TOL if prec == 0 else MIXED_TOL["E"])
+        assert rel_err(F, ref.F) <= tol
+        assert rel_err(W, ref.W) <= (FP64_TOL if prec == 0 else MIXED_TOL["W"])
+    else:
+        g = np.random.Generator(np.random.PCG64(77))
+        atoms = np.sort(g.choice(n, natoms_sample, replace=False))
+        Fs, res, _ = O.forces_for_atoms(p, beta, cfg.pos, cfg.box, atoms)
+        scale = np.abs(F).max()
+        assert np.abs(F[atoms] - Fs).max() <= tol * scale
+        etol = FP64_TOL if prec == 0 else MIXED_TOL["E"]
+        assert np.abs(E[atoms] - res.E[atoms]).max() <= etol * np.abs(res.E[atoms]).max()
+    assert np.abs(F.sum(0)).max() <= (1e-9 if prec == 0 else 1e-5) * np.abs(F).max() * np.sqrt(n)
+
+
+def test_caller_neighbour_list(snapmod):
+    """A caller-supplied full list (from the oracle's builder) gives the same
+    result as the device builder."""
+    cfg = inputs.bcc(3, disp=0.1, seed=10)
+    beta = inputs.beta(8)
+    pairs = O.build_neighbors(cfg.pos, cfg.box, inputs.RCUT)
+    n, cap = cfg.natoms, 40
+    cnt = np.bincount(pairs.i, minlength=n).astype(np.int32)
+    idx = np.zeros((n, cap), np.int32)
+    img = np.zeros((n, cap, 3), np.int8)
+    fill = np.zeros(n, int)
+    for q in range(len(pairs.i)):
+        i = pairs.i[q]
+        idx[i, fill[i]] = pairs.k[q]
+        img[i, fill[i]] = pairs.img[q]
+        fill[i] += 1
+    dev = "cuda:0"
+    s = snapmod.Snap(8, beta)
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device=dev)
+    nb = (torch.tensor(cnt, device=dev), torch.tensor(idx, device=dev), torch.tensor(img, device=dev))
+    E1, F1, W1 = [x.cpu().numpy() for x in s.compute(pos, cfg.box, neighbors=nb)]
+    E2, F2, W2 = [x.cpu().numpy() for x in s.compute(pos, cfg.box)]
+    s.close()
+    assert rel_err(E1, E2) < 1e-12 and rel_err(F1, F2) < 1e-12 and rel_err(W1, W2) < 1e-12
+
+
+def test_neighbour_overflow_is_reported_and_recoverable(snapmod):
+    cfg = inputs.bcc(4, disp=0.1)
+    s = snapmod.Snap(4, inputs.beta(4))
+    s.set_neigh_cap(8)
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(snapmod.SnapError) as ei:
+        s.compute(pos, cfg.box)
+    assert ei.value.code == snapmod.ERR_NEIGH_OVERFLOW
+    assert s.neigh_max() == 26
+    s.set_neigh_cap(32)
+    E, F, W = s.compute(pos, cfg.box)
+    assert torch.isfinite(F).all()
+    s.close()
+
+
+def test_bad_box_and_empty_system(snapmod):
+    s = snapmod.Snap(4, inputs.beta(4))
+    pos = torch.zeros((4, 3), dtype=torch.float64, device="cuda:0")
+    for box in ([0.0, 5.0, 5.0], [np.inf, 5, 5], [5.0, -1.0, 5.0]):
+        with pytest.raises(snapmod.SnapError) as ei:
+            s.compute(pos, box)
+        assert ei.value.code == snapmod.ERR_BOX
+    empty = torch.zeros((0, 3), dtype=torch.float64, device="cuda:0")
+    E, F, W = s.compute(empty, [5.0, 5.0, 5.0])
+    assert E.numel() == 0 and F.numel() == 0 and float(W.abs().sum()) == 0.0
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_host_entry_point_and_determinism(snapmod, prec):
+    cfg = inputs.bcc(4, disp=0.1)
+    beta = inputs.beta(8)
+    s = snapmod.Snap(8, beta, precision=prec)
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device="cuda:0")
+    E1, F1, W1 = [x.cpu().numpy() for x in s.compute(pos, cfg.box)]
+    E2, F2, W2 = [x.cpu().numpy() for x in s.compute(pos, cfg.box)]
+    E3, F3, W3 = s.compute_host(cfg.pos, cfg.box)
+    s.close()
+    for a, b, c in ((E1, E2, E3), (F1, F2, F3), (W1, W2, W3)):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_set_beta_linearity(snapmod):
+    cfg = inputs.bcc(3, disp=0.1)
+    b1, b2 = inputs.beta(8, seed=1), inputs.beta(8, seed=2)
+    s = snapmod.Snap(8, b1)
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device="cuda:0")
+    out = []
+    for b in (b1, b2, b1 + b2):
+        s.set_beta(b)
+        out.append([x.cpu().numpy().copy() for x in s.compute(pos, cfg.box)])
+    s.close()
+    (E1, F1, _), (E2, F2, _), (E12, F12, _) = out
+    assert rel_err(E12, E1 + E2) < 1e-12
+    assert rel_err(F12, F1 + F2) < 1e-11
+    _, ref = O.evaluate(O.Params(8), b1 + b2, cfg.pos, cfg.box)
+    assert rel_err(F12, ref.F) < FP64_TOL
