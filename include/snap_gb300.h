@@ -181,6 +181,32 @@ long long snap_get_buffer(snap_ctx* ctx, int which, void* dst_host, size_t bytes
 int snap_half_index(int twojmax, int t, int ma, int mb);
 int snap_half_size(int twojmax);
 
+/* Neighbour list for callers that cannot allocate device memory -- for
+ * example code running inside a CUDA graph capture, where cudaMalloc is not
+ * allowed, or programs whose device memory belongs to another allocator.
+ * The paper has no counterpart: this is a deployment variant of the device
+ * builder used by snap_compute, and it builds the same list (same order).
+ * It allocates nothing: its scratch is a fixed 1 MiB device array inside the
+ * library, held by every GPU that loads the library until the process exits.
+ *   natoms  : 0..65536 (more returns SNAP_ERR_ARG)
+ *   pos     : device, [natoms][3] doubles
+ *   box     : HOST, 3 box lengths (periodic, orthorhombic)
+ *   rcut    : cutoff, > 0
+ *   cap     : slots per atom, 1..64
+ *   cnt, nbr, img, rij : device outputs, [natoms], [natoms][cap],
+ *             [natoms][cap][3] signed char image shifts, [natoms][cap][3]
+ *             doubles r_k + s L - r_i; counts above cap are truncated
+ *   max_count : device, 1 int, receives the largest count (a value above cap
+ *             means the list overflowed), or NULL
+ *   stream  : cudaStream_t (void*); the call only enqueues work.
+ * The first call on a device looks up the device address of the scratch
+ * array; make that first call before any stream capture.  All calls share
+ * the one array: calls that may overlap on the GPU (different streams, or
+ * several host threads) race and must be serialised by the caller. */
+int snap_neighbors_noalloc(int natoms, const double* pos, const double* box, double rcut,
+                           int cap, int* cnt, int* nbr, signed char* img, double* rij,
+                           int* max_count, void* stream);
+
 /* Release the context and its device memory. */
 int snap_destroy(snap_ctx* ctx);
 

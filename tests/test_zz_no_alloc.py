@@ -1,0 +1,106 @@
+"""snap_neighbors_noalloc: the neighbour-list entry point for callers that
+cannot allocate device memory (for example inside a CUDA graph capture, or
+under another owner's allocator).  It must produce the same list as the
+existing entry point (snap_compute's device builder, read back with
+snap_get_buffer), call after call, although all calls share one fixed scratch
+array inside the library.
+
+This file is collected last on purpose, and it also passes alone in a fresh
+process.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2011_12875_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2011_12875_gb300 import build, snap
+    build.build()
+    L = snap.load()
+    p, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.snap_neighbors_noalloc.argtypes = [i, p, p, d, i, p, p, p, p, p, p]
+    L.snap_neighbors_noalloc.restype = i
+    return L
+
+
+def existing_lists(cfg, cap):
+    """Neighbour list of the existing entry point (snap_compute)."""
+    from paper_2011_12875_gb300 import snap
+    s = snap.Snap(4, inputs.beta(4))
+    s.set_neigh_cap(cap)
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device="cuda:0")
+    s.compute(pos, cfg.box)
+    n = cfg.natoms
+    out = (s.get_buffer(snap.BUF_NBR_CNT).copy(),
+           s.get_buffer(snap.BUF_NBR_IDX).reshape(n, cap).copy(),
+           s.get_buffer(snap.BUF_NBR_IMG).reshape(n, cap, 3).copy(),
+           s.get_buffer(snap.BUF_RIJ).reshape(n, cap, 3).copy())
+    s.close()
+    return out
+
+
+def noalloc_lists(lib, cfg, cap):
+    n = cfg.natoms
+    dev = "cuda:0"
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device=dev)
+    cnt = torch.full((n,), -1, dtype=torch.int32, device=dev)
+    nbr = torch.full((n, cap), -1, dtype=torch.int32, device=dev)
+    img = torch.zeros((n, cap, 3), dtype=torch.int8, device=dev)
+    rij = torch.zeros((n, cap, 3), dtype=torch.float64, device=dev)
+    mx = torch.zeros(1, dtype=torch.int32, device=dev)
+    box = np.ascontiguousarray(cfg.box, dtype=np.float64)
+    stream = torch.cuda.current_stream().cuda_stream
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    rc = lib.snap_neighbors_noalloc(n, ptr(pos), box.ctypes.data_as(ctypes.c_void_p),
+                                    inputs.RCUT, cap, ptr(cnt), ptr(nbr), ptr(img), ptr(rij),
+                                    ptr(mx), ctypes.c_void_p(stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    return (cnt.cpu().numpy(), nbr.cpu().numpy(), img.cpu().numpy(), rij.cpu().numpy(),
+            int(mx.item()))
+
+
+def same(got, want):
+    cnt, nbr, img, rij = want
+    assert np.array_equal(got[0], cnt)
+    for i in range(len(cnt)):
+        c = cnt[i]
+        assert np.array_equal(got[1][i, :c], nbr[i, :c])
+        assert np.array_equal(got[2][i, :c], img[i, :c])
+        # exact FP64 separations; the parity tolerance is 1e-10 relative
+        np.testing.assert_allclose(got[3][i, :c], rij[i, :c], rtol=0, atol=1e-10 * 4.73442)
+
+
+def test_noalloc_matches_existing_entry_point_on_consecutive_calls(lib):
+    """Two calls in a row on different configurations (a large box with
+    nearest images and a small box with many images of each atom): both match
+    the existing entry point, so the shared scratch is reset between calls."""
+    cap = 32
+    a = inputs.bcc(4, disp=0.1)
+    b = inputs.bcc(2, disp=0.15, seed=3)
+    want_a, want_b = existing_lists(a, cap), existing_lists(b, cap)
+    got_a = noalloc_lists(lib, a, cap)
+    got_b = noalloc_lists(lib, b, cap)
+    same(got_a[:4], want_a)
+    same(got_b[:4], want_b)
+    assert got_a[4] == want_a[0].max() == 26
+    assert got_b[4] == want_b[0].max()
+    again = noalloc_lists(lib, a, cap)
+    same(again[:4], want_a)
+
+
+def test_noalloc_reports_overflow_and_rejects_oversized_input(lib):
+    cfg = inputs.bcc(4, disp=0.1)
+    got = noalloc_lists(lib, cfg, 8)
+    assert got[4] == 26 and got[0].max() == 8
+    box = np.ascontiguousarray(cfg.box, dtype=np.float64)
+    rc = lib.snap_neighbors_noalloc(65537, None, box.ctypes.data_as(ctypes.c_void_p), 4.7, 32,
+                                    None, None, None, None, None, None)
+    assert rc == -1  # SNAP_ERR_ARG: more atoms than the fixed scratch holds
