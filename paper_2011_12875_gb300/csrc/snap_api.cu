@@ -169,15 +169,11 @@ int ensure_workspace(snap_ctx* c, int n, int K) {
 }
 
 int ensure_slices(snap_ctx* c, int n) {
-  const int nblk = (n + 31) / 32;
-  const int target_warps = c->nsm * 16;
-  int ns = (target_warps + nblk - 1) / nblk;
-  ns = std::max(4, std::min(ns, 256));
-  ns = (ns + 3) / 4 * 4;
-  if (ns == c->nslices) return SNAP_OK;
-  int rc = upload(c, &c->d_yslice, c->tab.slices(ns));
+  const snap::YiGeometry g = snap::yi_geometry((int)c->rsize(), c->tab.H, n, c->nsm);
+  if (g.nslices == c->nslices) return SNAP_OK;
+  int rc = upload(c, &c->d_yslice, c->tab.slices(g.nslices));
   if (rc) return rc;
-  c->nslices = ns;
+  c->nslices = g.nslices;
   return SNAP_OK;
 }
 
@@ -287,15 +283,16 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   a.yjobs = c->d_jobs;
   a.yslice = c->d_yslice;
   a.nslices = c->nslices;
+  a.nsm = c->nsm;
   a.cg = c->d_cg;
   a.betaw = c->d_betaw;
   a.rootpq = c->d_root;
 
+  const bool mixed = c->precision == SNAP_MIXED;
   SNAP_CUDA(c, snap::launch_rev(a, c->d_rev, s));
   SNAP_CUDA(c, mark());
-  SNAP_CUDA(c, snap::launch_geom(a, s));
+  SNAP_CUDA(c, mixed ? snap::launch_geom<float>(a, s) : snap::launch_geom<double>(a, s));
   SNAP_CUDA(c, mark());
-  const bool mixed = c->precision == SNAP_MIXED;
   SNAP_CUDA(c, mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s));
   SNAP_CUDA(c, mark());
   SNAP_CUDA(c, mixed ? snap::launch_yi<float>(a, s) : snap::launch_yi<double>(a, s));
@@ -314,6 +311,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
 
 int check_flags(snap_ctx* c) {
   c->last_nmax = c->h_flags[0];
+  if (c->h_flags[3]) return fail(c, SNAP_ERR_TIMEOUT, "a bounded device wait (TMA staging) gave up");
   if (c->h_flags[2]) return fail(c, SNAP_ERR_ARG, "neighbour list: count outside 0..cap or index outside 0..N-1");
   if (c->h_flags[0] > c->last_K)
     return fail(c, SNAP_ERR_NEIGH_OVERFLOW,
@@ -395,7 +393,7 @@ int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switch
   }
   int rc = upload(c, &c->d_half_tmm, c->tab.half_tmm);
   if (!rc) rc = upload(c, &c->d_jobs, c->tab.jobs);
-  if (!rc) rc = upload_r(c, &c->d_cg, c->tab.cg);
+  if (!rc) rc = upload_r(c, &c->d_cg, c->tab.cgpad);
   if (!rc) rc = upload_r(c, &c->d_root, c->tab.rootpq);
   if (!rc) rc = upload_r(c, &c->d_betaw, c->tab.beta_weights(c->beta.data()));
   if (rc) {

@@ -27,16 +27,20 @@ __host__ __device__ constexpr int tmm_t(int p) { return p & 0xff; }
 __host__ __device__ constexpr int tmm_ma(int p) { return (p >> 8) & 0xff; }
 __host__ __device__ constexpr int tmm_mb(int p) { return (p >> 16) & 0xff; }
 
-// Per neighbour slot geometry, FP64 (Cayley-Klein parameters, Sec. II-A):
+// Per neighbour slot geometry (Cayley-Klein parameters, Sec. II-A), computed
+// in FP64 and stored in the working precision R:
 //  [0..1] a, [2..3] b, [4] f_c, [5..7] d f_c / d r_d,
 //  [8..13] d a / d r_d (re, im per d), [14..19] d b / d r_d.
 // A slot with r >= rcut has f_c = 0 and zero derivatives.
 
-// Y-kernel work item: one half-matrix element of one Z^t_{t1 t2}.
-//  x: t1 | t2<<4 | t<<8 | ma<<12 | mb<<16
+// Rows of one compute_Y work item (kYiRW consecutive ma of one column).
+constexpr int kYiRW = 4;
+
+// compute_Y work item: rows ma0..ma0+nr-1 of column mb of one Z^t_{t1 t2}.
+//  x: t1 | t2<<4 | t<<8 | ma0<<12 | mb<<16 | nr<<20
 //  y: half base of t1 | half base of t2 << 16
-//  z: offset of the (t1, t2, t) Clebsch-Gordan block
-//  w: index of the (t1, t2, t) triple | output half index << 16
+//  z: offset of the padded (t1, t2, t) Clebsch-Gordan block
+//  w: index of the (t1, t2, t) triple | half index of (t, ma0, mb) << 16
 struct YJob {
   int x, y, z, w;
 };
@@ -79,7 +83,7 @@ struct WorkArgs {
   const signed char* img;
   const int* rev;
   double* rij;
-  double* geom;
+  void* geom;  // R [N][K][kGeomStride]: Cayley-Klein geometry in the working precision
   void* Ure;
   void* Uim;
   void* Yre;
@@ -94,6 +98,7 @@ struct WorkArgs {
   const YJob* yjobs;
   const int* yslice;
   int nslices;
+  int nsm;
   const void* cg;
   const void* betaw;
   const void* rootpq;
@@ -107,11 +112,21 @@ cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, doub
                                 const signed char* uimg, int ucap, int* cnt, int* nbr,
                                 signed char* img, double* rij, int* flags, cudaStream_t s);
 cudaError_t launch_rev(const WorkArgs& a, int* rev, cudaStream_t s);
-cudaError_t launch_geom(const WorkArgs& a, cudaStream_t s);
+template <typename G> cudaError_t launch_geom(const WorkArgs& a, cudaStream_t s);
 
 // Launchers (snap_kernels.cu), R = float (mixed) or double (FP64)
 template <typename R> cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s);
 template <typename R> cudaError_t launch_yi(const WorkArgs& a, cudaStream_t s);
+
+// Launch shape of compute_Y for N atoms: grid (nblk, ysplit), `threads` per
+// CTA, nslices = ysplit * warps per CTA work slices per 32-atom block; the
+// block's Ulisttot is staged in `smem` bytes of shared memory when it fits.
+struct YiGeometry {
+  int nblk, ysplit, threads, nslices;
+  size_t smem;
+  bool staged;
+};
+YiGeometry yi_geometry(int rsize, int H, int n, int nsm);
 template <typename R> cudaError_t launch_de(const WorkArgs& a, cudaStream_t s);
 template <typename R> cudaError_t launch_force(const WorkArgs& a, cudaStream_t s);
 int force_blocks(int n);

@@ -7,6 +7,8 @@
 // results are deterministic; there are no global atomics in the data path.
 #include <math.h>
 
+#include <algorithm>
+
 #include "snap_internal.h"
 
 namespace snap {
@@ -91,10 +93,10 @@ __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
   cx<R>* b1 = b0 + L;
   const int cnt = a.cnt[i];
   for (int s = warp; s < cnt; s += NW) {
-    const double* g = a.geom + ((long)i * a.K + s) * kGeomStride;
-    const cx<R> ca = mk<R>((R)g[0], (R)g[1]);
-    const cx<R> cb = mk<R>((R)g[2], (R)g[3]);
-    const R fc = (R)g[4];
+    const R* g = reinterpret_cast<const R*>(a.geom) + ((long)i * a.K + s) * kGeomStride;
+    const cx<R> ca = mk<R>(g[0], g[1]);
+    const cx<R> cb = mk<R>(g[2], g[3]);
+    const R fc = g[4];
     cx<R>* cur = b0;
     cx<R>* nxt = b1;
     if (lane == 0) {
@@ -152,85 +154,206 @@ __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
 
 // ------------------------------------------------------------- compute_Y
 // Lanes = 32 consecutive atoms (the paper's warp-of-atoms AoSoA layout,
-// Sec. V-B), so the Clebsch-Gordan coefficients and all indices are uniform
-// across the warp and every U/Y access is one coalesced line.  Each warp owns
-// a contiguous run of work items sorted by output element, so each Y element
-// is accumulated in registers and written once (no atomics):
-//   Z^t_{t1t2}[ma][mb] = sum_{mb1} C_b sum_{ma1} C_a U_t1[ma1][mb1] U_t2[ma2][mb2]
-//   Y_t[ma][mb]       += betaw(t1, t2, t) Z^t_{t1t2}[ma][mb]            (Eq. y)
-// with ma2 = ma - ma1 + (t1+t2-t)/2 and the same for mb.  betaw carries beta
-// of the bispectrum component the triple belongs to and the factor that makes
-// Y the derivative of E_i with respect to U (see the table builder).
-template <typename R>
-__device__ __forceinline__ cx<R> u_full(const R* __restrict__ Ure, const R* __restrict__ Uim,
-                                        int base, int t, int ma, int mb, int lane) {
-  if (2 * mb <= t) {
-    const int idx = (base + mb * (t + 1) + ma) * 32 + lane;
-    return mk<R>(__ldg(Ure + idx), __ldg(Uim + idx));
-  }
-  const int idx = (base + (t - mb) * (t + 1) + (t - ma)) * 32 + lane;
-  const R s = ((ma + mb) & 1) ? R(-1) : R(1);
-  return mk<R>(s * __ldg(Ure + idx), -s * __ldg(Uim + idx));
+// Sec. V-B): every Clebsch-Gordan coefficient and index is uniform across the
+// warp.  The 32 atoms' Ulisttot (re and im planes, [H][32]) is staged into
+// shared memory with one TMA bulk copy per plane.  A work item is rows
+// ma0..ma0+3 of column mb of one Z^t_{t1t2} (Eq. z):
+//   Z[ma][mb] = sum_{mb1} C_b sum_{ma1} C_a U_t1[ma1][mb1] U_t2[ma+d-ma1][mb+d-mb1],
+// d = (t1+t2-t)/2.  For fixed (mb1, ma1) the four rows read four consecutive
+// elements of one U_t2 column, so a sliding window of four registers needs one
+// new U_t2 load per ma1 step.  Y_t[ma][mb] += betaw(t1,t2,t) Z (Eq. y);
+// betaw carries beta of the component the triple belongs to and the factor
+// that makes Y the derivative of E_i with respect to U.  Work items are sorted
+// by output group, so each warp accumulates its outputs in registers and
+// writes them once (no atomics).
+constexpr unsigned kSpinLimit = 1u << 24;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
 }
 
-template <typename R, int WPB>
-__global__ void __launch_bounds__(WPB * 32) yi_kernel(WorkArgs a) {
+// Element x of column `col` (mb) of layer t: stored at base + x*dir, or the
+// mirror of a stored column, (-1)^(x+mb) conj(.).
+template <typename R>
+struct UCol {
+  int base, dir, mb;
+  bool mir;
+};
+template <typename R>
+__device__ __forceinline__ UCol<R> ucol(int hb, int t, int mb) {
+  UCol<R> c;
+  c.mb = mb;
+  if (2 * mb <= t) {
+    c.base = hb + mb * (t + 1);
+    c.dir = 1;
+    c.mir = false;
+  } else {
+    c.base = hb + (t - mb) * (t + 1) + t;
+    c.dir = -1;
+    c.mir = true;
+  }
+  return c;
+}
+template <typename R>
+__device__ __forceinline__ cx<R> uget(const R* __restrict__ ure, const R* __restrict__ uim, const UCol<R>& c,
+                                      int x, int lane) {
+  const int idx = (c.base + c.dir * x) * 32 + lane;
+  R re = ure[idx], im = uim[idx];
+  if (c.mir) {
+    const R sg = ((x + c.mb) & 1) ? R(-1) : R(1);
+    re *= sg;
+    im *= -sg;
+  }
+  return mk<R>(re, im);
+}
+
+template <typename R, bool STAGED>
+__global__ void __launch_bounds__(512) yi_kernel(WorkArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int RW = kYiRW;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int slice = blockIdx.y * WPB + warp;
-  if (slice >= a.nslices) return;
   const long blk = blockIdx.x;
   const int H = a.H;
-  const R* Ure = reinterpret_cast<const R*>(a.Ure) + blk * H * 32;
-  const R* Uim = reinterpret_cast<const R*>(a.Uim) + blk * H * 32;
+  const R* ure = reinterpret_cast<const R*>(a.Ure) + blk * H * 32;
+  const R* uim = reinterpret_cast<const R*>(a.Uim) + blk * H * 32;
+  if (STAGED) {
+    R* sre = reinterpret_cast<R*>(smem);
+    R* sim = sre + H * 32;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sim + H * 32);
+    const unsigned bytes = (unsigned)(H * 32 * sizeof(R));
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, 2 * bytes);
+      bulk_g2s(sre, ure, bytes, bar);
+      bulk_g2s(sim, uim, bytes, bar);
+    }
+    bool ok = false;
+    for (unsigned it = 0; it < kSpinLimit; ++it)
+      if (mbar_try_wait(bar, 0)) {
+        ok = true;
+        break;
+      }
+    if (!ok) {
+      if (threadIdx.x == 0) atomicMax(&a.flags[3], 1);
+      return;
+    }
+    ure = sre;
+    uim = sim;
+  }
+  const int slice = blockIdx.y * (blockDim.x >> 5) + warp;
+  if (slice >= a.nslices) return;
   R* Yre = reinterpret_cast<R*>(a.Yre) + blk * H * 32;
   R* Yim = reinterpret_cast<R*>(a.Yim) + blk * H * 32;
-  const R* cg = reinterpret_cast<const R*>(a.cg);
-  const R* betaw = reinterpret_cast<const R*>(a.betaw);
+  const R* __restrict__ cg = reinterpret_cast<const R*>(a.cg);
+  const R* __restrict__ betaw = reinterpret_cast<const R*>(a.betaw);
   const int q0 = a.yslice[slice], q1 = a.yslice[slice + 1];
-  cx<R> y = mk<R>(0, 0);
-  int out = -1;
+  R yr[RW], yi[RW];
+#pragma unroll
+  for (int r = 0; r < RW; ++r) yr[r] = yi[r] = R(0);
+  int og = -1, ognr = 0;
   for (int q = q0; q < q1; ++q) {
     const YJob job = a.yjobs[q];
     const int t1 = job.x & 15, t2 = (job.x >> 4) & 15, t = (job.x >> 8) & 15;
-    const int ma = (job.x >> 12) & 15, mb = (job.x >> 16) & 15;
+    const int ma0 = (job.x >> 12) & 15, mb = (job.x >> 16) & 15, nr = (job.x >> 20) & 15;
     const int u1b = job.y & 0xffff, u2b = job.y >> 16;
-    const int cgb = job.z;
+    const int cgo = job.z;
     const int trip = job.w & 0xffff, o = job.w >> 16;
-    if (o != out) {
-      if (out >= 0) {
-        Yre[out * 32 + lane] = y.re;
-        Yim[out * 32 + lane] = y.im;
+    if (o != og) {
+      if (og >= 0) {
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+          if (r < ognr) {
+            Yre[(og + r) * 32 + lane] = yr[r];
+            Yim[(og + r) * 32 + lane] = yi[r];
+          }
       }
-      y = mk<R>(0, 0);
-      out = o;
+#pragma unroll
+      for (int r = 0; r < RW; ++r) yr[r] = yi[r] = R(0);
+      og = o;
+      ognr = nr;
     }
     const int dl = (t1 + t2 - t) >> 1;
-    const int ma1lo = max(0, ma + dl - t2), ma1hi = min(t1, ma + dl);
+    const int w2 = t2 + 1 + 2 * RW;
     const int mb1lo = max(0, mb + dl - t2), mb1hi = min(t1, mb + dl);
-    cx<R> z = mk<R>(0, 0);
+    const int ma1lo = max(0, ma0 + dl - t2), ma1hi = min(t1, ma0 + nr - 1 + dl);
+    R zr[RW], zi[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) zr[r] = zi[r] = R(0);
     for (int mb1 = mb1lo; mb1 <= mb1hi; ++mb1) {
       const int mb2 = mb + dl - mb1;
-      const R cgbv = __ldg(cg + cgb + mb1 * (t2 + 1) + mb2);
-      cx<R> zz = mk<R>(0, 0);
-      for (int ma1 = ma1lo; ma1 <= ma1hi; ++ma1) {
-        const int ma2 = ma + dl - ma1;
-        const R cgav = __ldg(cg + cgb + ma1 * (t2 + 1) + ma2);
-        const cx<R> u1 = u_full(Ure, Uim, u1b, t1, ma1, mb1, lane);
-        const cx<R> u2 = u_full(Ure, Uim, u2b, t2, ma2, mb2, lane);
-        const cx<R> p = mul(u1, u2);
-        zz.re += cgav * p.re;
-        zz.im += cgav * p.im;
+      const R cgbv = cg[cgo + mb1 * w2 + mb2 + RW];
+      const UCol<R> c1 = ucol<R>(u1b, t1, mb1);
+      const UCol<R> c2 = ucol<R>(u2b, t2, mb2);
+      cx<R> w[RW];
+#pragma unroll
+      for (int r = 0; r < RW; ++r) {
+        const int x = ma0 + r + dl - ma1lo;
+        w[r] = (x >= 0 && x <= t2) ? uget(ure, uim, c2, x, lane) : mk<R>(0, 0);
       }
-      z.re += cgbv * zz.re;
-      z.im += cgbv * zz.im;
+      R zzr[RW], zzi[RW];
+#pragma unroll
+      for (int r = 0; r < RW; ++r) zzr[r] = zzi[r] = R(0);
+      for (int ma1 = ma1lo;;) {
+        const cx<R> u1 = uget(ure, uim, c1, ma1, lane);
+        const R* ca = cg + cgo + ma1 * w2 + (ma0 + dl - ma1) + RW;
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+          const cx<R> p = mul(u1, w[r]);
+          const R cv = ca[r];
+          zzr[r] += cv * p.re;
+          zzi[r] += cv * p.im;
+        }
+        if (++ma1 > ma1hi) break;
+#pragma unroll
+        for (int r = RW - 1; r > 0; --r) w[r] = w[r - 1];
+        const int x = ma0 + dl - ma1;
+        w[0] = (x >= 0 && x <= t2) ? uget(ure, uim, c2, x, lane) : mk<R>(0, 0);
+      }
+#pragma unroll
+      for (int r = 0; r < RW; ++r) {
+        zr[r] += cgbv * zzr[r];
+        zi[r] += cgbv * zzi[r];
+      }
     }
-    const R bw = __ldg(betaw + trip);
-    y.re += bw * z.re;
-    y.im += bw * z.im;
+    const R bw = betaw[trip];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      yr[r] += bw * zr[r];
+      yi[r] += bw * zi[r];
+    }
   }
-  if (out >= 0) {
-    Yre[out * 32 + lane] = y.re;
-    Yim[out * 32 + lane] = y.im;
+  if (og >= 0) {
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+      if (r < ognr) {
+        Yre[(og + r) * 32 + lane] = yr[r];
+        Yim[(og + r) * 32 + lane] = yi[r];
+      }
   }
 }
 
@@ -272,9 +395,9 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
   const int cnt = a.cnt[i];
   for (int s = warp; s < cnt; s += NW) {
     const long slot = (long)i * a.K + s;
-    const double* g = a.geom + slot * kGeomStride;
-    const cx<R> ca = mk<R>((R)g[0], (R)g[1]);
-    const cx<R> cb = mk<R>((R)g[2], (R)g[3]);
+    const R* g = reinterpret_cast<const R*>(a.geom) + slot * kGeomStride;
+    const cx<R> ca = mk<R>(g[0], g[1]);
+    const cx<R> cb = mk<R>(g[2], g[3]);
     // forward: all layers of u (half layout) and S
     R S = 0;
     if (lane == 0) {
@@ -373,17 +496,13 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
     ga.im = warp_sum(ga.im);
     gb.re = warp_sum(gb.re);
     gb.im = warp_sum(gb.im);
-    if (lane == 0) {
-      const double fc = g[4];
-      const double Sd = (double)S;
-      const double gar = (double)ga.re, gai = (double)ga.im;
-      const double gbr = (double)gb.re, gbi = (double)gb.im;
-      for (int d = 0; d < 3; ++d) {
-        const double dar = g[8 + 2 * d], dai = g[9 + 2 * d];
-        const double dbr = g[14 + 2 * d], dbi = g[15 + 2 * d];
-        const double ds = gar * dar + gai * dai + gbr * dbr + gbi * dbi;
-        a.dedr[slot * 3 + d] = g[5 + d] * Sd + fc * ds;
-      }
+    // lanes 0..2: component d of dE_i/dr_ik in the working precision; the
+    // per-atom force and virial sums over pairs are FP64 (force_kernel)
+    if (lane < 3) {
+      const int d = lane;
+      const R ds = ga.re * g[8 + 2 * d] + ga.im * g[9 + 2 * d] + gb.re * g[14 + 2 * d] +
+                   gb.im * g[15 + 2 * d];
+      a.dedr[slot * 3 + d] = (double)(g[5 + d] * S + g[4] * ds);
     }
     __syncwarp();
   }
@@ -475,7 +594,6 @@ __global__ void virial_reduce_kernel(const double* __restrict__ vpart, int nb, d
 
 constexpr int kUiWarps = 4;
 constexpr int kDeWarps = 4;
-constexpr int kYiWarps = 4;
 
 template <typename R>
 size_t ui_smem(int H, int L) {
@@ -506,12 +624,35 @@ cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+YiGeometry yi_geometry(int rsize, int H, int n, int nsm) {
+  YiGeometry g;
+  g.nblk = (n + 31) / 32;
+  const size_t stage = (size_t)2 * H * 32 * rsize + 16;
+  g.staged = stage <= 200 * 1024;
+  g.smem = g.staged ? stage : 0;
+  g.threads = (g.smem > 100 * 1024) ? 512 : 256;
+  int cps = 2048 / g.threads;
+  if (g.staged) cps = std::max(1, std::min(cps, (int)((227 * 1024) / g.smem)));
+  const int target = nsm * cps * 2;
+  g.ysplit = std::max(1, (target + g.nblk - 1) / g.nblk);
+  g.ysplit = std::min(g.ysplit, 64);
+  g.nslices = g.ysplit * (g.threads / 32);
+  return g;
+}
+
 template <typename R>
 cudaError_t launch_yi(const WorkArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const int nblk = (a.n + 31) / 32;
-  dim3 grid(nblk, (a.nslices + kYiWarps - 1) / kYiWarps);
-  yi_kernel<R, kYiWarps><<<grid, kYiWarps * 32, 0, s>>>(a);
+  const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm);
+  if (g.nslices != a.nslices) return cudaErrorInvalidValue;
+  dim3 grid(g.nblk, g.ysplit);
+  if (g.staged) {
+    cudaError_t e = allow_smem(yi_kernel<R, true>, g.smem);
+    if (e != cudaSuccess) return e;
+    yi_kernel<R, true><<<grid, g.threads, g.smem, s>>>(a);
+  } else {
+    yi_kernel<R, false><<<grid, g.threads, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

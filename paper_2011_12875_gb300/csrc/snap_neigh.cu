@@ -36,14 +36,61 @@ __device__ __forceinline__ double norm2(double x, double y, double z) {
   return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
 }
 
-// One warp per centre atom i; lanes test 32 candidates k at a time, first in
-// FP32 with a margin, then exactly in FP64.  Accepted pairs are appended in a
-// fixed order (tile, image, lane) with a ballot, so the list is deterministic.
+// One warp per centre atom i.  Lanes first test 32 atoms k at a time in
+// FP32 with a margin (all images in range); the survivors are appended, in a
+// fixed order (tile, image, lane), to a per-warp candidate list in shared
+// memory.  Every 32 candidates, the list is checked exactly in FP64 with all
+// lanes busy, and accepted pairs are appended to the output with a ballot, so
+// the list is deterministic and FP64 work is spent only on real candidates.
+constexpr int kCandCap = 64;
+
+__device__ __forceinline__ int pack_img(int x, int y, int z) {
+  return (x + 128) | ((y + 128) << 8) | ((z + 128) << 16);
+}
+
+__device__ __forceinline__ void exact_batch(const NeighArgs& a, int i, double xi, double yi,
+                                            double zi, double rc2, const int* cj, const int* cs,
+                                            int nb, int lane, int& count) {
+  bool in = false;
+  double ex = 0, ey = 0, ez = 0;
+  int j = 0, ix = 0, iy = 0, iz = 0;
+  if (lane < nb) {
+    j = cj[lane];
+    const int pk = cs[lane];
+    ix = (pk & 0xff) - 128;
+    iy = ((pk >> 8) & 0xff) - 128;
+    iz = ((pk >> 16) & 0xff) - 128;
+    ex = sep1(i, j, xi, a.pos[3 * j], ix, a.Lx);
+    ey = sep1(i, j, yi, a.pos[3 * j + 1], iy, a.Ly);
+    ez = sep1(i, j, zi, a.pos[3 * j + 2], iz, a.Lz);
+    in = norm2(ex, ey, ez) < rc2;
+  }
+  const unsigned m = __ballot_sync(kFull, in);
+  if (in) {
+    const int slot = count + __popc(m & ((1u << lane) - 1u));
+    if (slot < a.K) {
+      const long q = (long)i * a.K + slot;
+      a.nbr[q] = j;
+      a.img[3 * q] = (signed char)ix;
+      a.img[3 * q + 1] = (signed char)iy;
+      a.img[3 * q + 2] = (signed char)iz;
+      a.rij[3 * q] = ex;
+      a.rij[3 * q + 1] = ey;
+      a.rij[3 * q + 2] = ez;
+    }
+  }
+  count += __popc(m);
+}
+
 __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a) {
   __shared__ float4 tile[kNbTile];
+  __shared__ int cand_j[kNbWarps][kCandCap];
+  __shared__ int cand_s[kNbWarps][kCandCap];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * kNbWarps + warp;
   const bool active = i < a.n;
+  int* cj = cand_j[warp];
+  int* cs = cand_s[warp];
   float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
   double xi = 0, yi = 0, zi = 0;
   if (active) {
@@ -58,7 +105,8 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
   const float rc2f = rcf * rcf;
   const double rc2 = a.rcut * a.rcut;
   const unsigned lt = (1u << lane) - 1u;
-  int count = 0;
+  int count = 0;  // accepted pairs (warp-uniform)
+  int ncand = 0;  // pending candidates (warp-uniform)
   for (int j0 = 0; j0 < a.n; j0 += kNbTile) {
     __syncthreads();
     for (int q = threadIdx.x; q < kNbTile; q += blockDim.x)
@@ -78,36 +126,42 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
             const int ix = nx + sx, iy = ny + sy, iz = nz + sz;
             const float fx = dx0 + (float)ix * Lx, fy = dy0 + (float)iy * Ly, fz = dz0 + (float)iz * Lz;
             const bool self = (j == i) && ix == 0 && iy == 0 && iz == 0;
-            bool in = false;
-            double ex = 0, ey = 0, ez = 0;
-            if (valid && !self && fx * fx + fy * fy + fz * fz < rc2f) {
-              const double xk = a.pos[3 * j], yk = a.pos[3 * j + 1], zk = a.pos[3 * j + 2];
-              ex = sep1(i, j, xi, xk, ix, a.Lx);
-              ey = sep1(i, j, yi, yk, iy, a.Ly);
-              ez = sep1(i, j, zi, zk, iz, a.Lz);
-              in = norm2(ex, ey, ez) < rc2;
+            const bool c = valid && !self && (fx * fx + fy * fy + fz * fz < rc2f);
+            const unsigned m = __ballot_sync(kFull, c);
+            if (c) {
+              const int pos = ncand + __popc(m & lt);
+              cj[pos] = j;
+              cs[pos] = pack_img(ix, iy, iz);
             }
-            const unsigned m = __ballot_sync(kFull, in);
-            if (in) {
-              const int slot = count + __popc(m & lt);
-              if (slot < a.K) {
-                const long q = (long)i * a.K + slot;
-                a.nbr[q] = j;
-                a.img[3 * q] = (signed char)ix;
-                a.img[3 * q + 1] = (signed char)iy;
-                a.img[3 * q + 2] = (signed char)iz;
-                a.rij[3 * q] = ex;
-                a.rij[3 * q + 1] = ey;
-                a.rij[3 * q + 2] = ez;
+            ncand += __popc(m);
+            if (ncand >= 32) {
+              __syncwarp();
+              exact_batch(a, i, xi, yi, zi, rc2, cj, cs, 32, lane, count);
+              __syncwarp();
+              const int rest = ncand - 32;
+              int mj = 0, ms = 0;
+              if (lane < rest) {
+                mj = cj[32 + lane];
+                ms = cs[32 + lane];
               }
+              __syncwarp();
+              if (lane < rest) {
+                cj[lane] = mj;
+                cs[lane] = ms;
+              }
+              ncand = rest;
+              __syncwarp();
             }
-            count += __popc(m);
           }
     }
   }
-  if (active && lane == 0) {
-    a.cnt[i] = min(count, a.K);
-    atomicMax(&a.flags[0], count);
+  if (active) {
+    __syncwarp();
+    if (ncand > 0) exact_batch(a, i, xi, yi, zi, rc2, cj, cs, ncand, lane, count);
+    if (lane == 0) {
+      a.cnt[i] = min(count, a.K);
+      atomicMax(&a.flags[0], count);
+    }
   }
 }
 
@@ -172,18 +226,20 @@ __global__ void rev_kernel(WorkArgs a, int* rev) {
 // reference): theta0 = rfac0 pi (r - rmin0)/(rcut - rmin0), z0 = r cot theta0,
 // r0 = sqrt(r^2 + z0^2), a = (z0 - i z)/r0, b = (y - i x)/r0, and the
 // cosine switching function f_c.
+template <typename G>
 __global__ void geom_kernel(WorkArgs a) {
   const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long)a.n * a.K) return;
   const int i = (int)(q / a.K), s = (int)(q - (long)i * a.K);
   if (s >= a.cnt[i]) return;
   const double x = a.rij[3 * q], y = a.rij[3 * q + 1], z = a.rij[3 * q + 2];
-  double* g = a.geom + q * kGeomStride;
+  // arithmetic in FP64; the result is stored in the working precision G
+  G* g = reinterpret_cast<G*>(a.geom) + q * kGeomStride;
   const double r2 = x * x + y * y + z * z;
   const double r = sqrt(r2);
   if (!(r < a.rcut)) {
-    for (int e = 0; e < kGeomStride; ++e) g[e] = 0.0;
-    g[0] = 1.0;
+    for (int e = 0; e < kGeomStride; ++e) g[e] = G(0);
+    g[0] = G(1);
     return;
   }
   const double span = a.rcut - a.rmin0;
@@ -198,10 +254,10 @@ __global__ void geom_kernel(WorkArgs a) {
   const double ir0 = 1.0 / r0;
   const double ar = z0 * ir0, ai = -z * ir0;
   const double br = y * ir0, bi = -x * ir0;
-  g[0] = ar;
-  g[1] = ai;
-  g[2] = br;
-  g[3] = bi;
+  g[0] = G(ar);
+  g[1] = G(ai);
+  g[2] = G(br);
+  g[3] = G(bi);
   double fc = 1.0, dfcdr = 0.0;
   if (a.switchflag && r > a.rmin0) {
     const double w = M_PI * (r - a.rmin0) / span;
@@ -210,19 +266,19 @@ __global__ void geom_kernel(WorkArgs a) {
     fc = 0.5 * (cw + 1.0);
     dfcdr = -0.5 * M_PI / span * sw;
   }
-  g[4] = fc;
+  g[4] = G(fc);
   const double rv[3] = {x, y, z};
   const double ir = 1.0 / r;
   for (int d = 0; d < 3; ++d) {
     const double ud = rv[d] * ir;
-    g[5 + d] = dfcdr * ud;
+    g[5 + d] = G(dfcdr * ud);
     const double dz0 = dz0dr * ud;
     const double dr0 = (r * ud + z0 * dz0) * ir0;
     // d a = (d(z0 - i z) - a d r0) / r0 ; d b = (d(y - i x) - b d r0) / r0
-    g[8 + 2 * d] = (dz0 - ar * dr0) * ir0;
-    g[9 + 2 * d] = ((d == 2 ? -1.0 : 0.0) - ai * dr0) * ir0;
-    g[14 + 2 * d] = ((d == 1 ? 1.0 : 0.0) - br * dr0) * ir0;
-    g[15 + 2 * d] = ((d == 0 ? -1.0 : 0.0) - bi * dr0) * ir0;
+    g[8 + 2 * d] = G((dz0 - ar * dr0) * ir0);
+    g[9 + 2 * d] = G(((d == 2 ? -1.0 : 0.0) - ai * dr0) * ir0);
+    g[14 + 2 * d] = G(((d == 1 ? 1.0 : 0.0) - br * dr0) * ir0);
+    g[15 + 2 * d] = G(((d == 0 ? -1.0 : 0.0) - bi * dr0) * ir0);
   }
 }
 
@@ -258,10 +314,13 @@ cudaError_t launch_rev(const WorkArgs& a, int* rev, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename G>
 cudaError_t launch_geom(const WorkArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  geom_kernel<<<blocks_for((long)a.n * a.K, 128), 128, 0, s>>>(a);
+  geom_kernel<G><<<blocks_for((long)a.n * a.K, 128), 128, 0, s>>>(a);
   return cudaGetLastError();
 }
+template cudaError_t launch_geom<float>(const WorkArgs&, cudaStream_t);
+template cudaError_t launch_geom<double>(const WorkArgs&, cudaStream_t);
 
 }  // namespace snap

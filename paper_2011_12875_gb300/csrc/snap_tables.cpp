@@ -129,33 +129,49 @@ void HostTables::build(int J2) {
         ztrip.push_back(z);
       }
 
-  // Work list: every half element (ma, mb <= t/2) of every triple, sorted by
-  // output element (stable in triple order).
+  // Padded Clebsch-Gordan blocks for compute_Y: rows x1 = 0..t1, columns
+  // x2 = -kYiRW .. t2 + kYiRW (zeros outside 0..t2), so the kernel reads the
+  // coefficients of kYiRW consecutive outputs without bounds checks.
+  cgpad.clear();
+  for (ZTrip& z : ztrip) {
+    z.cgpad_off = (int)cgpad.size();
+    const int w2 = z.t2 + 1 + 2 * kYiRW;
+    for (int x1 = 0; x1 <= z.t1; ++x1)
+      for (int c = 0; c < w2; ++c) {
+        const int x2 = c - kYiRW;
+        cgpad.push_back((x2 >= 0 && x2 <= z.t2) ? cg[z.cg_off + x1 * (z.t2 + 1) + x2] : 0.0);
+      }
+  }
+
+  // Work list: for every triple and every half column mb <= t/2, groups of
+  // kYiRW consecutive rows ma0..ma0+kYiRW-1, sorted by output group (stable in
+  // triple order), so all contributions to one group are adjacent.
   jobs.clear();
   cost.clear();
   struct Tmp {
-    int out, trip, ma, mb;
+    int out, trip, ma0, mb, nr;
   };
   std::vector<Tmp> tmp;
   for (int q = 0; q < (int)ztrip.size(); ++q) {
     const ZTrip& z = ztrip[q];
     for (int mb = 0; 2 * mb <= z.t; ++mb)
-      for (int ma = 0; ma <= z.t; ++ma)
-        tmp.push_back({half_base(z.t) + mb * (z.t + 1) + ma, q, ma, mb});
+      for (int ma0 = 0; ma0 <= z.t; ma0 += kYiRW)
+        tmp.push_back({half_base(z.t) + mb * (z.t + 1) + ma0, q, ma0, mb,
+                       std::min(kYiRW, z.t + 1 - ma0)});
   }
   std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& x, const Tmp& y) { return x.out < y.out; });
   for (const Tmp& w : tmp) {
     const ZTrip& z = ztrip[w.trip];
     YJob j;
-    j.x = z.t1 | (z.t2 << 4) | (z.t << 8) | (w.ma << 12) | (w.mb << 16);
+    j.x = z.t1 | (z.t2 << 4) | (z.t << 8) | (w.ma0 << 12) | (w.mb << 16) | (w.nr << 20);
     j.y = half_base(z.t1) | (half_base(z.t2) << 16);
-    j.z = z.cg_off;
+    j.z = z.cgpad_off;
     j.w = w.trip | (w.out << 16);
     jobs.push_back(j);
     const int dl = (z.t1 + z.t2 - z.t) / 2;
-    const int na = std::min(z.t1, w.ma + dl) - std::max(0, w.ma + dl - z.t2) + 1;
+    const int na = std::min(z.t1, w.ma0 + w.nr - 1 + dl) - std::max(0, w.ma0 + dl - z.t2) + 1;
     const int nb = std::min(z.t1, w.mb + dl) - std::max(0, w.mb + dl - z.t2) + 1;
-    cost.push_back(std::max(na, 0) * std::max(nb, 0) + 2);
+    cost.push_back(std::max(nb, 0) * (std::max(na, 0) * kYiRW + 8) + 16);
   }
 
   rootpq.assign(kRootDim * kRootDim, 0.0);

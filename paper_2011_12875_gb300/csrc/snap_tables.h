@@ -9,6 +9,7 @@ namespace snap {
 struct ZTrip {
   int t1, t2, t;  // Y triple: Z^t_{t1 t2} with t1 >= t2
   int cg_off;     // offset of its cg[x1][x2] block
+  int cgpad_off;  // offset of its padded block in cgpad
   int bidx;       // canonical bispectrum component it belongs to
   double fac;     // multiplicity / rank factor of the derivative
 };
@@ -18,6 +19,7 @@ struct HostTables {
   std::vector<int> half_tmm;
   std::vector<ZTrip> ztrip;
   std::vector<double> cg;
+  std::vector<double> cgpad;
   std::vector<YJob> jobs;
   std::vector<int> cost;
   std::vector<double> rootpq;
