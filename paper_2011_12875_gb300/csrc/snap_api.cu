@@ -30,9 +30,9 @@ struct snap_ctx {
 
   // device tables
   int* d_half_tmm = nullptr;
-  snap::YJob* d_jobs = nullptr;
-  void* d_cg = nullptr;
-  void* d_betaw = nullptr;
+  unsigned* d_yterm = nullptr;
+  void* d_ycoef = nullptr;
+  int* d_yfirst = nullptr;
   void* d_root = nullptr;
   int* d_yslice = nullptr;
   int nslices = -1;
@@ -280,12 +280,12 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   a.virial = virial;
   a.flags = c->d_flags;
   a.half_tmm = c->d_half_tmm;
-  a.yjobs = c->d_jobs;
+  a.yterm = c->d_yterm;
+  a.ycoef = c->d_ycoef;
+  a.yfirst = c->d_yfirst;
   a.yslice = c->d_yslice;
   a.nslices = c->nslices;
   a.nsm = c->nsm;
-  a.cg = c->d_cg;
-  a.betaw = c->d_betaw;
   a.rootpq = c->d_root;
 
   const bool mixed = c->precision == SNAP_MIXED;
@@ -392,10 +392,10 @@ int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switch
     return SNAP_ERR_CUDA;
   }
   int rc = upload(c, &c->d_half_tmm, c->tab.half_tmm);
-  if (!rc) rc = upload(c, &c->d_jobs, c->tab.jobs);
-  if (!rc) rc = upload_r(c, &c->d_cg, c->tab.cgpad);
+  if (!rc) rc = upload(c, &c->d_yterm, c->tab.terms);
+  if (!rc) rc = upload(c, &c->d_yfirst, c->tab.term_out_first);
   if (!rc) rc = upload_r(c, &c->d_root, c->tab.rootpq);
-  if (!rc) rc = upload_r(c, &c->d_betaw, c->tab.beta_weights(c->beta.data()));
+  if (!rc) rc = upload_r(c, &c->d_ycoef, c->tab.term_coef(c->beta.data()));
   if (rc) {
     g_create_error = c->err;
     snap_destroy(c);
@@ -409,7 +409,7 @@ int snap_set_beta(snap_ctx* c, const double* beta) {
   if (!c || !beta) return fail(c, SNAP_ERR_ARG, "NULL argument");
   cudaDeviceSynchronize();
   c->beta.assign(beta, beta + 1 + c->tab.ncoeff);
-  return upload_r(c, &c->d_betaw, c->tab.beta_weights(c->beta.data()));
+  return upload_r(c, &c->d_ycoef, c->tab.term_coef(c->beta.data()));
 }
 
 int snap_set_neigh_cap(snap_ctx* c, int cap) {
@@ -597,9 +597,9 @@ int snap_destroy(snap_ctx* c) {
   cudaDeviceSynchronize();
   free_workspace(c);
   dfree(c->d_half_tmm);
-  dfree(c->d_jobs);
-  dfree(c->d_cg);
-  dfree(c->d_betaw);
+  dfree(c->d_yterm);
+  dfree(c->d_ycoef);
+  dfree(c->d_yfirst);
   dfree(c->d_root);
   dfree(c->d_yslice);
   dfree(c->d_flags);

@@ -33,33 +33,6 @@ __host__ __device__ constexpr int tmm_mb(int p) { return (p >> 16) & 0xff; }
 //  [8..13] d a / d r_d (re, im per d), [14..19] d b / d r_d.
 // A slot with r >= rcut has f_c = 0 and zero derivatives.
 
-// Rows of one compute_Y work item (kYiRW consecutive ma of one column).
-constexpr int kYiRW = 4;
-
-// compute_Y work item: rows ma0..ma0+nr-1 of column mb of one Z^t_{t1 t2}.
-//  x: t1 | t2<<4 | t<<8 | ma0<<12 | mb<<16 | nr<<20
-//  y: half base of t1 | half base of t2 << 16
-//  z: offset of the padded (t1, t2, t) Clebsch-Gordan block
-//  w: index of the (t1, t2, t) triple | half index of (t, ma0, mb) << 16
-struct YJob {
-  int x, y, z, w;
-};
-
-// Device copies of the per-context tables.
-struct DevTables {
-  int twojmax = 0;
-  int H = 0;        // half size
-  int lmax = 0;     // largest half layer
-  int nztrip = 0;   // (t1 >= t2, t) triples
-  int njobs = 0;
-  int* half_tmm = nullptr;  // [H]
-  YJob* yjobs = nullptr;    // [njobs], sorted by output element
-  void* cg = nullptr;       // R [ncg]: per triple, cg[x1][x2] of <j1 m1 j2 m2|j m1+m2>
-  void* betaw = nullptr;    // R [nztrip]: weighted beta of each triple
-  void* rootpq = nullptr;   // R [16*16]: sqrt(p/q)
-  double* cg64 = nullptr;   // host-built FP64 tables kept for re-upload
-};
-
 struct NeighArgs {
   int n, K;
   const double* pos;     // [n][3]
@@ -95,12 +68,12 @@ struct WorkArgs {
   double* virial;
   int* flags;
   const int* half_tmm;
-  const YJob* yjobs;
+  const unsigned* yterm;  // compute_Y term records (see snap_tables.cpp)
+  const void* ycoef;      // R [nterms] term coefficients
+  const int* yfirst;      // [H+1] first term of each output element
   const int* yslice;
   int nslices;
   int nsm;
-  const void* cg;
-  const void* betaw;
   const void* rootpq;
 };
 

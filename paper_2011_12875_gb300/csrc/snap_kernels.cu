@@ -154,18 +154,16 @@ __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
 
 // ------------------------------------------------------------- compute_Y
 // Lanes = 32 consecutive atoms (the paper's warp-of-atoms AoSoA layout,
-// Sec. V-B): every Clebsch-Gordan coefficient and index is uniform across the
-// warp.  The 32 atoms' Ulisttot (re and im planes, [H][32]) is staged into
-// shared memory with one TMA bulk copy per plane.  A work item is rows
-// ma0..ma0+3 of column mb of one Z^t_{t1t2} (Eq. z):
-//   Z[ma][mb] = sum_{mb1} C_b sum_{ma1} C_a U_t1[ma1][mb1] U_t2[ma+d-ma1][mb+d-mb1],
-// d = (t1+t2-t)/2.  For fixed (mb1, ma1) the four rows read four consecutive
-// elements of one U_t2 column, so a sliding window of four registers needs one
-// new U_t2 load per ma1 step.  Y_t[ma][mb] += betaw(t1,t2,t) Z (Eq. y);
-// betaw carries beta of the component the triple belongs to and the factor
-// that makes Y the derivative of E_i with respect to U.  Work items are sorted
-// by output group, so each warp accumulates its outputs in registers and
-// writes them once (no atomics).
+// Sec. V-B), so every index and coefficient is uniform across the warp.  The
+// 32 atoms' Ulisttot (re and im planes, [H][32]) is staged into shared memory
+// with one TMA bulk copy per plane.  The contraction of Eq. (z) and the sum of
+// Eq. (y) are walked as one list of terms, sorted by output element:
+//   Y_t[ma][mb] += coef * U_t1[ma1][mb1] * U_t2[ma2][mb2],
+// coef = betaw * C(ma1,ma2) C(mb1,mb2) (with the mirror signs), where a U
+// element past the stored half columns is read conjugated from its mirror.
+// A term record is 10 + 10 index bits, two conjugation flags and an
+// end-of-output flag.  Each warp owns a contiguous run of outputs, so every Y
+// element is accumulated in registers and written once (no atomics).
 constexpr unsigned kSpinLimit = 1u << 24;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -196,45 +194,43 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
   return ok != 0;
 }
 
-// Element x of column `col` (mb) of layer t: stored at base + x*dir, or the
-// mirror of a stored column, (-1)^(x+mb) conj(.).
-template <typename R>
-struct UCol {
-  int base, dir, mb;
-  bool mir;
-};
-template <typename R>
-__device__ __forceinline__ UCol<R> ucol(int hb, int t, int mb) {
-  UCol<R> c;
-  c.mb = mb;
-  if (2 * mb <= t) {
-    c.base = hb + mb * (t + 1);
-    c.dir = 1;
-    c.mir = false;
-  } else {
-    c.base = hb + (t - mb) * (t + 1) + t;
-    c.dir = -1;
-    c.mir = true;
-  }
-  return c;
+__device__ __forceinline__ float flip_if(float v, unsigned bit) {
+  return __int_as_float(__float_as_int(v) ^ (bit << 31));
 }
+__device__ __forceinline__ double flip_if(double v, unsigned bit) {
+  return bit ? -v : v;
+}
+
 template <typename R>
-__device__ __forceinline__ cx<R> uget(const R* __restrict__ ure, const R* __restrict__ uim, const UCol<R>& c,
-                                      int x, int lane) {
-  const int idx = (c.base + c.dir * x) * 32 + lane;
-  R re = ure[idx], im = uim[idx];
-  if (c.mir) {
-    const R sg = ((x + c.mb) & 1) ? R(-1) : R(1);
-    re *= sg;
-    im *= -sg;
+struct YAcc {
+  R re, im;
+  int o;
+};
+
+template <typename R>
+__device__ __forceinline__ void y_term(unsigned w, R c, const R* __restrict__ ure, const R* __restrict__ uim,
+                                       R* __restrict__ Yre, R* __restrict__ Yim, int lane, YAcc<R>& y) {
+  const int e1 = (int)(w & 1023u), e2 = (int)((w >> 10) & 1023u);
+  const R a = ure[e1 * 32 + lane];
+  const R b = flip_if(uim[e1 * 32 + lane], (w >> 20) & 1u);
+  const R cc = ure[e2 * 32 + lane];
+  const R d = flip_if(uim[e2 * 32 + lane], (w >> 21) & 1u);
+  const R pr = a * cc - b * d;
+  const R pi = a * d + b * cc;
+  y.re += c * pr;
+  y.im += c * pi;
+  if (w & (1u << 22)) {
+    Yre[y.o * 32 + lane] = y.re;
+    Yim[y.o * 32 + lane] = y.im;
+    y.re = R(0);
+    y.im = R(0);
+    ++y.o;
   }
-  return mk<R>(re, im);
 }
 
 template <typename R, bool STAGED>
 __global__ void __launch_bounds__(512) yi_kernel(WorkArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  constexpr int RW = kYiRW;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long blk = blockIdx.x;
   const int H = a.H;
@@ -267,94 +263,31 @@ __global__ void __launch_bounds__(512) yi_kernel(WorkArgs a) {
   }
   const int slice = blockIdx.y * (blockDim.x >> 5) + warp;
   if (slice >= a.nslices) return;
+  const int o0 = a.yslice[slice], o1 = a.yslice[slice + 1];
+  if (o0 >= o1) return;
   R* Yre = reinterpret_cast<R*>(a.Yre) + blk * H * 32;
   R* Yim = reinterpret_cast<R*>(a.Yim) + blk * H * 32;
-  const R* __restrict__ cg = reinterpret_cast<const R*>(a.cg);
-  const R* __restrict__ betaw = reinterpret_cast<const R*>(a.betaw);
-  const int q0 = a.yslice[slice], q1 = a.yslice[slice + 1];
-  R yr[RW], yi[RW];
+  const unsigned* __restrict__ tw = a.yterm;
+  const R* __restrict__ tc = reinterpret_cast<const R*>(a.ycoef);
+  const int q1 = a.yfirst[o1];
+  int q = a.yfirst[o0];
+  YAcc<R> y;
+  y.re = R(0);
+  y.im = R(0);
+  y.o = o0;
+  constexpr int U = 8;
+  for (; q + U <= q1; q += U) {
+    unsigned w[U];
+    R c[U];
 #pragma unroll
-  for (int r = 0; r < RW; ++r) yr[r] = yi[r] = R(0);
-  int og = -1, ognr = 0;
-  for (int q = q0; q < q1; ++q) {
-    const YJob job = a.yjobs[q];
-    const int t1 = job.x & 15, t2 = (job.x >> 4) & 15, t = (job.x >> 8) & 15;
-    const int ma0 = (job.x >> 12) & 15, mb = (job.x >> 16) & 15, nr = (job.x >> 20) & 15;
-    const int u1b = job.y & 0xffff, u2b = job.y >> 16;
-    const int cgo = job.z;
-    const int trip = job.w & 0xffff, o = job.w >> 16;
-    if (o != og) {
-      if (og >= 0) {
-#pragma unroll
-        for (int r = 0; r < RW; ++r)
-          if (r < ognr) {
-            Yre[(og + r) * 32 + lane] = yr[r];
-            Yim[(og + r) * 32 + lane] = yi[r];
-          }
-      }
-#pragma unroll
-      for (int r = 0; r < RW; ++r) yr[r] = yi[r] = R(0);
-      og = o;
-      ognr = nr;
+    for (int k = 0; k < U; ++k) {
+      w[k] = __ldg(tw + q + k);
+      c[k] = __ldg(tc + q + k);
     }
-    const int dl = (t1 + t2 - t) >> 1;
-    const int w2 = t2 + 1 + 2 * RW;
-    const int mb1lo = max(0, mb + dl - t2), mb1hi = min(t1, mb + dl);
-    const int ma1lo = max(0, ma0 + dl - t2), ma1hi = min(t1, ma0 + nr - 1 + dl);
-    R zr[RW], zi[RW];
 #pragma unroll
-    for (int r = 0; r < RW; ++r) zr[r] = zi[r] = R(0);
-    for (int mb1 = mb1lo; mb1 <= mb1hi; ++mb1) {
-      const int mb2 = mb + dl - mb1;
-      const R cgbv = cg[cgo + mb1 * w2 + mb2 + RW];
-      const UCol<R> c1 = ucol<R>(u1b, t1, mb1);
-      const UCol<R> c2 = ucol<R>(u2b, t2, mb2);
-      cx<R> w[RW];
-#pragma unroll
-      for (int r = 0; r < RW; ++r) {
-        const int x = ma0 + r + dl - ma1lo;
-        w[r] = (x >= 0 && x <= t2) ? uget(ure, uim, c2, x, lane) : mk<R>(0, 0);
-      }
-      R zzr[RW], zzi[RW];
-#pragma unroll
-      for (int r = 0; r < RW; ++r) zzr[r] = zzi[r] = R(0);
-      for (int ma1 = ma1lo;;) {
-        const cx<R> u1 = uget(ure, uim, c1, ma1, lane);
-        const R* ca = cg + cgo + ma1 * w2 + (ma0 + dl - ma1) + RW;
-#pragma unroll
-        for (int r = 0; r < RW; ++r) {
-          const cx<R> p = mul(u1, w[r]);
-          const R cv = ca[r];
-          zzr[r] += cv * p.re;
-          zzi[r] += cv * p.im;
-        }
-        if (++ma1 > ma1hi) break;
-#pragma unroll
-        for (int r = RW - 1; r > 0; --r) w[r] = w[r - 1];
-        const int x = ma0 + dl - ma1;
-        w[0] = (x >= 0 && x <= t2) ? uget(ure, uim, c2, x, lane) : mk<R>(0, 0);
-      }
-#pragma unroll
-      for (int r = 0; r < RW; ++r) {
-        zr[r] += cgbv * zzr[r];
-        zi[r] += cgbv * zzi[r];
-      }
-    }
-    const R bw = betaw[trip];
-#pragma unroll
-    for (int r = 0; r < RW; ++r) {
-      yr[r] += bw * zr[r];
-      yi[r] += bw * zi[r];
-    }
+    for (int k = 0; k < U; ++k) y_term(w[k], c[k], ure, uim, Yre, Yim, lane, y);
   }
-  if (og >= 0) {
-#pragma unroll
-    for (int r = 0; r < RW; ++r)
-      if (r < ognr) {
-        Yre[(og + r) * 32 + lane] = yr[r];
-        Yim[(og + r) * 32 + lane] = yi[r];
-      }
-  }
+  for (; q < q1; ++q) y_term(__ldg(tw + q), __ldg(tc + q), ure, uim, Yre, Yim, lane, y);
 }
 
 // ------------------------------------------------------ fused dU + dE/dr

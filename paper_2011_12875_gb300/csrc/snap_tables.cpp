@@ -129,50 +129,64 @@ void HostTables::build(int J2) {
         ztrip.push_back(z);
       }
 
-  // Padded Clebsch-Gordan blocks for compute_Y: rows x1 = 0..t1, columns
-  // x2 = -kYiRW .. t2 + kYiRW (zeros outside 0..t2), so the kernel reads the
-  // coefficients of kYiRW consecutive outputs without bounds checks.
-  cgpad.clear();
-  for (ZTrip& z : ztrip) {
-    z.cgpad_off = (int)cgpad.size();
-    const int w2 = z.t2 + 1 + 2 * kYiRW;
-    for (int x1 = 0; x1 <= z.t1; ++x1)
-      for (int c = 0; c < w2; ++c) {
-        const int x2 = c - kYiRW;
-        cgpad.push_back((x2 >= 0 && x2 <= z.t2) ? cg[z.cg_off + x1 * (z.t2 + 1) + x2] : 0.0);
-      }
-  }
-
-  // Work list: for every triple and every half column mb <= t/2, groups of
-  // kYiRW consecutive rows ma0..ma0+kYiRW-1, sorted by output group (stable in
-  // triple order), so all contributions to one group are adjacent.
-  jobs.clear();
-  cost.clear();
-  struct Tmp {
-    int out, trip, ma0, mb, nr;
+  // compute_Y term list.  For every half-layout output element (t, ma, mb)
+  // of Y, in output order, every nonzero term of every triple (t1 >= t2)
+  // with output rank t:
+  //   Y_t[ma][mb] += betaw * C(ma1, ma2) C(mb1, mb2) U_t1[ma1][mb1] U_t2[ma2][mb2],
+  // ma2 = ma + d - ma1, mb2 = mb + d - mb1, d = (t1+t2-t)/2.  An element of U
+  // past the stored half columns is (-1)^(ma+mb) conj of its mirror, so each
+  // term stores the two half-layout indices, two conjugation flags, and a
+  // coefficient with the signs, the CG product and betaw folded in.
+  terms.clear();
+  term_cg.clear();
+  term_trip.clear();
+  term_out_first.clear();
+  auto half_elem = [&](int tt, int xa, int xb, int& idx, int& conj, double& sgn) {
+    if (2 * xb <= tt) {
+      idx = half_base(tt) + xb * (tt + 1) + xa;
+      conj = 0;
+      sgn = 1.0;
+    } else {
+      idx = half_base(tt) + (tt - xb) * (tt + 1) + (tt - xa);
+      conj = 1;
+      sgn = ((xa + xb) & 1) ? -1.0 : 1.0;
+    }
   };
-  std::vector<Tmp> tmp;
-  for (int q = 0; q < (int)ztrip.size(); ++q) {
-    const ZTrip& z = ztrip[q];
-    for (int mb = 0; 2 * mb <= z.t; ++mb)
-      for (int ma0 = 0; ma0 <= z.t; ma0 += kYiRW)
-        tmp.push_back({half_base(z.t) + mb * (z.t + 1) + ma0, q, ma0, mb,
-                       std::min(kYiRW, z.t + 1 - ma0)});
-  }
-  std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& x, const Tmp& y) { return x.out < y.out; });
-  for (const Tmp& w : tmp) {
-    const ZTrip& z = ztrip[w.trip];
-    YJob j;
-    j.x = z.t1 | (z.t2 << 4) | (z.t << 8) | (w.ma0 << 12) | (w.mb << 16) | (w.nr << 20);
-    j.y = half_base(z.t1) | (half_base(z.t2) << 16);
-    j.z = z.cgpad_off;
-    j.w = w.trip | (w.out << 16);
-    jobs.push_back(j);
-    const int dl = (z.t1 + z.t2 - z.t) / 2;
-    const int na = std::min(z.t1, w.ma0 + w.nr - 1 + dl) - std::max(0, w.ma0 + dl - z.t2) + 1;
-    const int nb = std::min(z.t1, w.mb + dl) - std::max(0, w.mb + dl - z.t2) + 1;
-    cost.push_back(std::max(nb, 0) * (std::max(na, 0) * kYiRW + 8) + 16);
-  }
+  // triples grouped by output rank
+  std::vector<std::vector<int>> by_t(J2 + 1);
+  for (int q = 0; q < (int)ztrip.size(); ++q) by_t[ztrip[q].t].push_back(q);
+  for (int t = 0; t <= J2; ++t)
+    for (int mb = 0; 2 * mb <= t; ++mb)
+      for (int ma = 0; ma <= t; ++ma) {
+        const size_t first = terms.size();
+        for (int q : by_t[t]) {
+          const ZTrip& z = ztrip[q];
+          const int dl = (z.t1 + z.t2 - t) / 2;
+          for (int mb1 = std::max(0, mb + dl - z.t2); mb1 <= std::min(z.t1, mb + dl); ++mb1) {
+            const int mb2 = mb + dl - mb1;
+            const double cb = cg[z.cg_off + mb1 * (z.t2 + 1) + mb2];
+            if (cb == 0.0) continue;
+            for (int ma1 = std::max(0, ma + dl - z.t2); ma1 <= std::min(z.t1, ma + dl); ++ma1) {
+              const int ma2 = ma + dl - ma1;
+              const double ca = cg[z.cg_off + ma1 * (z.t2 + 1) + ma2];
+              if (ca == 0.0) continue;
+              int i1, c1, i2, c2;
+              double s1, s2;
+              half_elem(z.t1, ma1, mb1, i1, c1, s1);
+              half_elem(z.t2, ma2, mb2, i2, c2, s2);
+              terms.push_back((unsigned)i1 | ((unsigned)i2 << 10) | ((unsigned)c1 << 20) |
+                              ((unsigned)c2 << 21));
+              term_cg.push_back(ca * cb * s1 * s2);
+              term_trip.push_back(q);
+            }
+          }
+        }
+        // every output has at least the term of the (t, 0, t) triple, whose
+        // Clebsch-Gordan product is 1; flag the last term of the output
+        if (terms.size() > first) terms.back() |= (1u << 22);
+        term_out_first.push_back((int)first);
+      }
+  term_out_first.push_back((int)terms.size());
 
   rootpq.assign(kRootDim * kRootDim, 0.0);
   for (int p = 0; p < kRootDim; ++p)
@@ -185,26 +199,28 @@ std::vector<double> HostTables::beta_weights(const double* beta) const {
   return w;
 }
 
+std::vector<double> HostTables::term_coef(const double* beta) const {
+  const std::vector<double> bw = beta_weights(beta);
+  std::vector<double> c(terms.size());
+  for (size_t k = 0; k < terms.size(); ++k) c[k] = term_cg[k] * bw[term_trip[k]];
+  return c;
+}
+
 std::vector<int> HostTables::slices(int nslices) const {
-  // contiguous runs of work items, cut only between output elements, with
-  // about equal total cost
-  long total = 0;
-  for (int c : cost) total += c;
-  std::vector<int> b;
-  b.push_back(0);
-  long acc = 0;
+  // nslices contiguous runs of output elements with about equal term counts;
+  // entry k is the first output of run k (entry nslices = H)
+  const long total = (long)terms.size();
+  std::vector<int> b(1, 0);
   int k = 1;
-  const int n = (int)jobs.size();
-  for (int q = 0; q < n; ++q) {
-    acc += cost[q];
-    const bool boundary = (q + 1 == n) || ((jobs[q + 1].w >> 16) != (jobs[q].w >> 16));
-    if (boundary && k < nslices && acc * nslices >= total * k) {
-      b.push_back(q + 1);
+  for (int o = 0; o < H; ++o) {
+    const long done = term_out_first[o + 1];
+    if (k < nslices && done * nslices >= total * k) {
+      b.push_back(o + 1);
       ++k;
     }
   }
-  while ((int)b.size() < nslices + 1) b.push_back(n);
-  b[nslices] = n;
+  while ((int)b.size() < nslices + 1) b.push_back(H);
+  b[nslices] = H;
   return b;
 }
 

@@ -9,7 +9,6 @@ namespace snap {
 struct ZTrip {
   int t1, t2, t;  // Y triple: Z^t_{t1 t2} with t1 >= t2
   int cg_off;     // offset of its cg[x1][x2] block
-  int cgpad_off;  // offset of its padded block in cgpad
   int bidx;       // canonical bispectrum component it belongs to
   double fac;     // multiplicity / rank factor of the derivative
 };
@@ -19,13 +18,16 @@ struct HostTables {
   std::vector<int> half_tmm;
   std::vector<ZTrip> ztrip;
   std::vector<double> cg;
-  std::vector<double> cgpad;
-  std::vector<YJob> jobs;
-  std::vector<int> cost;
+  // compute_Y terms: packed indices/flags, CG product with signs, triple
+  std::vector<unsigned> terms;
+  std::vector<double> term_cg;
+  std::vector<int> term_trip;
+  std::vector<int> term_out_first;  // [H+1] first term of every output
   std::vector<double> rootpq;
 
   void build(int twojmax);
   std::vector<double> beta_weights(const double* beta) const;
+  std::vector<double> term_coef(const double* beta) const;
   std::vector<int> slices(int nslices) const;
 };
 
