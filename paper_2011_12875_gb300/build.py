@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsnap_gb300.so")
-SOURCES = ["snap_api.cu", "snap_neigh.cu", "snap_kernels.cu", "snap_tables.cpp", "snap_noalloc.cu"]
+SOURCES = ["snap_api.cu", "snap_neigh.cu", "snap_kernels.cu", "snap_tables.cpp", "snap_noalloc.cu",
+           "snap_col_f32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

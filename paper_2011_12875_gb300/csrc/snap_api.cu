@@ -293,11 +293,14 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   SNAP_CUDA(c, mark());
   SNAP_CUDA(c, mixed ? snap::launch_geom<float>(a, s) : snap::launch_geom<double>(a, s));
   SNAP_CUDA(c, mark());
-  SNAP_CUDA(c, mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s));
+  const bool colk = mixed && c->twojmax >= 1;  // register column-chain kernels
+  SNAP_CUDA(c, colk ? snap::launch_ui_col<float>(a, s)
+                    : (mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s)));
   SNAP_CUDA(c, mark());
   SNAP_CUDA(c, mixed ? snap::launch_yi<float>(a, s) : snap::launch_yi<double>(a, s));
   SNAP_CUDA(c, mark());
-  SNAP_CUDA(c, mixed ? snap::launch_de<float>(a, s) : snap::launch_de<double>(a, s));
+  SNAP_CUDA(c, colk ? snap::launch_de_col<float>(a, s)
+                    : (mixed ? snap::launch_de<float>(a, s) : snap::launch_de<double>(a, s)));
   SNAP_CUDA(c, mark());
   SNAP_CUDA(c, mixed ? snap::launch_force<float>(a, s) : snap::launch_force<double>(a, s));
   SNAP_CUDA(c, mark());

@@ -1,0 +1,31 @@
+// snap_col_f32.cu -- register column-chain compute_U and fused dE kernels,
+// FP32 working precision (mixed mode), one instance per 2J.
+#include "snap_colkernels.cuh"
+
+namespace snap {
+
+template <>
+cudaError_t launch_ui_col<float>(const WorkArgs& a, cudaStream_t s) {
+  switch (a.twojmax) {
+#define SNAP_CASE(J) \
+  case J: return col::launch_ui_col_t<float, J>(a, s);
+    SNAP_CASE(1) SNAP_CASE(2) SNAP_CASE(3) SNAP_CASE(4) SNAP_CASE(5) SNAP_CASE(6) SNAP_CASE(7)
+    SNAP_CASE(8) SNAP_CASE(9) SNAP_CASE(10) SNAP_CASE(11) SNAP_CASE(12) SNAP_CASE(13) SNAP_CASE(14)
+#undef SNAP_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_de_col<float>(const WorkArgs& a, cudaStream_t s) {
+  switch (a.twojmax) {
+#define SNAP_CASE(J) \
+  case J: return col::launch_de_col_t<float, J>(a, s);
+    SNAP_CASE(1) SNAP_CASE(2) SNAP_CASE(3) SNAP_CASE(4) SNAP_CASE(5) SNAP_CASE(6) SNAP_CASE(7)
+    SNAP_CASE(8) SNAP_CASE(9) SNAP_CASE(10) SNAP_CASE(11) SNAP_CASE(12) SNAP_CASE(13) SNAP_CASE(14)
+#undef SNAP_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace snap

@@ -1,0 +1,373 @@
+// snap_colkernels.cuh -- compute_U and the fused dU + dE/dr kernel with the
+// layer recursion held in registers, one lane per half-matrix column.
+//
+// Eq. (hysphrecur) of arXiv:2011.12875 builds u_t from u_{t-1}; element
+// (ma, mb) only reads elements (ma, mb) and (ma-1, mb) of the previous layer,
+// so every column mb evolves on its own:
+//   u_t[ma][mb] = sqrt((t-ma)/(t-mb)) conj(a) u_{t-1}[ma][mb]
+//               - sqrt(ma/(t-mb))     conj(b) u_{t-1}[ma-1][mb].
+// Column mb enters the stored half at layer t = 2 mb, from column mb of layer
+// t-1, which is the mirror of column mb-1 of that layer:
+//   u_{t-1}[m][mb] = (-1)^(m+mb) conj(u_{t-1}[t-1-m][mb-1]).
+// Here one lane carries one column of one neighbour pair through all layers
+// (twojmax/2 + 1 lanes per pair, several pairs per warp); the layer loop is
+// unrolled at compile time, so the column lives in registers and the seed is
+// one warp shuffle per element.  This file is included by one translation
+// unit per working precision.
+#pragma once
+#include <type_traits>
+
+#include "snap_internal.h"
+
+namespace snap {
+namespace col {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename R>
+struct c2 {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ c2<R> mk(R re, R im) {
+  c2<R> c;
+  c.re = re;
+  c.im = im;
+  return c;
+}
+
+// sqrt(k) for the small integers of the recursion, folded at compile time.
+template <typename R>
+__device__ __forceinline__ constexpr R sqrt_int(int k) {
+  return k == 0   ? R(0)
+         : k == 1 ? R(1)
+         : k == 2 ? R(1.4142135623730950488)
+         : k == 3 ? R(1.7320508075688772935)
+         : k == 4 ? R(2)
+         : k == 5 ? R(2.2360679774997896964)
+         : k == 6 ? R(2.4494897427831780982)
+         : k == 7 ? R(2.6457513110645905905)
+         : k == 8 ? R(2.8284271247461900976)
+         : k == 9 ? R(3)
+         : k == 10 ? R(3.1622776601683793320)
+         : k == 11 ? R(3.3166247903553998491)
+         : k == 12 ? R(3.4641016151377545871)
+         : k == 13 ? R(3.6055512754639892931)
+         : k == 14 ? R(3.7416573867739413856)
+                   : R(3.8729833462074168852);
+}
+
+// Compile-time loop B..E (inclusive): f(std::integral_constant<int, k>).
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B <= E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R shfl_up(R v) {
+  return __shfl_up_sync(kFull, v, 1);
+}
+
+// Weight of a half-layout element in a full-matrix contraction (see
+// snap_kernels.cu): 2 below the middle column, on it 2 / 1 / 0.
+__device__ __forceinline__ int hweight(int t, int ma, int mb) {
+  if (2 * mb < t) return 2;
+  return ma < mb ? 2 : (ma == mb ? 1 : 0);
+}
+
+// Lane layout: NC = J2/2 + 1 lanes per pair, P pairs per warp.
+template <int J2>
+struct Shape {
+  static constexpr int NC = J2 / 2 + 1;
+  static constexpr int P = 32 / NC;
+};
+
+// Replace column mc = t/2 (on the lane with mb == mc) by the mirror of the
+// column held one lane below, for layer t-1 (length t).
+template <typename R, int T, int N>
+__device__ __forceinline__ void seed_column(c2<R> (&v)[N], bool take) {
+  constexpr int mc = T / 2;
+  c2<R> src[T];
+#pragma unroll
+  for (int k = 0; k < T; ++k) {
+    src[k].re = shfl_up(v[k].re);
+    src[k].im = shfl_up(v[k].im);
+  }
+  if (take) {
+#pragma unroll
+    for (int m = 0; m < T; ++m) {
+      const R s = (((T - 1 - m) + (mc - 1)) & 1) ? R(-1) : R(1);
+      v[m] = mk<R>(s * src[T - 1 - m].re, -s * src[T - 1 - m].im);
+    }
+  }
+}
+
+// ------------------------------------------------------------- compute_U
+// CTA = one atom, NW warps; each warp takes P pairs at a time.  Each pair
+// group sums f_c u_t into its own shared-memory copy of Ulisttot (no two
+// lanes write one address), and the copies are added in a fixed order.
+template <typename R, int J2, int NW>
+__global__ void __launch_bounds__(NW * 32) ui_col_kernel(WorkArgs a) {
+  using S = Shape<J2>;
+  constexpr int NC = S::NC, P = S::P;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int H = a.H;
+  c2<R>* acc = reinterpret_cast<c2<R>*>(smem);  // [NW*P][H]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / NC, mb = lane - g * NC;
+  const bool grp = g < P;
+  const int i = blockIdx.x;
+  for (int e = threadIdx.x; e < NW * P * H; e += blockDim.x) acc[e] = mk<R>(0, 0);
+  __syncthreads();
+  c2<R>* my = acc + (warp * P + (grp ? g : 0)) * H;
+  R rs[J2 + 1];
+#pragma unroll
+  for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
+  const int cnt = a.cnt[i];
+  for (int s0 = warp * P; s0 < cnt; s0 += NW * P) {
+    const int s = s0 + g;
+    const bool ok = grp && s < cnt;
+    c2<R> ca = mk<R>(1, 0), cb = mk<R>(0, 0);
+    R fc = 0;
+    if (ok) {
+      const R* gm = reinterpret_cast<const R*>(a.geom) + ((long)i * a.K + s) * kGeomStride;
+      ca = mk<R>(gm[0], -gm[1]);  // conj(a)
+      cb = mk<R>(gm[2], -gm[3]);  // conj(b)
+      fc = gm[4];
+    }
+    c2<R> u[J2 + 1];
+#pragma unroll
+    for (int k = 0; k <= J2; ++k) u[k] = mk<R>(0, 0);
+    if (mb == 0) u[0] = mk<R>(1, 0);
+    if (ok && mb == 0) my[0].re += fc;
+    static_for<1, J2>([&](auto tc) {
+      constexpr int t = decltype(tc)::value;
+      if constexpr ((t & 1) == 0) seed_column<R, t>(u, mb == t / 2);
+      const R r = rs[t];
+      const c2<R> A = mk<R>(r * ca.re, r * ca.im), B = mk<R>(r * cb.re, r * cb.im);
+      // in place, ma descending: u[ma] <- sqrt(t-ma) A u[ma] - sqrt(ma) B u[ma-1]
+#pragma unroll
+      for (int ma = t; ma >= 0; --ma) {
+        c2<R> v = mk<R>(0, 0);
+        if (ma < t) {
+          const R c = sqrt_int<R>(t - ma);
+          v.re = c * (A.re * u[ma].re - A.im * u[ma].im);
+          v.im = c * (A.re * u[ma].im + A.im * u[ma].re);
+        }
+        if (ma > 0) {
+          const R c = sqrt_int<R>(ma);
+          v.re -= c * (B.re * u[ma - 1].re - B.im * u[ma - 1].im);
+          v.im -= c * (B.re * u[ma - 1].im + B.im * u[ma - 1].re);
+        }
+        u[ma] = v;
+      }
+      if (ok && 2 * mb <= t) {
+        c2<R>* dst = my + half_base(t) + mb * (t + 1);
+#pragma unroll
+        for (int ma = 0; ma <= t; ++ma) {
+          dst[ma].re += fc * u[ma].re;
+          dst[ma].im += fc * u[ma].im;
+        }
+      }
+    });
+  }
+  __syncthreads();
+  R* Ure = reinterpret_cast<R*>(a.Ure);
+  R* Uim = reinterpret_cast<R*>(a.Uim);
+  const long blk = i >> 5;
+  const int li = i & 31;
+  for (int e = threadIdx.x; e < H; e += blockDim.x) {
+    R sr = 0, si = 0;
+    for (int c = 0; c < NW * P; ++c) {
+      sr += acc[c * H + e].re;
+      si += acc[c * H + e].im;
+    }
+    const int p = a.half_tmm[e];
+    if (tmm_ma(p) == tmm_mb(p)) sr += (R)a.wself;
+    Ure[(blk * H + e) * 32 + li] = sr;
+    Uim[(blk * H + e) * 32 + li] = si;
+  }
+}
+
+// ------------------------------------------------------ fused dU + dE/dr
+// CTA = one atom with its weighted Y_i in shared memory; each lane carries
+// column mb of u and of du/dr_x, du/dr_y, du/dr_z (the recursion
+// differentiated, Sec. V-A) and accumulates Re(conj(Y) u), Re(conj(Y) du_d)
+// over its column; the pair's lanes are summed in shared memory and
+//   dE_i/dr_ik,d = (df_c/dr_d) S + f_c D_d      (Eq. snapforce2).
+template <typename R, int J2, int NW>
+__global__ void __launch_bounds__(NW * 32) de_col_kernel(WorkArgs a) {
+  using S_ = Shape<J2>;
+  constexpr int NC = S_::NC, P = S_::P;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int H = a.H;
+  c2<R>* Yw = reinterpret_cast<c2<R>*>(smem);                 // [H]
+  R* red = reinterpret_cast<R*>(Yw + H);                       // [NW][32][4]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / NC, mb = lane - g * NC;
+  const bool grp = g < P;
+  const int i = blockIdx.x;
+  {
+    const R* Yre = reinterpret_cast<const R*>(a.Yre);
+    const R* Yim = reinterpret_cast<const R*>(a.Yim);
+    const long blk = i >> 5;
+    const int li = i & 31;
+    for (int e = threadIdx.x; e < H; e += blockDim.x) {
+      const int p = a.half_tmm[e];
+      const R w = (R)hweight(tmm_t(p), tmm_ma(p), tmm_mb(p));
+      Yw[e] = mk<R>(w * Yre[(blk * H + e) * 32 + li], w * Yim[(blk * H + e) * 32 + li]);
+    }
+  }
+  __syncthreads();
+  R rs[J2 + 1];
+#pragma unroll
+  for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
+  R* myred = red + (warp * 32 + lane) * 4;
+  const int cnt = a.cnt[i];
+  for (int s0 = warp * P; s0 < cnt; s0 += NW * P) {
+    const int s = s0 + g;
+    const bool ok = grp && s < cnt;
+    const long slot = (long)i * a.K + (ok ? s : 0);
+    const R* gm = reinterpret_cast<const R*>(a.geom) + slot * kGeomStride;
+    c2<R> ca = mk<R>(1, 0), cb = mk<R>(0, 0);  // conj(a), conj(b)
+    c2<R> cda[3], cdb[3];                      // conj(da/dr_d), conj(db/dr_d)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) cda[d] = cdb[d] = mk<R>(0, 0);
+    if (ok) {
+      ca = mk<R>(gm[0], -gm[1]);
+      cb = mk<R>(gm[2], -gm[3]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        cda[d] = mk<R>(gm[8 + 2 * d], -gm[9 + 2 * d]);
+        cdb[d] = mk<R>(gm[14 + 2 * d], -gm[15 + 2 * d]);
+      }
+    }
+    c2<R> u[J2 + 1], du[3][J2 + 1];
+#pragma unroll
+    for (int k = 0; k <= J2; ++k) {
+      u[k] = mk<R>(0, 0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) du[d][k] = mk<R>(0, 0);
+    }
+    R Ssum = 0, D[3] = {0, 0, 0};
+    if (mb == 0) {
+      u[0] = mk<R>(1, 0);
+      Ssum = Yw[0].re;
+    }
+    static_for<1, J2>([&](auto tc) {
+      constexpr int t = decltype(tc)::value;
+      if constexpr ((t & 1) == 0) {
+        const bool take = mb == t / 2;
+        seed_column<R, t>(u, take);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) seed_column<R, t>(du[d], take);
+      }
+      const R r = rs[t];
+      const c2<R> A = mk<R>(r * ca.re, r * ca.im), B = mk<R>(r * cb.re, r * cb.im);
+      c2<R> dA[3], dB[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        dA[d] = mk<R>(r * cda[d].re, r * cda[d].im);
+        dB[d] = mk<R>(r * cdb[d].re, r * cdb[d].im);
+      }
+      const bool act = 2 * mb <= t;
+      const c2<R>* yrow = Yw + half_base(t) + (act ? mb * (t + 1) : 0);
+#pragma unroll
+      for (int ma = t; ma >= 0; --ma) {
+        c2<R> v = mk<R>(0, 0), dv[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) dv[d] = mk<R>(0, 0);
+        if (ma < t) {
+          const R c = sqrt_int<R>(t - ma);
+          const c2<R> Ac = mk<R>(c * A.re, c * A.im);
+          const c2<R> p = u[ma];
+          v.re = Ac.re * p.re - Ac.im * p.im;
+          v.im = Ac.re * p.im + Ac.im * p.re;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const c2<R> q = du[d][ma];
+            const R dr = c * dA[d].re, di = c * dA[d].im;
+            dv[d].re = dr * p.re - di * p.im + Ac.re * q.re - Ac.im * q.im;
+            dv[d].im = dr * p.im + di * p.re + Ac.re * q.im + Ac.im * q.re;
+          }
+        }
+        if (ma > 0) {
+          const R c = sqrt_int<R>(ma);
+          const c2<R> Bc = mk<R>(c * B.re, c * B.im);
+          const c2<R> p = u[ma - 1];
+          v.re -= Bc.re * p.re - Bc.im * p.im;
+          v.im -= Bc.re * p.im + Bc.im * p.re;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const c2<R> q = du[d][ma - 1];
+            const R dr = c * dB[d].re, di = c * dB[d].im;
+            dv[d].re -= dr * p.re - di * p.im + Bc.re * q.re - Bc.im * q.im;
+            dv[d].im -= dr * p.im + di * p.re + Bc.re * q.im + Bc.im * q.re;
+          }
+        }
+        u[ma] = v;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) du[d][ma] = dv[d];
+        if (act) {
+          const c2<R> y = yrow[ma];
+          Ssum += y.re * v.re + y.im * v.im;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) D[d] += y.re * dv[d].re + y.im * dv[d].im;
+        }
+      }
+    });
+    myred[0] = Ssum;
+    myred[1] = D[0];
+    myred[2] = D[1];
+    myred[3] = D[2];
+    __syncwarp();
+    if (ok && mb == 0) {
+      R t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+      for (int c = 0; c < NC; ++c) {
+        const R* q = red + (warp * 32 + lane + c) * 4;
+        t0 += q[0];
+        t1 += q[1];
+        t2 += q[2];
+        t3 += q[3];
+      }
+      const R fc = gm[4];
+      a.dedr[slot * 3 + 0] = (double)(gm[5] * t0 + fc * t1);
+      a.dedr[slot * 3 + 1] = (double)(gm[6] * t0 + fc * t2);
+      a.dedr[slot * 3 + 2] = (double)(gm[7] * t0 + fc * t3);
+    }
+    __syncwarp();
+  }
+}
+
+template <typename K>
+inline cudaError_t col_allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+constexpr int kColWarps = 4;
+
+template <typename R, int J2>
+cudaError_t launch_ui_col_t(const WorkArgs& a, cudaStream_t s) {
+  const size_t sm = sizeof(c2<R>) * (size_t)kColWarps * Shape<J2>::P * a.H;
+  cudaError_t e = col_allow_smem(ui_col_kernel<R, J2, kColWarps>, sm);
+  if (e != cudaSuccess) return e;
+  ui_col_kernel<R, J2, kColWarps><<<a.n, kColWarps * 32, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, int J2>
+cudaError_t launch_de_col_t(const WorkArgs& a, cudaStream_t s) {
+  const size_t sm = sizeof(c2<R>) * (size_t)a.H + sizeof(R) * kColWarps * 32 * 4;
+  cudaError_t e = col_allow_smem(de_col_kernel<R, J2, kColWarps>, sm);
+  if (e != cudaSuccess) return e;
+  de_col_kernel<R, J2, kColWarps><<<a.n, kColWarps * 32, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace col
+}  // namespace snap

@@ -104,4 +104,9 @@ template <typename R> cudaError_t launch_de(const WorkArgs& a, cudaStream_t s);
 template <typename R> cudaError_t launch_force(const WorkArgs& a, cudaStream_t s);
 int force_blocks(int n);
 
+// Register column-chain kernels (snap_col_*.cu), for 1 <= twojmax <= 14;
+// cudaErrorInvalidValue when no instance exists for the precision/2J.
+template <typename R> cudaError_t launch_ui_col(const WorkArgs& a, cudaStream_t s);
+template <typename R> cudaError_t launch_de_col(const WorkArgs& a, cudaStream_t s);
+
 }  // namespace snap

@@ -229,7 +229,7 @@ __device__ __forceinline__ void y_term(unsigned w, R c, const R* __restrict__ ur
 }
 
 template <typename R, bool STAGED>
-__global__ void __launch_bounds__(512) yi_kernel(WorkArgs a) {
+__global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long blk = blockIdx.x;
@@ -563,7 +563,7 @@ YiGeometry yi_geometry(int rsize, int H, int n, int nsm) {
   const size_t stage = (size_t)2 * H * 32 * rsize + 16;
   g.staged = stage <= 200 * 1024;
   g.smem = g.staged ? stage : 0;
-  g.threads = (g.smem > 100 * 1024) ? 512 : 256;
+  g.threads = (g.smem > 100 * 1024) ? 1024 : 256;
   int cps = 2048 / g.threads;
   if (g.staged) cps = std::max(1, std::min(cps, (int)((227 * 1024) / g.smem)));
   const int target = nsm * cps * 2;

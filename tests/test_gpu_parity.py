@@ -85,6 +85,13 @@ def test_fp64_2j14(snapmod):
     full_check(snapmod, 14, inputs.bcc(2, disp=0.1, seed=4), snapmod.FP64)
 
 
+@pytest.mark.parametrize("twojmax", list(range(0, 15)))
+def test_mixed_precision_all_orders(snapmod, twojmax):
+    """Mixed path at every 2J (each 2J has its own register-resident kernel
+    instance), 16 atoms in a box smaller than 2 rcut."""
+    full_check(snapmod, twojmax, inputs.bcc(2, disp=0.15, seed=3), snapmod.MIXED)
+
+
 @pytest.mark.parametrize("twojmax", [2, 8, 14])
 def test_mixed_precision(snapmod, twojmax):
     cfg = inputs.bcc(3 if twojmax < 14 else 2, disp=0.1, seed=5)
