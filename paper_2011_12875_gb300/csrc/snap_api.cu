@@ -162,7 +162,7 @@ int ensure_workspace(snap_ctx* c, int n, int K) {
   // lanes past the last atom read zeros in compute_Y
   SNAP_CUDA(c, cudaMemset(c->d_Ure, 0, uy));
   SNAP_CUDA(c, cudaMemset(c->d_Uim, 0, uy));
-  SNAP_CUDA(c, cudaMalloc(&c->d_vpart, sizeof(double) * 6 * (snap::force_blocks(ncap) + 1)));
+  SNAP_CUDA(c, cudaMalloc(&c->d_vpart, sizeof(double) * 6 * (4 * nblk + 1)));
   c->cap_n = ncap;
   c->cap_nk = nkcap;
   return SNAP_OK;
@@ -195,12 +195,12 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   int rc = ensure_workspace(c, n, K);
   if (rc) return rc;
   if (!c->d_flags) {
-    SNAP_CUDA(c, cudaMalloc(&c->d_flags, 4 * sizeof(int)));
-    SNAP_CUDA(c, cudaMallocHost(&c->h_flags, 4 * sizeof(int)));
+    SNAP_CUDA(c, cudaMalloc(&c->d_flags, 8 * sizeof(int)));
+    SNAP_CUDA(c, cudaMallocHost(&c->h_flags, 8 * sizeof(int)));
   }
   rc = ensure_slices(c, n);
   if (rc) return rc;
-  SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), s));
+  SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 8 * sizeof(int), s));
   std::vector<cudaEvent_t> ev;
   if (c->prof_on) {
     if (!c->prof_free.empty()) {
@@ -260,6 +260,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   a.rcut = c->rcut;
   a.rfac0 = c->rfac0;
   a.rmin0 = c->rmin0;
+  a.inv_span = 1.0 / (c->rcut - c->rmin0);
   a.wself = c->wself;
   a.beta0 = c->beta[0];
   a.switchflag = c->switchflag;
@@ -289,9 +290,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   a.rootpq = c->d_root;
 
   const bool mixed = c->precision == SNAP_MIXED;
-  SNAP_CUDA(c, snap::launch_rev(a, c->d_rev, s));
-  SNAP_CUDA(c, mark());
-  SNAP_CUDA(c, mixed ? snap::launch_geom<float>(a, s) : snap::launch_geom<double>(a, s));
+  SNAP_CUDA(c, mixed ? snap::launch_pairs<float>(a, c->d_rev, s) : snap::launch_pairs<double>(a, c->d_rev, s));
   SNAP_CUDA(c, mark());
   const bool colk = mixed && c->twojmax >= 1;  // register column-chain kernels
   SNAP_CUDA(c, colk ? snap::launch_ui_col<float>(a, s)
@@ -304,7 +303,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   SNAP_CUDA(c, mark());
   SNAP_CUDA(c, mixed ? snap::launch_force<float>(a, s) : snap::launch_force<double>(a, s));
   SNAP_CUDA(c, mark());
-  c->launches += 6 + (virial ? 1 : 0);
+  c->launches += 5;
   if (!ev.empty()) c->prof_pending.push_back(ev);
   SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   c->last_n = n;
@@ -498,9 +497,8 @@ int snap_profile_read(snap_ctx* c, double* ms, long long* calls, int nstages) {
 }
 
 const char* snap_stage_name(int stage) {
-  static const char* names[SNAP_NSTAGES] = {"neighbor_build", "reverse_map", "ck_geometry",
-                                            "compute_ui", "compute_yi", "fused_dE",
-                                            "force_virial"};
+  static const char* names[SNAP_NSTAGES] = {"neighbor_build", "pair_geometry", "compute_ui",
+                                            "compute_yi", "fused_dE", "energy_force_virial"};
   return (stage >= 0 && stage < SNAP_NSTAGES) ? names[stage] : "";
 }
 

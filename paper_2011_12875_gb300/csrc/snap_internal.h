@@ -50,6 +50,7 @@ struct NeighArgs {
 struct WorkArgs {
   int n, K, twojmax, H, lmax;
   double rcut, rfac0, rmin0, wself, beta0;
+  double inv_span;  // 1 / (rcut - rmin0)
   int switchflag;
   const int* cnt;
   const int* nbr;
@@ -84,8 +85,8 @@ cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, doub
                                 double Lz, const int* ucnt, const int* uidx,
                                 const signed char* uimg, int ucap, int* cnt, int* nbr,
                                 signed char* img, double* rij, int* flags, cudaStream_t s);
-cudaError_t launch_rev(const WorkArgs& a, int* rev, cudaStream_t s);
-template <typename G> cudaError_t launch_geom(const WorkArgs& a, cudaStream_t s);
+// reverse-slot map + geometry in the working precision G (one kernel)
+template <typename G> cudaError_t launch_pairs(const WorkArgs& a, int* rev, cudaStream_t s);
 
 // Launchers (snap_kernels.cu), R = float (mixed) or double (FP64)
 template <typename R> cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s);
@@ -102,7 +103,6 @@ struct YiGeometry {
 YiGeometry yi_geometry(int rsize, int H, int n, int nsm);
 template <typename R> cudaError_t launch_de(const WorkArgs& a, cudaStream_t s);
 template <typename R> cudaError_t launch_force(const WorkArgs& a, cudaStream_t s);
-int force_blocks(int n);
 
 // Register column-chain kernels (snap_col_*.cu), for 1 <= twojmax <= 14;
 // cudaErrorInvalidValue when no instance exists for the precision/2J.

@@ -442,39 +442,49 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
 }
 
 // --------------------------------------------- energy, forces and virial
-// One warp per atom.  E_i - beta_0 is a cubic form in U, so by Euler's
+// One CTA per 32-atom block (lanes = atoms for the energy, so the U and Y
+// reads are coalesced).  E_i - beta_0 is a cubic form in U, so by Euler's
 // relation E_i = beta_0 + (1/3) Re sum_t Y_t : conj(U_t) (full matrices; half
-// layout with half_weight).  F_i = sum_k dE_i/dr_ik - sum_k dE_k/dr_ki, the
-// second term gathered through the reverse-slot map (no atomics).  The
-// virial W_ab = -sum dE_i/dr_ik,a r_ik,b is reduced per CTA into vpart.
-constexpr int kForceWarps = 4;
+// layout with half_weight), accumulated in FP64.  Forces: one warp per atom,
+// lanes over slots, F_i = sum_k dE_i/dr_ik - sum_k dE_k/dr_ki with the second
+// term gathered through the reverse-slot map (no atomics).  The virial
+// W_ab = -sum dE_i/dr_ik,a r_ik,b is reduced per CTA; the last CTA to finish
+// adds the CTA partials in a fixed order.
+constexpr int kForceWarps = 8;
 
 template <typename R>
 __global__ void __launch_bounds__(kForceWarps * 32) force_kernel(WorkArgs a) {
+  __shared__ double ep[kForceWarps][32];
   __shared__ double vs[kForceWarps][6];
+  __shared__ bool last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kForceWarps + warp;
-  double v[6] = {0, 0, 0, 0, 0, 0};
-  if (i < a.n) {
-    const int H = a.H;
-    const R* Ure = reinterpret_cast<const R*>(a.Ure);
-    const R* Uim = reinterpret_cast<const R*>(a.Uim);
-    const R* Yre = reinterpret_cast<const R*>(a.Yre);
-    const R* Yim = reinterpret_cast<const R*>(a.Yim);
-    const long blk = i >> 5;
-    const int li = i & 31;
-    double e = 0.0;
-    for (int el = lane; el < H; el += 32) {
+  const long blk = blockIdx.x;
+  const int part = blockIdx.y;  // quarter of the block's atoms for the forces
+  const int H = a.H;
+  if (part == 0) {
+    // per-warp partial over every 8th element in the working precision,
+    // combined over warps in FP64
+    const R* Ure = reinterpret_cast<const R*>(a.Ure) + blk * H * 32;
+    const R* Uim = reinterpret_cast<const R*>(a.Uim) + blk * H * 32;
+    const R* Yre = reinterpret_cast<const R*>(a.Yre) + blk * H * 32;
+    const R* Yim = reinterpret_cast<const R*>(a.Yim) + blk * H * 32;
+    R e = R(0);
+    for (int el = warp; el < H; el += kForceWarps) {
       const int p = a.half_tmm[el];
-      const int w = half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
-      const long idx = (blk * H + el) * 32 + li;
-      e += (double)w * ((double)Yre[idx] * (double)Ure[idx] + (double)Yim[idx] * (double)Uim[idx]);
+      const R w = (R)half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
+      const int idx = el * 32 + lane;
+      e += w * (Yre[idx] * Ure[idx] + Yim[idx] * Uim[idx]);
     }
-    e = warp_sum(e);
+    ep[warp][lane] = (double)e;
+  }
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  for (int aa = part * kForceWarps + warp; aa < (part + 1) * kForceWarps; aa += kForceWarps) {
+    const long i = blk * 32 + aa;
+    if (i >= a.n) break;
     double f[3] = {0, 0, 0};
     const int cnt = a.cnt[i];
     for (int s = lane; s < cnt; s += 32) {
-      const long q = (long)i * a.K + s;
+      const long q = i * a.K + s;
       const int k = a.nbr[q];
       const int r = a.rev[q];
       const double* d = a.dedr + q * 3;
@@ -492,36 +502,37 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_kernel(WorkArgs a) {
       v[5] -= d[1] * rv[2];
     }
     for (int c = 0; c < 3; ++c) f[c] = warp_sum(f[c]);
-    if (lane == 0) {
-      if (a.energy) a.energy[i] = a.beta0 + e / 3.0;
-      for (int c = 0; c < 3; ++c) a.forces[3 * (long)i + c] = f[c];
-    }
+    if (lane == 0)
+      for (int c = 0; c < 3; ++c) a.forces[3 * i + c] = f[c];
   }
   for (int c = 0; c < 6; ++c) v[c] = warp_sum(v[c]);
   if (lane == 0)
     for (int c = 0; c < 6; ++c) vs[warp][c] = v[c];
   __syncthreads();
+  if (part == 0 && warp == 0) {
+    const long i = blk * 32 + lane;
+    double e = 0.0;
+    for (int w = 0; w < kForceWarps; ++w) e += ep[w][lane];
+    if (a.energy && i < a.n) a.energy[i] = a.beta0 + e / 3.0;
+  }
+  if (!a.virial) return;
+  const int cta = blockIdx.x * gridDim.y + part;
+  const int ncta = gridDim.x * gridDim.y;
   if (threadIdx.x < 6) {
     double t = 0.0;
     for (int w = 0; w < kForceWarps; ++w) t += vs[w][threadIdx.x];
-    a.vpart[6 * (long)blockIdx.x + threadIdx.x] = t;
+    a.vpart[6 * cta + threadIdx.x] = t;
+    __threadfence();
   }
-}
-
-// Fixed-order sum of the per-CTA virial partials (deterministic).
-__global__ void virial_reduce_kernel(const double* __restrict__ vpart, int nb, double* virial) {
-  __shared__ double red[256];
-  for (int c = 0; c < 6; ++c) {
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&a.flags[4], 1) == ncta - 1);
+  __syncthreads();
+  if (last && threadIdx.x < 6) {
+    __threadfence();
+    const volatile double* vp = a.vpart;
     double t = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += vpart[6 * (long)b + c];
-    red[threadIdx.x] = t;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) virial[c] = red[0];
-    __syncthreads();
+    for (int b = 0; b < ncta; ++b) t += vp[6 * b + threadIdx.x];
+    a.virial[threadIdx.x] = t;
   }
 }
 
@@ -545,7 +556,6 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 
 }  // namespace
 
-int force_blocks(int n) { return (n + kForceWarps - 1) / kForceWarps; }
 
 template <typename R>
 cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s) {
@@ -602,11 +612,7 @@ cudaError_t launch_de(const WorkArgs& a, cudaStream_t s) {
 template <typename R>
 cudaError_t launch_force(const WorkArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const int nb = force_blocks(a.n);
-  force_kernel<R><<<nb, kForceWarps * 32, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !a.virial) return e;
-  virial_reduce_kernel<<<1, 256, 0, s>>>(a.vpart, nb, a.virial);
+  force_kernel<R><<<dim3((a.n + 31) / 32, 32 / kForceWarps), kForceWarps * 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -82,6 +82,7 @@ __device__ __forceinline__ void exact_batch(const NeighArgs& a, int i, double xi
   count += __popc(m);
 }
 
+template <bool NEAREST>
 __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a) {
   __shared__ float4 tile[kNbTile];
   __shared__ int cand_j[kNbWarps][kCandCap];
@@ -119,14 +120,57 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
       const bool valid = (jj + lane) < jn;
       const float4 pj = tile[jj + lane];
       const float dx0 = pj.x - pi4.x, dy0 = pj.y - pi4.y, dz0 = pj.z - pi4.z;
-      const int nx = -(int)rintf(dx0 * iLx), ny = -(int)rintf(dy0 * iLy), nz = -(int)rintf(dz0 * iLz);
-      for (int sx = -a.Sx; sx <= a.Sx; ++sx)
-        for (int sy = -a.Sy; sy <= a.Sy; ++sy)
-          for (int sz = -a.Sz; sz <= a.Sz; ++sz) {
-            const int ix = nx + sx, iy = ny + sy, iz = nz + sz;
-            const float fx = dx0 + (float)ix * Lx, fy = dy0 + (float)iy * Ly, fz = dz0 + (float)iz * Lz;
-            const bool self = (j == i) && ix == 0 && iy == 0 && iz == 0;
-            const bool c = valid && !self && (fx * fx + fy * fy + fz * fz < rc2f);
+      // nearest-image shift counts, kept in float (int <-> float conversions
+      // run on a slow pipe and are only done for the rare candidates)
+      const float nxf = -rintf(dx0 * iLx), nyf = -rintf(dy0 * iLy), nzf = -rintf(dz0 * iLz);
+      const float bx = dx0 + nxf * Lx, by = dy0 + nyf * Ly, bz = dz0 + nzf * Lz;
+      if (NEAREST) {
+        // box > 2 (rcut + margin) in every direction: only the nearest image
+        bool c = valid && (bx * bx + by * by + bz * bz < rc2f) && (j != i);
+        const unsigned m = __ballot_sync(kFull, c);
+        if (m) {
+          if (c) {
+            const int pos = ncand + __popc(m & lt);
+            cj[pos] = j;
+            cs[pos] = pack_img((int)nxf, (int)nyf, (int)nzf);
+          }
+          ncand += __popc(m);
+          if (ncand >= 32) {
+            __syncwarp();
+            exact_batch(a, i, xi, yi, zi, rc2, cj, cs, 32, lane, count);
+            __syncwarp();
+            const int rest = ncand - 32;
+            int mj = 0, ms = 0;
+            if (lane < rest) {
+              mj = cj[32 + lane];
+              ms = cs[32 + lane];
+            }
+            __syncwarp();
+            if (lane < rest) {
+              cj[lane] = mj;
+              cs[lane] = ms;
+            }
+            ncand = rest;
+            __syncwarp();
+          }
+        }
+        continue;
+      }
+      float sxf = -(float)a.Sx;
+      for (int sx = -a.Sx; sx <= a.Sx; ++sx, sxf += 1.f) {
+        float syf = -(float)a.Sy;
+        for (int sy = -a.Sy; sy <= a.Sy; ++sy, syf += 1.f) {
+          float szf = -(float)a.Sz;
+          for (int sz = -a.Sz; sz <= a.Sz; ++sz, szf += 1.f) {
+            const float fx = bx + sxf * Lx, fy = by + syf * Ly, fz = bz + szf * Lz;
+            bool c = valid && (fx * fx + fy * fy + fz * fz < rc2f);
+            int ix = 0, iy = 0, iz = 0;
+            if (c) {
+              ix = (int)(nxf + sxf);
+              iy = (int)(nyf + syf);
+              iz = (int)(nzf + szf);
+              c = !((j == i) && ix == 0 && iy == 0 && iz == 0);
+            }
             const unsigned m = __ballot_sync(kFull, c);
             if (c) {
               const int pos = ncand + __popc(m & lt);
@@ -153,16 +197,23 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
               __syncwarp();
             }
           }
+        }
+      }
     }
   }
+  __shared__ int cmax;
+  if (threadIdx.x == 0) cmax = 0;
+  __syncthreads();
   if (active) {
     __syncwarp();
     if (ncand > 0) exact_batch(a, i, xi, yi, zi, rc2, cj, cs, ncand, lane, count);
     if (lane == 0) {
       a.cnt[i] = min(count, a.K);
-      atomicMax(&a.flags[0], count);
+      atomicMax(&cmax, count);
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(&a.flags[0], cmax);
 }
 
 // Caller-supplied list -> internal [N][K] tables with exact separations.
@@ -200,85 +251,156 @@ __global__ void neigh_ingest_kernel(int n, int K, const double* __restrict__ pos
   rij[3 * q + 2] = sep1(i, k, pos[3 * i + 2], pos[3 * k + 2], iz, Lz);
 }
 
-// rev[i][s] = slot s' of k = nbr[i][s] whose entry is (i, -img).
-__global__ void rev_kernel(WorkArgs a, int* rev) {
-  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (long)a.n * a.K) return;
-  const int i = (int)(q / a.K), s = (int)(q - (long)i * a.K);
-  if (s >= a.cnt[i]) return;
-  const int k = a.nbr[q];
-  const int ix = -a.img[3 * q], iy = -a.img[3 * q + 1], iz = -a.img[3 * q + 2];
-  const int ck = a.cnt[k];
-  int found = -1;
-  for (int t = 0; t < ck; ++t) {
-    const long p = (long)k * a.K + t;
-    if (a.nbr[p] == i && a.img[3 * p] == ix && a.img[3 * p + 1] == iy && a.img[3 * p + 2] == iz) {
-      found = t;
-      break;
-    }
+// Reverse-slot map and FP64 Cayley-Klein geometry, once per unordered pair.
+//
+// rev[i][s] is the slot of the opposite pair (k, i, -s) in k's list (the
+// force gather reads dE_k/dr_ki through it).  The geometry of a slot
+// (Sec. II-A: the neighbour vector mapped to the 3-sphere, with constants
+// from the paper's SNAP reference): theta0 = rfac0 pi (r - rmin0)/(rcut -
+// rmin0), z0 = r cot theta0, r0 = sqrt(r^2 + z0^2), a = (z0 - i z)/r0,
+// b = (y - i x)/r0, the cosine switching function f_c, and the derivatives
+// of a, b and f_c with respect to r.  For the opposite vector -r the same
+// quantities are a' = conj(a), b' = -b, grad f_c' = -grad f_c,
+// da'/dr = -conj(da/dr), db'/dr = db/dr, exactly, so only one slot of each
+// pair is evaluated (in FP64) and both are written (in the working
+// precision G).  A CTA collects the canonical slots of kPairAtoms atoms in
+// shared memory first, so the FP64 work runs on dense lanes.
+constexpr int kPairAtoms = 2;
+constexpr int kPairThreads = 64;
+
+template <typename G>
+__device__ void write_geom(G* g, G* gm, double ar, double ai, double br, double bi, double fc,
+                           const double* dfc, const double* da, const double* db) {
+  G v[kGeomStride];
+  v[0] = G(ar);
+  v[1] = G(ai);
+  v[2] = G(br);
+  v[3] = G(bi);
+  v[4] = G(fc);
+  for (int d = 0; d < 3; ++d) {
+    v[5 + d] = G(dfc[d]);
+    v[8 + 2 * d] = G(da[2 * d]);
+    v[9 + 2 * d] = G(da[2 * d + 1]);
+    v[14 + 2 * d] = G(db[2 * d]);
+    v[15 + 2 * d] = G(db[2 * d + 1]);
   }
-  rev[q] = found;
-  if (found < 0) atomicMax(&a.flags[1], 1);
+  for (int e = 0; e < kGeomStride; ++e) g[e] = v[e];
+  if (!gm) return;
+  // opposite vector: a -> conj(a), b -> -b, grad f_c -> -grad f_c,
+  // da -> -conj(da), db -> db (negation is exact in any precision)
+  gm[0] = v[0];
+  gm[1] = -v[1];
+  gm[2] = -v[2];
+  gm[3] = -v[3];
+  gm[4] = v[4];
+  for (int d = 0; d < 3; ++d) {
+    gm[5 + d] = -v[5 + d];
+    gm[8 + 2 * d] = -v[8 + 2 * d];
+    gm[9 + 2 * d] = v[9 + 2 * d];
+    gm[14 + 2 * d] = v[14 + 2 * d];
+    gm[15 + 2 * d] = v[15 + 2 * d];
+  }
 }
 
-// Per-slot Cayley-Klein parameters and derivatives, FP64 (Sec. II-A: the
-// neighbour vector mapped to the 3-sphere; constants from the paper's SNAP
-// reference): theta0 = rfac0 pi (r - rmin0)/(rcut - rmin0), z0 = r cot theta0,
-// r0 = sqrt(r^2 + z0^2), a = (z0 - i z)/r0, b = (y - i x)/r0, and the
-// cosine switching function f_c.
 template <typename G>
-__global__ void geom_kernel(WorkArgs a) {
-  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (long)a.n * a.K) return;
-  const int i = (int)(q / a.K), s = (int)(q - (long)i * a.K);
-  if (s >= a.cnt[i]) return;
-  const double x = a.rij[3 * q], y = a.rij[3 * q + 1], z = a.rij[3 * q + 2];
-  // arithmetic in FP64; the result is stored in the working precision G
-  G* g = reinterpret_cast<G*>(a.geom) + q * kGeomStride;
-  const double r2 = x * x + y * y + z * z;
-  const double r = sqrt(r2);
-  if (!(r < a.rcut)) {
-    for (int e = 0; e < kGeomStride; ++e) g[e] = G(0);
-    g[0] = G(1);
-    return;
+__global__ void __launch_bounds__(kPairThreads) pairs_kernel(WorkArgs a, int* rev) {
+  __shared__ long qs[kPairAtoms * kMaxNeighCap];
+  __shared__ long qm[kPairAtoms * kMaxNeighCap];
+  __shared__ int ncanon;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  if (threadIdx.x == 0) ncanon = 0;
+  __syncthreads();
+  constexpr int per_warp = kPairAtoms / (kPairThreads / 32);
+  for (int aa = 0; aa < per_warp; ++aa) {
+    const int i = blockIdx.x * kPairAtoms + warp * per_warp + aa;
+    if (i >= a.n) break;
+    const int cnt = a.cnt[i];
+    for (int s0 = 0; s0 < cnt; s0 += 32) {
+      const int s = s0 + lane;
+      bool canon = false;
+      long q = 0, q2 = -1;
+      if (s < cnt) {
+        q = (long)i * a.K + s;
+        const int k = a.nbr[q];
+        const int sx = a.img[3 * q], sy = a.img[3 * q + 1], sz = a.img[3 * q + 2];
+        const int ck = a.cnt[k];
+        int found = -1;
+        // all of k's slots are read with independent loads (no early exit)
+        const int* kn = a.nbr + (long)k * a.K;
+        for (int t0 = 0; t0 < ck; t0 += 8) {
+          int nb[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) nb[u] = (t0 + u < ck) ? kn[t0 + u] : -1;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (nb[u] == i && found < 0) {
+              const long p = (long)k * a.K + t0 + u;
+              if (a.img[3 * p] == -sx && a.img[3 * p + 1] == -sy && a.img[3 * p + 2] == -sz) found = t0 + u;
+            }
+          }
+        }
+        rev[q] = found;
+        if (found < 0) atomicMax(&a.flags[1], 1);
+        const bool pos = sx > 0 || (sx == 0 && (sy > 0 || (sy == 0 && sz > 0)));
+        canon = found < 0 || i < k || (i == k && pos);
+        if (found >= 0) q2 = (long)k * a.K + found;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, canon);
+      int base = 0;
+      if (lane == 0) base = atomicAdd(&ncanon, __popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (canon) {
+        const int p = base + __popc(m & lt);
+        qs[p] = q;
+        qm[p] = q2;
+      }
+    }
   }
-  const double span = a.rcut - a.rmin0;
-  const double c = a.rfac0 * M_PI / span;  // d theta0 / d r
-  const double theta0 = c * (r - a.rmin0);
-  double st, ct;
-  sincos(theta0, &st, &ct);
-  const double ist = 1.0 / st;
-  const double z0 = r * ct * ist;
-  const double dz0dr = ct * ist - r * c * ist * ist;
-  const double r0 = sqrt(r2 + z0 * z0);
-  const double ir0 = 1.0 / r0;
-  const double ar = z0 * ir0, ai = -z * ir0;
-  const double br = y * ir0, bi = -x * ir0;
-  g[0] = G(ar);
-  g[1] = G(ai);
-  g[2] = G(br);
-  g[3] = G(bi);
-  double fc = 1.0, dfcdr = 0.0;
-  if (a.switchflag && r > a.rmin0) {
-    const double w = M_PI * (r - a.rmin0) / span;
-    double sw, cw;
-    sincos(w, &sw, &cw);
-    fc = 0.5 * (cw + 1.0);
-    dfcdr = -0.5 * M_PI / span * sw;
-  }
-  g[4] = G(fc);
-  const double rv[3] = {x, y, z};
-  const double ir = 1.0 / r;
-  for (int d = 0; d < 3; ++d) {
-    const double ud = rv[d] * ir;
-    g[5 + d] = G(dfcdr * ud);
-    const double dz0 = dz0dr * ud;
-    const double dr0 = (r * ud + z0 * dz0) * ir0;
-    // d a = (d(z0 - i z) - a d r0) / r0 ; d b = (d(y - i x) - b d r0) / r0
-    g[8 + 2 * d] = G((dz0 - ar * dr0) * ir0);
-    g[9 + 2 * d] = G(((d == 2 ? -1.0 : 0.0) - ai * dr0) * ir0);
-    g[14 + 2 * d] = G(((d == 1 ? 1.0 : 0.0) - br * dr0) * ir0);
-    g[15 + 2 * d] = G(((d == 0 ? -1.0 : 0.0) - bi * dr0) * ir0);
+  __syncthreads();
+  const int nc = ncanon;
+  for (int p = threadIdx.x; p < nc; p += blockDim.x) {
+    const long q = qs[p], q2 = qm[p];
+    G* g = reinterpret_cast<G*>(a.geom) + q * kGeomStride;
+    G* gm = q2 >= 0 ? reinterpret_cast<G*>(a.geom) + q2 * kGeomStride : nullptr;
+    const double x = a.rij[3 * q], y = a.rij[3 * q + 1], z = a.rij[3 * q + 2];
+    const double r2 = x * x + y * y + z * z;
+    const double ir = rsqrt(r2);
+    const double r = r2 * ir;
+    double dfc[3] = {0, 0, 0}, da[6] = {0, 0, 0, 0, 0, 0}, db[6] = {0, 0, 0, 0, 0, 0};
+    if (!(r < a.rcut)) {  // outside the cutoff (caller lists): no contribution
+      write_geom(g, gm, 1.0, 0.0, 0.0, 0.0, 0.0, dfc, da, db);
+      continue;
+    }
+    const double c = a.rfac0 * M_PI * a.inv_span;  // d theta0 / d r
+    double st, ct;
+    sincospi(a.rfac0 * (r - a.rmin0) * a.inv_span, &st, &ct);
+    const double ist = 1.0 / st;
+    const double z0 = r * ct * ist;
+    const double dz0dr = ct * ist - r * c * ist * ist;
+    const double ir0 = rsqrt(r2 + z0 * z0);
+    const double ar = z0 * ir0, ai = -z * ir0;
+    const double br = y * ir0, bi = -x * ir0;
+    double fc = 1.0, dfcdr = 0.0;
+    if (a.switchflag && r > a.rmin0) {
+      double sw, cw;
+      sincospi((r - a.rmin0) * a.inv_span, &sw, &cw);
+      fc = 0.5 * (cw + 1.0);
+      dfcdr = -0.5 * M_PI * a.inv_span * sw;
+    }
+    const double rv[3] = {x, y, z};
+    for (int d = 0; d < 3; ++d) {
+      const double ud = rv[d] * ir;
+      dfc[d] = dfcdr * ud;
+      const double dz0 = dz0dr * ud;
+      const double dr0 = (r * ud + z0 * dz0) * ir0;
+      // d a = (d(z0 - i z) - a d r0) / r0 ; d b = (d(y - i x) - b d r0) / r0
+      da[2 * d] = (dz0 - ar * dr0) * ir0;
+      da[2 * d + 1] = ((d == 2 ? -1.0 : 0.0) - ai * dr0) * ir0;
+      db[2 * d] = ((d == 1 ? 1.0 : 0.0) - br * dr0) * ir0;
+      db[2 * d + 1] = ((d == 0 ? -1.0 : 0.0) - bi * dr0) * ir0;
+    }
+    write_geom(g, gm, ar, ai, br, bi, fc, dfc, da, db);
   }
 }
 
@@ -294,7 +416,10 @@ cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s) 
 
 cudaError_t launch_neigh_build(const NeighArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  neigh_build_kernel<<<blocks_for(a.n, kNbWarps), kNbWarps * 32, 0, s>>>(a);
+  if (a.Sx == 0 && a.Sy == 0 && a.Sz == 0)
+    neigh_build_kernel<true><<<blocks_for(a.n, kNbWarps), kNbWarps * 32, 0, s>>>(a);
+  else
+    neigh_build_kernel<false><<<blocks_for(a.n, kNbWarps), kNbWarps * 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -308,19 +433,13 @@ cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_rev(const WorkArgs& a, int* rev, cudaStream_t s) {
-  if (a.n <= 0) return cudaSuccess;
-  rev_kernel<<<blocks_for((long)a.n * a.K, 256), 256, 0, s>>>(a, rev);
-  return cudaGetLastError();
-}
-
 template <typename G>
-cudaError_t launch_geom(const WorkArgs& a, cudaStream_t s) {
+cudaError_t launch_pairs(const WorkArgs& a, int* rev, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  geom_kernel<G><<<blocks_for((long)a.n * a.K, 128), 128, 0, s>>>(a);
+  pairs_kernel<G><<<blocks_for(a.n, kPairAtoms), kPairThreads, 0, s>>>(a, rev);
   return cudaGetLastError();
 }
-template cudaError_t launch_geom<float>(const WorkArgs&, cudaStream_t);
-template cudaError_t launch_geom<double>(const WorkArgs&, cudaStream_t);
+template cudaError_t launch_pairs<float>(const WorkArgs&, int*, cudaStream_t);
+template cudaError_t launch_pairs<double>(const WorkArgs&, int*, cudaStream_t);
 
 }  // namespace snap

@@ -41,7 +41,7 @@ EXPORTS = ("snap_num_coeff", "snap_create", "snap_set_beta", "snap_set_neigh_cap
            "snap_compute_host", "snap_get_buffer", "snap_half_index", "snap_half_size",
            "snap_destroy", "snap_last_error", "snap_profile", "snap_profile_read",
            "snap_stage_name", "snap_launches_per_call")
-NSTAGES = 7
+NSTAGES = 6
 
 _lib = None
 
