@@ -30,8 +30,7 @@ struct snap_ctx {
 
   // device tables
   int* d_half_tmm = nullptr;
-  unsigned* d_yterm = nullptr;
-  void* d_ycoef = nullptr;
+  void* d_yrec = nullptr;
   int* d_yfirst = nullptr;
   void* d_root = nullptr;
   int* d_yslice = nullptr;
@@ -48,10 +47,8 @@ struct snap_ctx {
   int* d_rev = nullptr;
   double* d_geom = nullptr;
   double* d_dedr = nullptr;
-  void* d_Ure = nullptr;
-  void* d_Uim = nullptr;
-  void* d_Yre = nullptr;
-  void* d_Yim = nullptr;
+  void* d_U = nullptr;  // complex AoSoA [ceil(N/32)][H][32]
+  void* d_Y = nullptr;
   double* d_vpart = nullptr;
   int* d_flags = nullptr;
   int* h_flags = nullptr;
@@ -120,6 +117,27 @@ int upload(snap_ctx* c, T** dst, const std::vector<T>& v) {
   return SNAP_OK;
 }
 
+// compute_Y term records (index word + coefficient in the working precision)
+int upload_yrec(snap_ctx* c) {
+  const std::vector<double> coef = c->tab.term_coef(c->beta.data());
+  const size_t n = c->tab.terms.size();
+  if (c->precision == SNAP_MIXED) {
+    std::vector<snap::YRec<float>> r(n);
+    for (size_t k = 0; k < n; ++k) {
+      r[k].w = c->tab.terms[k];
+      r[k].c = (float)coef[k];
+    }
+    return upload(c, reinterpret_cast<snap::YRec<float>**>(&c->d_yrec), r);
+  }
+  std::vector<snap::YRec<double>> r(n);
+  for (size_t k = 0; k < n; ++k) {
+    r[k].w = c->tab.terms[k];
+    r[k].pad = 0;
+    r[k].c = coef[k];
+  }
+  return upload(c, reinterpret_cast<snap::YRec<double>**>(&c->d_yrec), r);
+}
+
 void free_workspace(snap_ctx* c) {
   dfree(c->d_pos4);
   dfree(c->d_cnt);
@@ -129,10 +147,8 @@ void free_workspace(snap_ctx* c) {
   dfree(c->d_rev);
   dfree(c->d_geom);
   dfree(c->d_dedr);
-  dfree(c->d_Ure);
-  dfree(c->d_Uim);
-  dfree(c->d_Yre);
-  dfree(c->d_Yim);
+  dfree(c->d_U);
+  dfree(c->d_Y);
   dfree(c->d_vpart);
   c->cap_nk = 0;
   c->cap_n = 0;
@@ -146,7 +162,7 @@ int ensure_workspace(snap_ctx* c, int n, int K) {
   const int ncap = std::max(n, 1);
   const long nkcap = std::max(nk, 1L);
   const long nblk = (ncap + 31) / 32;
-  const size_t uy = (size_t)nblk * 32 * c->tab.H * c->rsize();
+  const size_t uy = (size_t)nblk * 32 * c->tab.H * 2 * c->rsize();
   SNAP_CUDA(c, cudaMalloc(&c->d_pos4, sizeof(float4) * ncap));
   SNAP_CUDA(c, cudaMalloc(&c->d_cnt, sizeof(int) * ncap));
   SNAP_CUDA(c, cudaMalloc(&c->d_nbr, sizeof(int) * nkcap));
@@ -155,13 +171,10 @@ int ensure_workspace(snap_ctx* c, int n, int K) {
   SNAP_CUDA(c, cudaMalloc(&c->d_rev, sizeof(int) * nkcap));
   SNAP_CUDA(c, cudaMalloc(&c->d_geom, sizeof(double) * snap::kGeomStride * nkcap));
   SNAP_CUDA(c, cudaMalloc(&c->d_dedr, sizeof(double) * 3 * nkcap));
-  SNAP_CUDA(c, cudaMalloc(&c->d_Ure, uy));
-  SNAP_CUDA(c, cudaMalloc(&c->d_Uim, uy));
-  SNAP_CUDA(c, cudaMalloc(&c->d_Yre, uy));
-  SNAP_CUDA(c, cudaMalloc(&c->d_Yim, uy));
+  SNAP_CUDA(c, cudaMalloc(&c->d_U, uy));
+  SNAP_CUDA(c, cudaMalloc(&c->d_Y, uy));
   // lanes past the last atom read zeros in compute_Y
-  SNAP_CUDA(c, cudaMemset(c->d_Ure, 0, uy));
-  SNAP_CUDA(c, cudaMemset(c->d_Uim, 0, uy));
+  SNAP_CUDA(c, cudaMemset(c->d_U, 0, uy));
   SNAP_CUDA(c, cudaMalloc(&c->d_vpart, sizeof(double) * 6 * (4 * nblk + 1)));
   c->cap_n = ncap;
   c->cap_nk = nkcap;
@@ -270,10 +283,8 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   a.rev = c->d_rev;
   a.rij = c->d_rij;
   a.geom = c->d_geom;
-  a.Ure = c->d_Ure;
-  a.Uim = c->d_Uim;
-  a.Yre = c->d_Yre;
-  a.Yim = c->d_Yim;
+  a.U = c->d_U;
+  a.Y = c->d_Y;
   a.dedr = c->d_dedr;
   a.energy = energy;
   a.forces = forces;
@@ -281,8 +292,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   a.virial = virial;
   a.flags = c->d_flags;
   a.half_tmm = c->d_half_tmm;
-  a.yterm = c->d_yterm;
-  a.ycoef = c->d_ycoef;
+  a.yrec = c->d_yrec;
   a.yfirst = c->d_yfirst;
   a.yslice = c->d_yslice;
   a.nslices = c->nslices;
@@ -394,10 +404,9 @@ int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switch
     return SNAP_ERR_CUDA;
   }
   int rc = upload(c, &c->d_half_tmm, c->tab.half_tmm);
-  if (!rc) rc = upload(c, &c->d_yterm, c->tab.terms);
   if (!rc) rc = upload(c, &c->d_yfirst, c->tab.term_out_first);
   if (!rc) rc = upload_r(c, &c->d_root, c->tab.rootpq);
-  if (!rc) rc = upload_r(c, &c->d_ycoef, c->tab.term_coef(c->beta.data()));
+  if (!rc) rc = upload_yrec(c);
   if (rc) {
     g_create_error = c->err;
     snap_destroy(c);
@@ -411,7 +420,7 @@ int snap_set_beta(snap_ctx* c, const double* beta) {
   if (!c || !beta) return fail(c, SNAP_ERR_ARG, "NULL argument");
   cudaDeviceSynchronize();
   c->beta.assign(beta, beta + 1 + c->tab.ncoeff);
-  return upload_r(c, &c->d_ycoef, c->tab.term_coef(c->beta.data()));
+  return upload_yrec(c);
 }
 
 int snap_set_neigh_cap(snap_ctx* c, int cap) {
@@ -564,27 +573,22 @@ long long snap_get_buffer(snap_ctx* c, int which, void* dst, size_t bytes) {
       const size_t size = sizeof(double) * 2 * n * H;
       if (!dst) return (long long)size;
       const long nblk = (n + 31) / 32;
-      const size_t cnt = (size_t)nblk * 32 * H;
-      const bool isU = which == SNAP_BUF_ULISTTOT;
-      const void* re = isU ? c->d_Ure : c->d_Yre;
-      const void* im = isU ? c->d_Uim : c->d_Yim;
-      std::vector<double> hre(cnt), him(cnt);
+      const size_t cnt = (size_t)nblk * 32 * H * 2;
+      const void* src = which == SNAP_BUF_ULISTTOT ? c->d_U : c->d_Y;
+      std::vector<double> hv(cnt);
       if (c->precision == SNAP_MIXED) {
         std::vector<float> f(cnt);
-        SNAP_CUDA(c, cudaMemcpy(f.data(), re, cnt * sizeof(float), cudaMemcpyDeviceToHost));
-        hre.assign(f.begin(), f.end());
-        SNAP_CUDA(c, cudaMemcpy(f.data(), im, cnt * sizeof(float), cudaMemcpyDeviceToHost));
-        him.assign(f.begin(), f.end());
+        SNAP_CUDA(c, cudaMemcpy(f.data(), src, cnt * sizeof(float), cudaMemcpyDeviceToHost));
+        hv.assign(f.begin(), f.end());
       } else {
-        SNAP_CUDA(c, cudaMemcpy(hre.data(), re, cnt * sizeof(double), cudaMemcpyDeviceToHost));
-        SNAP_CUDA(c, cudaMemcpy(him.data(), im, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+        SNAP_CUDA(c, cudaMemcpy(hv.data(), src, cnt * sizeof(double), cudaMemcpyDeviceToHost));
       }
       std::vector<double> out(2 * n * H);
       for (long i = 0; i < n; ++i)
         for (long e = 0; e < H; ++e) {
-          const size_t src = ((size_t)(i >> 5) * H + e) * 32 + (i & 31);
-          out[2 * (i * H + e)] = hre[src];
-          out[2 * (i * H + e) + 1] = him[src];
+          const size_t q = ((size_t)(i >> 5) * H + e) * 32 + (i & 31);
+          out[2 * (i * H + e)] = hv[2 * q];
+          out[2 * (i * H + e) + 1] = hv[2 * q + 1];
         }
       std::memcpy(dst, out.data(), std::min(size, bytes));
       return (long long)size;
@@ -598,8 +602,7 @@ int snap_destroy(snap_ctx* c) {
   cudaDeviceSynchronize();
   free_workspace(c);
   dfree(c->d_half_tmm);
-  dfree(c->d_yterm);
-  dfree(c->d_ycoef);
+  dfree(c->d_yrec);
   dfree(c->d_yfirst);
   dfree(c->d_root);
   dfree(c->d_yslice);

@@ -25,7 +25,7 @@ namespace col {
 constexpr unsigned kFull = 0xffffffffu;
 
 template <typename R>
-struct c2 {
+struct __align__(2 * sizeof(R)) c2 {
   R re, im;
 };
 
@@ -176,8 +176,7 @@ __global__ void __launch_bounds__(NW * 32) ui_col_kernel(WorkArgs a) {
     });
   }
   __syncthreads();
-  R* Ure = reinterpret_cast<R*>(a.Ure);
-  R* Uim = reinterpret_cast<R*>(a.Uim);
+  c2<R>* Ug = reinterpret_cast<c2<R>*>(a.U);
   const long blk = i >> 5;
   const int li = i & 31;
   for (int e = threadIdx.x; e < H; e += blockDim.x) {
@@ -188,8 +187,7 @@ __global__ void __launch_bounds__(NW * 32) ui_col_kernel(WorkArgs a) {
     }
     const int p = a.half_tmm[e];
     if (tmm_ma(p) == tmm_mb(p)) sr += (R)a.wself;
-    Ure[(blk * H + e) * 32 + li] = sr;
-    Uim[(blk * H + e) * 32 + li] = si;
+    Ug[(blk * H + e) * 32 + li] = mk<R>(sr, si);
   }
 }
 
@@ -212,14 +210,14 @@ __global__ void __launch_bounds__(NW * 32) de_col_kernel(WorkArgs a) {
   const bool grp = g < P;
   const int i = blockIdx.x;
   {
-    const R* Yre = reinterpret_cast<const R*>(a.Yre);
-    const R* Yim = reinterpret_cast<const R*>(a.Yim);
+    const c2<R>* Yg = reinterpret_cast<const c2<R>*>(a.Y);
     const long blk = i >> 5;
     const int li = i & 31;
     for (int e = threadIdx.x; e < H; e += blockDim.x) {
       const int p = a.half_tmm[e];
       const R w = (R)hweight(tmm_t(p), tmm_ma(p), tmm_mb(p));
-      Yw[e] = mk<R>(w * Yre[(blk * H + e) * 32 + li], w * Yim[(blk * H + e) * 32 + li]);
+      const c2<R> y = Yg[(blk * H + e) * 32 + li];
+      Yw[e] = mk<R>(w * y.re, w * y.im);
     }
   }
   __syncthreads();

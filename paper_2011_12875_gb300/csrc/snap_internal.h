@@ -27,6 +27,22 @@ __host__ __device__ constexpr int tmm_t(int p) { return p & 0xff; }
 __host__ __device__ constexpr int tmm_ma(int p) { return (p >> 8) & 0xff; }
 __host__ __device__ constexpr int tmm_mb(int p) { return (p >> 16) & 0xff; }
 
+// compute_Y term record: w = index of U_t1 element (10 bits) | index of the
+// U_t2 element << 10 | conj U_t1 << 20 | conj U_t2 << 21 | last term of the
+// output << 22; c = coefficient in the working precision.
+template <typename R>
+struct YRec;
+template <>
+struct __align__(8) YRec<float> {
+  unsigned w;
+  float c;
+};
+template <>
+struct __align__(16) YRec<double> {
+  unsigned w, pad;
+  double c;
+};
+
 // Per neighbour slot geometry (Cayley-Klein parameters, Sec. II-A), computed
 // in FP64 and stored in the working precision R:
 //  [0..1] a, [2..3] b, [4] f_c, [5..7] d f_c / d r_d,
@@ -58,10 +74,9 @@ struct WorkArgs {
   const int* rev;
   double* rij;
   void* geom;  // R [N][K][kGeomStride]: Cayley-Klein geometry in the working precision
-  void* Ure;
-  void* Uim;
-  void* Yre;
-  void* Yim;
+  // Ulisttot and Y: complex (re, im interleaved), AoSoA [ceil(N/32)][H][32]
+  void* U;
+  void* Y;
   double* dedr;
   double* energy;
   double* forces;
@@ -69,8 +84,7 @@ struct WorkArgs {
   double* virial;
   int* flags;
   const int* half_tmm;
-  const unsigned* yterm;  // compute_Y term records (see snap_tables.cpp)
-  const void* ycoef;      // R [nterms] term coefficients
+  const void* yrec;       // compute_Y term records (see snap_tables.cpp)
   const int* yfirst;      // [H+1] first term of each output element
   const int* yslice;
   int nslices;

@@ -18,7 +18,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 template <typename R>
-struct cx {
+struct __align__(2 * sizeof(R)) cx {
   R re, im;
 };
 
@@ -135,8 +135,7 @@ __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
     __syncwarp();
   }
   __syncthreads();
-  R* Ure = reinterpret_cast<R*>(a.Ure);
-  R* Uim = reinterpret_cast<R*>(a.Uim);
+  cx<R>* Ug = reinterpret_cast<cx<R>*>(a.U);
   const long blk = i >> 5;
   const int li = i & 31;
   for (int e = threadIdx.x; e < H; e += blockDim.x) {
@@ -147,8 +146,7 @@ __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
     }
     const int p = a.half_tmm[e];
     if (tmm_ma(p) == tmm_mb(p)) s.re += (R)a.wself;
-    Ure[(blk * H + e) * 32 + li] = s.re;
-    Uim[(blk * H + e) * 32 + li] = s.im;
+    Ug[(blk * H + e) * 32 + li] = s;
   }
 }
 
@@ -208,20 +206,18 @@ struct YAcc {
 };
 
 template <typename R>
-__device__ __forceinline__ void y_term(unsigned w, R c, const R* __restrict__ ure, const R* __restrict__ uim,
-                                       R* __restrict__ Yre, R* __restrict__ Yim, int lane, YAcc<R>& y) {
-  const int e1 = (int)(w & 1023u), e2 = (int)((w >> 10) & 1023u);
-  const R a = ure[e1 * 32 + lane];
-  const R b = flip_if(uim[e1 * 32 + lane], (w >> 20) & 1u);
-  const R cc = ure[e2 * 32 + lane];
-  const R d = flip_if(uim[e2 * 32 + lane], (w >> 21) & 1u);
-  const R pr = a * cc - b * d;
-  const R pi = a * d + b * cc;
+__device__ __forceinline__ void y_term(unsigned w, R c, const cx<R>* __restrict__ us,
+                                       cx<R>* __restrict__ Yg, int lane, YAcc<R>& y) {
+  const cx<R> u1 = us[(int)(w & 1023u) * 32 + lane];
+  const cx<R> u2 = us[(int)((w >> 10) & 1023u) * 32 + lane];
+  const R b = flip_if(u1.im, (w >> 20) & 1u);
+  const R d = flip_if(u2.im, (w >> 21) & 1u);
+  const R pr = u1.re * u2.re - b * d;
+  const R pi = u1.re * d + b * u2.re;
   y.re += c * pr;
   y.im += c * pi;
   if (w & (1u << 22)) {
-    Yre[y.o * 32 + lane] = y.re;
-    Yim[y.o * 32 + lane] = y.im;
+    Yg[y.o * 32 + lane] = mk<R>(y.re, y.im);
     y.re = R(0);
     y.im = R(0);
     ++y.o;
@@ -234,19 +230,16 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long blk = blockIdx.x;
   const int H = a.H;
-  const R* ure = reinterpret_cast<const R*>(a.Ure) + blk * H * 32;
-  const R* uim = reinterpret_cast<const R*>(a.Uim) + blk * H * 32;
+  const cx<R>* us = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
   if (STAGED) {
-    R* sre = reinterpret_cast<R*>(smem);
-    R* sim = sre + H * 32;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sim + H * 32);
-    const unsigned bytes = (unsigned)(H * 32 * sizeof(R));
+    cx<R>* su = reinterpret_cast<cx<R>*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(su + H * 32);
+    const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
-      mbar_expect_tx(bar, 2 * bytes);
-      bulk_g2s(sre, ure, bytes, bar);
-      bulk_g2s(sim, uim, bytes, bar);
+      mbar_expect_tx(bar, bytes);
+      bulk_g2s(su, us, bytes, bar);
     }
     bool ok = false;
     for (unsigned it = 0; it < kSpinLimit; ++it)
@@ -258,36 +251,47 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
       if (threadIdx.x == 0) atomicMax(&a.flags[3], 1);
       return;
     }
-    ure = sre;
-    uim = sim;
+    us = su;
   }
   const int slice = blockIdx.y * (blockDim.x >> 5) + warp;
   if (slice >= a.nslices) return;
   const int o0 = a.yslice[slice], o1 = a.yslice[slice + 1];
   if (o0 >= o1) return;
-  R* Yre = reinterpret_cast<R*>(a.Yre) + blk * H * 32;
-  R* Yim = reinterpret_cast<R*>(a.Yim) + blk * H * 32;
-  const unsigned* __restrict__ tw = a.yterm;
-  const R* __restrict__ tc = reinterpret_cast<const R*>(a.ycoef);
+  cx<R>* Yg = reinterpret_cast<cx<R>*>(a.Y) + blk * H * 32;
+  const YRec<R>* __restrict__ rec = reinterpret_cast<const YRec<R>*>(a.yrec);
   const int q1 = a.yfirst[o1];
   int q = a.yfirst[o0];
   YAcc<R> y;
   y.re = R(0);
   y.im = R(0);
   y.o = o0;
-  constexpr int U = 8;
-  for (; q + U <= q1; q += U) {
-    unsigned w[U];
-    R c[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      w[k] = __ldg(tw + q + k);
-      c[k] = __ldg(tc + q + k);
+  if constexpr (sizeof(R) == 4) {
+    // two 8-byte records per 16-byte load
+    if ((q & 1) && q < q1) {
+      y_term<R>(rec[q].w, rec[q].c, us, Yg, lane, y);
+      ++q;
     }
+    for (; q + 8 <= q1; q += 8) {
+      uint4 v[4];
 #pragma unroll
-    for (int k = 0; k < U; ++k) y_term(w[k], c[k], ure, uim, Yre, Yim, lane, y);
+      for (int k = 0; k < 4; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(rec + q) + k);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        y_term<R>(v[k].x, __uint_as_float(v[k].y), us, Yg, lane, y);
+        y_term<R>(v[k].z, __uint_as_float(v[k].w), us, Yg, lane, y);
+      }
+    }
+  } else {
+    for (; q + 4 <= q1; q += 4) {
+      uint4 v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(rec + q + k));
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        y_term<R>(v[k].x, (R)__hiloint2double((int)v[k].w, (int)v[k].z), us, Yg, lane, y);
+    }
   }
-  for (; q < q1; ++q) y_term(__ldg(tw + q), __ldg(tc + q), ure, uim, Yre, Yim, lane, y);
+  for (; q < q1; ++q) y_term<R>(rec[q].w, rec[q].c, us, Yg, lane, y);
 }
 
 // ------------------------------------------------------ fused dU + dE/dr
@@ -311,14 +315,14 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
   const R* rootg = reinterpret_cast<const R*>(a.rootpq);
   for (int e = threadIdx.x; e < kRootDim * kRootDim; e += blockDim.x) root[e] = rootg[e];
   {
-    const R* Yre = reinterpret_cast<const R*>(a.Yre);
-    const R* Yim = reinterpret_cast<const R*>(a.Yim);
+    const cx<R>* Yg = reinterpret_cast<const cx<R>*>(a.Y);
     const long blk = i >> 5;
     const int li = i & 31;
     for (int e = threadIdx.x; e < H; e += blockDim.x) {
       const int p = a.half_tmm[e];
       const R w = (R)half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
-      Yw[e] = mk<R>(w * Yre[(blk * H + e) * 32 + li], w * Yim[(blk * H + e) * 32 + li]);
+      const cx<R> y = Yg[(blk * H + e) * 32 + li];
+      Yw[e] = mk<R>(w * y.re, w * y.im);
     }
   }
   __syncthreads();
@@ -464,16 +468,14 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_kernel(WorkArgs a) {
   if (part == 0) {
     // per-warp partial over every 8th element in the working precision,
     // combined over warps in FP64
-    const R* Ure = reinterpret_cast<const R*>(a.Ure) + blk * H * 32;
-    const R* Uim = reinterpret_cast<const R*>(a.Uim) + blk * H * 32;
-    const R* Yre = reinterpret_cast<const R*>(a.Yre) + blk * H * 32;
-    const R* Yim = reinterpret_cast<const R*>(a.Yim) + blk * H * 32;
+    const cx<R>* Ug = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
+    const cx<R>* Yg = reinterpret_cast<const cx<R>*>(a.Y) + blk * H * 32;
     R e = R(0);
     for (int el = warp; el < H; el += kForceWarps) {
       const int p = a.half_tmm[el];
       const R w = (R)half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
-      const int idx = el * 32 + lane;
-      e += w * (Yre[idx] * Ure[idx] + Yim[idx] * Uim[idx]);
+      const cx<R> u = Ug[el * 32 + lane], y = Yg[el * 32 + lane];
+      e += w * (y.re * u.re + y.im * u.im);
     }
     ep[warp][lane] = (double)e;
   }
@@ -570,7 +572,7 @@ cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s) {
 YiGeometry yi_geometry(int rsize, int H, int n, int nsm) {
   YiGeometry g;
   g.nblk = (n + 31) / 32;
-  const size_t stage = (size_t)2 * H * 32 * rsize + 16;
+  const size_t stage = (size_t)2 * H * 32 * rsize + 16;  // complex [H][32] + mbarrier
   g.staged = stage <= 200 * 1024;
   g.smem = g.staged ? stage : 0;
   g.threads = (g.smem > 100 * 1024) ? 1024 : 256;
