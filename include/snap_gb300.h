@@ -140,6 +140,16 @@ int snap_profile_read(snap_ctx* ctx, double* ms, long long* calls, int nstages);
 const char* snap_stage_name(int stage);
 int snap_launches_per_call(const snap_ctx* ctx);
 
+/* Bispectrum components of every atom, the SNAP descriptors used to fit
+ * beta (Sec. II-A, Eq. z): B[i][l] = Re sum over the full (2j+1)^2 matrix of
+ * Z^j_{j1j2} : conj(U_j) for the canonical (2j1, 2j2, 2j) of component l
+ * (order as for beta, without beta_0).  Arguments as snap_compute; B is a
+ * device array [N][N_B] of doubles (computed in the context's working
+ * precision).  Returns after the stream has finished. */
+int snap_compute_bispectrum(snap_ctx* ctx, int natoms, const double* pos, const double* box,
+                            const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
+                            int nbr_cap, double* B, void* stream);
+
 /* Same as snap_compute with HOST buffers and the device neighbour builder:
  * copies pos to the device, computes, and copies energy (may be NULL),
  * forces and virial (may be NULL) back, all on the given stream.  The host

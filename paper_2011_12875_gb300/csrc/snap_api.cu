@@ -32,6 +32,10 @@ struct snap_ctx {
   int* d_half_tmm = nullptr;
   void* d_yrec = nullptr;
   int* d_yfirst = nullptr;
+  void* d_brec = nullptr;
+  int* d_bout = nullptr;
+  int* d_bfirst = nullptr;
+  int* d_bgfirst = nullptr;
   void* d_root = nullptr;
   int* d_yslice = nullptr;
   int nslices = -1;
@@ -138,6 +142,26 @@ int upload_yrec(snap_ctx* c) {
   return upload(c, reinterpret_cast<snap::YRec<double>**>(&c->d_yrec), r);
 }
 
+// bispectrum term records (coefficients do not depend on beta)
+int upload_brec(snap_ctx* c) {
+  const size_t n = c->tab.bterms.size();
+  if (c->precision == SNAP_MIXED) {
+    std::vector<snap::YRec<float>> r(n);
+    for (size_t k = 0; k < n; ++k) {
+      r[k].w = c->tab.bterms[k];
+      r[k].c = (float)c->tab.bterm_coef[k];
+    }
+    return upload(c, reinterpret_cast<snap::YRec<float>**>(&c->d_brec), r);
+  }
+  std::vector<snap::YRec<double>> r(n);
+  for (size_t k = 0; k < n; ++k) {
+    r[k].w = c->tab.bterms[k];
+    r[k].pad = 0;
+    r[k].c = c->tab.bterm_coef[k];
+  }
+  return upload(c, reinterpret_cast<snap::YRec<double>**>(&c->d_brec), r);
+}
+
 void free_workspace(snap_ctx* c) {
   dfree(c->d_pos4);
   dfree(c->d_cnt);
@@ -198,9 +222,10 @@ bool box_ok(const double* box) {
 }
 
 // Enqueue the whole evaluation on stream s (no synchronisation).
+// mode 0: energy, forces, virial; mode 1: bispectrum components into B.
 int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int* ucnt,
             const int* uidx, const signed char* uimg, int ucap, double* energy, double* forces,
-            double* virial, cudaStream_t s) {
+            double* virial, cudaStream_t s, int mode = 0, double* B = nullptr) {
   const bool user = (ucnt || uidx || uimg);
   if (user && (!ucnt || !uidx || !uimg || ucap < 1 || ucap > snap::kMaxNeighCap))
     return fail(c, SNAP_ERR_ARG, "neighbour list: cnt, idx and img must all be given with 1 <= cap <= 64");
@@ -215,7 +240,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   if (rc) return rc;
   SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 8 * sizeof(int), s));
   std::vector<cudaEvent_t> ev;
-  if (c->prof_on) {
+  if (c->prof_on && mode == 0) {
     if (!c->prof_free.empty()) {
       ev = c->prof_free.back();
       c->prof_free.pop_back();
@@ -297,6 +322,12 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   a.yslice = c->d_yslice;
   a.nslices = c->nslices;
   a.nsm = c->nsm;
+  a.ncoeff = c->tab.ncoeff;
+  a.brec = c->d_brec;
+  a.bout = c->d_bout;
+  a.bfirst = c->d_bfirst;
+  a.bgfirst = c->d_bgfirst;
+  a.B = B;
   a.rootpq = c->d_root;
 
   const bool mixed = c->precision == SNAP_MIXED;
@@ -306,6 +337,14 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   SNAP_CUDA(c, colk ? snap::launch_ui_col<float>(a, s)
                     : (mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s)));
   SNAP_CUDA(c, mark());
+  if (mode == 1) {
+    SNAP_CUDA(c, mixed ? snap::launch_bi<float>(a, s) : snap::launch_bi<double>(a, s));
+    c->launches += 1;
+    SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    c->last_n = n;
+    c->last_K = K;
+    return SNAP_OK;
+  }
   SNAP_CUDA(c, mixed ? snap::launch_yi<float>(a, s) : snap::launch_yi<double>(a, s));
   SNAP_CUDA(c, mark());
   SNAP_CUDA(c, colk ? snap::launch_de_col<float>(a, s)
@@ -315,7 +354,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   SNAP_CUDA(c, mark());
   c->launches += 5;
   if (!ev.empty()) c->prof_pending.push_back(ev);
-  SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
   c->last_n = n;
   c->last_K = K;
   return SNAP_OK;
@@ -407,6 +446,10 @@ int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switch
   if (!rc) rc = upload(c, &c->d_yfirst, c->tab.term_out_first);
   if (!rc) rc = upload_r(c, &c->d_root, c->tab.rootpq);
   if (!rc) rc = upload_yrec(c);
+  if (!rc) rc = upload_brec(c);
+  if (!rc) rc = upload(c, &c->d_bout, c->tab.bout);
+  if (!rc) rc = upload(c, &c->d_bfirst, c->tab.bcomp_first);
+  if (!rc) rc = upload(c, &c->d_bgfirst, c->tab.bgroup_first);
   if (rc) {
     g_create_error = c->err;
     snap_destroy(c);
@@ -513,6 +556,22 @@ const char* snap_stage_name(int stage) {
 
 int snap_launches_per_call(const snap_ctx* c) { return c ? c->launches : -1; }
 
+int snap_compute_bispectrum(snap_ctx* c, int natoms, const double* pos, const double* box,
+                            const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
+                            int nbr_cap, double* B, void* stream) {
+  if (!c) return SNAP_ERR_ARG;
+  if (natoms < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
+  if (!box_ok(box)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+  if (natoms == 0) return SNAP_OK;
+  if (!pos || !B) return fail(c, SNAP_ERR_ARG, "pos and B are required");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = enqueue(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, nullptr, nullptr, nullptr, s,
+                   1, B);
+  if (rc) return rc;
+  SNAP_CUDA(c, cudaStreamSynchronize(s));
+  return check_flags(c);
+}
+
 int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const double* box,
                       double* energy_host, double* forces_host, double* virial_host, void* stream) {
   if (!c) return SNAP_ERR_ARG;
@@ -604,6 +663,10 @@ int snap_destroy(snap_ctx* c) {
   dfree(c->d_half_tmm);
   dfree(c->d_yrec);
   dfree(c->d_yfirst);
+  dfree(c->d_brec);
+  dfree(c->d_bout);
+  dfree(c->d_bfirst);
+  dfree(c->d_bgfirst);
   dfree(c->d_root);
   dfree(c->d_yslice);
   dfree(c->d_flags);

@@ -89,6 +89,13 @@ struct WorkArgs {
   const int* yslice;
   int nslices;
   int nsm;
+  // bispectrum output
+  int ncoeff;
+  const void* brec;       // YRec<R> records of the bispectrum terms
+  const int* bout;        // U element of every output group
+  const int* bfirst;      // [ncoeff+1] first term of each component
+  const int* bgfirst;     // [ncoeff+1] first output group of each component
+  double* B;              // [N][ncoeff]
   const void* rootpq;
 };
 
@@ -117,6 +124,7 @@ struct YiGeometry {
 YiGeometry yi_geometry(int rsize, int H, int n, int nsm);
 template <typename R> cudaError_t launch_de(const WorkArgs& a, cudaStream_t s);
 template <typename R> cudaError_t launch_force(const WorkArgs& a, cudaStream_t s);
+template <typename R> cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s);
 
 // Register column-chain kernels (snap_col_*.cu), for 1 <= twojmax <= 14;
 // cudaErrorInvalidValue when no instance exists for the precision/2J.

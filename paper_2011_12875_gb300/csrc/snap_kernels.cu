@@ -294,6 +294,66 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   for (; q < q1; ++q) y_term<R>(rec[q].w, rec[q].c, us, Yg, lane, y);
 }
 
+// ------------------------------------------------------- bispectrum B_l
+// Descriptor output (Sec. II-A, Eq. z): B_l = Re Z^t_{t1t2} : conj(U_t) for
+// every canonical component l, for 32 atoms per warp (lanes = atoms, U staged
+// in shared memory as in compute_Y).  One warp per component: its terms are
+// summed per output element and each output is dotted with conj(U_t).
+template <typename R, bool STAGED>
+__global__ void __launch_bounds__(256) bi_kernel(WorkArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long blk = blockIdx.x;
+  const int H = a.H;
+  const cx<R>* us = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
+  if (STAGED) {
+    cx<R>* su = reinterpret_cast<cx<R>*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(su + H * 32);
+    const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, bytes);
+      bulk_g2s(su, us, bytes, bar);
+    }
+    bool ok = false;
+    for (unsigned it = 0; it < kSpinLimit; ++it)
+      if (mbar_try_wait(bar, 0)) {
+        ok = true;
+        break;
+      }
+    if (!ok) {
+      if (threadIdx.x == 0) atomicMax(&a.flags[3], 1);
+      return;
+    }
+    us = su;
+  }
+  const int l = blockIdx.y * (blockDim.x >> 5) + warp;
+  if (l >= a.ncoeff) return;
+  const YRec<R>* __restrict__ rec = reinterpret_cast<const YRec<R>*>(a.brec);
+  int g = a.bgfirst[l];
+  R zr = R(0), zi = R(0), acc = R(0);
+  for (int q = a.bfirst[l]; q < a.bfirst[l + 1]; ++q) {
+    const unsigned w = rec[q].w;
+    const R c = rec[q].c;
+    const cx<R> u1 = us[(int)(w & 1023u) * 32 + lane];
+    const cx<R> u2 = us[(int)((w >> 10) & 1023u) * 32 + lane];
+    const R b = flip_if(u1.im, (w >> 20) & 1u);
+    const R d = flip_if(u2.im, (w >> 21) & 1u);
+    zr += c * (u1.re * u2.re - b * d);
+    zi += c * (u1.re * d + b * u2.re);
+    if (w & (1u << 22)) {
+      const cx<R> u = us[a.bout[g] * 32 + lane];
+      acc += u.re * zr + u.im * zi;
+      zr = R(0);
+      zi = R(0);
+      ++g;
+    }
+  }
+  const long i = blk * 32 + lane;
+  if (i < a.n) a.B[i * a.ncoeff + l] = (double)acc;
+}
+
 // ------------------------------------------------------ fused dU + dE/dr
 // One CTA per atom i with Y_i (weighted by half_weight) staged in shared
 // memory; one warp per pair.  For a pair, S(a, b) = sum_t Re Y_t : conj(u_t)
@@ -617,6 +677,23 @@ cudaError_t launch_force(const WorkArgs& a, cudaStream_t s) {
   force_kernel<R><<<dim3((a.n + 31) / 32, 32 / kForceWarps), kForceWarps * 32, 0, s>>>(a);
   return cudaGetLastError();
 }
+
+template <typename R>
+cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm);
+  dim3 grid(g.nblk, (a.ncoeff + 7) / 8);
+  if (g.staged) {
+    cudaError_t e = allow_smem(bi_kernel<R, true>, g.smem);
+    if (e != cudaSuccess) return e;
+    bi_kernel<R, true><<<grid, 256, g.smem, s>>>(a);
+  } else {
+    bi_kernel<R, false><<<grid, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_bi<float>(const WorkArgs&, cudaStream_t);
+template cudaError_t launch_bi<double>(const WorkArgs&, cudaStream_t);
 
 template cudaError_t launch_ui<float>(const WorkArgs&, cudaStream_t);
 template cudaError_t launch_ui<double>(const WorkArgs&, cudaStream_t);

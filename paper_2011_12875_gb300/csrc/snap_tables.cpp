@@ -188,6 +188,57 @@ void HostTables::build(int J2) {
       }
   term_out_first.push_back((int)terms.size());
 
+  // Bispectrum term list (descriptor output, Eq. z): for every canonical
+  // component l = (t1 >= t2, t >= t1), for every half-layout element (t, ma,
+  // mb) with a nonzero half weight w,
+  //   B_l += Re( conj(U_t[ma][mb]) * w * sum C(ma1,ma2) C(mb1,mb2) U_t1 U_t2 ),
+  // so B_l = Re Z^t_{t1t2} : conj(U_t) over the full matrix.  The records
+  // use the compute_Y format with w folded into the coefficient; bit 22 ends
+  // an output element, bit 23 ends a component; bout holds the U_t element
+  // index of every output group in order.
+  bterms.clear();
+  bterm_coef.clear();
+  bout.clear();
+  bcomp_first.clear();
+  bgroup_first.clear();
+  for (int q = 0; q < (int)ztrip.size(); ++q) {
+    const ZTrip& z = ztrip[q];
+    if (z.t < z.t1) continue;  // canonical components only
+    bcomp_first.push_back((int)bterms.size());
+    bgroup_first.push_back((int)bout.size());
+    const int t = z.t, dl = (z.t1 + z.t2 - t) / 2;
+    for (int mb = 0; 2 * mb <= t; ++mb)
+      for (int ma = 0; ma <= t; ++ma) {
+        const int wgt = (2 * mb < t) ? 2 : (ma < mb ? 2 : (ma == mb ? 1 : 0));
+        if (wgt == 0) continue;
+        const size_t first = bterms.size();
+        for (int mb1 = std::max(0, mb + dl - z.t2); mb1 <= std::min(z.t1, mb + dl); ++mb1) {
+          const int mb2 = mb + dl - mb1;
+          const double cb = cg[z.cg_off + mb1 * (z.t2 + 1) + mb2];
+          if (cb == 0.0) continue;
+          for (int ma1 = std::max(0, ma + dl - z.t2); ma1 <= std::min(z.t1, ma + dl); ++ma1) {
+            const int ma2 = ma + dl - ma1;
+            const double ca = cg[z.cg_off + ma1 * (z.t2 + 1) + ma2];
+            if (ca == 0.0) continue;
+            int i1, c1, i2, c2;
+            double s1, s2;
+            half_elem(z.t1, ma1, mb1, i1, c1, s1);
+            half_elem(z.t2, ma2, mb2, i2, c2, s2);
+            bterms.push_back((unsigned)i1 | ((unsigned)i2 << 10) | ((unsigned)c1 << 20) |
+                             ((unsigned)c2 << 21));
+            bterm_coef.push_back(wgt * ca * cb * s1 * s2);
+          }
+        }
+        if (bterms.size() > first) {
+          bterms.back() |= (1u << 22);
+          bout.push_back(half_base(t) + mb * (t + 1) + ma);
+        }
+      }
+    bterms.back() |= (1u << 23);
+  }
+  bcomp_first.push_back((int)bterms.size());
+  bgroup_first.push_back((int)bout.size());
+
   rootpq.assign(kRootDim * kRootDim, 0.0);
   for (int p = 0; p < kRootDim; ++p)
     for (int q = 1; q < kRootDim; ++q) rootpq[p * kRootDim + q] = std::sqrt((double)p / (double)q);
@@ -204,6 +255,22 @@ std::vector<double> HostTables::term_coef(const double* beta) const {
   std::vector<double> c(terms.size());
   for (size_t k = 0; k < terms.size(); ++k) c[k] = term_cg[k] * bw[term_trip[k]];
   return c;
+}
+
+std::vector<int> HostTables::bslices(int nslices) const {
+  // contiguous runs of components with about equal term counts
+  const long total = (long)bterms.size();
+  std::vector<int> b(1, 0);
+  int k = 1;
+  for (int l = 0; l < ncoeff; ++l) {
+    if (k < nslices && (long)bcomp_first[l + 1] * nslices >= total * k) {
+      b.push_back(l + 1);
+      ++k;
+    }
+  }
+  while ((int)b.size() < nslices + 1) b.push_back(ncoeff);
+  b[nslices] = ncoeff;
+  return b;
 }
 
 std::vector<int> HostTables::slices(int nslices) const {

@@ -23,12 +23,20 @@ struct HostTables {
   std::vector<double> term_cg;
   std::vector<int> term_trip;
   std::vector<int> term_out_first;  // [H+1] first term of every output
+  // bispectrum terms (records as above, coefficient without beta), the U
+  // element of each output group, and the first term of each component
+  std::vector<unsigned> bterms;
+  std::vector<double> bterm_coef;
+  std::vector<int> bout;
+  std::vector<int> bcomp_first;
+  std::vector<int> bgroup_first;  // [ncoeff+1] first output group of each component
   std::vector<double> rootpq;
 
   void build(int twojmax);
   std::vector<double> beta_weights(const double* beta) const;
   std::vector<double> term_coef(const double* beta) const;
   std::vector<int> slices(int nslices) const;
+  std::vector<int> bslices(int nslices) const;
 };
 
 double clebsch_gordan(int tj1, int tm1, int tj2, int tm2, int tj, int tm);

@@ -40,7 +40,7 @@ EXPORTS = ("snap_num_coeff", "snap_create", "snap_set_beta", "snap_set_neigh_cap
            "snap_neigh_max", "snap_compute", "snap_compute_async", "snap_sync",
            "snap_compute_host", "snap_get_buffer", "snap_half_index", "snap_half_size",
            "snap_destroy", "snap_last_error", "snap_profile", "snap_profile_read",
-           "snap_stage_name", "snap_launches_per_call")
+           "snap_stage_name", "snap_launches_per_call", "snap_compute_bispectrum")
 NSTAGES = 6
 
 _lib = None
@@ -86,6 +86,8 @@ def load(path: str | None = None):
     L.snap_stage_name.restype = ctypes.c_char_p
     L.snap_launches_per_call.argtypes = [p]
     L.snap_launches_per_call.restype = i
+    L.snap_compute_bispectrum.argtypes = [p, i, p, p, p, p, p, i, p, p]
+    L.snap_compute_bispectrum.restype = i
     L.snap_compute_host.argtypes = [p, i, p, p, p, p, p, p]
     L.snap_compute_host.restype = i
     L.snap_get_buffer.argtypes = [p, i, p, ctypes.c_size_t]
@@ -199,6 +201,28 @@ class Snap:
                        _t_ptr(img), cap, _t_ptr(energy), _t_ptr(forces), _t_ptr(virial),
                        ctypes.c_void_p(stream)))
         return energy, forces, virial
+
+    def bispectrum(self, pos, box, out=None, neighbors=None, stream=None):
+        """Bispectrum components B [N, N_B] (float64 device tensor)."""
+        import torch
+        if pos.dtype != torch.float64 or not pos.is_cuda or not pos.is_contiguous():
+            raise ValueError("pos must be a contiguous float64 CUDA tensor")
+        n = pos.shape[0]
+        nc = self._lib.snap_num_coeff(self.twojmax)
+        if out is None:
+            out = torch.empty((n, nc), dtype=torch.float64, device=pos.device)
+        boxa = np.ascontiguousarray(box, dtype=np.float64)
+        if stream is None:
+            stream = torch.cuda.current_stream(pos.device).cuda_stream
+        cnt = idx = img = None
+        cap = 0
+        if neighbors is not None:
+            cnt, idx, img = neighbors
+            cap = idx.shape[1]
+        self._check(self._lib.snap_compute_bispectrum(
+            self._h, n, _t_ptr(pos), _np_ptr(boxa), _t_ptr(cnt), _t_ptr(idx), _t_ptr(img), cap,
+            _t_ptr(out), ctypes.c_void_p(stream)))
+        return out
 
     def sync(self, stream=None):
         """Wait for the stream; raise if the last asynchronous compute failed."""
