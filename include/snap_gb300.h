@@ -150,6 +150,29 @@ int snap_compute_bispectrum(snap_ctx* ctx, int natoms, const double* pos, const 
                             const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
                             int nbr_cap, double* B, void* stream);
 
+/* Derivative of every atom's bispectrum along a displacement field g of the
+ * atoms (forward mode, dB/dr is never stored):
+ *   dB[i][l] = sum_k g_k . dB_l(i)/dr_k      (Sec. II-A, Eqs. z and dbidrk)
+ * g: device [N][3] doubles; dB: device [N][N_B] doubles.  Since
+ * F_k = -sum_i sum_l beta_l dB_l(i)/dr_k, the force-matching gradient is
+ * d(sum_k g_k . F_k)/d(beta_l) = -sum_i dB[i][l].  Other arguments as
+ * snap_compute.  Returns after the stream has finished. */
+int snap_bispectrum_deriv(snap_ctx* ctx, int natoms, const double* pos, const double* box,
+                          const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
+                          int nbr_cap, const double* g, double* dB, void* stream);
+
+/* Gradient of sum_i w_i E_i with respect to the positions, for the atoms,
+ * neighbour lists and dE_i/dr_ik of the last snap_compute /
+ * snap_compute_async on ctx (the adjoint backward of the per-atom energies):
+ *   grad[k] = sum_i w_i dE_i/dr_k,   w: device [N], grad: device [N][3].
+ * w = 1 gives -forces.  Enqueued on stream; returns SNAP_ERR_ARG if ctx has
+ * no energy evaluation. */
+int snap_force_weighted(snap_ctx* ctx, const double* weight, double* grad, void* stream);
+
+/* Number of evaluations enqueued on ctx so far (lets a caller check that the
+ * buffers used by snap_force_weighted are still those of its evaluation). */
+long long snap_generation(const snap_ctx* ctx);
+
 /* Same as snap_compute with HOST buffers and the device neighbour builder:
  * copies pos to the device, computes, and copies energy (may be NULL),
  * forces and virial (may be NULL) back, all on the given stream.  The host

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsnap_gb300.so")
 SOURCES = ["snap_api.cu", "snap_neigh.cu", "snap_kernels.cu", "snap_tables.cpp", "snap_noalloc.cu",
-           "snap_col_f32.cu"]
+           "snap_col_f32.cu", "snap_col_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -53,6 +53,10 @@ struct snap_ctx {
   double* d_dedr = nullptr;
   void* d_U = nullptr;  // complex AoSoA [ceil(N/32)][H][32]
   void* d_Y = nullptr;
+  void* d_dU = nullptr;  // tangent of U (bispectrum derivative)
+  long long generation = 0;  // number of evaluations enqueued
+  snap::WorkArgs last_args;   // arguments of the last evaluation (weighted gather)
+  bool have_last = false;
   double* d_vpart = nullptr;
   int* d_flags = nullptr;
   int* h_flags = nullptr;
@@ -173,6 +177,7 @@ void free_workspace(snap_ctx* c) {
   dfree(c->d_dedr);
   dfree(c->d_U);
   dfree(c->d_Y);
+  dfree(c->d_dU);
   dfree(c->d_vpart);
   c->cap_nk = 0;
   c->cap_n = 0;
@@ -197,6 +202,7 @@ int ensure_workspace(snap_ctx* c, int n, int K) {
   SNAP_CUDA(c, cudaMalloc(&c->d_dedr, sizeof(double) * 3 * nkcap));
   SNAP_CUDA(c, cudaMalloc(&c->d_U, uy));
   SNAP_CUDA(c, cudaMalloc(&c->d_Y, uy));
+  SNAP_CUDA(c, cudaMalloc(&c->d_dU, uy));
   // lanes past the last atom read zeros in compute_Y
   SNAP_CUDA(c, cudaMemset(c->d_U, 0, uy));
   SNAP_CUDA(c, cudaMalloc(&c->d_vpart, sizeof(double) * 6 * (4 * nblk + 1)));
@@ -222,10 +228,12 @@ bool box_ok(const double* box) {
 }
 
 // Enqueue the whole evaluation on stream s (no synchronisation).
-// mode 0: energy, forces, virial; mode 1: bispectrum components into B.
+// mode 0: energy, forces, virial; mode 1: bispectrum components into B;
+// mode 2: derivative of the bispectrum along the displacement field g into B.
 int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int* ucnt,
             const int* uidx, const signed char* uimg, int ucap, double* energy, double* forces,
-            double* virial, cudaStream_t s, int mode = 0, double* B = nullptr) {
+            double* virial, cudaStream_t s, int mode = 0, double* B = nullptr,
+            const double* g = nullptr) {
   const bool user = (ucnt || uidx || uimg);
   if (user && (!ucnt || !uidx || !uimg || ucap < 1 || ucap > snap::kMaxNeighCap))
     return fail(c, SNAP_ERR_ARG, "neighbour list: cnt, idx and img must all be given with 1 <= cap <= 64");
@@ -337,9 +345,20 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   SNAP_CUDA(c, colk ? snap::launch_ui_col<float>(a, s)
                     : (mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s)));
   SNAP_CUDA(c, mark());
-  if (mode == 1) {
-    SNAP_CUDA(c, mixed ? snap::launch_bi<float>(a, s) : snap::launch_bi<double>(a, s));
-    c->launches += 1;
+  c->generation += 1;
+  c->last_args = a;
+  c->have_last = (mode == 0);
+  if (mode == 1 || mode == 2) {
+    if (mode == 1) {
+      SNAP_CUDA(c, mixed ? snap::launch_bi<float>(a, s) : snap::launch_bi<double>(a, s));
+      c->launches += 1;
+    } else {
+      SNAP_CUDA(c, mixed ? snap::launch_tan_col<float>(a, g, c->d_dU, s)
+                         : snap::launch_tan_col<double>(a, g, c->d_dU, s));
+      SNAP_CUDA(c, mixed ? snap::launch_dbi<float>(a, c->d_dU, B, s)
+                         : snap::launch_dbi<double>(a, c->d_dU, B, s));
+      c->launches += 2;
+    }
     SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
     c->last_n = n;
     c->last_K = K;
@@ -571,6 +590,33 @@ int snap_compute_bispectrum(snap_ctx* c, int natoms, const double* pos, const do
   SNAP_CUDA(c, cudaStreamSynchronize(s));
   return check_flags(c);
 }
+
+int snap_bispectrum_deriv(snap_ctx* c, int natoms, const double* pos, const double* box,
+                          const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
+                          int nbr_cap, const double* g, double* dB, void* stream) {
+  if (!c) return SNAP_ERR_ARG;
+  if (natoms < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
+  if (!box_ok(box)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+  if (natoms == 0) return SNAP_OK;
+  if (!pos || !g || !dB) return fail(c, SNAP_ERR_ARG, "pos, g and dB are required");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = enqueue(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, nullptr, nullptr, nullptr, s,
+                   2, dB, g);
+  if (rc) return rc;
+  SNAP_CUDA(c, cudaStreamSynchronize(s));
+  return check_flags(c);
+}
+
+int snap_force_weighted(snap_ctx* c, const double* weight, double* grad, void* stream) {
+  if (!c) return SNAP_ERR_ARG;
+  if (!c->have_last) return fail(c, SNAP_ERR_ARG, "no energy/force evaluation to differentiate");
+  if (!weight || !grad) return fail(c, SNAP_ERR_ARG, "weight and grad are required");
+  if (c->last_n == 0) return SNAP_OK;
+  SNAP_CUDA(c, snap::launch_force_weighted(c->last_args, weight, grad, (cudaStream_t)stream));
+  return SNAP_OK;
+}
+
+long long snap_generation(const snap_ctx* c) { return c ? c->generation : -1; }
 
 int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const double* box,
                       double* energy_host, double* forces_host, double* virial_host, void* stream) {

@@ -341,6 +341,120 @@ __global__ void __launch_bounds__(NW * 32) de_col_kernel(WorkArgs a) {
   }
 }
 
+// ------------------------------------------- tangent of Ulisttot along g
+// Forward-mode derivative of Eq. (u) along a displacement field g of the
+// atoms: the pair (i, k) moves by delta = g_k - g_i, so
+//   dU_t = sum_k d/de [ f_c(r_ik + e delta) u_t(r_ik + e delta) ] at e = 0
+//        = sum_k (grad f_c . delta) u_t + f_c (du_t/dr . delta).
+// One tangent chain rides along the layer recursion (the recursion is linear
+// in u, so the tangent obeys the differentiated recursion with conj(da) and
+// conj(db) along delta).  Layout and accumulation as ui_col_kernel; no w_self.
+template <typename R, int J2, int NW>
+__global__ void __launch_bounds__(NW * 32) tan_col_kernel(WorkArgs a, const double* __restrict__ gd,
+                                                          void* dUout) {
+  using S = Shape<J2>;
+  constexpr int NC = S::NC, P = S::P;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int H = a.H;
+  c2<R>* acc = reinterpret_cast<c2<R>*>(smem);  // [NW*P][H]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / NC, mb = lane - g * NC;
+  const bool grp = g < P;
+  const int i = blockIdx.x;
+  for (int e = threadIdx.x; e < NW * P * H; e += blockDim.x) acc[e] = mk<R>(0, 0);
+  __syncthreads();
+  c2<R>* my = acc + (warp * P + (grp ? g : 0)) * H;
+  R rs[J2 + 1];
+#pragma unroll
+  for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
+  const int cnt = a.cnt[i];
+  for (int s0 = warp * P; s0 < cnt; s0 += NW * P) {
+    const int s = s0 + g;
+    const bool ok = grp && s < cnt;
+    c2<R> ca = mk<R>(1, 0), cb = mk<R>(0, 0), cda = mk<R>(0, 0), cdb = mk<R>(0, 0);
+    R fc = 0, dfc = 0;
+    if (ok) {
+      const long slot = (long)i * a.K + s;
+      const R* gm = reinterpret_cast<const R*>(a.geom) + slot * kGeomStride;
+      const int k = a.nbr[slot];
+      R dl[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) dl[d] = (R)(gd[3 * (long)k + d] - gd[3 * (long)i + d]);
+      ca = mk<R>(gm[0], -gm[1]);
+      cb = mk<R>(gm[2], -gm[3]);
+      fc = gm[4];
+      R ar = 0, ai = 0, br = 0, bi = 0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        dfc += dl[d] * gm[5 + d];
+        ar += dl[d] * gm[8 + 2 * d];
+        ai += dl[d] * gm[9 + 2 * d];
+        br += dl[d] * gm[14 + 2 * d];
+        bi += dl[d] * gm[15 + 2 * d];
+      }
+      cda = mk<R>(ar, -ai);  // conj(da along delta)
+      cdb = mk<R>(br, -bi);
+    }
+    c2<R> u[J2 + 1], du[J2 + 1];
+#pragma unroll
+    for (int k = 0; k <= J2; ++k) u[k] = du[k] = mk<R>(0, 0);
+    if (mb == 0) u[0] = mk<R>(1, 0);
+    if (ok && mb == 0) my[0].re += dfc;
+    static_for<1, J2>([&](auto tc) {
+      constexpr int t = decltype(tc)::value;
+      if constexpr ((t & 1) == 0) {
+        seed_column<R, t>(u, mb == t / 2);
+        seed_column<R, t>(du, mb == t / 2);
+      }
+      const R r = rs[t];
+      const c2<R> A = mk<R>(r * ca.re, r * ca.im), B = mk<R>(r * cb.re, r * cb.im);
+      const c2<R> dA = mk<R>(r * cda.re, r * cda.im), dB = mk<R>(r * cdb.re, r * cdb.im);
+#pragma unroll
+      for (int ma = t; ma >= 0; --ma) {
+        c2<R> v = mk<R>(0, 0), dv = mk<R>(0, 0);
+        if (ma < t) {
+          const R c = sqrt_int<R>(t - ma);
+          const c2<R> p = u[ma], q = du[ma];
+          v.re = c * (A.re * p.re - A.im * p.im);
+          v.im = c * (A.re * p.im + A.im * p.re);
+          dv.re = c * (dA.re * p.re - dA.im * p.im + A.re * q.re - A.im * q.im);
+          dv.im = c * (dA.re * p.im + dA.im * p.re + A.re * q.im + A.im * q.re);
+        }
+        if (ma > 0) {
+          const R c = sqrt_int<R>(ma);
+          const c2<R> p = u[ma - 1], q = du[ma - 1];
+          v.re -= c * (B.re * p.re - B.im * p.im);
+          v.im -= c * (B.re * p.im + B.im * p.re);
+          dv.re -= c * (dB.re * p.re - dB.im * p.im + B.re * q.re - B.im * q.im);
+          dv.im -= c * (dB.re * p.im + dB.im * p.re + B.re * q.im + B.im * q.re);
+        }
+        u[ma] = v;
+        du[ma] = dv;
+      }
+      if (ok && 2 * mb <= t) {
+        c2<R>* dst = my + half_base(t) + mb * (t + 1);
+#pragma unroll
+        for (int ma = 0; ma <= t; ++ma) {
+          dst[ma].re += dfc * u[ma].re + fc * du[ma].re;
+          dst[ma].im += dfc * u[ma].im + fc * du[ma].im;
+        }
+      }
+    });
+  }
+  __syncthreads();
+  c2<R>* Ug = reinterpret_cast<c2<R>*>(dUout);
+  const long blk = i >> 5;
+  const int li = i & 31;
+  for (int e = threadIdx.x; e < H; e += blockDim.x) {
+    R sr = 0, si = 0;
+    for (int c = 0; c < NW * P; ++c) {
+      sr += acc[c * H + e].re;
+      si += acc[c * H + e].im;
+    }
+    Ug[(blk * H + e) * 32 + li] = mk<R>(sr, si);
+  }
+}
+
 template <typename K>
 inline cudaError_t col_allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
@@ -364,6 +478,15 @@ cudaError_t launch_de_col_t(const WorkArgs& a, cudaStream_t s) {
   cudaError_t e = col_allow_smem(de_col_kernel<R, J2, kColWarps>, sm);
   if (e != cudaSuccess) return e;
   de_col_kernel<R, J2, kColWarps><<<a.n, kColWarps * 32, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, int J2>
+cudaError_t launch_tan_col_t(const WorkArgs& a, const double* g, void* dU, cudaStream_t s) {
+  const size_t sm = sizeof(c2<R>) * (size_t)kColWarps * Shape<J2>::P * a.H;
+  cudaError_t e = col_allow_smem(tan_col_kernel<R, J2, kColWarps>, sm);
+  if (e != cudaSuccess) return e;
+  tan_col_kernel<R, J2, kColWarps><<<a.n, kColWarps * 32, sm, s>>>(a, g, dU);
   return cudaGetLastError();
 }
 

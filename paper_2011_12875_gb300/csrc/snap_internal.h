@@ -130,5 +130,12 @@ template <typename R> cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s);
 // cudaErrorInvalidValue when no instance exists for the precision/2J.
 template <typename R> cudaError_t launch_ui_col(const WorkArgs& a, cudaStream_t s);
 template <typename R> cudaError_t launch_de_col(const WorkArgs& a, cudaStream_t s);
+// Tangent of Ulisttot along the displacement field g ([N][3], device); 0..14.
+template <typename R>
+cudaError_t launch_tan_col(const WorkArgs& a, const double* g, void* dU, cudaStream_t s);
+
+// d B_l along the tangent dU (snap_kernels.cu) and the weighted force gather.
+template <typename R> cudaError_t launch_dbi(const WorkArgs& a, const void* dU, double* dB, cudaStream_t s);
+cudaError_t launch_force_weighted(const WorkArgs& a, const double* w, double* grad, cudaStream_t s);
 
 }  // namespace snap

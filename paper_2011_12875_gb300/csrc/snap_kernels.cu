@@ -354,6 +354,102 @@ __global__ void __launch_bounds__(256) bi_kernel(WorkArgs a) {
   if (i < a.n) a.B[i * a.ncoeff + l] = (double)acc;
 }
 
+// ------------------------------------------- d B_l along a displacement
+// Directional derivative of the bispectrum (Eq. z) along the tangent dU of
+// Ulisttot: B_l is trilinear in (U_t1, U_t2, conj U_t), so
+//   dB_l = Re [ (Z(dU_t1, U_t2) + Z(U_t1, dU_t2)) : conj(U_t) + Z : conj(dU_t) ],
+// the same term list as bi_kernel (dU has the inversion symmetry of U, so
+// the conjugation flags apply to both).  U is staged as in bi_kernel; dU is
+// read from global memory.
+template <typename R, bool STAGED>
+__global__ void __launch_bounds__(256) dbi_kernel(WorkArgs a, const cx<R>* __restrict__ dUg, double* dB) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long blk = blockIdx.x;
+  const int H = a.H;
+  const cx<R>* us = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
+  const cx<R>* ds = dUg + blk * H * 32;
+  if (STAGED) {
+    cx<R>* su = reinterpret_cast<cx<R>*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(su + H * 32);
+    const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, bytes);
+      bulk_g2s(su, us, bytes, bar);
+    }
+    bool ok = false;
+    for (unsigned it = 0; it < kSpinLimit; ++it)
+      if (mbar_try_wait(bar, 0)) {
+        ok = true;
+        break;
+      }
+    if (!ok) {
+      if (threadIdx.x == 0) atomicMax(&a.flags[3], 1);
+      return;
+    }
+    us = su;
+  }
+  const int l = blockIdx.y * (blockDim.x >> 5) + warp;
+  if (l >= a.ncoeff) return;
+  const YRec<R>* __restrict__ rec = reinterpret_cast<const YRec<R>*>(a.brec);
+  int g = a.bgfirst[l];
+  R zr = R(0), zi = R(0), dzr = R(0), dzi = R(0), acc = R(0);
+  for (int q = a.bfirst[l]; q < a.bfirst[l + 1]; ++q) {
+    const unsigned w = rec[q].w;
+    const R c = rec[q].c;
+    const int e1 = (int)(w & 1023u), e2 = (int)((w >> 10) & 1023u);
+    const unsigned f1 = (w >> 20) & 1u, f2 = (w >> 21) & 1u;
+    const cx<R> u1 = us[e1 * 32 + lane], u2 = us[e2 * 32 + lane];
+    const cx<R> d1 = ds[e1 * 32 + lane], d2 = ds[e2 * 32 + lane];
+    const R b = flip_if(u1.im, f1), d = flip_if(u2.im, f2);
+    const R db1 = flip_if(d1.im, f1), db2 = flip_if(d2.im, f2);
+    zr += c * (u1.re * u2.re - b * d);
+    zi += c * (u1.re * d + b * u2.re);
+    // d(u1 u2) = du1 u2 + u1 du2
+    dzr += c * (d1.re * u2.re - db1 * d + u1.re * d2.re - b * db2);
+    dzi += c * (d1.re * d + db1 * u2.re + u1.re * db2 + b * d2.re);
+    if (w & (1u << 22)) {
+      const int o = a.bout[g];
+      const cx<R> u = us[o * 32 + lane], du = ds[o * 32 + lane];
+      acc += u.re * dzr + u.im * dzi + du.re * zr + du.im * zi;
+      zr = zi = dzr = dzi = R(0);
+      ++g;
+    }
+  }
+  const long i = blk * 32 + lane;
+  if (i < a.n) dB[i * a.ncoeff + l] = (double)acc;
+}
+
+// ------------------------------------------- weighted force (autograd)
+// grad_k = sum_i w_i dE_i/dr_k = -( w_k sum_s dE_k/dr_ks - sum_s w_{k_s} dE_{k_s}/dr_{k_s,k} ),
+// gathered through the reverse-slot map like the forces (w = 1 gives -F).
+__global__ void __launch_bounds__(256) force_weighted_kernel(WorkArgs a, const double* __restrict__ wt,
+                                                             double* __restrict__ grad) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long k = (long)blockIdx.x * 8 + warp;
+  if (k >= a.n) return;
+  const double wk = wt[k];
+  double f[3] = {0, 0, 0};
+  const int cnt = a.cnt[k];
+  for (int s = lane; s < cnt; s += 32) {
+    const long q = k * a.K + s;
+    const int j = a.nbr[q];
+    const int r = a.rev[q];
+    const double* d = a.dedr + q * 3;
+    for (int c = 0; c < 3; ++c) f[c] += wk * d[c];
+    if (r >= 0) {
+      const double wj = wt[j];
+      const double* dj = a.dedr + ((long)j * a.K + r) * 3;
+      for (int c = 0; c < 3; ++c) f[c] -= wj * dj[c];
+    }
+  }
+  for (int c = 0; c < 3; ++c) f[c] = warp_sum(f[c]);
+  if (lane == 0)
+    for (int c = 0; c < 3; ++c) grad[3 * k + c] = -f[c];
+}
+
 // ------------------------------------------------------ fused dU + dE/dr
 // One CTA per atom i with Y_i (weighted by half_weight) staged in shared
 // memory; one warp per pair.  For a pair, S(a, b) = sum_t Re Y_t : conj(u_t)
@@ -694,6 +790,30 @@ cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s) {
 }
 template cudaError_t launch_bi<float>(const WorkArgs&, cudaStream_t);
 template cudaError_t launch_bi<double>(const WorkArgs&, cudaStream_t);
+
+template <typename R>
+cudaError_t launch_dbi(const WorkArgs& a, const void* dU, double* dB, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm);
+  dim3 grid(g.nblk, (a.ncoeff + 7) / 8);
+  const cx<R>* d = reinterpret_cast<const cx<R>*>(dU);
+  if (g.staged) {
+    cudaError_t e = allow_smem(dbi_kernel<R, true>, g.smem);
+    if (e != cudaSuccess) return e;
+    dbi_kernel<R, true><<<grid, 256, g.smem, s>>>(a, d, dB);
+  } else {
+    dbi_kernel<R, false><<<grid, 256, 0, s>>>(a, d, dB);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_dbi<float>(const WorkArgs&, const void*, double*, cudaStream_t);
+template cudaError_t launch_dbi<double>(const WorkArgs&, const void*, double*, cudaStream_t);
+
+cudaError_t launch_force_weighted(const WorkArgs& a, const double* w, double* grad, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  force_weighted_kernel<<<(a.n + 7) / 8, 256, 0, s>>>(a, w, grad);
+  return cudaGetLastError();
+}
 
 template cudaError_t launch_ui<float>(const WorkArgs&, cudaStream_t);
 template cudaError_t launch_ui<double>(const WorkArgs&, cudaStream_t);

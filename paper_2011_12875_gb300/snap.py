@@ -40,7 +40,8 @@ EXPORTS = ("snap_num_coeff", "snap_create", "snap_set_beta", "snap_set_neigh_cap
            "snap_neigh_max", "snap_compute", "snap_compute_async", "snap_sync",
            "snap_compute_host", "snap_get_buffer", "snap_half_index", "snap_half_size",
            "snap_destroy", "snap_last_error", "snap_profile", "snap_profile_read",
-           "snap_stage_name", "snap_launches_per_call", "snap_compute_bispectrum")
+           "snap_stage_name", "snap_launches_per_call", "snap_compute_bispectrum",
+           "snap_bispectrum_deriv", "snap_force_weighted", "snap_generation")
 NSTAGES = 6
 
 _lib = None
@@ -88,6 +89,12 @@ def load(path: str | None = None):
     L.snap_launches_per_call.restype = i
     L.snap_compute_bispectrum.argtypes = [p, i, p, p, p, p, p, i, p, p]
     L.snap_compute_bispectrum.restype = i
+    L.snap_bispectrum_deriv.argtypes = [p, i, p, p, p, p, p, i, p, p, p]
+    L.snap_bispectrum_deriv.restype = i
+    L.snap_force_weighted.argtypes = [p, p, p, p]
+    L.snap_force_weighted.restype = i
+    L.snap_generation.argtypes = [p]
+    L.snap_generation.restype = ctypes.c_longlong
     L.snap_compute_host.argtypes = [p, i, p, p, p, p, p, p]
     L.snap_compute_host.restype = i
     L.snap_get_buffer.argtypes = [p, i, p, ctypes.c_size_t]
@@ -223,6 +230,46 @@ class Snap:
             self._h, n, _t_ptr(pos), _np_ptr(boxa), _t_ptr(cnt), _t_ptr(idx), _t_ptr(img), cap,
             _t_ptr(out), ctypes.c_void_p(stream)))
         return out
+
+    def bispectrum_deriv(self, pos, box, g, out=None, neighbors=None, stream=None):
+        """dB[i, l] = sum_k g_k . dB_l(i)/dr_k for a displacement field g [N, 3]."""
+        import torch
+        for t in (pos, g):
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("pos and g must be contiguous float64 CUDA tensors")
+        n = pos.shape[0]
+        nc = self._lib.snap_num_coeff(self.twojmax)
+        if out is None:
+            out = torch.empty((n, nc), dtype=torch.float64, device=pos.device)
+        boxa = np.ascontiguousarray(box, dtype=np.float64)
+        if stream is None:
+            stream = torch.cuda.current_stream(pos.device).cuda_stream
+        cnt = idx = img = None
+        cap = 0
+        if neighbors is not None:
+            cnt, idx, img = neighbors
+            cap = idx.shape[1]
+        self._check(self._lib.snap_bispectrum_deriv(
+            self._h, n, _t_ptr(pos), _np_ptr(boxa), _t_ptr(cnt), _t_ptr(idx), _t_ptr(img), cap,
+            _t_ptr(g), _t_ptr(out), ctypes.c_void_p(stream)))
+        return out
+
+    def force_weighted(self, weight, out=None, stream=None):
+        """Gradient of sum_i w_i E_i w.r.t. positions for the last evaluation."""
+        import torch
+        if weight.dtype != torch.float64 or not weight.is_cuda or not weight.is_contiguous():
+            raise ValueError("weight must be a contiguous float64 CUDA tensor")
+        n = weight.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float64, device=weight.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(weight.device).cuda_stream
+        self._check(self._lib.snap_force_weighted(self._h, _t_ptr(weight), _t_ptr(out),
+                                                  ctypes.c_void_p(stream)))
+        return out
+
+    def generation(self) -> int:
+        return int(self._lib.snap_generation(self._h))
 
     def sync(self, stream=None):
         """Wait for the stream; raise if the last asynchronous compute failed."""

@@ -55,3 +55,114 @@ def test_bispectrum_full_size_and_energy_identity(snapmod):
     _, ref = O.evaluate(O.Params(8), beta, cfg.pos, cfg.box, want_B=True)
     assert rel_err(B, ref.B) <= FP64_TOL
     np.testing.assert_allclose(beta[0] + B @ beta[1:], E.cpu().numpy(), rtol=1e-12)
+
+
+def oracle_weighted_grad(pairs, dedr, w, n):
+    """sum_i w_i dE_i/dr_k from the oracle's per-pair dE_i/dr_ik."""
+    g = np.zeros((n, 3))
+    np.add.at(g, pairs.k, w[pairs.i][:, None] * dedr)
+    np.add.at(g, pairs.i, -w[pairs.i][:, None] * dedr)
+    return g
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_weighted_force_and_autograd(snapmod, prec):
+    """Backward of the per-atom energies: grad_k = sum_i w_i dE_i/dr_k for
+    random upstream weights, through torch.autograd and the C ABI."""
+    from paper_2011_12875_gb300 import autograd as AG
+    cfg = inputs.bcc(3, disp=0.15, seed=21)
+    beta = inputs.beta(8)
+    n = cfg.natoms
+    pairs, ref = O.evaluate(O.Params(8), beta, cfg.pos, cfg.box)
+    w = np.random.Generator(np.random.PCG64(5)).uniform(-1, 1, n)
+    want = oracle_weighted_grad(pairs, ref.dedr, w, n)
+    s = snapmod.Snap(8, beta, precision=prec)
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device="cuda:0", requires_grad=True)
+    E = AG.energy(s, pos, cfg.box)
+    wt = torch.tensor(w, device="cuda:0")
+    (gpos,) = torch.autograd.grad((E * wt).sum(), pos)
+    tol = FP64_TOL if prec == 0 else 2e-4
+    assert rel_err(gpos.cpu().numpy(), want) <= tol
+    # uniform weights give minus the forces
+    _, F, _ = s.compute(pos.detach(), cfg.box)
+    g1 = s.force_weighted(torch.ones(n, dtype=torch.float64, device="cuda:0"))
+    assert rel_err(g1.cpu().numpy(), -F.cpu().numpy()) <= 1e-14
+    s.close()
+
+
+def test_autograd_matches_energy_finite_differences(snapmod):
+    """d(sum_i c_i E_i)/dr by central differences of the GPU FP64 energies."""
+    from paper_2011_12875_gb300 import autograd as AG
+    cfg = inputs.bcc(2, disp=0.15, seed=22)
+    beta = inputs.beta(6)
+    s = snapmod.Snap(6, beta)
+    n = cfg.natoms
+    c = torch.tensor(np.random.Generator(np.random.PCG64(6)).uniform(0.5, 1.5, n), device="cuda:0")
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device="cuda:0", requires_grad=True)
+    (g,) = torch.autograd.grad((AG.energy(s, pos, cfg.box) * c).sum(), pos)
+    g = g.cpu().numpy()
+    h = 1e-5
+    for a in (0, 5, n - 1):
+        for d in range(3):
+            vals = []
+            for sgn in (1, -1):
+                q = cfg.pos.copy()
+                q[a, d] += sgn * h
+                E, _, _ = s.compute(torch.tensor(q, device="cuda:0"), cfg.box)
+                vals.append(float((E * c).sum()))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert fd == pytest.approx(g[a, d], abs=1e-6 * np.abs(g).max())
+    s.close()
+
+
+@pytest.mark.parametrize("prec,twojmax", [(0, 2), (0, 5), (0, 8), (1, 8), (0, 14), (1, 14)])
+def test_bispectrum_derivative_vs_oracle_differences(snapmod, prec, twojmax):
+    """dB[i][l] = sum_k g_k . dB_l(i)/dr_k against central differences of the
+    oracle's B along g (h = 1e-5 A)."""
+    cfg = inputs.bcc(2, disp=0.15, seed=23)
+    beta = inputs.beta(twojmax)
+    p = O.Params(twojmax)
+    g = np.random.Generator(np.random.PCG64(7)).normal(size=cfg.pos.shape)
+    h = 1e-5
+    _, bp = O.evaluate(p, beta, cfg.pos + h * g, cfg.box, want_B=True)
+    _, bm = O.evaluate(p, beta, cfg.pos - h * g, cfg.box, want_B=True)
+    fd = (bp.B - bm.B) / (2 * h)
+    s = snapmod.Snap(twojmax, beta, precision=prec)
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device="cuda:0")
+    dB = s.bispectrum_deriv(pos, cfg.box, torch.tensor(g, device="cuda:0")).cpu().numpy()
+    s.close()
+    assert rel_err(dB, fd) <= (2e-7 if prec == 0 else 3e-5)
+
+
+def test_force_matching_gradient(snapmod):
+    """dL/dbeta from the bispectrum derivative equals central differences of
+    L(beta) = sum |F(beta) - F_ref|^2 (exact: L is quadratic in beta), and
+    -sum_i sum_l beta_l dB_g[i][l] equals sum_k g_k . F_k."""
+    from paper_2011_12875_gb300 import autograd as AG
+    cfg = inputs.bcc(3, disp=0.2, seed=24)
+    beta = inputs.beta(6)
+    s = snapmod.Snap(6, beta)
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device="cuda:0")
+    f_ref = torch.tensor(np.random.Generator(np.random.PCG64(8)).normal(size=cfg.pos.shape),
+                         device="cuda:0")
+    loss, grad = AG.force_matching_grad(s, pos, cfg.box, f_ref)
+    grad = grad.cpu().numpy()
+    assert grad[0] == 0.0
+    _, F, _ = s.compute(pos, cfg.box)
+    g = 2 * (F - f_ref)
+    dB = s.bispectrum_deriv(pos, cfg.box, g.contiguous()).cpu().numpy()
+    lhs = -(dB @ beta[1:]).sum()
+    rhs = float((g * F).sum())
+    assert lhs == pytest.approx(rhs, rel=1e-10)
+    h = 1e-3
+    for l in (1, 7, len(beta) - 1):
+        vals = []
+        for sgn in (1, -1):
+            b = beta.copy()
+            b[l] += sgn * h
+            s.set_beta(b)
+            _, Fb, _ = s.compute(pos, cfg.box)
+            vals.append(float(((Fb - f_ref) ** 2).sum()))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert fd == pytest.approx(grad[l], rel=1e-8, abs=1e-8 * np.abs(grad).max())
+    s.close()
