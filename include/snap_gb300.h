@@ -173,6 +173,35 @@ int snap_force_weighted(snap_ctx* ctx, const double* weight, double* grad, void*
  * buffers used by snap_force_weighted are still those of its evaluation). */
 long long snap_generation(const snap_ctx* ctx);
 
+/* Many independent configurations in one evaluation: their atoms are
+ * concatenated and every stage runs once over all of them (one launch per
+ * stage), or, with use_graph != 0, as one CUDA graph captured on the first
+ * call for this batch shape and these buffers and replayed afterwards.
+ *   nconf   : number of configurations
+ *   natoms  : HOST [nconf] atom counts (configuration k owns atoms
+ *             start_k .. start_k + natoms[k] - 1, start_k = sum of earlier counts)
+ *   boxes   : HOST [nconf][3] orthorhombic box lengths
+ *   pos     : device [sum natoms][3]; energy device [sum natoms] or NULL;
+ *             forces device [sum natoms][3]; virial device [nconf][6] or NULL
+ * Asynchronous like snap_compute_async (status of the device-side checks
+ * from snap_sync).  Results equal those of one snap_compute per
+ * configuration (virial up to summation order). */
+int snap_compute_batch(snap_ctx* ctx, int nconf, const int* natoms, const double* boxes,
+                       const double* pos, double* energy, double* forces, double* virial,
+                       int use_graph, void* stream);
+
+/* Launch-shape tunables: col_warps (2, 4 or 8 warps per CTA, i.e. neighbour
+ * pairs per CTA, of the register column-chain kernels) and yi_waves (1..8,
+ * compute_Y work items per SM).  snap_autotune times every combination of
+ * col_warps in {2, 4, 8} and yi_waves in {1, 2, 4} on the given batch
+ * (reps timed calls each, CUDA events on `stream`), keeps the fastest, and
+ * reports its median time in *best_ms.  Synchronous. */
+int snap_set_tuning(snap_ctx* ctx, int col_warps, int yi_waves);
+int snap_get_tuning(const snap_ctx* ctx, int* col_warps, int* yi_waves);
+int snap_autotune(snap_ctx* ctx, int nconf, const int* natoms, const double* boxes,
+                  const double* pos, double* energy, double* forces, double* virial, int reps,
+                  double* best_ms, void* stream);
+
 /* Same as snap_compute with HOST buffers and the device neighbour builder:
  * copies pos to the device, computes, and copies energy (may be NULL),
  * forces and virial (may be NULL) back, all on the given stream.  The host

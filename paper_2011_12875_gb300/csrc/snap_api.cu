@@ -24,6 +24,8 @@ struct snap_ctx {
   HostTables tab;
   std::vector<double> beta;
   int K = 32;
+  int col_warps = 4;  // tunables (snap_set_tuning / snap_autotune)
+  int yi_waves = 2;
   int last_nmax = 0;
   int last_n = 0, last_K = 0;
   std::string err;
@@ -67,6 +69,19 @@ struct snap_ctx {
   double prof_ms[SNAP_NSTAGES] = {0};
   long long prof_calls[SNAP_NSTAGES] = {0};
   int launches = 0;
+
+  // batches of configurations
+  std::vector<int> bat_n;
+  std::vector<double> bat_box;
+  snap::NeighConf* d_confs = nullptr;
+  int2* d_ctamap = nullptr;
+  int bat_ncta = 0, bat_nconf = 0, bat_total = 0;
+  double* d_vatom = nullptr;
+  int cap_vatom = 0;
+  // captured CUDA graph of the last batch (shape and pointers baked in)
+  cudaStream_t gstream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_key[4] = {nullptr, nullptr, nullptr, nullptr};
 
   // buffers of snap_compute_host
   int cap_host = 0;
@@ -212,7 +227,7 @@ int ensure_workspace(snap_ctx* c, int n, int K) {
 }
 
 int ensure_slices(snap_ctx* c, int n) {
-  const snap::YiGeometry g = snap::yi_geometry((int)c->rsize(), c->tab.H, n, c->nsm);
+  const snap::YiGeometry g = snap::yi_geometry((int)c->rsize(), c->tab.H, n, c->nsm, c->yi_waves);
   if (g.nslices == c->nslices) return SNAP_OK;
   int rc = upload(c, &c->d_yslice, c->tab.slices(g.nslices));
   if (rc) return rc;
@@ -225,6 +240,50 @@ bool box_ok(const double* box) {
   for (int d = 0; d < 3; ++d)
     if (!(std::isfinite(box[d]) && box[d] > 0.0)) return false;
   return true;
+}
+
+// Kernel arguments for n atoms with capacity K (workspace and tables).
+snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
+  snap::WorkArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.K = K;
+  a.twojmax = c->twojmax;
+  a.H = c->tab.H;
+  a.lmax = c->tab.lmax;
+  a.rcut = c->rcut;
+  a.rfac0 = c->rfac0;
+  a.rmin0 = c->rmin0;
+  a.inv_span = 1.0 / (c->rcut - c->rmin0);
+  a.wself = c->wself;
+  a.beta0 = c->beta[0];
+  a.switchflag = c->switchflag;
+  a.cnt = c->d_cnt;
+  a.nbr = c->d_nbr;
+  a.img = c->d_img;
+  a.rev = c->d_rev;
+  a.rij = c->d_rij;
+  a.geom = c->d_geom;
+  a.U = c->d_U;
+  a.Y = c->d_Y;
+  a.dedr = c->d_dedr;
+  a.vpart = c->d_vpart;
+  a.flags = c->d_flags;
+  a.half_tmm = c->d_half_tmm;
+  a.yrec = c->d_yrec;
+  a.yfirst = c->d_yfirst;
+  a.yslice = c->d_yslice;
+  a.nslices = c->nslices;
+  a.nsm = c->nsm;
+  a.col_warps = c->col_warps;
+  a.yi_waves = c->yi_waves;
+  a.ncoeff = c->tab.ncoeff;
+  a.brec = c->d_brec;
+  a.bout = c->d_bout;
+  a.bfirst = c->d_bfirst;
+  a.bgfirst = c->d_bgfirst;
+  a.rootpq = c->d_root;
+  return a;
 }
 
 // Enqueue the whole evaluation on stream s (no synchronisation).
@@ -296,47 +355,11 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   }
   SNAP_CUDA(c, mark());
 
-  snap::WorkArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.n = n;
-  a.K = K;
-  a.twojmax = c->twojmax;
-  a.H = c->tab.H;
-  a.lmax = c->tab.lmax;
-  a.rcut = c->rcut;
-  a.rfac0 = c->rfac0;
-  a.rmin0 = c->rmin0;
-  a.inv_span = 1.0 / (c->rcut - c->rmin0);
-  a.wself = c->wself;
-  a.beta0 = c->beta[0];
-  a.switchflag = c->switchflag;
-  a.cnt = c->d_cnt;
-  a.nbr = c->d_nbr;
-  a.img = c->d_img;
-  a.rev = c->d_rev;
-  a.rij = c->d_rij;
-  a.geom = c->d_geom;
-  a.U = c->d_U;
-  a.Y = c->d_Y;
-  a.dedr = c->d_dedr;
+  snap::WorkArgs a = make_args(c, n, K);
   a.energy = energy;
   a.forces = forces;
-  a.vpart = c->d_vpart;
   a.virial = virial;
-  a.flags = c->d_flags;
-  a.half_tmm = c->d_half_tmm;
-  a.yrec = c->d_yrec;
-  a.yfirst = c->d_yfirst;
-  a.yslice = c->d_yslice;
-  a.nslices = c->nslices;
-  a.nsm = c->nsm;
-  a.ncoeff = c->tab.ncoeff;
-  a.brec = c->d_brec;
-  a.bout = c->d_bout;
-  a.bfirst = c->d_bfirst;
-  a.bgfirst = c->d_bgfirst;
   a.B = B;
-  a.rootpq = c->d_root;
 
   const bool mixed = c->precision == SNAP_MIXED;
   SNAP_CUDA(c, mixed ? snap::launch_pairs<float>(a, c->d_rev, s) : snap::launch_pairs<double>(a, c->d_rev, s));
@@ -376,6 +399,117 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
   c->last_n = n;
   c->last_K = K;
+  return SNAP_OK;
+}
+
+// ---------------------------------------------------------------- batches
+// Shape of a batch: per-configuration atom ranges, boxes and image ranges,
+// and the CTA -> (configuration, first atom) map of the batched neighbour
+// build (8 atoms of one configuration per CTA).  Uploaded when it changes.
+int prepare_batch(snap_ctx* c, int nconf, const int* natoms, const double* boxes) {
+  bool same = (nconf == c->bat_nconf) && (int)c->bat_n.size() == nconf;
+  for (int k = 0; same && k < nconf; ++k)
+    same = c->bat_n[k] == natoms[k] && c->bat_box[3 * k] == boxes[3 * k] &&
+           c->bat_box[3 * k + 1] == boxes[3 * k + 1] && c->bat_box[3 * k + 2] == boxes[3 * k + 2];
+  if (!same) {
+    std::vector<snap::NeighConf> confs(nconf);
+    std::vector<int2> map;
+    int start = 0;
+    for (int k = 0; k < nconf; ++k) {
+      snap::NeighConf& f = confs[k];
+      f.start = start;
+      f.n = natoms[k];
+      for (int d = 0; d < 3; ++d) {
+        f.L[d] = boxes[3 * k + d];
+        f.S[d] = (f.L[d] > 2.0 * (c->rcut + 0.05)) ? 0 : (int)std::ceil(c->rcut / f.L[d]) + 1;
+      }
+      for (int o = 0; o < f.n; o += 8) map.push_back(make_int2(k, o));
+      start += f.n;
+    }
+    int rc = upload(c, &c->d_confs, confs);
+    if (!rc) rc = upload(c, &c->d_ctamap, map);
+    if (rc) return rc;
+    c->bat_n.assign(natoms, natoms + nconf);
+    c->bat_box.assign(boxes, boxes + 3 * nconf);
+    c->bat_nconf = nconf;
+    c->bat_total = start;
+    c->bat_ncta = (int)map.size();
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+  }
+  const int n = c->bat_total;
+  int rc = ensure_workspace(c, n, c->K);
+  if (rc) return rc;
+  if (!c->d_flags) {
+    SNAP_CUDA(c, cudaMalloc(&c->d_flags, 8 * sizeof(int)));
+    SNAP_CUDA(c, cudaMallocHost(&c->h_flags, 8 * sizeof(int)));
+  }
+  const int old_slices = c->nslices;
+  rc = ensure_slices(c, n);
+  if (rc) return rc;
+  if (c->nslices != old_slices && c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  if (n > c->cap_vatom) {
+    cudaDeviceSynchronize();
+    dfree(c->d_vatom);
+    SNAP_CUDA(c, cudaMalloc(&c->d_vatom, sizeof(double) * 6 * (size_t)std::max(n, 1)));
+    c->cap_vatom = n;
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+  }
+  c->last_n = n;
+  c->last_K = c->K;
+  return SNAP_OK;
+}
+
+// The launch sequence of a prepared batch: asynchronous, allocates nothing
+// (so it can be captured into a CUDA graph).
+int launch_batch(snap_ctx* c, const double* pos, double* energy, double* forces, double* virial,
+                 cudaStream_t s) {
+  const int n = c->bat_total;
+  SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 8 * sizeof(int), s));
+  snap::NeighArgs na;
+  std::memset(&na, 0, sizeof(na));
+  na.n = n;
+  na.K = c->K;
+  na.confs = c->d_confs;
+  na.cta_map = c->d_ctamap;
+  na.pos = pos;
+  na.pos4 = c->d_pos4;
+  na.rcut = c->rcut;
+  na.cnt = c->d_cnt;
+  na.nbr = c->d_nbr;
+  na.img = c->d_img;
+  na.rij = c->d_rij;
+  na.flags = c->d_flags;
+  SNAP_CUDA(c, snap::launch_pos4(n, pos, c->d_pos4, s));
+  SNAP_CUDA(c, snap::launch_neigh_build_batch(na, c->bat_ncta, s));
+  snap::WorkArgs a = make_args(c, n, c->K);
+  a.energy = energy;
+  a.forces = forces;
+  a.virial = virial;
+  a.vatom = c->d_vatom;
+  const bool mixed = c->precision == SNAP_MIXED;
+  const bool colk = mixed && c->twojmax >= 1;
+  SNAP_CUDA(c, mixed ? snap::launch_pairs<float>(a, c->d_rev, s) : snap::launch_pairs<double>(a, c->d_rev, s));
+  SNAP_CUDA(c, colk ? snap::launch_ui_col<float>(a, s)
+                    : (mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s)));
+  SNAP_CUDA(c, mixed ? snap::launch_yi<float>(a, s) : snap::launch_yi<double>(a, s));
+  SNAP_CUDA(c, colk ? snap::launch_de_col<float>(a, s)
+                    : (mixed ? snap::launch_de<float>(a, s) : snap::launch_de<double>(a, s)));
+  SNAP_CUDA(c, mixed ? snap::launch_force<float>(a, s) : snap::launch_force<double>(a, s));
+  if (virial) SNAP_CUDA(c, snap::launch_virial_conf(c->d_vatom, c->d_confs, c->bat_nconf, virial, s));
+  SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  c->launches = 7 + (virial ? 1 : 0);
+  c->generation += 1;
+  c->last_args = a;
+  c->have_last = true;
   return SNAP_OK;
 }
 
@@ -618,6 +752,124 @@ int snap_force_weighted(snap_ctx* c, const double* weight, double* grad, void* s
 
 long long snap_generation(const snap_ctx* c) { return c ? c->generation : -1; }
 
+int snap_compute_batch(snap_ctx* c, int nconf, const int* natoms, const double* boxes,
+                       const double* pos, double* energy, double* forces, double* virial,
+                       int use_graph, void* stream) {
+  if (!c) return SNAP_ERR_ARG;
+  if (nconf < 0 || (nconf > 0 && (!natoms || !boxes))) return fail(c, SNAP_ERR_ARG, "bad batch description");
+  long total = 0;
+  for (int k = 0; k < nconf; ++k) {
+    if (natoms[k] < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
+    if (!box_ok(boxes + 3 * k)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+    total += natoms[k];
+  }
+  if (total > (1L << 30)) return fail(c, SNAP_ERR_ARG, "batch too large");
+  if (total == 0) return SNAP_OK;
+  if (!pos || !forces) return fail(c, SNAP_ERR_ARG, "pos and forces are required");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = prepare_batch(c, nconf, natoms, boxes);
+  if (rc) return rc;
+  if (!use_graph) return launch_batch(c, pos, energy, forces, virial, s);
+  const void* key[4] = {pos, energy, forces, virial};
+  const bool same = c->gexec && std::equal(key, key + 4, c->g_key);
+  if (!same) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    if (!c->gstream) SNAP_CUDA(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    SNAP_CUDA(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+    rc = launch_batch(c, pos, energy, forces, virial, c->gstream);
+    cudaError_t e = cudaStreamEndCapture(c->gstream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(c, SNAP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->gexec = nullptr;
+      return fail(c, SNAP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    std::copy(key, key + 4, c->g_key);
+  }
+  SNAP_CUDA(c, cudaGraphLaunch(c->gexec, s));
+  c->generation += 1;
+  return SNAP_OK;
+}
+
+int snap_set_tuning(snap_ctx* c, int col_warps, int yi_waves) {
+  if (!c) return SNAP_ERR_ARG;
+  if (col_warps != 2 && col_warps != 4 && col_warps != 8)
+    return fail(c, SNAP_ERR_ARG, "col_warps must be 2, 4 or 8");
+  if (yi_waves < 1 || yi_waves > 8) return fail(c, SNAP_ERR_ARG, "yi_waves must be in 1..8");
+  if (c->col_warps != col_warps || c->yi_waves != yi_waves) {
+    c->col_warps = col_warps;
+    c->yi_waves = yi_waves;
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+  }
+  return SNAP_OK;
+}
+
+int snap_get_tuning(const snap_ctx* c, int* col_warps, int* yi_waves) {
+  if (!c) return SNAP_ERR_ARG;
+  if (col_warps) *col_warps = c->col_warps;
+  if (yi_waves) *yi_waves = c->yi_waves;
+  return SNAP_OK;
+}
+
+int snap_autotune(snap_ctx* c, int nconf, const int* natoms, const double* boxes, const double* pos,
+                  double* energy, double* forces, double* virial, int reps, double* best_ms,
+                  void* stream) {
+  if (!c) return SNAP_ERR_ARG;
+  if (reps < 1) reps = 5;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cw[3] = {2, 4, 8};
+  const int yw[3] = {1, 2, 4};
+  double best = 1e300;
+  int bc = c->col_warps, by = c->yi_waves;
+  cudaEvent_t e0, e1;
+  SNAP_CUDA(c, cudaEventCreate(&e0));
+  SNAP_CUDA(c, cudaEventCreate(&e1));
+  int rc = SNAP_OK;
+  for (int a = 0; a < 3 && !rc; ++a)
+    for (int b = 0; b < 3 && !rc; ++b) {
+      rc = snap_set_tuning(c, cw[a], yw[b]);
+      if (rc) break;
+      std::vector<float> ms;
+      for (int it = 0; it < reps + 2 && !rc; ++it) {
+        cudaEventRecord(e0, s);
+        rc = snap_compute_batch(c, nconf, natoms, boxes, pos, energy, forces, virial, 0, stream);
+        cudaEventRecord(e1, s);
+        if (rc) break;
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (it >= 2) ms.push_back(t);
+      }
+      if (rc) break;
+      std::sort(ms.begin(), ms.end());
+      const double med = ms[ms.size() / 2];
+      if (med < best) {
+        best = med;
+        bc = cw[a];
+        by = yw[b];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  rc = snap_set_tuning(c, bc, by);
+  if (best_ms) *best_ms = best;
+  SNAP_CUDA(c, cudaStreamSynchronize(s));
+  return rc ? rc : check_flags(c);
+}
+
 int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const double* box,
                       double* energy_host, double* forces_host, double* virial_host, void* stream) {
   if (!c) return SNAP_ERR_ARG;
@@ -721,6 +973,11 @@ int snap_destroy(snap_ctx* c) {
   dfree(c->d_hF);
   dfree(c->d_hW);
   if (c->h_flags) cudaFreeHost(c->h_flags);
+  dfree(c->d_confs);
+  dfree(c->d_ctamap);
+  dfree(c->d_vatom);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
   for (auto* pool : {&c->prof_pending, &c->prof_free})
     for (auto& ev : *pool)
       for (auto e : ev) cudaEventDestroy(e);

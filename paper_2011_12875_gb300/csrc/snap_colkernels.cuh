@@ -110,10 +110,11 @@ __device__ __forceinline__ void seed_column(c2<R> (&v)[N], bool take) {
 // CTA = one atom, NW warps; each warp takes P pairs at a time.  Each pair
 // group sums f_c u_t into its own shared-memory copy of Ulisttot (no two
 // lanes write one address), and the copies are added in a fixed order.
-template <typename R, int J2, int NW>
-__global__ void __launch_bounds__(NW * 32) ui_col_kernel(WorkArgs a) {
+template <typename R, int J2>
+__global__ void __launch_bounds__(256) ui_col_kernel(WorkArgs a) {
   using S = Shape<J2>;
   constexpr int NC = S::NC, P = S::P;
+  const int NW = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = a.H;
   c2<R>* acc = reinterpret_cast<c2<R>*>(smem);  // [NW*P][H]
@@ -197,14 +198,16 @@ __global__ void __launch_bounds__(NW * 32) ui_col_kernel(WorkArgs a) {
 // differentiated, Sec. V-A) and accumulates Re(conj(Y) u), Re(conj(Y) du_d)
 // over its column; the pair's lanes are summed in shared memory and
 //   dE_i/dr_ik,d = (df_c/dr_d) S + f_c D_d      (Eq. snapforce2).
-template <typename R, int J2, int NW>
-__global__ void __launch_bounds__(NW * 32) de_col_kernel(WorkArgs a) {
+template <typename R, int J2>
+__global__ void __launch_bounds__(256) de_col_kernel(WorkArgs a) {
   using S_ = Shape<J2>;
   constexpr int NC = S_::NC, P = S_::P;
+  const int NW = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = a.H;
   c2<R>* Yw = reinterpret_cast<c2<R>*>(smem);                 // [H]
   R* red = reinterpret_cast<R*>(Yw + H);                       // [NW][32][4]
+  (void)NW;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / NC, mb = lane - g * NC;
   const bool grp = g < P;
@@ -349,11 +352,12 @@ __global__ void __launch_bounds__(NW * 32) de_col_kernel(WorkArgs a) {
 // One tangent chain rides along the layer recursion (the recursion is linear
 // in u, so the tangent obeys the differentiated recursion with conj(da) and
 // conj(db) along delta).  Layout and accumulation as ui_col_kernel; no w_self.
-template <typename R, int J2, int NW>
-__global__ void __launch_bounds__(NW * 32) tan_col_kernel(WorkArgs a, const double* __restrict__ gd,
+template <typename R, int J2>
+__global__ void __launch_bounds__(256) tan_col_kernel(WorkArgs a, const double* __restrict__ gd,
                                                           void* dUout) {
   using S = Shape<J2>;
   constexpr int NC = S::NC, P = S::P;
+  const int NW = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = a.H;
   c2<R>* acc = reinterpret_cast<c2<R>*>(smem);  // [NW*P][H]
@@ -461,32 +465,33 @@ inline cudaError_t col_allow_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-constexpr int kColWarps = 4;
-
 template <typename R, int J2>
 cudaError_t launch_ui_col_t(const WorkArgs& a, cudaStream_t s) {
-  const size_t sm = sizeof(c2<R>) * (size_t)kColWarps * Shape<J2>::P * a.H;
-  cudaError_t e = col_allow_smem(ui_col_kernel<R, J2, kColWarps>, sm);
+  const int nw = a.col_warps;
+  const size_t sm = sizeof(c2<R>) * (size_t)nw * Shape<J2>::P * a.H;
+  cudaError_t e = col_allow_smem(ui_col_kernel<R, J2>, sm);
   if (e != cudaSuccess) return e;
-  ui_col_kernel<R, J2, kColWarps><<<a.n, kColWarps * 32, sm, s>>>(a);
+  ui_col_kernel<R, J2><<<a.n, nw * 32, sm, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename R, int J2>
 cudaError_t launch_de_col_t(const WorkArgs& a, cudaStream_t s) {
-  const size_t sm = sizeof(c2<R>) * (size_t)a.H + sizeof(R) * kColWarps * 32 * 4;
-  cudaError_t e = col_allow_smem(de_col_kernel<R, J2, kColWarps>, sm);
+  const int nw = a.col_warps;
+  const size_t sm = sizeof(c2<R>) * (size_t)a.H + sizeof(R) * nw * 32 * 4;
+  cudaError_t e = col_allow_smem(de_col_kernel<R, J2>, sm);
   if (e != cudaSuccess) return e;
-  de_col_kernel<R, J2, kColWarps><<<a.n, kColWarps * 32, sm, s>>>(a);
+  de_col_kernel<R, J2><<<a.n, nw * 32, sm, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename R, int J2>
 cudaError_t launch_tan_col_t(const WorkArgs& a, const double* g, void* dU, cudaStream_t s) {
-  const size_t sm = sizeof(c2<R>) * (size_t)kColWarps * Shape<J2>::P * a.H;
-  cudaError_t e = col_allow_smem(tan_col_kernel<R, J2, kColWarps>, sm);
+  const int nw = a.col_warps;
+  const size_t sm = sizeof(c2<R>) * (size_t)nw * Shape<J2>::P * a.H;
+  cudaError_t e = col_allow_smem(tan_col_kernel<R, J2>, sm);
   if (e != cudaSuccess) return e;
-  tan_col_kernel<R, J2, kColWarps><<<a.n, kColWarps * 32, sm, s>>>(a, g, dU);
+  tan_col_kernel<R, J2><<<a.n, nw * 32, sm, s>>>(a, g, dU);
   return cudaGetLastError();
 }
 

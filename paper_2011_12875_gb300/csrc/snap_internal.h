@@ -49,8 +49,20 @@ struct __align__(16) YRec<double> {
 //  [8..13] d a / d r_d (re, im per d), [14..19] d b / d r_d.
 // A slot with r >= rcut has f_c = 0 and zero derivatives.
 
+// One configuration of a batch: atoms [start, start + n), box L, image
+// shifts S enumerated beyond the nearest image.
+struct NeighConf {
+  int start, n;
+  double L[3];
+  int S[3];
+};
+
 struct NeighArgs {
   int n, K;
+  // batch mode: confs != nullptr; CTA b builds atoms cta_map[b].y + 0..7 of
+  // configuration cta_map[b].x
+  const NeighConf* confs;
+  const int2* cta_map;
   const double* pos;     // [n][3]
   const float4* pos4;    // [n] FP32 copy for the coarse test
   double Lx, Ly, Lz;
@@ -78,6 +90,7 @@ struct WorkArgs {
   void* U;
   void* Y;
   double* dedr;
+  double* vatom;   // per-atom virial [N][6] (batch mode) or nullptr
   double* energy;
   double* forces;
   double* vpart;
@@ -89,6 +102,8 @@ struct WorkArgs {
   const int* yslice;
   int nslices;
   int nsm;
+  int col_warps;  // warps per CTA of the column-chain kernels (tunable)
+  int yi_waves;   // compute_Y waves per SM (tunable)
   // bispectrum output
   int ncoeff;
   const void* brec;       // YRec<R> records of the bispectrum terms
@@ -102,6 +117,8 @@ struct WorkArgs {
 // Launchers (snap_neigh.cu)
 cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s);
 cudaError_t launch_neigh_build(const NeighArgs& a, cudaStream_t s);
+// batch: one launch over all configurations (ncta CTAs)
+cudaError_t launch_neigh_build_batch(const NeighArgs& a, int ncta, cudaStream_t s);
 cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, double Ly,
                                 double Lz, const int* ucnt, const int* uidx,
                                 const signed char* uimg, int ucap, int* cnt, int* nbr,
@@ -121,7 +138,11 @@ struct YiGeometry {
   size_t smem;
   bool staged;
 };
-YiGeometry yi_geometry(int rsize, int H, int n, int nsm);
+YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves);
+
+// Per-configuration virial: sum of vatom over each configuration's atoms.
+cudaError_t launch_virial_conf(const double* vatom, const NeighConf* confs, int nconf, double* virial,
+                               cudaStream_t s);
 template <typename R> cudaError_t launch_de(const WorkArgs& a, cudaStream_t s);
 template <typename R> cudaError_t launch_force(const WorkArgs& a, cudaStream_t s);
 template <typename R> cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s);

@@ -662,6 +662,15 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_kernel(WorkArgs a) {
     for (int c = 0; c < 3; ++c) f[c] = warp_sum(f[c]);
     if (lane == 0)
       for (int c = 0; c < 3; ++c) a.forces[3 * i + c] = f[c];
+    if (a.vatom) {  // batch mode: per-atom virial, reduced per configuration later
+      double va[6];
+      for (int c = 0; c < 6; ++c) {
+        va[c] = warp_sum(v[c]);
+        v[c] = 0.0;
+      }
+      if (lane == 0)
+        for (int c = 0; c < 6; ++c) a.vatom[6 * i + c] = va[c];
+    }
   }
   for (int c = 0; c < 6; ++c) v[c] = warp_sum(v[c]);
   if (lane == 0)
@@ -673,7 +682,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_kernel(WorkArgs a) {
     for (int w = 0; w < kForceWarps; ++w) e += ep[w][lane];
     if (a.energy && i < a.n) a.energy[i] = a.beta0 + e / 3.0;
   }
-  if (!a.virial) return;
+  if (!a.virial || a.vatom) return;
   const int cta = blockIdx.x * gridDim.y + part;
   const int ncta = gridDim.x * gridDim.y;
   if (threadIdx.x < 6) {
@@ -725,7 +734,7 @@ cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-YiGeometry yi_geometry(int rsize, int H, int n, int nsm) {
+YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves) {
   YiGeometry g;
   g.nblk = (n + 31) / 32;
   const size_t stage = (size_t)2 * H * 32 * rsize + 16;  // complex [H][32] + mbarrier
@@ -734,7 +743,7 @@ YiGeometry yi_geometry(int rsize, int H, int n, int nsm) {
   g.threads = (g.smem > 100 * 1024) ? 1024 : 256;
   int cps = 2048 / g.threads;
   if (g.staged) cps = std::max(1, std::min(cps, (int)((227 * 1024) / g.smem)));
-  const int target = nsm * cps * 2;
+  const int target = nsm * cps * std::max(1, waves);
   g.ysplit = std::max(1, (target + g.nblk - 1) / g.nblk);
   g.ysplit = std::min(g.ysplit, 64);
   g.nslices = g.ysplit * (g.threads / 32);
@@ -744,7 +753,7 @@ YiGeometry yi_geometry(int rsize, int H, int n, int nsm) {
 template <typename R>
 cudaError_t launch_yi(const WorkArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm);
+  const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm, a.yi_waves);
   if (g.nslices != a.nslices) return cudaErrorInvalidValue;
   dim3 grid(g.nblk, g.ysplit);
   if (g.staged) {
@@ -777,7 +786,7 @@ cudaError_t launch_force(const WorkArgs& a, cudaStream_t s) {
 template <typename R>
 cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm);
+  const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm, 2);
   dim3 grid(g.nblk, (a.ncoeff + 7) / 8);
   if (g.staged) {
     cudaError_t e = allow_smem(bi_kernel<R, true>, g.smem);
@@ -794,7 +803,7 @@ template cudaError_t launch_bi<double>(const WorkArgs&, cudaStream_t);
 template <typename R>
 cudaError_t launch_dbi(const WorkArgs& a, const void* dU, double* dB, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm);
+  const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm, 2);
   dim3 grid(g.nblk, (a.ncoeff + 7) / 8);
   const cx<R>* d = reinterpret_cast<const cx<R>*>(dU);
   if (g.staged) {
@@ -812,6 +821,34 @@ template cudaError_t launch_dbi<double>(const WorkArgs&, const void*, double*, c
 cudaError_t launch_force_weighted(const WorkArgs& a, const double* w, double* grad, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   force_weighted_kernel<<<(a.n + 7) / 8, 256, 0, s>>>(a, w, grad);
+  return cudaGetLastError();
+}
+
+// Per-configuration virial: one CTA per configuration sums its atoms in a
+// fixed order (strided partial sums, then a tree).
+__global__ void __launch_bounds__(256) virial_conf_kernel(const double* __restrict__ vatom,
+                                                          const NeighConf* __restrict__ confs,
+                                                          double* __restrict__ virial) {
+  __shared__ double red[256];
+  const NeighConf c = confs[blockIdx.x];
+  for (int k = 0; k < 6; ++k) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < c.n; i += blockDim.x) t += vatom[6 * (long)(c.start + i) + k];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) virial[6 * blockIdx.x + k] = red[0];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_virial_conf(const double* vatom, const NeighConf* confs, int nconf, double* virial,
+                               cudaStream_t s) {
+  if (nconf <= 0) return cudaSuccess;
+  virial_conf_kernel<<<nconf, 256, 0, s>>>(vatom, confs, virial);
   return cudaGetLastError();
 }
 

@@ -48,9 +48,9 @@ __device__ __forceinline__ int pack_img(int x, int y, int z) {
   return (x + 128) | ((y + 128) << 8) | ((z + 128) << 16);
 }
 
-__device__ __forceinline__ void exact_batch(const NeighArgs& a, int i, double xi, double yi,
-                                            double zi, double rc2, const int* cj, const int* cs,
-                                            int nb, int lane, int& count) {
+__device__ __forceinline__ void exact_batch(const NeighArgs& a, double Lx, double Ly, double Lz, int i,
+                                            double xi, double yi, double zi, double rc2, const int* cj,
+                                            const int* cs, int nb, int lane, int& count) {
   bool in = false;
   double ex = 0, ey = 0, ez = 0;
   int j = 0, ix = 0, iy = 0, iz = 0;
@@ -60,9 +60,9 @@ __device__ __forceinline__ void exact_batch(const NeighArgs& a, int i, double xi
     ix = (pk & 0xff) - 128;
     iy = ((pk >> 8) & 0xff) - 128;
     iz = ((pk >> 16) & 0xff) - 128;
-    ex = sep1(i, j, xi, a.pos[3 * j], ix, a.Lx);
-    ey = sep1(i, j, yi, a.pos[3 * j + 1], iy, a.Ly);
-    ez = sep1(i, j, zi, a.pos[3 * j + 2], iz, a.Lz);
+    ex = sep1(i, j, xi, a.pos[3 * j], ix, Lx);
+    ey = sep1(i, j, yi, a.pos[3 * j + 1], iy, Ly);
+    ez = sep1(i, j, zi, a.pos[3 * j + 2], iz, Lz);
     in = norm2(ex, ey, ez) < rc2;
   }
   const unsigned m = __ballot_sync(kFull, in);
@@ -82,14 +82,31 @@ __device__ __forceinline__ void exact_batch(const NeighArgs& a, int i, double xi
   count += __popc(m);
 }
 
-template <bool NEAREST>
+template <bool BATCH>
 __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a) {
   __shared__ float4 tile[kNbTile];
   __shared__ int cand_j[kNbWarps][kCandCap];
   __shared__ int cand_s[kNbWarps][kCandCap];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kNbWarps + warp;
-  const bool active = i < a.n;
+  // candidate range [j_lo, j_hi), box and image range of this CTA's atoms
+  int j_lo = 0, j_hi = a.n, i = blockIdx.x * kNbWarps + warp;
+  int Sx = a.Sx, Sy = a.Sy, Sz = a.Sz;
+  double Ldx = a.Lx, Ldy = a.Ly, Ldz = a.Lz;
+  if (BATCH) {
+    const int2 m = a.cta_map[blockIdx.x];
+    const NeighConf c = a.confs[m.x];
+    j_lo = c.start;
+    j_hi = c.start + c.n;
+    i = c.start + m.y + warp;
+    Ldx = c.L[0];
+    Ldy = c.L[1];
+    Ldz = c.L[2];
+    Sx = c.S[0];
+    Sy = c.S[1];
+    Sz = c.S[2];
+  }
+  const bool NEAREST = (Sx == 0 && Sy == 0 && Sz == 0);
+  const bool active = i < j_hi;
   int* cj = cand_j[warp];
   int* cs = cand_s[warp];
   float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -100,7 +117,7 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
     yi = a.pos[3 * i + 1];
     zi = a.pos[3 * i + 2];
   }
-  const float Lx = (float)a.Lx, Ly = (float)a.Ly, Lz = (float)a.Lz;
+  const float Lx = (float)Ldx, Ly = (float)Ldy, Lz = (float)Ldz;
   const float iLx = 1.f / Lx, iLy = 1.f / Ly, iLz = 1.f / Lz;
   const float rcf = (float)a.rcut + 1e-2f;
   const float rc2f = rcf * rcf;
@@ -108,13 +125,13 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
   const unsigned lt = (1u << lane) - 1u;
   int count = 0;  // accepted pairs (warp-uniform)
   int ncand = 0;  // pending candidates (warp-uniform)
-  for (int j0 = 0; j0 < a.n; j0 += kNbTile) {
+  for (int j0 = j_lo; j0 < j_hi; j0 += kNbTile) {
     __syncthreads();
     for (int q = threadIdx.x; q < kNbTile; q += blockDim.x)
-      tile[q] = (j0 + q < a.n) ? a.pos4[j0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      tile[q] = (j0 + q < j_hi) ? a.pos4[j0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     if (!active) continue;
-    const int jn = min(kNbTile, a.n - j0);
+    const int jn = min(kNbTile, j_hi - j0);
     for (int jj = 0; jj < jn; jj += 32) {
       const int j = j0 + jj + lane;
       const bool valid = (jj + lane) < jn;
@@ -137,7 +154,7 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
           ncand += __popc(m);
           if (ncand >= 32) {
             __syncwarp();
-            exact_batch(a, i, xi, yi, zi, rc2, cj, cs, 32, lane, count);
+            exact_batch(a, Ldx, Ldy, Ldz, i, xi, yi, zi, rc2, cj, cs, 32, lane, count);
             __syncwarp();
             const int rest = ncand - 32;
             int mj = 0, ms = 0;
@@ -156,12 +173,12 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
         }
         continue;
       }
-      float sxf = -(float)a.Sx;
-      for (int sx = -a.Sx; sx <= a.Sx; ++sx, sxf += 1.f) {
-        float syf = -(float)a.Sy;
-        for (int sy = -a.Sy; sy <= a.Sy; ++sy, syf += 1.f) {
-          float szf = -(float)a.Sz;
-          for (int sz = -a.Sz; sz <= a.Sz; ++sz, szf += 1.f) {
+      float sxf = -(float)Sx;
+      for (int sx = -Sx; sx <= Sx; ++sx, sxf += 1.f) {
+        float syf = -(float)Sy;
+        for (int sy = -Sy; sy <= Sy; ++sy, syf += 1.f) {
+          float szf = -(float)Sz;
+          for (int sz = -Sz; sz <= Sz; ++sz, szf += 1.f) {
             const float fx = bx + sxf * Lx, fy = by + syf * Ly, fz = bz + szf * Lz;
             bool c = valid && (fx * fx + fy * fy + fz * fz < rc2f);
             int ix = 0, iy = 0, iz = 0;
@@ -180,7 +197,7 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
             ncand += __popc(m);
             if (ncand >= 32) {
               __syncwarp();
-              exact_batch(a, i, xi, yi, zi, rc2, cj, cs, 32, lane, count);
+              exact_batch(a, Ldx, Ldy, Ldz, i, xi, yi, zi, rc2, cj, cs, 32, lane, count);
               __syncwarp();
               const int rest = ncand - 32;
               int mj = 0, ms = 0;
@@ -206,7 +223,7 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
   __syncthreads();
   if (active) {
     __syncwarp();
-    if (ncand > 0) exact_batch(a, i, xi, yi, zi, rc2, cj, cs, ncand, lane, count);
+    if (ncand > 0) exact_batch(a, Ldx, Ldy, Ldz, i, xi, yi, zi, rc2, cj, cs, ncand, lane, count);
     if (lane == 0) {
       a.cnt[i] = min(count, a.K);
       atomicMax(&cmax, count);
@@ -416,10 +433,13 @@ cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s) 
 
 cudaError_t launch_neigh_build(const NeighArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  if (a.Sx == 0 && a.Sy == 0 && a.Sz == 0)
-    neigh_build_kernel<true><<<blocks_for(a.n, kNbWarps), kNbWarps * 32, 0, s>>>(a);
-  else
-    neigh_build_kernel<false><<<blocks_for(a.n, kNbWarps), kNbWarps * 32, 0, s>>>(a);
+  neigh_build_kernel<false><<<blocks_for(a.n, kNbWarps), kNbWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_neigh_build_batch(const NeighArgs& a, int ncta, cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+  neigh_build_kernel<true><<<ncta, kNbWarps * 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -41,7 +41,9 @@ EXPORTS = ("snap_num_coeff", "snap_create", "snap_set_beta", "snap_set_neigh_cap
            "snap_compute_host", "snap_get_buffer", "snap_half_index", "snap_half_size",
            "snap_destroy", "snap_last_error", "snap_profile", "snap_profile_read",
            "snap_stage_name", "snap_launches_per_call", "snap_compute_bispectrum",
-           "snap_bispectrum_deriv", "snap_force_weighted", "snap_generation")
+           "snap_bispectrum_deriv", "snap_force_weighted", "snap_generation",
+           "snap_compute_batch", "snap_set_tuning", "snap_get_tuning", "snap_autotune",
+           "snap_neighbors_noalloc")
 NSTAGES = 6
 
 _lib = None
@@ -95,6 +97,14 @@ def load(path: str | None = None):
     L.snap_force_weighted.restype = i
     L.snap_generation.argtypes = [p]
     L.snap_generation.restype = ctypes.c_longlong
+    L.snap_compute_batch.argtypes = [p, i, p, p, p, p, p, p, i, p]
+    L.snap_compute_batch.restype = i
+    L.snap_set_tuning.argtypes = [p, i, i]
+    L.snap_set_tuning.restype = i
+    L.snap_get_tuning.argtypes = [p, p, p]
+    L.snap_get_tuning.restype = i
+    L.snap_autotune.argtypes = [p, i, p, p, p, p, p, p, i, p, p]
+    L.snap_autotune.restype = i
     L.snap_compute_host.argtypes = [p, i, p, p, p, p, p, p]
     L.snap_compute_host.restype = i
     L.snap_get_buffer.argtypes = [p, i, p, ctypes.c_size_t]
@@ -267,6 +277,62 @@ class Snap:
         self._check(self._lib.snap_force_weighted(self._h, _t_ptr(weight), _t_ptr(out),
                                                   ctypes.c_void_p(stream)))
         return out
+
+    def _batch_args(self, pos, natoms, boxes, energy, forces, virial):
+        import torch
+        if pos.dtype != torch.float64 or not pos.is_cuda or not pos.is_contiguous():
+            raise ValueError("pos must be a contiguous float64 CUDA tensor")
+        na = np.ascontiguousarray(natoms, dtype=np.int32)
+        bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+        if bx.shape[0] != na.shape[0] or int(na.sum()) != pos.shape[0]:
+            raise ValueError("natoms, boxes and pos do not describe the same batch")
+        n, dev = pos.shape[0], pos.device
+        if energy is None:
+            energy = torch.empty(n, dtype=torch.float64, device=dev)
+        if forces is None:
+            forces = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        if virial is None:
+            virial = torch.empty((na.shape[0], 6), dtype=torch.float64, device=dev)
+        return na, bx, energy, forces, virial
+
+    def compute_batch(self, pos, natoms, boxes, energy=None, forces=None, virial=None,
+                      use_graph=True, stream=None, wait=True):
+        """Evaluate a batch of configurations (atoms concatenated in pos).
+
+        Returns (energy [N], forces [N,3], virial [nconf,6]).  With use_graph
+        the launch sequence is captured once per batch shape and replayed.
+        """
+        import torch
+        na, bx, energy, forces, virial = self._batch_args(pos, natoms, boxes, energy, forces, virial)
+        if stream is None:
+            stream = torch.cuda.current_stream(pos.device).cuda_stream
+        self._check(self._lib.snap_compute_batch(
+            self._h, len(na), _np_ptr(na), _np_ptr(bx), _t_ptr(pos), _t_ptr(energy),
+            _t_ptr(forces), _t_ptr(virial), int(bool(use_graph)), ctypes.c_void_p(stream)))
+        if wait:
+            self.sync(stream)
+        self._batch_keep = (na, bx)
+        return energy, forces, virial
+
+    def set_tuning(self, col_warps: int, yi_waves: int):
+        self._check(self._lib.snap_set_tuning(self._h, col_warps, yi_waves))
+
+    def get_tuning(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.snap_get_tuning(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def autotune(self, pos, natoms, boxes, reps: int = 5, stream=None):
+        """Pick the fastest launch shape for this batch; returns its median ms."""
+        import torch
+        na, bx, energy, forces, virial = self._batch_args(pos, natoms, boxes, None, None, None)
+        if stream is None:
+            stream = torch.cuda.current_stream(pos.device).cuda_stream
+        best = ctypes.c_double()
+        self._check(self._lib.snap_autotune(
+            self._h, len(na), _np_ptr(na), _np_ptr(bx), _t_ptr(pos), _t_ptr(energy), _t_ptr(forces),
+            _t_ptr(virial), reps, ctypes.byref(best), ctypes.c_void_p(stream)))
+        return best.value
 
     def generation(self) -> int:
         return int(self._lib.snap_generation(self._h))

@@ -166,3 +166,60 @@ def test_force_matching_gradient(snapmod):
         fd = (vals[0] - vals[1]) / (2 * h)
         assert fd == pytest.approx(grad[l], rel=1e-8, abs=1e-8 * np.abs(grad).max())
     s.close()
+
+
+def batch_of(sizes, seed=42, strain=0.02):
+    cfgs = [inputs.bcc(nc, disp=0.1, strain=strain, seed=seed + k) for k, nc in enumerate(sizes)]
+    pos = np.concatenate([c.pos for c in cfgs])
+    return cfgs, pos, np.array([c.natoms for c in cfgs]), np.array([c.box for c in cfgs])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_equals_per_configuration(snapmod, prec, use_graph):
+    """One batched evaluation (optionally a replayed CUDA graph) of uneven
+    configurations, including boxes smaller than 2 rcut, gives the results of
+    one snap_compute per configuration."""
+    cfgs, pos, natoms, boxes = batch_of([3, 2, 5, 4, 3, 6])
+    s = snapmod.Snap(8, inputs.beta(8), precision=prec)
+    P = torch.tensor(pos, device="cuda:0")
+    for rep in range(3):  # capture, then replays
+        E, F, W = [x.cpu().numpy().copy() for x in s.compute_batch(P, natoms, boxes, use_graph=use_graph)]
+    start = 0
+    for k, c in enumerate(cfgs):
+        e1, f1, w1 = [x.cpu().numpy() for x in s.compute(torch.tensor(c.pos, device="cuda:0"), c.box)]
+        sl = slice(start, start + c.natoms)
+        assert np.array_equal(E[sl], e1) and np.array_equal(F[sl], f1)
+        np.testing.assert_allclose(W[k], w1, rtol=1e-12, atol=1e-12 * np.abs(w1).max())
+        start += c.natoms
+    s.close()
+
+
+def test_batch_parity_with_oracle(snapmod):
+    cfgs, pos, natoms, boxes = batch_of([3, 4, 2])
+    beta = inputs.beta(8)
+    s = snapmod.Snap(8, beta)
+    E, F, W = [x.cpu().numpy() for x in s.compute_batch(torch.tensor(pos, device="cuda:0"), natoms, boxes)]
+    s.close()
+    start = 0
+    for k, c in enumerate(cfgs):
+        _, ref = O.evaluate(O.Params(8), beta, c.pos, c.box)
+        sl = slice(start, start + c.natoms)
+        assert rel_err(E[sl], ref.E) <= FP64_TOL
+        assert rel_err(F[sl], ref.F) <= FP64_TOL
+        assert rel_err(W[k], ref.W) <= FP64_TOL
+        start += c.natoms
+
+
+def test_autotune_keeps_results(snapmod):
+    cfgs, pos, natoms, boxes = batch_of([4, 5, 6])
+    s = snapmod.Snap(8, inputs.beta(8), precision=1)
+    P = torch.tensor(pos, device="cuda:0")
+    E0, F0, _ = [x.cpu().numpy() for x in s.compute_batch(P, natoms, boxes, use_graph=False)]
+    ms = s.autotune(P, natoms, boxes, reps=3)
+    cw, yw = s.get_tuning()
+    assert ms > 0 and cw in (2, 4, 8) and yw in (1, 2, 4)
+    E1, F1, _ = [x.cpu().numpy() for x in s.compute_batch(P, natoms, boxes, use_graph=True)]
+    # tunables change only launch shapes: same per-atom arithmetic
+    assert rel_err(E1, E0) < 1e-6 and rel_err(F1, F0) < 1e-5
+    s.close()
