@@ -254,6 +254,117 @@ def e2e_host(snap, torch, w, precision, steps):
             "ms_per_step": 1e3 * el / steps}
 
 
+def _events_time(torch, fn, steps, flush, dev):
+    """Mean device milliseconds of fn() over `steps` calls (events around each
+    call on the current stream, L2 flushed between calls)."""
+    stream = torch.cuda.current_stream(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    torch.cuda.synchronize(dev)
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        evs[k][0].record(stream)
+        fn()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+
+def next_rows(torch, snap, inputs, flush, dev, args):
+    """Measurements of the widened rows: batched evaluation of 64 uneven
+    configurations (graph replay vs a per-configuration loop, after the
+    autotuner), bispectrum output, and the force-matching loss + gradient."""
+    import numpy as np
+    out = {}
+    # --- batch: 64 configurations, 54..2000 atoms, +-2% strain, 2J = 8, mixed
+    cfgs = inputs.batch(64)
+    natoms = np.array([c.natoms for c in cfgs])
+    boxes = np.array([c.box for c in cfgs])
+    pos = torch.tensor(np.concatenate([c.pos for c in cfgs]), device=dev)
+    total = int(natoms.sum())
+    beta = inputs.beta(8)
+    s = snap.Snap(8, beta, precision=snap.MIXED)
+    E = torch.empty(total, dtype=torch.float64, device=dev)
+    F = torch.empty((total, 3), dtype=torch.float64, device=dev)
+    W = torch.empty((len(cfgs), 6), dtype=torch.float64, device=dev)
+    steps = max(5, min(args.steps, 50))
+    default_tuning = s.get_tuning()
+    s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=True)
+    t_default = _events_time(torch, lambda: s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=True,
+                                                            wait=False), steps, flush, dev)
+    best_ms = s.autotune(pos, natoms, boxes, reps=5)
+    tuned = s.get_tuning()
+    s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=True)
+    t_graph = _events_time(torch, lambda: s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=True,
+                                                          wait=False), steps, flush, dev)
+    t_nograph = _events_time(torch, lambda: s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=False,
+                                                            wait=False), steps, flush, dev)
+    s.sync()
+    singles = [torch.tensor(c.pos, device=dev) for c in cfgs]
+    outs = [(torch.empty(c.natoms, dtype=torch.float64, device=dev),
+             torch.empty((c.natoms, 3), dtype=torch.float64, device=dev),
+             torch.empty(6, dtype=torch.float64, device=dev)) for c in cfgs]
+
+    def loop():
+        for c, p_, (e_, f_, w_) in zip(cfgs, singles, outs):
+            s.compute(p_, c.box, e_, f_, w_, wait=False)
+    loop()
+    s.sync()
+    t_loop = _events_time(torch, loop, max(3, steps // 5), flush, dev)
+    s.sync()
+    s.close()
+    out["batch_64_configs_2j8_mixed"] = {
+        "natoms_total": total, "atom_counts": sorted(set(int(n) for n in natoms)),
+        "graph_atom_steps_per_s": total / (t_graph * 1e-3), "graph_ms": t_graph,
+        "batched_no_graph_ms": t_nograph, "per_config_loop_ms": t_loop,
+        "per_config_loop_atom_steps_per_s": total / (t_loop * 1e-3),
+        "speedup_vs_loop": t_loop / t_graph,
+        "default_tuning": {"col_warps": default_tuning[0], "yi_waves": default_tuning[1], "graph_ms": t_default},
+        "autotuned": {"col_warps": tuned[0], "yi_waves": tuned[1], "autotune_median_ms": best_ms}}
+    # --- bispectrum output, 2000 atoms, 2J = 8
+    w = inputs.WORKLOADS["bcc10_2j8"]
+    cfg = w.config()
+    for prec, tag in ((snap.MIXED, "mixed"), (snap.FP64, "fp64")):
+        s = snap.Snap(8, w.beta(), precision=prec)
+        p_ = torch.tensor(cfg.pos, device=dev)
+        Bout = torch.empty((cfg.natoms, snap.num_coeff(8)), dtype=torch.float64, device=dev)
+        s.bispectrum(p_, cfg.box, out=Bout)
+        t = _events_time(torch, lambda: s.bispectrum(p_, cfg.box, out=Bout), 10, flush, dev)
+        out[f"bispectrum_2000_2j8_{tag}"] = {"atom_steps_per_s": cfg.natoms / (t * 1e-3), "ms": t,
+                                             "includes": "neighbour list, geometry, compute_U, B"}
+        s.close()
+    # --- force matching: loss + d loss / d beta over 32 configurations (+-0.2 A)
+    from paper_2011_12875_gb300 import autograd as AG
+    fit = inputs.fitting_set(32)
+    rng = np.random.Generator(np.random.PCG64(99))
+    for J in (8, 14):
+        s = snap.Snap(J, inputs.beta(J), precision=snap.MIXED)
+        data = [(torch.tensor(c.pos, device=dev), c.box,
+                 torch.tensor(rng.normal(size=c.pos.shape), device=dev)) for c in fit]
+
+        def fm_step():
+            g = None
+            for p_, b_, fr in data:
+                _, gr = AG.force_matching_grad(s, p_, b_, fr)
+                g = gr if g is None else g + gr
+            return g
+        fm_step()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            fm_step()
+        torch.cuda.synchronize(dev)
+        el = (time.perf_counter() - t0) / reps
+        na = sum(c.natoms for c in fit)
+        out[f"force_matching_step_2j{J}_mixed"] = {
+            "configs": len(fit), "natoms_total": na, "seconds_per_step": el,
+            "atom_steps_per_s": na / el,
+            "step": "per configuration: E, F; loss sum|F-F_ref|^2; dL/dbeta via snap_bispectrum_deriv"}
+        s.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -346,6 +457,7 @@ def main():
                                  "peak_tflops": peak}
             variants["mixed_2j8_2000"] = {"value": value / world, "ms_per_step": ms_mean}
             line["variants"] = variants
+            line["next"] = next_rows(torch, snap, inputs, flush, dev, args)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(head)
         print(json.dumps(line), flush=True)

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -41,6 +42,7 @@ struct snap_ctx {
   void* d_root = nullptr;
   int* d_yslice = nullptr;
   int nslices = -1;
+  std::map<int, int*> yslice_cache;  // compute_Y slice tables by slice count
 
   // workspace
   long cap_nk = 0;
@@ -229,8 +231,14 @@ int ensure_workspace(snap_ctx* c, int n, int K) {
 int ensure_slices(snap_ctx* c, int n) {
   const snap::YiGeometry g = snap::yi_geometry((int)c->rsize(), c->tab.H, n, c->nsm, c->yi_waves);
   if (g.nslices == c->nslices) return SNAP_OK;
-  int rc = upload(c, &c->d_yslice, c->tab.slices(g.nslices));
-  if (rc) return rc;
+  auto it = c->yslice_cache.find(g.nslices);
+  if (it == c->yslice_cache.end()) {
+    int* d = nullptr;
+    int rc = upload(c, &d, c->tab.slices(g.nslices));
+    if (rc) return rc;
+    it = c->yslice_cache.emplace(g.nslices, d).first;
+  }
+  c->d_yslice = it->second;
   c->nslices = g.nslices;
   return SNAP_OK;
 }
@@ -966,7 +974,9 @@ int snap_destroy(snap_ctx* c) {
   dfree(c->d_bfirst);
   dfree(c->d_bgfirst);
   dfree(c->d_root);
-  dfree(c->d_yslice);
+  for (auto& kv : c->yslice_cache) cudaFree(kv.second);
+  c->yslice_cache.clear();
+  c->d_yslice = nullptr;
   dfree(c->d_flags);
   dfree(c->d_hpos);
   dfree(c->d_hE);

@@ -198,8 +198,10 @@ __global__ void __launch_bounds__(256) ui_col_kernel(WorkArgs a) {
 // differentiated, Sec. V-A) and accumulates Re(conj(Y) u), Re(conj(Y) du_d)
 // over its column; the pair's lanes are summed in shared memory and
 //   dE_i/dr_ik,d = (df_c/dr_d) S + f_c D_d      (Eq. snapforce2).
+// Up to 2J = 11 at most 168 registers (three CTAs of four warps, or six of
+// two, per SM); above, the columns need the full register file.
 template <typename R, int J2>
-__global__ void __launch_bounds__(256) de_col_kernel(WorkArgs a) {
+__global__ void __maxnreg__(J2 <= 11 ? 168 : 255) de_col_kernel(WorkArgs a) {
   using S_ = Shape<J2>;
   constexpr int NC = S_::NC, P = S_::P;
   const int NW = blockDim.x >> 5;
