@@ -20,7 +20,7 @@ template <>
 cudaError_t launch_de_col<float>(const WorkArgs& a, cudaStream_t s) {
   switch (a.twojmax) {
 #define SNAP_CASE(J) \
-  case J: return col::launch_de_col_t<float, J>(a, s);
+  case J: return col::launch_de_rev_col_t<float, J>(a, s);
     SNAP_CASE(1) SNAP_CASE(2) SNAP_CASE(3) SNAP_CASE(4) SNAP_CASE(5) SNAP_CASE(6) SNAP_CASE(7)
     SNAP_CASE(8) SNAP_CASE(9) SNAP_CASE(10) SNAP_CASE(11) SNAP_CASE(12) SNAP_CASE(13) SNAP_CASE(14)
 #undef SNAP_CASE

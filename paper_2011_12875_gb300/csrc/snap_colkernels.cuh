@@ -461,6 +461,199 @@ __global__ void __launch_bounds__(256) tan_col_kernel(WorkArgs a, const double* 
   }
 }
 
+// --------------------------------------- fused dU + dE/dr, reverse mode
+// Same lane layout.  For one pair, S(a, b) = Re sum_t Y_t : conj(u_t) is a real
+// function of the Cayley-Klein parameters; its gradient comes from one
+// forward pass of the recursion (each lane stores its column of every layer
+// in shared memory) and one adjoint pass through the same recursion, with
+// the adjoint lambda_t of a column in registers:
+//   lambda_{t-1}[m][mb] = Yw_{t-1}[m][mb] + a A - b B,
+//   A = sqrt((t-m)/(t-mb)) lambda_t[m][mb],  B = sqrt((m+1)/(t-mb)) lambda_t[m+1][mb],
+//   g_a += conj(A) u_{t-1}[m][mb],           g_b -= conj(B) u_{t-1}[m][mb],
+// plus, for even t, the part of layer t's column t/2 that read the mirror of
+// column t/2-1 (its adjoint comes one lane down by shuffle).  Then
+//   dE_i/dr_ik = S grad f_c + f_c (<g_a, da/dr> + <g_b, db/dr>)   (Eq. snapforce2).
+template <typename R>
+__device__ __forceinline__ R shfl_down(R v) {
+  return __shfl_down_sync(kFull, v, 1);
+}
+
+template <typename R, int J2>
+__global__ void __launch_bounds__(256) de_rev_col_kernel(WorkArgs a) {
+  using S_ = Shape<J2>;
+  constexpr int NC = S_::NC, P = S_::P;
+  const int NW = blockDim.x >> 5;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int H = a.H;
+  c2<R>* Yw = reinterpret_cast<c2<R>*>(smem);  // [H]
+  c2<R>* ust = Yw + H;                         // [NW*P][H] forward columns
+  R* red = reinterpret_cast<R*>(ust + (size_t)NW * P * H);  // [NW][32][5]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / NC, mb = lane - g * NC;
+  const bool grp = g < P;
+  const int i = blockIdx.x;
+  {
+    const c2<R>* Yg = reinterpret_cast<const c2<R>*>(a.Y);
+    const long blk = i >> 5;
+    const int li = i & 31;
+    for (int e = threadIdx.x; e < H; e += blockDim.x) {
+      const int p = a.half_tmm[e];
+      const R w = (R)hweight(tmm_t(p), tmm_ma(p), tmm_mb(p));
+      const c2<R> y = Yg[(blk * H + e) * 32 + li];
+      Yw[e] = mk<R>(w * y.re, w * y.im);
+    }
+  }
+  __syncthreads();
+  c2<R>* my = ust + (warp * P + (grp ? g : 0)) * H;
+  R rs[J2 + 1];
+#pragma unroll
+  for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
+  R* myred = red + (warp * 32 + lane) * 5;
+  const int cnt = a.cnt[i];
+  for (int s0 = warp * P; s0 < cnt; s0 += NW * P) {
+    const int s = s0 + g;
+    const bool ok = grp && s < cnt;
+    const long slot = (long)i * a.K + (ok ? s : 0);
+    const R* gm = reinterpret_cast<const R*>(a.geom) + slot * kGeomStride;
+    c2<R> ka = mk<R>(1, 0), kb = mk<R>(0, 0);  // a and b
+    if (ok) {
+      ka = mk<R>(gm[0], gm[1]);
+      kb = mk<R>(gm[2], gm[3]);
+    }
+    // ---- forward: u columns, stored per layer
+    c2<R> u[J2 + 1];
+#pragma unroll
+    for (int k = 0; k <= J2; ++k) u[k] = mk<R>(0, 0);
+    R Ssum = 0;
+    if (mb == 0) {
+      u[0] = mk<R>(1, 0);
+      Ssum = Yw[0].re;
+      if (grp) my[0] = u[0];  // lanes past the last pair group own no storage
+    }
+    static_for<1, J2>([&](auto tc) {
+      constexpr int t = decltype(tc)::value;
+      if constexpr ((t & 1) == 0) seed_column<R, t>(u, mb == t / 2);
+      const R r = rs[t];
+      // conj(a) and conj(b) scaled by 1/sqrt(t - mb)
+      const c2<R> A = mk<R>(r * ka.re, -r * ka.im), B = mk<R>(r * kb.re, -r * kb.im);
+#pragma unroll
+      for (int ma = t; ma >= 0; --ma) {
+        c2<R> v = mk<R>(0, 0);
+        if (ma < t) {
+          const R c = sqrt_int<R>(t - ma);
+          v.re = c * (A.re * u[ma].re - A.im * u[ma].im);
+          v.im = c * (A.re * u[ma].im + A.im * u[ma].re);
+        }
+        if (ma > 0) {
+          const R c = sqrt_int<R>(ma);
+          v.re -= c * (B.re * u[ma - 1].re - B.im * u[ma - 1].im);
+          v.im -= c * (B.re * u[ma - 1].im + B.im * u[ma - 1].re);
+        }
+        u[ma] = v;
+      }
+      if (grp && 2 * mb <= t) {
+        c2<R>* dst = my + half_base(t) + mb * (t + 1);
+        const c2<R>* yr = Yw + half_base(t) + mb * (t + 1);
+#pragma unroll
+        for (int ma = 0; ma <= t; ++ma) {
+          dst[ma] = u[ma];
+          Ssum += yr[ma].re * u[ma].re + yr[ma].im * u[ma].im;
+        }
+      }
+    });
+    __syncwarp();
+    // ---- reverse: adjoint columns
+    c2<R> lam[J2 + 1];
+#pragma unroll
+    for (int k = 0; k <= J2; ++k) lam[k] = mk<R>(0, 0);
+    if (2 * mb <= J2) {
+      const c2<R>* yr = Yw + half_base(J2) + mb * (J2 + 1);
+#pragma unroll
+      for (int k = 0; k <= J2; ++k) lam[k] = yr[k];
+    }
+    c2<R> ga = mk<R>(0, 0), gb = mk<R>(0, 0);
+    static_for<1, J2>([&](auto tc) {
+      constexpr int t = J2 + 1 - decltype(tc)::value;  // J2 down to 1
+      constexpr int tp = t - 1;
+      constexpr int mc = t / 2;
+      constexpr bool even = (t & 1) == 0;
+      c2<R> recv[t + 1];
+      if constexpr (even) {
+#pragma unroll
+        for (int k = 0; k <= t; ++k) {
+          recv[k].re = shfl_down(lam[k].re);
+          recv[k].im = shfl_down(lam[k].im);
+        }
+      }
+      const bool act = grp && 2 * mb <= tp;
+      const bool mir = even && act && (mb == mc - 1);
+      const R r = rs[t];
+      const c2<R>* ucol = my + half_base(tp) + (act ? mb * (tp + 1) : 0);
+      const c2<R>* yr = Yw + half_base(tp) + (act ? mb * (tp + 1) : 0);
+      const R rmc = even ? R(1) / sqrt_int<R>(t - mc) : R(0);
+#pragma unroll
+      for (int m = 0; m <= tp; ++m) {
+        const c2<R> uu = act ? ucol[m] : mk<R>(0, 0);
+        const R c1 = sqrt_int<R>(t - m) * r, c2v = sqrt_int<R>(m + 1) * r;
+        const c2<R> Av = mk<R>(c1 * lam[m].re, c1 * lam[m].im);
+        const c2<R> Bv = mk<R>(c2v * lam[m + 1].re, c2v * lam[m + 1].im);
+        // g_a += conj(A) u ; g_b -= conj(B) u
+        ga.re += Av.re * uu.re + Av.im * uu.im;
+        ga.im += Av.re * uu.im - Av.im * uu.re;
+        gb.re -= Bv.re * uu.re + Bv.im * uu.im;
+        gb.im -= Bv.re * uu.im - Bv.im * uu.re;
+        // new adjoint: Yw + a A - b B
+        const c2<R> y = act ? yr[m] : mk<R>(0, 0);
+        c2<R> nl;
+        nl.re = y.re + ka.re * Av.re - ka.im * Av.im - (kb.re * Bv.re - kb.im * Bv.im);
+        nl.im = y.im + ka.re * Av.im + ka.im * Av.re - (kb.re * Bv.im + kb.im * Bv.re);
+        if constexpr (even) {
+          if (mir) {
+            const int mp = tp - m;
+            const R d1 = sqrt_int<R>(t - mp) * rmc, d2 = sqrt_int<R>(mp + 1) * rmc;
+            const R sg = ((m + mc - 1) & 1) ? R(-1) : R(1);
+            const c2<R> v = mk<R>(sg * uu.re, -sg * uu.im);
+            const c2<R> A2 = mk<R>(d1 * recv[mp].re, d1 * recv[mp].im);
+            const c2<R> B2 = mk<R>(d2 * recv[mp + 1].re, d2 * recv[mp + 1].im);
+            ga.re += A2.re * v.re + A2.im * v.im;
+            ga.im += A2.re * v.im - A2.im * v.re;
+            gb.re -= B2.re * v.re + B2.im * v.im;
+            gb.im -= B2.re * v.im - B2.im * v.re;
+            const R lr = ka.re * A2.re - ka.im * A2.im - (kb.re * B2.re - kb.im * B2.im);
+            const R li = ka.re * A2.im + ka.im * A2.re - (kb.re * B2.im + kb.im * B2.re);
+            nl.re += sg * lr;
+            nl.im -= sg * li;
+          }
+        }
+        lam[m] = nl;
+      }
+      lam[tp + 1] = mk<R>(0, 0);
+    });
+    myred[0] = Ssum;
+    myred[1] = ga.re;
+    myred[2] = ga.im;
+    myred[3] = gb.re;
+    myred[4] = gb.im;
+    __syncwarp();
+    if (ok && mb == 0) {
+      R q[5] = {0, 0, 0, 0, 0};
+      for (int c = 0; c < NC; ++c) {
+        const R* p = red + (warp * 32 + lane + c) * 5;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) q[k] += p[k];
+      }
+      const R fc = gm[4];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const R ds = q[1] * gm[8 + 2 * d] + q[2] * gm[9 + 2 * d] + q[3] * gm[14 + 2 * d] +
+                     q[4] * gm[15 + 2 * d];
+        a.dedr[slot * 3 + d] = (double)(gm[5 + d] * q[0] + fc * ds);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <typename K>
 inline cudaError_t col_allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
@@ -494,6 +687,17 @@ cudaError_t launch_tan_col_t(const WorkArgs& a, const double* g, void* dU, cudaS
   cudaError_t e = col_allow_smem(tan_col_kernel<R, J2>, sm);
   if (e != cudaSuccess) return e;
   tan_col_kernel<R, J2><<<a.n, nw * 32, sm, s>>>(a, g, dU);
+  return cudaGetLastError();
+}
+
+template <typename R, int J2>
+cudaError_t launch_de_rev_col_t(const WorkArgs& a, cudaStream_t s) {
+  const int nw = a.col_warps;
+  const size_t sm = sizeof(c2<R>) * ((size_t)a.H + (size_t)nw * Shape<J2>::P * a.H) +
+                    sizeof(R) * nw * 32 * 5;
+  cudaError_t e = col_allow_smem(de_rev_col_kernel<R, J2>, sm);
+  if (e != cudaSuccess) return e;
+  de_rev_col_kernel<R, J2><<<a.n, nw * 32, sm, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -627,8 +627,9 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_kernel(WorkArgs a) {
     const cx<R>* Ug = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
     const cx<R>* Yg = reinterpret_cast<const cx<R>*>(a.Y) + blk * H * 32;
     R e = R(0);
+#pragma unroll 4
     for (int el = warp; el < H; el += kForceWarps) {
-      const int p = a.half_tmm[el];
+      const int p = __ldg(a.half_tmm + el);
       const R w = (R)half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
       const cx<R> u = Ug[el * 32 + lane], y = Yg[el * 32 + lane];
       e += w * (y.re * u.re + y.im * u.im);
@@ -694,12 +695,22 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_kernel(WorkArgs a) {
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(&a.flags[4], 1) == ncta - 1);
   __syncthreads();
-  if (last && threadIdx.x < 6) {
-    __threadfence();
-    const volatile double* vp = a.vpart;
+  if (!last) return;
+  // last CTA: every thread sums a fixed strided subset of the partials, then
+  // a tree over the threads (fixed order, so the virial is deterministic)
+  __threadfence();
+  __shared__ double red[kForceWarps * 32];
+  for (int c = 0; c < 6; ++c) {
     double t = 0.0;
-    for (int b = 0; b < ncta; ++b) t += vp[6 * b + threadIdx.x];
-    a.virial[threadIdx.x] = t;
+    for (int b = threadIdx.x; b < ncta; b += blockDim.x) t += __ldcg(a.vpart + 6 * b + c);
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) a.virial[c] = red[0];
+    __syncthreads();
   }
 }
 
