@@ -146,17 +146,27 @@ int upload(snap_ctx* c, T** dst, const std::vector<T>& v) {
 int upload_yrec(snap_ctx* c) {
   const std::vector<double> coef = c->tab.term_coef(c->beta.data());
   const size_t n = c->tab.terms.size();
+  // With a staged conjugate plane the index word holds 2H-range indices
+  // (element + H for a conjugated read) and no conjugation flags.
+  const bool cp = snap::yi_conjplane((int)c->rsize(), c->tab.H);
+  const unsigned H = (unsigned)c->tab.H;
+  auto word = [&](unsigned w) -> unsigned {
+    if (!cp) return w;
+    const unsigned e1 = (w & 1023u) + ((w >> 20) & 1u) * H;
+    const unsigned e2 = ((w >> 10) & 1023u) + ((w >> 21) & 1u) * H;
+    return e1 | (e2 << 11) | (w & (1u << 22));
+  };
   if (c->precision == SNAP_MIXED) {
     std::vector<snap::YRec<float>> r(n);
     for (size_t k = 0; k < n; ++k) {
-      r[k].w = c->tab.terms[k];
+      r[k].w = word(c->tab.terms[k]);
       r[k].c = (float)coef[k];
     }
     return upload(c, reinterpret_cast<snap::YRec<float>**>(&c->d_yrec), r);
   }
   std::vector<snap::YRec<double>> r(n);
   for (size_t k = 0; k < n; ++k) {
-    r[k].w = c->tab.terms[k];
+    r[k].w = word(c->tab.terms[k]);
     r[k].pad = 0;
     r[k].c = coef[k];
   }

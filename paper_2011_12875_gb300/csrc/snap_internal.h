@@ -137,7 +137,10 @@ struct YiGeometry {
   int nblk, ysplit, threads, nslices;
   size_t smem;
   bool staged;
+  bool conjplane;  // a conjugated copy of the block is staged too (records index it)
 };
+// Whether compute_Y stages U and its conjugate (records in the 2H-index format).
+bool yi_conjplane(int rsize, int H);
 YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves);
 
 // Per-configuration virial: sum of vatom over each configuration's atoms.

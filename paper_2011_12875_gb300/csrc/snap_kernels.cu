@@ -224,7 +224,26 @@ __device__ __forceinline__ void y_term(unsigned w, R c, const cx<R>* __restrict_
   }
 }
 
-template <typename R, bool STAGED>
+// Term with the U elements addressed in a staged [2][H][32] block whose
+// second half is the conjugate of the first (no conjugation flags).
+template <typename R>
+__device__ __forceinline__ void y_term_cp(unsigned w, R c, const cx<R>* __restrict__ us,
+                                          cx<R>* __restrict__ Yg, int lane, YAcc<R>& y) {
+  const cx<R> u1 = us[(int)(w & 2047u) * 32 + lane];
+  const cx<R> u2 = us[(int)((w >> 11) & 2047u) * 32 + lane];
+  const R pr = u1.re * u2.re - u1.im * u2.im;
+  const R pi = u1.re * u2.im + u1.im * u2.re;
+  y.re += c * pr;
+  y.im += c * pi;
+  if (w & (1u << 22)) {
+    Yg[y.o * 32 + lane] = mk<R>(y.re, y.im);
+    y.re = R(0);
+    y.im = R(0);
+    ++y.o;
+  }
+}
+
+template <typename R, bool STAGED, bool CP>
 __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -233,7 +252,7 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   const cx<R>* us = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
   if (STAGED) {
     cx<R>* su = reinterpret_cast<cx<R>*>(smem);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(su + H * 32);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(su + (CP ? 2 : 1) * H * 32);
     const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
@@ -251,6 +270,13 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
       if (threadIdx.x == 0) atomicMax(&a.flags[3], 1);
       return;
     }
+    if (CP) {
+      for (int e = threadIdx.x; e < H * 32; e += blockDim.x) {
+        const cx<R> v = su[e];
+        su[H * 32 + e] = mk<R>(v.re, -v.im);
+      }
+      __syncthreads();
+    }
     us = su;
   }
   const int slice = blockIdx.y * (blockDim.x >> 5) + warp;
@@ -265,10 +291,16 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   y.re = R(0);
   y.im = R(0);
   y.o = o0;
+  auto term = [&](unsigned w, R c) {
+    if constexpr (CP)
+      y_term_cp<R>(w, c, us, Yg, lane, y);
+    else
+      y_term<R>(w, c, us, Yg, lane, y);
+  };
   if constexpr (sizeof(R) == 4) {
     // two 8-byte records per 16-byte load
     if ((q & 1) && q < q1) {
-      y_term<R>(rec[q].w, rec[q].c, us, Yg, lane, y);
+      term(rec[q].w, rec[q].c);
       ++q;
     }
     for (; q + 8 <= q1; q += 8) {
@@ -277,8 +309,8 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
       for (int k = 0; k < 4; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(rec + q) + k);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        y_term<R>(v[k].x, __uint_as_float(v[k].y), us, Yg, lane, y);
-        y_term<R>(v[k].z, __uint_as_float(v[k].w), us, Yg, lane, y);
+        term(v[k].x, __uint_as_float(v[k].y));
+        term(v[k].z, __uint_as_float(v[k].w));
       }
     }
   } else {
@@ -287,11 +319,10 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(rec + q + k));
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        y_term<R>(v[k].x, (R)__hiloint2double((int)v[k].w, (int)v[k].z), us, Yg, lane, y);
+      for (int k = 0; k < 4; ++k) term(v[k].x, (R)__hiloint2double((int)v[k].w, (int)v[k].z));
     }
   }
-  for (; q < q1; ++q) y_term<R>(rec[q].w, rec[q].c, us, Yg, lane, y);
+  for (; q < q1; ++q) term(rec[q].w, rec[q].c);
 }
 
 // ------------------------------------------------------- bispectrum B_l
@@ -745,13 +776,16 @@ cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+bool yi_conjplane(int rsize, int H) { return (size_t)4 * H * 32 * rsize + 16 <= 100 * 1024; }
+
 YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves) {
   YiGeometry g;
   g.nblk = (n + 31) / 32;
   const size_t stage = (size_t)2 * H * 32 * rsize + 16;  // complex [H][32] + mbarrier
   g.staged = stage <= 200 * 1024;
-  g.smem = g.staged ? stage : 0;
-  g.threads = (g.smem > 100 * 1024) ? 1024 : 256;
+  g.conjplane = yi_conjplane(rsize, H);
+  g.smem = g.staged ? (g.conjplane ? 2 * stage - 16 : stage) : 0;
+  g.threads = (g.smem > 100 * 1024) ? 1024 : (g.smem > 60 * 1024 ? 512 : 256);
   int cps = 2048 / g.threads;
   if (g.staged) cps = std::max(1, std::min(cps, (int)((227 * 1024) / g.smem)));
   const int target = nsm * cps * std::max(1, waves);
@@ -767,12 +801,16 @@ cudaError_t launch_yi(const WorkArgs& a, cudaStream_t s) {
   const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm, a.yi_waves);
   if (g.nslices != a.nslices) return cudaErrorInvalidValue;
   dim3 grid(g.nblk, g.ysplit);
-  if (g.staged) {
-    cudaError_t e = allow_smem(yi_kernel<R, true>, g.smem);
+  if (g.staged && g.conjplane) {
+    cudaError_t e = allow_smem(yi_kernel<R, true, true>, g.smem);
     if (e != cudaSuccess) return e;
-    yi_kernel<R, true><<<grid, g.threads, g.smem, s>>>(a);
+    yi_kernel<R, true, true><<<grid, g.threads, g.smem, s>>>(a);
+  } else if (g.staged) {
+    cudaError_t e = allow_smem(yi_kernel<R, true, false>, g.smem);
+    if (e != cudaSuccess) return e;
+    yi_kernel<R, true, false><<<grid, g.threads, g.smem, s>>>(a);
   } else {
-    yi_kernel<R, false><<<grid, g.threads, 0, s>>>(a);
+    yi_kernel<R, false, false><<<grid, g.threads, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -799,10 +837,11 @@ cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm, 2);
   dim3 grid(g.nblk, (a.ncoeff + 7) / 8);
+  const size_t sm = (size_t)2 * a.H * 32 * sizeof(R) + 16;
   if (g.staged) {
-    cudaError_t e = allow_smem(bi_kernel<R, true>, g.smem);
+    cudaError_t e = allow_smem(bi_kernel<R, true>, sm);
     if (e != cudaSuccess) return e;
-    bi_kernel<R, true><<<grid, 256, g.smem, s>>>(a);
+    bi_kernel<R, true><<<grid, 256, sm, s>>>(a);
   } else {
     bi_kernel<R, false><<<grid, 256, 0, s>>>(a);
   }
@@ -817,10 +856,11 @@ cudaError_t launch_dbi(const WorkArgs& a, const void* dU, double* dB, cudaStream
   const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm, 2);
   dim3 grid(g.nblk, (a.ncoeff + 7) / 8);
   const cx<R>* d = reinterpret_cast<const cx<R>*>(dU);
+  const size_t sm = (size_t)2 * a.H * 32 * sizeof(R) + 16;
   if (g.staged) {
-    cudaError_t e = allow_smem(dbi_kernel<R, true>, g.smem);
+    cudaError_t e = allow_smem(dbi_kernel<R, true>, sm);
     if (e != cudaSuccess) return e;
-    dbi_kernel<R, true><<<grid, 256, g.smem, s>>>(a, d, dB);
+    dbi_kernel<R, true><<<grid, 256, sm, s>>>(a, d, dB);
   } else {
     dbi_kernel<R, false><<<grid, 256, 0, s>>>(a, d, dB);
   }
