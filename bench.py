@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant-seconds", type=float, default=1.0)
+    ap.add_argument("--workload", default="bcc10_2j8",
+                    help="headline workload (bcc4_2j8, bcc10_2j8, bcc10_2j14, bcc20_2j14)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     return ap.parse_args()
 
 
@@ -157,7 +160,7 @@ def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return
-    w = inputs.WORKLOADS["bcc10_2j8"]
+    w = inputs.WORKLOADS[args.workload]
     cfg, beta = w.config(), w.beta()
     p = O.Params(w.twojmax)
     pairs = O.build_neighbors(cfg.pos, cfg.box, p.rcut)
@@ -384,13 +387,15 @@ def main():
     snap.load()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    head = inputs.WORKLOADS["bcc10_2j8"]
+    head = inputs.WORKLOADS[args.workload]
+    hprec = snap.MIXED if args.precision == "mixed" else snap.FP64
+    hpeak = FP32_PEAK_TFLOPS if hprec == snap.MIXED else FP64_PEAK_TFLOPS
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     sampler = ClockSampler(int(cvd) if cvd.isdigit() else local)
     if pg:
         pg.barrier()
     sampler.start()
-    r = time_variant(torch, snap, head, snap.MIXED, args.steps, args.warmup, flush, dev,
+    r = time_variant(torch, snap, head, hprec, args.steps, args.warmup, flush, dev,
                      profile=True)
     clocks = sampler.stop()
     ms_mean = statistics.mean(r["ms"])
@@ -415,23 +420,25 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max, "ms_per_step_median": ms_med,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 recursions + f64 geometry/accumulation",
+        "dtype": "f32 recursions + f64 geometry/accumulation" if hprec == snap.MIXED else "f64",
         "data": "synthetic BCC (a=3.1803 A, +-0.1 A displacements, seeded beta)",
         "config": {"workload": head.name, "natoms": r["natoms"], "twojmax": head.twojmax,
-                   "neighbors": r["npairs"] / r["natoms"], "precision": "mixed",
+                   "neighbors": r["npairs"] / r["natoms"], "precision": args.precision,
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": r["launches"] * args.steps,
         "stages": stages,
         "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "peak": hpeak, "unit": "TFLOP/s", "frac": achieved / hpeak,
+                     "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+                                     if hprec == snap.MIXED else
+                                     "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
                      "flops_per_launch": fl.get(dom, 0),
                      "traffic": read_traffic(dom, head.name)},
         "clocks": clocks,
     }
     if rank == 0:
-        line["e2e"] = e2e_host(snap, torch, head, snap.MIXED, min(args.steps, 300))
+        line["e2e"] = e2e_host(snap, torch, head, hprec, min(args.steps, 300))
         if not args.no_variants:
             variants = {}
             for name, prec, tag in (("bcc10_2j8", snap.FP64, "fp64_2j8_2000"),

@@ -190,9 +190,12 @@ int snap_compute_batch(snap_ctx* ctx, int nconf, const int* natoms, const double
                        const double* pos, double* energy, double* forces, double* virial,
                        int use_graph, void* stream);
 
-/* Launch-shape tunables: col_warps (2, 4 or 8 warps per CTA, i.e. neighbour
- * pairs per CTA, of the register column-chain kernels) and yi_waves (1..8,
- * compute_Y work items per SM).  snap_autotune times every combination of
+/* Launch-shape tunables: col_warps (2, 4 or 8 warps per CTA of the register
+ * column-chain kernels; each warp computes one atom, so this is atoms per CTA,
+ * halved where the CTA's shared memory would pass 227 KB) and yi_waves (1..8,
+ * fineness of the compute_Y split: the slices per 32-atom block minimise
+ * ceil(CTAs / resident CTAs) * (1/slices + 0.02/yi_waves)).  Neither changes
+ * a result bit.  snap_autotune times every combination of
  * col_warps in {2, 4, 8} and yi_waves in {1, 2, 4} on the given batch
  * (reps timed calls each, CUDA events on `stream`), keeps the fastest, and
  * reports its median time in *best_ms.  Synchronous. */

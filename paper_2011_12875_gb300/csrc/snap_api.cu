@@ -146,15 +146,25 @@ int upload(snap_ctx* c, T** dst, const std::vector<T>& v) {
 int upload_yrec(snap_ctx* c) {
   const std::vector<double> coef = c->tab.term_coef(c->beta.data());
   const size_t n = c->tab.terms.size();
-  // With a staged conjugate plane the index word holds 2H-range indices
-  // (element + H for a conjugated read) and no conjugation flags.
+  // Kernel word: bits 8-17 the second factor's element, 18-27 the first's
+  // (each times 256 is the byte offset of the element's [32] lanes of
+  // complex float), bit 28 ends a group, 29 an output, 30 / 31 conjugate the
+  // first / second factor (the sign bit of its imaginary part).  With a
+  // staged conjugate plane the elements run over 2H (element + H for a
+  // conjugated read) and the conjugation bits are clear.
   const bool cp = snap::yi_conjplane((int)c->rsize(), c->tab.H);
   const unsigned H = (unsigned)c->tab.H;
+  if ((cp ? 2 * H : H) > 1024u) return fail(c, SNAP_ERR_ARG, "compute_Y element index exceeds 10 bits");
   auto word = [&](unsigned w) -> unsigned {
-    if (!cp) return w;
-    const unsigned e1 = (w & 1023u) + ((w >> 20) & 1u) * H;
-    const unsigned e2 = ((w >> 10) & 1023u) + ((w >> 21) & 1u) * H;
-    return e1 | (e2 << 11) | (w & (1u << 22));
+    unsigned e1 = w & 1023u, e2 = (w >> 10) & 1023u;
+    unsigned c1 = (w >> 20) & 1u, c2 = (w >> 21) & 1u;
+    if (cp) {
+      e1 += c1 * H;
+      e2 += c2 * H;
+      c1 = c2 = 0;
+    }
+    return (e2 << 8) | (e1 << 18) | (((w >> 23) & 1u) << 28) | (((w >> 22) & 1u) << 29) |
+           (c1 << 30) | (c2 << 31);
   };
   if (c->precision == SNAP_MIXED) {
     std::vector<snap::YRec<float>> r(n);
@@ -423,7 +433,8 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
 // ---------------------------------------------------------------- batches
 // Shape of a batch: per-configuration atom ranges, boxes and image ranges,
 // and the CTA -> (configuration, first atom) map of the batched neighbour
-// build (8 atoms of one configuration per CTA).  Uploaded when it changes.
+// build (kNeighAtomsPerCta atoms of one configuration per CTA).  Uploaded
+// when it changes.
 int prepare_batch(snap_ctx* c, int nconf, const int* natoms, const double* boxes) {
   bool same = (nconf == c->bat_nconf) && (int)c->bat_n.size() == nconf;
   for (int k = 0; same && k < nconf; ++k)
@@ -441,7 +452,7 @@ int prepare_batch(snap_ctx* c, int nconf, const int* natoms, const double* boxes
         f.L[d] = boxes[3 * k + d];
         f.S[d] = (f.L[d] > 2.0 * (c->rcut + 0.05)) ? 0 : (int)std::ceil(c->rcut / f.L[d]) + 1;
       }
-      for (int o = 0; o < f.n; o += 8) map.push_back(make_int2(k, o));
+      for (int o = 0; o < f.n; o += snap::kNeighAtomsPerCta) map.push_back(make_int2(k, o));
       start += f.n;
     }
     int rc = upload(c, &c->d_confs, confs);

@@ -107,29 +107,34 @@ __device__ __forceinline__ void seed_column(c2<R> (&v)[N], bool take) {
 }
 
 // ------------------------------------------------------------- compute_U
-// CTA = one atom, NW warps; each warp takes P pairs at a time.  Each pair
-// group sums f_c u_t into its own shared-memory copy of Ulisttot (no two
-// lanes write one address), and the copies are added in a fixed order.
+// Warp = one atom (the CTA's warps are independent atoms, so no CTA-wide
+// barrier and no idle warps when the pair count is not a multiple of the
+// CTA's pairs); the warp takes P pairs at a time.  Pair group g sums f_c u_t
+// of pairs g, g + P, ... into its own shared-memory copy of Ulisttot (no two
+// lanes write one address) and the P copies are added in a fixed order, so
+// the result does not depend on the launch shape.
 template <typename R, int J2>
 __global__ void __launch_bounds__(256) ui_col_kernel(WorkArgs a) {
+  pdl_wait();
+  pdl_trigger();
   using S = Shape<J2>;
   constexpr int NC = S::NC, P = S::P;
-  const int NW = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = a.H;
-  c2<R>* acc = reinterpret_cast<c2<R>*>(smem);  // [NW*P][H]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long i = (long)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (i >= a.n) return;  // whole warp
+  c2<R>* acc = reinterpret_cast<c2<R>*>(smem) + (size_t)warp * P * H;  // [P][H]
   const int g = lane / NC, mb = lane - g * NC;
   const bool grp = g < P;
-  const int i = blockIdx.x;
-  for (int e = threadIdx.x; e < NW * P * H; e += blockDim.x) acc[e] = mk<R>(0, 0);
-  __syncthreads();
-  c2<R>* my = acc + (warp * P + (grp ? g : 0)) * H;
+  for (int e = lane; e < P * H; e += 32) acc[e] = mk<R>(0, 0);
+  __syncwarp();
+  c2<R>* my = acc + (grp ? g : 0) * H;
   R rs[J2 + 1];
 #pragma unroll
   for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
   const int cnt = a.cnt[i];
-  for (int s0 = warp * P; s0 < cnt; s0 += NW * P) {
+  for (int s0 = 0; s0 < cnt; s0 += P) {
     const int s = s0 + g;
     const bool ok = grp && s < cnt;
     c2<R> ca = mk<R>(1, 0), cb = mk<R>(0, 0);
@@ -176,173 +181,20 @@ __global__ void __launch_bounds__(256) ui_col_kernel(WorkArgs a) {
       }
     });
   }
-  __syncthreads();
+  __syncwarp();
   c2<R>* Ug = reinterpret_cast<c2<R>*>(a.U);
   const long blk = i >> 5;
-  const int li = i & 31;
-  for (int e = threadIdx.x; e < H; e += blockDim.x) {
+  const int li = (int)(i & 31);
+  for (int e = lane; e < H; e += 32) {
     R sr = 0, si = 0;
-    for (int c = 0; c < NW * P; ++c) {
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
       sr += acc[c * H + e].re;
       si += acc[c * H + e].im;
     }
     const int p = a.half_tmm[e];
     if (tmm_ma(p) == tmm_mb(p)) sr += (R)a.wself;
     Ug[(blk * H + e) * 32 + li] = mk<R>(sr, si);
-  }
-}
-
-// ------------------------------------------------------ fused dU + dE/dr
-// CTA = one atom with its weighted Y_i in shared memory; each lane carries
-// column mb of u and of du/dr_x, du/dr_y, du/dr_z (the recursion
-// differentiated, Sec. V-A) and accumulates Re(conj(Y) u), Re(conj(Y) du_d)
-// over its column; the pair's lanes are summed in shared memory and
-//   dE_i/dr_ik,d = (df_c/dr_d) S + f_c D_d      (Eq. snapforce2).
-// Up to 2J = 11 at most 168 registers (three CTAs of four warps, or six of
-// two, per SM); above, the columns need the full register file.
-template <typename R, int J2>
-__global__ void __maxnreg__(J2 <= 11 ? 168 : 255) de_col_kernel(WorkArgs a) {
-  using S_ = Shape<J2>;
-  constexpr int NC = S_::NC, P = S_::P;
-  const int NW = blockDim.x >> 5;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int H = a.H;
-  c2<R>* Yw = reinterpret_cast<c2<R>*>(smem);                 // [H]
-  R* red = reinterpret_cast<R*>(Yw + H);                       // [NW][32][4]
-  (void)NW;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane / NC, mb = lane - g * NC;
-  const bool grp = g < P;
-  const int i = blockIdx.x;
-  {
-    const c2<R>* Yg = reinterpret_cast<const c2<R>*>(a.Y);
-    const long blk = i >> 5;
-    const int li = i & 31;
-    for (int e = threadIdx.x; e < H; e += blockDim.x) {
-      const int p = a.half_tmm[e];
-      const R w = (R)hweight(tmm_t(p), tmm_ma(p), tmm_mb(p));
-      const c2<R> y = Yg[(blk * H + e) * 32 + li];
-      Yw[e] = mk<R>(w * y.re, w * y.im);
-    }
-  }
-  __syncthreads();
-  R rs[J2 + 1];
-#pragma unroll
-  for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
-  R* myred = red + (warp * 32 + lane) * 4;
-  const int cnt = a.cnt[i];
-  for (int s0 = warp * P; s0 < cnt; s0 += NW * P) {
-    const int s = s0 + g;
-    const bool ok = grp && s < cnt;
-    const long slot = (long)i * a.K + (ok ? s : 0);
-    const R* gm = reinterpret_cast<const R*>(a.geom) + slot * kGeomStride;
-    c2<R> ca = mk<R>(1, 0), cb = mk<R>(0, 0);  // conj(a), conj(b)
-    c2<R> cda[3], cdb[3];                      // conj(da/dr_d), conj(db/dr_d)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) cda[d] = cdb[d] = mk<R>(0, 0);
-    if (ok) {
-      ca = mk<R>(gm[0], -gm[1]);
-      cb = mk<R>(gm[2], -gm[3]);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        cda[d] = mk<R>(gm[8 + 2 * d], -gm[9 + 2 * d]);
-        cdb[d] = mk<R>(gm[14 + 2 * d], -gm[15 + 2 * d]);
-      }
-    }
-    c2<R> u[J2 + 1], du[3][J2 + 1];
-#pragma unroll
-    for (int k = 0; k <= J2; ++k) {
-      u[k] = mk<R>(0, 0);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) du[d][k] = mk<R>(0, 0);
-    }
-    R Ssum = 0, D[3] = {0, 0, 0};
-    if (mb == 0) {
-      u[0] = mk<R>(1, 0);
-      Ssum = Yw[0].re;
-    }
-    static_for<1, J2>([&](auto tc) {
-      constexpr int t = decltype(tc)::value;
-      if constexpr ((t & 1) == 0) {
-        const bool take = mb == t / 2;
-        seed_column<R, t>(u, take);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) seed_column<R, t>(du[d], take);
-      }
-      const R r = rs[t];
-      const c2<R> A = mk<R>(r * ca.re, r * ca.im), B = mk<R>(r * cb.re, r * cb.im);
-      c2<R> dA[3], dB[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        dA[d] = mk<R>(r * cda[d].re, r * cda[d].im);
-        dB[d] = mk<R>(r * cdb[d].re, r * cdb[d].im);
-      }
-      const bool act = 2 * mb <= t;
-      const c2<R>* yrow = Yw + half_base(t) + (act ? mb * (t + 1) : 0);
-#pragma unroll
-      for (int ma = t; ma >= 0; --ma) {
-        c2<R> v = mk<R>(0, 0), dv[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) dv[d] = mk<R>(0, 0);
-        if (ma < t) {
-          const R c = sqrt_int<R>(t - ma);
-          const c2<R> Ac = mk<R>(c * A.re, c * A.im);
-          const c2<R> p = u[ma];
-          v.re = Ac.re * p.re - Ac.im * p.im;
-          v.im = Ac.re * p.im + Ac.im * p.re;
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const c2<R> q = du[d][ma];
-            const R dr = c * dA[d].re, di = c * dA[d].im;
-            dv[d].re = dr * p.re - di * p.im + Ac.re * q.re - Ac.im * q.im;
-            dv[d].im = dr * p.im + di * p.re + Ac.re * q.im + Ac.im * q.re;
-          }
-        }
-        if (ma > 0) {
-          const R c = sqrt_int<R>(ma);
-          const c2<R> Bc = mk<R>(c * B.re, c * B.im);
-          const c2<R> p = u[ma - 1];
-          v.re -= Bc.re * p.re - Bc.im * p.im;
-          v.im -= Bc.re * p.im + Bc.im * p.re;
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const c2<R> q = du[d][ma - 1];
-            const R dr = c * dB[d].re, di = c * dB[d].im;
-            dv[d].re -= dr * p.re - di * p.im + Bc.re * q.re - Bc.im * q.im;
-            dv[d].im -= dr * p.im + di * p.re + Bc.re * q.im + Bc.im * q.re;
-          }
-        }
-        u[ma] = v;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) du[d][ma] = dv[d];
-        if (act) {
-          const c2<R> y = yrow[ma];
-          Ssum += y.re * v.re + y.im * v.im;
-#pragma unroll
-          for (int d = 0; d < 3; ++d) D[d] += y.re * dv[d].re + y.im * dv[d].im;
-        }
-      }
-    });
-    myred[0] = Ssum;
-    myred[1] = D[0];
-    myred[2] = D[1];
-    myred[3] = D[2];
-    __syncwarp();
-    if (ok && mb == 0) {
-      R t0 = 0, t1 = 0, t2 = 0, t3 = 0;
-      for (int c = 0; c < NC; ++c) {
-        const R* q = red + (warp * 32 + lane + c) * 4;
-        t0 += q[0];
-        t1 += q[1];
-        t2 += q[2];
-        t3 += q[3];
-      }
-      const R fc = gm[4];
-      a.dedr[slot * 3 + 0] = (double)(gm[5] * t0 + fc * t1);
-      a.dedr[slot * 3 + 1] = (double)(gm[6] * t0 + fc * t2);
-      a.dedr[slot * 3 + 2] = (double)(gm[7] * t0 + fc * t3);
-    }
-    __syncwarp();
   }
 }
 
@@ -357,24 +209,26 @@ __global__ void __maxnreg__(J2 <= 11 ? 168 : 255) de_col_kernel(WorkArgs a) {
 template <typename R, int J2>
 __global__ void __launch_bounds__(256) tan_col_kernel(WorkArgs a, const double* __restrict__ gd,
                                                           void* dUout) {
+  pdl_wait();
+  pdl_trigger();
   using S = Shape<J2>;
   constexpr int NC = S::NC, P = S::P;
-  const int NW = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = a.H;
-  c2<R>* acc = reinterpret_cast<c2<R>*>(smem);  // [NW*P][H]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long i = (long)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (i >= a.n) return;  // whole warp
+  c2<R>* acc = reinterpret_cast<c2<R>*>(smem) + (size_t)warp * P * H;  // [P][H]
   const int g = lane / NC, mb = lane - g * NC;
   const bool grp = g < P;
-  const int i = blockIdx.x;
-  for (int e = threadIdx.x; e < NW * P * H; e += blockDim.x) acc[e] = mk<R>(0, 0);
-  __syncthreads();
-  c2<R>* my = acc + (warp * P + (grp ? g : 0)) * H;
+  for (int e = lane; e < P * H; e += 32) acc[e] = mk<R>(0, 0);
+  __syncwarp();
+  c2<R>* my = acc + (grp ? g : 0) * H;
   R rs[J2 + 1];
 #pragma unroll
   for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
   const int cnt = a.cnt[i];
-  for (int s0 = warp * P; s0 < cnt; s0 += NW * P) {
+  for (int s0 = 0; s0 < cnt; s0 += P) {
     const int s = s0 + g;
     const bool ok = grp && s < cnt;
     c2<R> ca = mk<R>(1, 0), cb = mk<R>(0, 0), cda = mk<R>(0, 0), cdb = mk<R>(0, 0);
@@ -447,13 +301,14 @@ __global__ void __launch_bounds__(256) tan_col_kernel(WorkArgs a, const double* 
       }
     });
   }
-  __syncthreads();
+  __syncwarp();
   c2<R>* Ug = reinterpret_cast<c2<R>*>(dUout);
   const long blk = i >> 5;
-  const int li = i & 31;
-  for (int e = threadIdx.x; e < H; e += blockDim.x) {
+  const int li = (int)(i & 31);
+  for (int e = lane; e < H; e += 32) {
     R sr = 0, si = 0;
-    for (int c = 0; c < NW * P; ++c) {
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
       sr += acc[c * H + e].re;
       si += acc[c * H + e].im;
     }
@@ -462,8 +317,9 @@ __global__ void __launch_bounds__(256) tan_col_kernel(WorkArgs a, const double* 
 }
 
 // --------------------------------------- fused dU + dE/dr, reverse mode
-// Same lane layout.  For one pair, S(a, b) = Re sum_t Y_t : conj(u_t) is a real
-// function of the Cayley-Klein parameters; its gradient comes from one
+// Same lane layout; warp = one atom, with its weighted Y_i in shared memory.
+// For one pair, S(a, b) = Re sum_t Y_t : conj(u_t) is a real function of the
+// Cayley-Klein parameters; its gradient comes from one
 // forward pass of the recursion (each lane stores its column of every layer
 // in shared memory) and one adjoint pass through the same recursion, with
 // the adjoint lambda_t of a column in registers:
@@ -479,41 +335,44 @@ __device__ __forceinline__ R shfl_down(R v) {
 }
 
 template <typename R, int J2>
-__global__ void __launch_bounds__(256) de_rev_col_kernel(WorkArgs a) {
+__global__ void __launch_bounds__(256, 2) de_rev_col_kernel(WorkArgs a) {
+  pdl_wait();
+  pdl_trigger();
   using S_ = Shape<J2>;
   constexpr int NC = S_::NC, P = S_::P;
   const int NW = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = a.H;
-  c2<R>* Yw = reinterpret_cast<c2<R>*>(smem);  // [H]
-  c2<R>* ust = Yw + H;                         // [NW*P][H] forward columns
-  R* red = reinterpret_cast<R*>(ust + (size_t)NW * P * H);  // [NW][32][5]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long i = (long)blockIdx.x * NW + warp;  // warp = one atom
+  if (i >= a.n) return;                          // whole warp
+  c2<R>* Yw = reinterpret_cast<c2<R>*>(smem) + (size_t)warp * H;  // [NW][H]
+  c2<R>* ust = reinterpret_cast<c2<R>*>(smem) + (size_t)NW * H;   // [NW*P][H] forward columns
+  R* red = reinterpret_cast<R*>(ust + (size_t)NW * P * H);       // [NW][32][5]
   const int g = lane / NC, mb = lane - g * NC;
   const bool grp = g < P;
-  const int i = blockIdx.x;
   {
     const c2<R>* Yg = reinterpret_cast<const c2<R>*>(a.Y);
     const long blk = i >> 5;
-    const int li = i & 31;
-    for (int e = threadIdx.x; e < H; e += blockDim.x) {
+    const int li = (int)(i & 31);
+    for (int e = lane; e < H; e += 32) {
       const int p = a.half_tmm[e];
       const R w = (R)hweight(tmm_t(p), tmm_ma(p), tmm_mb(p));
       const c2<R> y = Yg[(blk * H + e) * 32 + li];
       Yw[e] = mk<R>(w * y.re, w * y.im);
     }
   }
-  __syncthreads();
+  __syncwarp();
   c2<R>* my = ust + (warp * P + (grp ? g : 0)) * H;
   R rs[J2 + 1];
 #pragma unroll
   for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
   R* myred = red + (warp * 32 + lane) * 5;
   const int cnt = a.cnt[i];
-  for (int s0 = warp * P; s0 < cnt; s0 += NW * P) {
+  for (int s0 = 0; s0 < cnt; s0 += P) {
     const int s = s0 + g;
     const bool ok = grp && s < cnt;
-    const long slot = (long)i * a.K + (ok ? s : 0);
+    const long slot = i * a.K + (ok ? s : 0);
     const R* gm = reinterpret_cast<const R*>(a.geom) + slot * kGeomStride;
     c2<R> ka = mk<R>(1, 0), kb = mk<R>(0, 0);  // a and b
     if (ok) {
@@ -660,45 +519,42 @@ inline cudaError_t col_allow_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename R, int J2>
-cudaError_t launch_ui_col_t(const WorkArgs& a, cudaStream_t s) {
-  const int nw = a.col_warps;
-  const size_t sm = sizeof(c2<R>) * (size_t)nw * Shape<J2>::P * a.H;
-  cudaError_t e = col_allow_smem(ui_col_kernel<R, J2>, sm);
-  if (e != cudaSuccess) return e;
-  ui_col_kernel<R, J2><<<a.n, nw * 32, sm, s>>>(a);
-  return cudaGetLastError();
+// Warps (= atoms) per CTA: the tunable, halved until the CTA's shared memory
+// (proportional to its warps) fits the 227 KB limit.
+inline int col_fit_warps(int nw, size_t per_warp) {
+  while (nw > 1 && per_warp * nw > (size_t)227 * 1024) nw >>= 1;
+  return nw;
 }
 
 template <typename R, int J2>
-cudaError_t launch_de_col_t(const WorkArgs& a, cudaStream_t s) {
-  const int nw = a.col_warps;
-  const size_t sm = sizeof(c2<R>) * (size_t)a.H + sizeof(R) * nw * 32 * 4;
-  cudaError_t e = col_allow_smem(de_col_kernel<R, J2>, sm);
+cudaError_t launch_ui_col_t(const WorkArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const size_t per = sizeof(c2<R>) * (size_t)Shape<J2>::P * a.H;
+  const int nw = col_fit_warps(a.col_warps, per);
+  cudaError_t e = col_allow_smem(ui_col_kernel<R, J2>, per * nw);
   if (e != cudaSuccess) return e;
-  de_col_kernel<R, J2><<<a.n, nw * 32, sm, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(ui_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a);
 }
 
 template <typename R, int J2>
 cudaError_t launch_tan_col_t(const WorkArgs& a, const double* g, void* dU, cudaStream_t s) {
-  const int nw = a.col_warps;
-  const size_t sm = sizeof(c2<R>) * (size_t)nw * Shape<J2>::P * a.H;
-  cudaError_t e = col_allow_smem(tan_col_kernel<R, J2>, sm);
+  if (a.n <= 0) return cudaSuccess;
+  const size_t per = sizeof(c2<R>) * (size_t)Shape<J2>::P * a.H;
+  const int nw = col_fit_warps(a.col_warps, per);
+  cudaError_t e = col_allow_smem(tan_col_kernel<R, J2>, per * nw);
   if (e != cudaSuccess) return e;
-  tan_col_kernel<R, J2><<<a.n, nw * 32, sm, s>>>(a, g, dU);
-  return cudaGetLastError();
+  return launch_pdl(tan_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a, g, dU);
 }
 
 template <typename R, int J2>
 cudaError_t launch_de_rev_col_t(const WorkArgs& a, cudaStream_t s) {
-  const int nw = a.col_warps;
-  const size_t sm = sizeof(c2<R>) * ((size_t)a.H + (size_t)nw * Shape<J2>::P * a.H) +
-                    sizeof(R) * nw * 32 * 5;
-  cudaError_t e = col_allow_smem(de_rev_col_kernel<R, J2>, sm);
+  if (a.n <= 0) return cudaSuccess;
+  // per warp: Yw [H], forward columns [P][H], lane partials [32][5]
+  const size_t per = sizeof(c2<R>) * (size_t)(1 + Shape<J2>::P) * a.H + sizeof(R) * 32 * 5;
+  const int nw = col_fit_warps(a.col_warps, per);
+  cudaError_t e = col_allow_smem(de_rev_col_kernel<R, J2>, per * nw);
   if (e != cudaSuccess) return e;
-  de_rev_col_kernel<R, J2><<<a.n, nw * 32, sm, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(de_rev_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a);
 }
 
 }  // namespace col

@@ -6,6 +6,35 @@
 
 namespace snap {
 
+// Programmatic dependent launch.  Every kernel of the library starts with
+// pdl_wait() (returns once the preceding kernel in the stream has completed
+// and its writes are visible; a no-op for a normal launch) followed by
+// pdl_trigger() (lets the next kernel be scheduled while this one runs), and
+// every launch goes through launch_pdl, so consecutive kernels overlap their
+// launch latency instead of leaving the GPU idle between them.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+#endif
+
 constexpr int kMaxTwoJ = 14;
 constexpr int kMaxNeighCap = 64;
 constexpr int kRootDim = 16;     // rootpq table is kRootDim x kRootDim
@@ -57,10 +86,13 @@ struct NeighConf {
   int S[3];
 };
 
+// centre atoms per CTA of the device neighbour build
+constexpr int kNeighAtomsPerCta = 2;
+
 struct NeighArgs {
   int n, K;
-  // batch mode: confs != nullptr; CTA b builds atoms cta_map[b].y + 0..7 of
-  // configuration cta_map[b].x
+  // batch mode: confs != nullptr; CTA b builds atoms
+  // cta_map[b].y + 0..kNeighAtomsPerCta-1 of configuration cta_map[b].x
   const NeighConf* confs;
   const int2* cta_map;
   const double* pos;     // [n][3]

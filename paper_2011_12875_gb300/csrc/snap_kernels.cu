@@ -77,6 +77,8 @@ __device__ __forceinline__ cx<R> prev_elem(const cx<R>* lay, int tp, int m, int 
 // and w_self is added on the diagonal (Eq. u).
 template <typename R, int NW>
 __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = a.H, L = a.lmax, J2 = a.twojmax;
   R* root = reinterpret_cast<R*>(smem);
@@ -159,9 +161,12 @@ __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
 //   Y_t[ma][mb] += coef * U_t1[ma1][mb1] * U_t2[ma2][mb2],
 // coef = betaw * C(ma1,ma2) C(mb1,mb2) (with the mirror signs), where a U
 // element past the stored half columns is read conjugated from its mirror.
-// A term record is 10 + 10 index bits, two conjugation flags and an
-// end-of-output flag.  Each warp owns a contiguous run of outputs, so every Y
-// element is accumulated in registers and written once (no atomics).
+// The terms of an output come grouped by their first factor, so a group
+// costs one load and one complex multiply of U_t1 and each term one load and
+// two FMAs: Y += U_t1 * sum_k coef_k U_t2,k.  A term record is a word (two
+// element offsets, conjugation flags, end-of-group and end-of-output bits)
+// and the coefficient.  Each warp owns a contiguous run of outputs, so every
+// Y element is accumulated in registers and written once (no atomics).
 constexpr unsigned kSpinLimit = 1u << 24;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -199,52 +204,54 @@ __device__ __forceinline__ double flip_if(double v, unsigned bit) {
   return bit ? -v : v;
 }
 
+// v with its sign bit XORed with bit 31 of m
+__device__ __forceinline__ float flip_sign(float v, unsigned m) {
+  return __int_as_float(__float_as_int(v) ^ (int)m);
+}
+__device__ __forceinline__ double flip_sign(double v, unsigned m) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)m << 32));
+}
+
 template <typename R>
 struct YAcc {
-  R re, im;
+  R re, im;  // the output element
+  R ar, ai;  // sum of coef * second factor over the current group
   int o;
 };
 
-template <typename R>
-__device__ __forceinline__ void y_term(unsigned w, R c, const cx<R>* __restrict__ us,
+// One term of an output: acc += coef * U2; at the end of a group (terms with
+// one first factor U1), Y += U1 * acc; at the end of an output, store Y.
+// `ul` points at lane 0's element 0 plus this lane (elements 256 B apart for
+// complex float, 512 B for complex double).  CP: the staged block is
+// [2][H][32] with the conjugate in its second half (no sign flips).
+template <typename R, bool CP>
+__device__ __forceinline__ void y_term(unsigned w, R c, const char* __restrict__ ul,
                                        cx<R>* __restrict__ Yg, int lane, YAcc<R>& y) {
-  const cx<R> u1 = us[(int)(w & 1023u) * 32 + lane];
-  const cx<R> u2 = us[(int)((w >> 10) & 1023u) * 32 + lane];
-  const R b = flip_if(u1.im, (w >> 20) & 1u);
-  const R d = flip_if(u2.im, (w >> 21) & 1u);
-  const R pr = u1.re * u2.re - b * d;
-  const R pi = u1.re * d + b * u2.re;
-  y.re += c * pr;
-  y.im += c * pi;
-  if (w & (1u << 22)) {
-    Yg[y.o * 32 + lane] = mk<R>(y.re, y.im);
-    y.re = R(0);
-    y.im = R(0);
-    ++y.o;
-  }
-}
-
-// Term with the U elements addressed in a staged [2][H][32] block whose
-// second half is the conjugate of the first (no conjugation flags).
-template <typename R>
-__device__ __forceinline__ void y_term_cp(unsigned w, R c, const cx<R>* __restrict__ us,
-                                          cx<R>* __restrict__ Yg, int lane, YAcc<R>& y) {
-  const cx<R> u1 = us[(int)(w & 2047u) * 32 + lane];
-  const cx<R> u2 = us[(int)((w >> 11) & 2047u) * 32 + lane];
-  const R pr = u1.re * u2.re - u1.im * u2.im;
-  const R pi = u1.re * u2.im + u1.im * u2.re;
-  y.re += c * pr;
-  y.im += c * pi;
-  if (w & (1u << 22)) {
-    Yg[y.o * 32 + lane] = mk<R>(y.re, y.im);
-    y.re = R(0);
-    y.im = R(0);
-    ++y.o;
+  constexpr int SH = sizeof(R) == 4 ? 0 : 1;
+  const cx<R> u2 = *reinterpret_cast<const cx<R>*>(ul + ((w & 0x3FF00u) << SH));
+  const R i2 = CP ? u2.im : flip_sign(u2.im, w & 0x80000000u);
+  y.ar += c * u2.re;
+  y.ai += c * i2;
+  if (w & (1u << 28)) {
+    const cx<R> u1 = *reinterpret_cast<const cx<R>*>(ul + (((w >> 10) & 0x3FF00u) << SH));
+    const R i1 = CP ? u1.im : flip_sign(u1.im, (w << 1) & 0x80000000u);
+    y.re += u1.re * y.ar - i1 * y.ai;
+    y.im += u1.re * y.ai + i1 * y.ar;
+    y.ar = R(0);
+    y.ai = R(0);
+    if (w & (1u << 29)) {
+      Yg[y.o * 32 + lane] = mk<R>(y.re, y.im);
+      y.re = R(0);
+      y.im = R(0);
+      ++y.o;
+    }
   }
 }
 
 template <typename R, bool STAGED, bool CP>
 __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long blk = blockIdx.x;
@@ -288,15 +295,10 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   const int q1 = a.yfirst[o1];
   int q = a.yfirst[o0];
   YAcc<R> y;
-  y.re = R(0);
-  y.im = R(0);
+  y.re = y.im = y.ar = y.ai = R(0);
   y.o = o0;
-  auto term = [&](unsigned w, R c) {
-    if constexpr (CP)
-      y_term_cp<R>(w, c, us, Yg, lane, y);
-    else
-      y_term<R>(w, c, us, Yg, lane, y);
-  };
+  const char* ul = reinterpret_cast<const char*>(us + lane);
+  auto term = [&](unsigned w, R c) { y_term<R, CP>(w, c, ul, Yg, lane, y); };
   if constexpr (sizeof(R) == 4) {
     // two 8-byte records per 16-byte load
     if ((q & 1) && q < q1) {
@@ -332,6 +334,8 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
 // summed per output element and each output is dotted with conj(U_t).
 template <typename R, bool STAGED>
 __global__ void __launch_bounds__(256) bi_kernel(WorkArgs a) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long blk = blockIdx.x;
@@ -394,6 +398,8 @@ __global__ void __launch_bounds__(256) bi_kernel(WorkArgs a) {
 // read from global memory.
 template <typename R, bool STAGED>
 __global__ void __launch_bounds__(256) dbi_kernel(WorkArgs a, const cx<R>* __restrict__ dUg, double* dB) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long blk = blockIdx.x;
@@ -458,6 +464,8 @@ __global__ void __launch_bounds__(256) dbi_kernel(WorkArgs a, const cx<R>* __res
 // gathered through the reverse-slot map like the forces (w = 1 gives -F).
 __global__ void __launch_bounds__(256) force_weighted_kernel(WorkArgs a, const double* __restrict__ wt,
                                                              double* __restrict__ grad) {
+  pdl_wait();
+  pdl_trigger();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long k = (long)blockIdx.x * 8 + warp;
   if (k >= a.n) return;
@@ -492,6 +500,8 @@ __global__ void __launch_bounds__(256) force_weighted_kernel(WorkArgs a, const d
 // <x, y> = Re(conj(x) y), which is Eq. (snapforce2) for this pair.
 template <typename R, int NW>
 __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = a.H, L = a.lmax, J2 = a.twojmax;
   R* root = reinterpret_cast<R*>(smem);
@@ -633,115 +643,197 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
 }
 
 // --------------------------------------------- energy, forces and virial
-// One CTA per 32-atom block (lanes = atoms for the energy, so the U and Y
-// reads are coalesced).  E_i - beta_0 is a cubic form in U, so by Euler's
-// relation E_i = beta_0 + (1/3) Re sum_t Y_t : conj(U_t) (full matrices; half
-// layout with half_weight), accumulated in FP64.  Forces: one warp per atom,
-// lanes over slots, F_i = sum_k dE_i/dr_ik - sum_k dE_k/dr_ki with the second
-// term gathered through the reverse-slot map (no atomics).  The virial
-// W_ab = -sum dE_i/dr_ik,a r_ik,b is reduced per CTA; the last CTA to finish
-// adds the CTA partials in a fixed order.
-constexpr int kForceWarps = 8;
+// CTA = kFAtoms consecutive atoms, kFThreads threads.  FP64 runs at 1/64 of
+// the FP32 rate on this part, so the FP64 work is laid out dense:
+//  * energy: E_i - beta_0 is a cubic form in U, so by Euler's relation
+//    E_i = beta_0 + (1/3) Re sum_t Y_t : conj(U_t) (full matrices; half layout
+//    with half_weight); kFSlices threads per atom take every kFSlices-th
+//    element in the working precision and their partials are added in FP64,
+//    in order;
+//  * forces: one thread per (atom, slot) forms
+//    g = dE_i/dr_ik - dE_k/dr_ki (the second term through the reverse-slot
+//    map, no atomics) and the virial products -dE_i/dr_ik,a r_ik,b; then one
+//    thread per (atom, component) adds its atom's g in slot order, so
+//    F_i = sum_k g in a fixed order;
+//  * virial: W_ab = -sum dE_i/dr_ik,a r_ik,b is reduced per CTA and the last
+//    CTA to finish adds the CTA partials in a fixed order (batch mode: per
+//    atom, in slot order, reduced per configuration afterwards).
+constexpr int kFAtoms = 8;
+constexpr int kFThreads = 128;
+constexpr int kFSlices = kFThreads / kFAtoms;  // energy partials per atom
+
+inline size_t force_smem(int K, bool vatom) {
+  return sizeof(double) * (size_t)kFAtoms * K * (vatom ? 9 : 3);
+}
 
 template <typename R>
-__global__ void __launch_bounds__(kForceWarps * 32) force_kernel(WorkArgs a) {
-  __shared__ double ep[kForceWarps][32];
-  __shared__ double vs[kForceWarps][6];
+__global__ void __launch_bounds__(kFThreads) force_kernel(WorkArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) double fsm[];  // g [kFAtoms*K][3], batch: + v [kFAtoms*K][6]
+  __shared__ int off[kFAtoms + 1];
+  __shared__ double ep[kFSlices][kFAtoms];
   __shared__ bool last;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long blk = blockIdx.x;
-  const int part = blockIdx.y;  // quarter of the block's atoms for the forces
-  const int H = a.H;
-  if (part == 0) {
-    // per-warp partial over every 8th element in the working precision,
-    // combined over warps in FP64
-    const cx<R>* Ug = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
-    const cx<R>* Yg = reinterpret_cast<const cx<R>*>(a.Y) + blk * H * 32;
+  const int K = a.K, H = a.H;
+  const int tid = threadIdx.x;
+  const long i0 = (long)blockIdx.x * kFAtoms;
+  const int na = (int)min((long)kFAtoms, a.n - i0);
+  double* gs = fsm;
+  double* vsm = fsm + (size_t)kFAtoms * K * 3;
+  if (tid < 32) {  // slot offsets: inclusive scan of the clamped counts
+    int c = tid < na ? min(a.cnt[i0 + tid], K) : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, c, o);
+      if (tid >= o) c += t;
+    }
+    if (tid < kFAtoms) off[tid + 1] = c;
+    if (tid == 0) off[0] = 0;
+  }
+  // energy partials (lanes over atoms, so the U and Y reads are coalesced)
+  if (a.energy) {
+    const int ai = tid % kFAtoms, sl = tid / kFAtoms;
     R e = R(0);
+    if (ai < na) {
+      const long i = i0 + ai;
+      const long blk = i >> 5;
+      const int li = (int)(i & 31);
+      const cx<R>* Ug = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32 + li;
+      const cx<R>* Yg = reinterpret_cast<const cx<R>*>(a.Y) + blk * H * 32 + li;
 #pragma unroll 4
-    for (int el = warp; el < H; el += kForceWarps) {
-      const int p = __ldg(a.half_tmm + el);
-      const R w = (R)half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
-      const cx<R> u = Ug[el * 32 + lane], y = Yg[el * 32 + lane];
-      e += w * (y.re * u.re + y.im * u.im);
-    }
-    ep[warp][lane] = (double)e;
-  }
-  double v[6] = {0, 0, 0, 0, 0, 0};
-  for (int aa = part * kForceWarps + warp; aa < (part + 1) * kForceWarps; aa += kForceWarps) {
-    const long i = blk * 32 + aa;
-    if (i >= a.n) break;
-    double f[3] = {0, 0, 0};
-    const int cnt = a.cnt[i];
-    for (int s = lane; s < cnt; s += 32) {
-      const long q = i * a.K + s;
-      const int k = a.nbr[q];
-      const int r = a.rev[q];
-      const double* d = a.dedr + q * 3;
-      const double* rv = a.rij + q * 3;
-      for (int c = 0; c < 3; ++c) f[c] += d[c];
-      if (r >= 0) {
-        const double* dk = a.dedr + ((long)k * a.K + r) * 3;
-        for (int c = 0; c < 3; ++c) f[c] -= dk[c];
+      for (int el = sl; el < H; el += kFSlices) {
+        const int p = __ldg(a.half_tmm + el);
+        const R w = (R)half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
+        const cx<R> u = Ug[el * 32], y = Yg[el * 32];
+        e += w * (y.re * u.re + y.im * u.im);
       }
-      v[0] -= d[0] * rv[0];
-      v[1] -= d[1] * rv[1];
-      v[2] -= d[2] * rv[2];
-      v[3] -= d[0] * rv[1];
-      v[4] -= d[0] * rv[2];
-      v[5] -= d[1] * rv[2];
     }
-    for (int c = 0; c < 3; ++c) f[c] = warp_sum(f[c]);
-    if (lane == 0)
-      for (int c = 0; c < 3; ++c) a.forces[3 * i + c] = f[c];
-    if (a.vatom) {  // batch mode: per-atom virial, reduced per configuration later
-      double va[6];
-      for (int c = 0; c < 6; ++c) {
-        va[c] = warp_sum(v[c]);
-        v[c] = 0.0;
-      }
-      if (lane == 0)
-        for (int c = 0; c < 6; ++c) a.vatom[6 * i + c] = va[c];
-    }
+    ep[sl][ai] = (double)e;
   }
-  for (int c = 0; c < 6; ++c) v[c] = warp_sum(v[c]);
-  if (lane == 0)
-    for (int c = 0; c < 6; ++c) vs[warp][c] = v[c];
   __syncthreads();
-  if (part == 0 && warp == 0) {
-    const long i = blk * 32 + lane;
-    double e = 0.0;
-    for (int w = 0; w < kForceWarps; ++w) e += ep[w][lane];
-    if (a.energy && i < a.n) a.energy[i] = a.beta0 + e / 3.0;
+  const int total = off[na];
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  for (int p0 = tid; p0 < total; p0 += 2 * kFThreads) {
+    // two slots per pass: all first-level loads before the reverse-slot ones
+    long q[2];
+    bool ok[2];
+    int rv_[2], kn[2];
+    double d[2][3], r[2][3], dk[2][3];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int p = p0 + u * kFThreads;
+      ok[u] = p < total;
+      int lo = 0, hi = na - 1;  // atom of flat slot p: last k with off[k] <= p
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= p) lo = mid;
+        else hi = mid - 1;
+      }
+      q[u] = (i0 + lo) * K + (ok[u] ? p - off[lo] : 0);
+      rv_[u] = -1;
+      kn[u] = 0;
+      for (int c = 0; c < 3; ++c) d[u][c] = r[u][c] = dk[u][c] = 0.0;
+      if (ok[u]) {
+        rv_[u] = a.rev[q[u]];
+        kn[u] = a.nbr[q[u]];
+        for (int c = 0; c < 3; ++c) {
+          d[u][c] = a.dedr[q[u] * 3 + c];
+          r[u][c] = a.rij[q[u] * 3 + c];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (ok[u] && rv_[u] >= 0)
+        for (int c = 0; c < 3; ++c) dk[u][c] = a.dedr[((long)kn[u] * K + rv_[u]) * 3 + c];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!ok[u]) continue;
+      const int p = p0 + u * kFThreads;
+      for (int c = 0; c < 3; ++c) gs[3 * p + c] = d[u][c] - dk[u][c];
+      const double vp[6] = {-d[u][0] * r[u][0], -d[u][1] * r[u][1], -d[u][2] * r[u][2],
+                            -d[u][0] * r[u][1], -d[u][0] * r[u][2], -d[u][1] * r[u][2]};
+      if (a.vatom) {
+        for (int c = 0; c < 6; ++c) vsm[6 * p + c] = vp[c];
+      } else {
+        for (int c = 0; c < 6; ++c) v[c] += vp[c];
+      }
+    }
   }
-  if (!a.virial || a.vatom) return;
-  const int cta = blockIdx.x * gridDim.y + part;
-  const int ncta = gridDim.x * gridDim.y;
-  if (threadIdx.x < 6) {
+  __syncthreads();
+  if (tid < 3 * na) {
+    const int ai = tid / 3, c = tid - 3 * ai;
+    double f = 0.0;
+    for (int p = off[ai]; p < off[ai + 1]; ++p) f += gs[3 * p + c];
+    a.forces[3 * (i0 + ai) + c] = f;
+  }
+  if (a.energy && tid < na) {
+    double e = 0.0;
+    for (int sl = 0; sl < kFSlices; ++sl) e += ep[sl][tid];
+    a.energy[i0 + tid] = a.beta0 + e / 3.0;
+  }
+  if (a.vatom) {  // batch mode: per-atom virial, reduced per configuration later
+    for (int t = tid; t < 6 * na; t += kFThreads) {
+      const int ai = t / 6, c = t - 6 * ai;
+      double w = 0.0;
+      for (int p = off[ai]; p < off[ai + 1]; ++p) w += vsm[6 * p + c];
+      a.vatom[6 * (i0 + ai) + c] = w;
+    }
+    return;
+  }
+  if (!a.virial) return;
+  // CTA partial of the virial: the threads' sums through shared memory,
+  // 16 strided FP64 chains per component, then those 16 in order
+  __shared__ double vt[6][kFThreads];
+  __shared__ double v16[6][16];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) vt[c][tid] = v[c];
+  __syncthreads();
+  if (tid < 96) {
+    const int c = tid >> 4, sub = tid & 15;
     double t = 0.0;
-    for (int w = 0; w < kForceWarps; ++w) t += vs[w][threadIdx.x];
-    a.vpart[6 * cta + threadIdx.x] = t;
+#pragma unroll
+    for (int k = sub; k < kFThreads; k += 16) t += vt[c][k];
+    v16[c][sub] = t;
+  }
+  __syncthreads();
+  const int cta = blockIdx.x, ncta = gridDim.x;
+  if (tid < 6) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) t += v16[tid][k];
+    a.vpart[6 * cta + tid] = t;
     __threadfence();
   }
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(&a.flags[4], 1) == ncta - 1);
+  if (tid == 0) last = (atomicAdd(&a.flags[4], 1) == ncta - 1);
   __syncthreads();
   if (!last) return;
-  // last CTA: every thread sums a fixed strided subset of the partials, then
-  // a tree over the threads (fixed order, so the virial is deterministic)
+  // last CTA: 16 strided chains per component over the CTA partials (loads
+  // issued 8 at a time), then the 16 in order: a fixed order, so the virial
+  // is deterministic
   __threadfence();
-  __shared__ double red[kForceWarps * 32];
-  for (int c = 0; c < 6; ++c) {
+  if (tid < 96) {
+    const int c = tid >> 4, sub = tid & 15;
     double t = 0.0;
-    for (int b = threadIdx.x; b < ncta; b += blockDim.x) t += __ldcg(a.vpart + 6 * b + c);
-    red[threadIdx.x] = t;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
+    for (int b0 = sub; b0 < ncta; b0 += 16 * 8) {
+      double x[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int b = b0 + 16 * k;
+        x[k] = b < ncta ? __ldcg(a.vpart + 6 * b + c) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) t += x[k];
     }
-    if (threadIdx.x == 0) a.virial[c] = red[0];
-    __syncthreads();
+    v16[c][sub] = t;
+  }
+  __syncthreads();
+  if (tid < 6) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) t += v16[tid][k];
+    a.virial[tid] = t;
   }
 }
 
@@ -772,8 +864,7 @@ cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s) {
   const size_t sm = ui_smem<R>(a.H, a.lmax);
   cudaError_t e = allow_smem(ui_kernel<R, kUiWarps>, sm);
   if (e != cudaSuccess) return e;
-  ui_kernel<R, kUiWarps><<<a.n, kUiWarps * 32, sm, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(ui_kernel<R, kUiWarps>, dim3(a.n), dim3(kUiWarps * 32), sm, s, a);
 }
 
 bool yi_conjplane(int rsize, int H) { return (size_t)4 * H * 32 * rsize + 16 <= 100 * 1024; }
@@ -788,9 +879,24 @@ YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves) {
   g.threads = (g.smem > 100 * 1024) ? 1024 : (g.smem > 60 * 1024 ? 512 : 256);
   int cps = 2048 / g.threads;
   if (g.staged) cps = std::max(1, std::min(cps, (int)((227 * 1024) / g.smem)));
-  const int target = nsm * cps * std::max(1, waves);
-  g.ysplit = std::max(1, (target + g.nblk - 1) / g.nblk);
-  g.ysplit = std::min(g.ysplit, 64);
+  // Split each 32-atom block's outputs into ysplit CTAs.  CTAs of one launch
+  // take about equal time, so the launch lasts ceil(CTAs / resident) CTA
+  // lifetimes; pick the split that minimises
+  //   ceil(nblk ysplit / resident) (1 / ysplit + c),
+  // c = the fixed per-CTA cost (staging U) relative to a whole block's terms,
+  // taken as 0.02 / waves (the tunable: more waves, finer splits).
+  const long resident = (long)nsm * cps;
+  const double c = 0.02 / std::max(1, waves);
+  double best = 1e300;
+  g.ysplit = 1;
+  for (int ys = 1; ys <= 64; ++ys) {
+    const long w = ((long)g.nblk * ys + resident - 1) / resident;
+    const double t = (double)w * (1.0 / ys + c);
+    if (t < best - 1e-12) {
+      best = t;
+      g.ysplit = ys;
+    }
+  }
   g.nslices = g.ysplit * (g.threads / 32);
   return g;
 }
@@ -804,15 +910,13 @@ cudaError_t launch_yi(const WorkArgs& a, cudaStream_t s) {
   if (g.staged && g.conjplane) {
     cudaError_t e = allow_smem(yi_kernel<R, true, true>, g.smem);
     if (e != cudaSuccess) return e;
-    yi_kernel<R, true, true><<<grid, g.threads, g.smem, s>>>(a);
+    return launch_pdl(yi_kernel<R, true, true>, dim3(grid), dim3(g.threads), g.smem, s, a);
   } else if (g.staged) {
     cudaError_t e = allow_smem(yi_kernel<R, true, false>, g.smem);
     if (e != cudaSuccess) return e;
-    yi_kernel<R, true, false><<<grid, g.threads, g.smem, s>>>(a);
-  } else {
-    yi_kernel<R, false, false><<<grid, g.threads, 0, s>>>(a);
+    return launch_pdl(yi_kernel<R, true, false>, dim3(grid), dim3(g.threads), g.smem, s, a);
   }
-  return cudaGetLastError();
+  return launch_pdl(yi_kernel<R, false, false>, dim3(grid), dim3(g.threads), 0, s, a);
 }
 
 template <typename R>
@@ -821,15 +925,16 @@ cudaError_t launch_de(const WorkArgs& a, cudaStream_t s) {
   const size_t sm = de_smem<R>(a.H, a.lmax);
   cudaError_t e = allow_smem(de_kernel<R, kDeWarps>, sm);
   if (e != cudaSuccess) return e;
-  de_kernel<R, kDeWarps><<<a.n, kDeWarps * 32, sm, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(de_kernel<R, kDeWarps>, dim3(a.n), dim3(kDeWarps * 32), sm, s, a);
 }
 
 template <typename R>
 cudaError_t launch_force(const WorkArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  force_kernel<R><<<dim3((a.n + 31) / 32, 32 / kForceWarps), kForceWarps * 32, 0, s>>>(a);
-  return cudaGetLastError();
+  const size_t sm = force_smem(a.K, a.vatom != nullptr);
+  cudaError_t e = allow_smem(force_kernel<R>, sm);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(force_kernel<R>, dim3((unsigned)((a.n + kFAtoms - 1) / kFAtoms)), dim3(kFThreads), sm, s, a);
 }
 
 template <typename R>
@@ -841,11 +946,9 @@ cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s) {
   if (g.staged) {
     cudaError_t e = allow_smem(bi_kernel<R, true>, sm);
     if (e != cudaSuccess) return e;
-    bi_kernel<R, true><<<grid, 256, sm, s>>>(a);
-  } else {
-    bi_kernel<R, false><<<grid, 256, 0, s>>>(a);
+    return launch_pdl(bi_kernel<R, true>, dim3(grid), dim3(256), sm, s, a);
   }
-  return cudaGetLastError();
+  return launch_pdl(bi_kernel<R, false>, dim3(grid), dim3(256), 0, s, a);
 }
 template cudaError_t launch_bi<float>(const WorkArgs&, cudaStream_t);
 template cudaError_t launch_bi<double>(const WorkArgs&, cudaStream_t);
@@ -860,19 +963,16 @@ cudaError_t launch_dbi(const WorkArgs& a, const void* dU, double* dB, cudaStream
   if (g.staged) {
     cudaError_t e = allow_smem(dbi_kernel<R, true>, sm);
     if (e != cudaSuccess) return e;
-    dbi_kernel<R, true><<<grid, 256, sm, s>>>(a, d, dB);
-  } else {
-    dbi_kernel<R, false><<<grid, 256, 0, s>>>(a, d, dB);
+    return launch_pdl(dbi_kernel<R, true>, dim3(grid), dim3(256), sm, s, a, d, dB);
   }
-  return cudaGetLastError();
+  return launch_pdl(dbi_kernel<R, false>, dim3(grid), dim3(256), 0, s, a, d, dB);
 }
 template cudaError_t launch_dbi<float>(const WorkArgs&, const void*, double*, cudaStream_t);
 template cudaError_t launch_dbi<double>(const WorkArgs&, const void*, double*, cudaStream_t);
 
 cudaError_t launch_force_weighted(const WorkArgs& a, const double* w, double* grad, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  force_weighted_kernel<<<(a.n + 7) / 8, 256, 0, s>>>(a, w, grad);
-  return cudaGetLastError();
+  return launch_pdl(force_weighted_kernel, dim3((a.n + 7) / 8), dim3(256), 0, s, a, w, grad);
 }
 
 // Per-configuration virial: one CTA per configuration sums its atoms in a
@@ -880,6 +980,8 @@ cudaError_t launch_force_weighted(const WorkArgs& a, const double* w, double* gr
 __global__ void __launch_bounds__(256) virial_conf_kernel(const double* __restrict__ vatom,
                                                           const NeighConf* __restrict__ confs,
                                                           double* __restrict__ virial) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[256];
   const NeighConf c = confs[blockIdx.x];
   for (int k = 0; k < 6; ++k) {
@@ -899,8 +1001,7 @@ __global__ void __launch_bounds__(256) virial_conf_kernel(const double* __restri
 cudaError_t launch_virial_conf(const double* vatom, const NeighConf* confs, int nconf, double* virial,
                                cudaStream_t s) {
   if (nconf <= 0) return cudaSuccess;
-  virial_conf_kernel<<<nconf, 256, 0, s>>>(vatom, confs, virial);
-  return cudaGetLastError();
+  return launch_pdl(virial_conf_kernel, dim3(nconf), dim3(256), 0, s, vatom, confs, virial);
 }
 
 template cudaError_t launch_ui<float>(const WorkArgs&, cudaStream_t);

@@ -14,11 +14,15 @@ namespace snap {
 
 namespace {
 
-constexpr int kNbWarps = 8;   // centre atoms per CTA (one warp each)
-constexpr int kNbTile = 256;  // candidate atoms staged per shared-memory tile
+constexpr int kNbWarps = 8;                       // warps per CTA
+constexpr int kNbSplit = 4;                       // warps per centre atom
+constexpr int kNbAtoms = kNbWarps / kNbSplit;     // centre atoms per CTA
+static_assert(kNbAtoms == kNeighAtomsPerCta, "batch CTA map and kernel disagree");
 constexpr unsigned kFull = 0xffffffffu;
 
 __global__ void pos4_kernel(int n, const double* __restrict__ pos, float4* __restrict__ pos4) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) pos4[i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], 0.f);
 }
@@ -36,60 +40,34 @@ __device__ __forceinline__ double norm2(double x, double y, double z) {
   return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
 }
 
-// One warp per centre atom i.  Lanes first test 32 atoms k at a time in
-// FP32 with a margin (all images in range); the survivors are appended, in a
-// fixed order (tile, image, lane), to a per-warp candidate list in shared
-// memory.  Every 32 candidates, the list is checked exactly in FP64 with all
-// lanes busy, and accepted pairs are appended to the output with a ballot, so
-// the list is deterministic and FP64 work is spent only on real candidates.
-constexpr int kCandCap = 64;
+// kNbSplit warps per centre atom i, each scanning one contiguous part of the
+// candidate range: lanes test 32 atoms k at a time in FP32 with a margin (all
+// images in range) and the survivors are appended, in a fixed order
+// (32-block, image, lane), to the part's candidate list in shared memory.
+// Then one warp per atom checks the parts' lists, concatenated in order,
+// exactly in FP64 32 candidates at a time (FP64 runs at 1/64 of the FP32 rate,
+// so it is spent once per atom, on dense lanes) and appends the accepted
+// pairs with a ballot: the list is deterministic and identical to a
+// sequential scan of all candidates.
+constexpr int kCandCap = 128;  // candidates per part (more: reported as overflow)
 
 __device__ __forceinline__ int pack_img(int x, int y, int z) {
   return (x + 128) | ((y + 128) << 8) | ((z + 128) << 16);
 }
 
-__device__ __forceinline__ void exact_batch(const NeighArgs& a, double Lx, double Ly, double Lz, int i,
-                                            double xi, double yi, double zi, double rc2, const int* cj,
-                                            const int* cs, int nb, int lane, int& count) {
-  bool in = false;
-  double ex = 0, ey = 0, ez = 0;
-  int j = 0, ix = 0, iy = 0, iz = 0;
-  if (lane < nb) {
-    j = cj[lane];
-    const int pk = cs[lane];
-    ix = (pk & 0xff) - 128;
-    iy = ((pk >> 8) & 0xff) - 128;
-    iz = ((pk >> 16) & 0xff) - 128;
-    ex = sep1(i, j, xi, a.pos[3 * j], ix, Lx);
-    ey = sep1(i, j, yi, a.pos[3 * j + 1], iy, Ly);
-    ez = sep1(i, j, zi, a.pos[3 * j + 2], iz, Lz);
-    in = norm2(ex, ey, ez) < rc2;
-  }
-  const unsigned m = __ballot_sync(kFull, in);
-  if (in) {
-    const int slot = count + __popc(m & ((1u << lane) - 1u));
-    if (slot < a.K) {
-      const long q = (long)i * a.K + slot;
-      a.nbr[q] = j;
-      a.img[3 * q] = (signed char)ix;
-      a.img[3 * q + 1] = (signed char)iy;
-      a.img[3 * q + 2] = (signed char)iz;
-      a.rij[3 * q] = ex;
-      a.rij[3 * q + 1] = ey;
-      a.rij[3 * q + 2] = ez;
-    }
-  }
-  count += __popc(m);
-}
-
 template <bool BATCH>
 __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a) {
-  __shared__ float4 tile[kNbTile];
+  pdl_wait();
+  pdl_trigger();
   __shared__ int cand_j[kNbWarps][kCandCap];
   __shared__ int cand_s[kNbWarps][kCandCap];
+  __shared__ int ncands[kNbWarps];
+  __shared__ int cmax;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int part = warp % kNbSplit, ai = warp / kNbSplit;
+  const unsigned lt = (1u << lane) - 1u;
   // candidate range [j_lo, j_hi), box and image range of this CTA's atoms
-  int j_lo = 0, j_hi = a.n, i = blockIdx.x * kNbWarps + warp;
+  int j_lo = 0, j_hi = a.n, i = blockIdx.x * kNbAtoms + ai;
   int Sx = a.Sx, Sy = a.Sy, Sz = a.Sz;
   double Ldx = a.Lx, Ldy = a.Ly, Ldz = a.Lz;
   if (BATCH) {
@@ -97,7 +75,7 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
     const NeighConf c = a.confs[m.x];
     j_lo = c.start;
     j_hi = c.start + c.n;
-    i = c.start + m.y + warp;
+    i = c.start + m.y + ai;
     Ldx = c.L[0];
     Ldy = c.L[1];
     Ldz = c.L[2];
@@ -105,37 +83,39 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
     Sy = c.S[1];
     Sz = c.S[2];
   }
+  if (threadIdx.x == 0) cmax = 0;
   const bool NEAREST = (Sx == 0 && Sy == 0 && Sz == 0);
   const bool active = i < j_hi;
+  // this warp's part of the candidate range, in 32-blocks
+  const int nblk32 = (j_hi - j_lo + 31) / 32;
+  const int per = (nblk32 + kNbSplit - 1) / kNbSplit;
+  const int c0 = j_lo + 32 * min(nblk32, per * part);
+  const int c1 = min(j_hi, j_lo + 32 * min(nblk32, per * (part + 1)));
   int* cj = cand_j[warp];
   int* cs = cand_s[warp];
+  int ncand = 0;  // candidates of this part (warp-uniform, may pass kCandCap)
   float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  double xi = 0, yi = 0, zi = 0;
-  if (active) {
-    pi4 = a.pos4[i];
-    xi = a.pos[3 * i];
-    yi = a.pos[3 * i + 1];
-    zi = a.pos[3 * i + 2];
-  }
+  if (active) pi4 = a.pos4[i];
   const float Lx = (float)Ldx, Ly = (float)Ldy, Lz = (float)Ldz;
   const float iLx = 1.f / Lx, iLy = 1.f / Ly, iLz = 1.f / Lz;
   const float rcf = (float)a.rcut + 1e-2f;
   const float rc2f = rcf * rcf;
-  const double rc2 = a.rcut * a.rcut;
-  const unsigned lt = (1u << lane) - 1u;
-  int count = 0;  // accepted pairs (warp-uniform)
-  int ncand = 0;  // pending candidates (warp-uniform)
-  for (int j0 = j_lo; j0 < j_hi; j0 += kNbTile) {
-    __syncthreads();
-    for (int q = threadIdx.x; q < kNbTile; q += blockDim.x)
-      tile[q] = (j0 + q < j_hi) ? a.pos4[j0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-    if (!active) continue;
-    const int jn = min(kNbTile, j_hi - j0);
-    for (int jj = 0; jj < jn; jj += 32) {
-      const int j = j0 + jj + lane;
-      const bool valid = (jj + lane) < jn;
-      const float4 pj = tile[jj + lane];
+  auto push = [&](bool c, int j, int pk) {
+    const unsigned m = __ballot_sync(kFull, c);
+    if (c) {
+      const int p = ncand + __popc(m & lt);
+      if (p < kCandCap) {
+        cj[p] = j;
+        cs[p] = pk;
+      }
+    }
+    ncand += __popc(m);
+  };
+  if (active) {
+    for (int j0 = c0; j0 < c1; j0 += 32) {
+      const int j = j0 + lane;
+      const bool valid = j < c1;
+      const float4 pj = valid ? __ldg(a.pos4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
       const float dx0 = pj.x - pi4.x, dy0 = pj.y - pi4.y, dz0 = pj.z - pi4.z;
       // nearest-image shift counts, kept in float (int <-> float conversions
       // run on a slow pipe and are only done for the rare candidates)
@@ -143,34 +123,8 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
       const float bx = dx0 + nxf * Lx, by = dy0 + nyf * Ly, bz = dz0 + nzf * Lz;
       if (NEAREST) {
         // box > 2 (rcut + margin) in every direction: only the nearest image
-        bool c = valid && (bx * bx + by * by + bz * bz < rc2f) && (j != i);
-        const unsigned m = __ballot_sync(kFull, c);
-        if (m) {
-          if (c) {
-            const int pos = ncand + __popc(m & lt);
-            cj[pos] = j;
-            cs[pos] = pack_img((int)nxf, (int)nyf, (int)nzf);
-          }
-          ncand += __popc(m);
-          if (ncand >= 32) {
-            __syncwarp();
-            exact_batch(a, Ldx, Ldy, Ldz, i, xi, yi, zi, rc2, cj, cs, 32, lane, count);
-            __syncwarp();
-            const int rest = ncand - 32;
-            int mj = 0, ms = 0;
-            if (lane < rest) {
-              mj = cj[32 + lane];
-              ms = cs[32 + lane];
-            }
-            __syncwarp();
-            if (lane < rest) {
-              cj[lane] = mj;
-              cs[lane] = ms;
-            }
-            ncand = rest;
-            __syncwarp();
-          }
-        }
+        const bool c = valid && (bx * bx + by * by + bz * bz < rc2f) && (j != i);
+        push(c, j, c ? pack_img((int)nxf, (int)nyf, (int)nzf) : 0);
         continue;
       }
       float sxf = -(float)Sx;
@@ -188,42 +142,64 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
               iz = (int)(nzf + szf);
               c = !((j == i) && ix == 0 && iy == 0 && iz == 0);
             }
-            const unsigned m = __ballot_sync(kFull, c);
-            if (c) {
-              const int pos = ncand + __popc(m & lt);
-              cj[pos] = j;
-              cs[pos] = pack_img(ix, iy, iz);
-            }
-            ncand += __popc(m);
-            if (ncand >= 32) {
-              __syncwarp();
-              exact_batch(a, Ldx, Ldy, Ldz, i, xi, yi, zi, rc2, cj, cs, 32, lane, count);
-              __syncwarp();
-              const int rest = ncand - 32;
-              int mj = 0, ms = 0;
-              if (lane < rest) {
-                mj = cj[32 + lane];
-                ms = cs[32 + lane];
-              }
-              __syncwarp();
-              if (lane < rest) {
-                cj[lane] = mj;
-                cs[lane] = ms;
-              }
-              ncand = rest;
-              __syncwarp();
-            }
+            push(c, j, c ? pack_img(ix, iy, iz) : 0);
           }
         }
       }
     }
   }
-  __shared__ int cmax;
-  if (threadIdx.x == 0) cmax = 0;
+  if (lane == 0) ncands[warp] = ncand;
   __syncthreads();
-  if (active) {
-    __syncwarp();
-    if (ncand > 0) exact_batch(a, Ldx, Ldy, Ldz, i, xi, yi, zi, rc2, cj, cs, ncand, lane, count);
+  if (active && part == 0) {
+    // exact FP64 check of the concatenated candidate lists
+    int off[kNbSplit + 1];
+    off[0] = 0;
+    bool over = false;
+    for (int p = 0; p < kNbSplit; ++p) {
+      const int c = ncands[warp + p];
+      over |= c > kCandCap;
+      off[p + 1] = off[p] + min(c, kCandCap);
+    }
+    const double xi = a.pos[3 * i], yi = a.pos[3 * i + 1], zi = a.pos[3 * i + 2];
+    const double rc2 = a.rcut * a.rcut;
+    int count = 0;
+    for (int e0 = 0; e0 < off[kNbSplit]; e0 += 32) {
+      const int e = e0 + lane;
+      bool in = false;
+      double ex = 0, ey = 0, ez = 0;
+      int j = 0, ix = 0, iy = 0, iz = 0;
+      if (e < off[kNbSplit]) {
+        int p = 0;
+        while (e >= off[p + 1]) ++p;
+        j = cand_j[warp + p][e - off[p]];
+        const int pk = cand_s[warp + p][e - off[p]];
+        ix = (pk & 0xff) - 128;
+        iy = ((pk >> 8) & 0xff) - 128;
+        iz = ((pk >> 16) & 0xff) - 128;
+        ex = sep1(i, j, xi, a.pos[3 * j], ix, Ldx);
+        ey = sep1(i, j, yi, a.pos[3 * j + 1], iy, Ldy);
+        ez = sep1(i, j, zi, a.pos[3 * j + 2], iz, Ldz);
+        in = norm2(ex, ey, ez) < rc2;
+      }
+      const unsigned m = __ballot_sync(kFull, in);
+      if (in) {
+        const int slot = count + __popc(m & lt);
+        if (slot < a.K) {
+          const long q = (long)i * a.K + slot;
+          a.nbr[q] = j;
+          a.img[3 * q] = (signed char)ix;
+          a.img[3 * q + 1] = (signed char)iy;
+          a.img[3 * q + 2] = (signed char)iz;
+          a.rij[3 * q] = ex;
+          a.rij[3 * q + 1] = ey;
+          a.rij[3 * q + 2] = ez;
+        }
+      }
+      count += __popc(m);
+    }
+    // a part with more candidates than it can hold is reported as a list
+    // overflow (the caller sees a count above any capacity)
+    if (over) count = max(count, 1 << 20);
     if (lane == 0) {
       a.cnt[i] = min(count, a.K);
       atomicMax(&cmax, count);
@@ -239,6 +215,8 @@ __global__ void neigh_ingest_kernel(int n, int K, const double* __restrict__ pos
                                     const int* __restrict__ uidx, const signed char* __restrict__ uimg,
                                     int ucap, int* cnt, int* nbr, signed char* img, double* rij,
                                     int* flags) {
+  pdl_wait();
+  pdl_trigger();
   const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long)n * K) return;
   const int i = (int)(q / K), s = (int)(q - (long)i * K);
@@ -285,21 +263,24 @@ __global__ void neigh_ingest_kernel(int n, int K, const double* __restrict__ pos
 constexpr int kPairAtoms = 2;
 constexpr int kPairThreads = 64;
 
+__device__ __forceinline__ void sincospi_g(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_g(double x, double* s, double* c) { sincospi(x, s, c); }
+
 template <typename G>
-__device__ void write_geom(G* g, G* gm, double ar, double ai, double br, double bi, double fc,
-                           const double* dfc, const double* da, const double* db) {
+__device__ void write_geom(G* g, G* gm, double ar, double ai, double br, double bi, G fc,
+                           const G* dfc, const G* da, const G* db) {
   G v[kGeomStride];
   v[0] = G(ar);
   v[1] = G(ai);
   v[2] = G(br);
   v[3] = G(bi);
-  v[4] = G(fc);
+  v[4] = fc;
   for (int d = 0; d < 3; ++d) {
-    v[5 + d] = G(dfc[d]);
-    v[8 + 2 * d] = G(da[2 * d]);
-    v[9 + 2 * d] = G(da[2 * d + 1]);
-    v[14 + 2 * d] = G(db[2 * d]);
-    v[15 + 2 * d] = G(db[2 * d + 1]);
+    v[5 + d] = dfc[d];
+    v[8 + 2 * d] = da[2 * d];
+    v[9 + 2 * d] = da[2 * d + 1];
+    v[14 + 2 * d] = db[2 * d];
+    v[15 + 2 * d] = db[2 * d + 1];
   }
   for (int e = 0; e < kGeomStride; ++e) g[e] = v[e];
   if (!gm) return;
@@ -321,6 +302,8 @@ __device__ void write_geom(G* g, G* gm, double ar, double ai, double br, double 
 
 template <typename G>
 __global__ void __launch_bounds__(kPairThreads) pairs_kernel(WorkArgs a, int* rev) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ long qs[kPairAtoms * kMaxNeighCap];
   __shared__ long qm[kPairAtoms * kMaxNeighCap];
   __shared__ int ncanon;
@@ -384,38 +367,44 @@ __global__ void __launch_bounds__(kPairThreads) pairs_kernel(WorkArgs a, int* re
     const double r2 = x * x + y * y + z * z;
     const double ir = rsqrt(r2);
     const double r = r2 * ir;
-    double dfc[3] = {0, 0, 0}, da[6] = {0, 0, 0, 0, 0, 0}, db[6] = {0, 0, 0, 0, 0, 0};
+    G dfc[3] = {0, 0, 0}, da[6] = {0, 0, 0, 0, 0, 0}, db[6] = {0, 0, 0, 0, 0, 0};
     if (!(r < a.rcut)) {  // outside the cutoff (caller lists): no contribution
-      write_geom(g, gm, 1.0, 0.0, 0.0, 0.0, 0.0, dfc, da, db);
+      write_geom(g, gm, 1.0, 0.0, 0.0, 0.0, G(0), dfc, da, db);
       continue;
     }
-    const double c = a.rfac0 * M_PI * a.inv_span;  // d theta0 / d r
+    // The Cayley-Klein parameters in FP64 (Sec. II-A): theta0, z0 = r cot theta0,
+    // r0 = sqrt(r^2 + z0^2), a = (z0 - i z) / r0, b = (y - i x) / r0.
     double st, ct;
     sincospi(a.rfac0 * (r - a.rmin0) * a.inv_span, &st, &ct);
     const double ist = 1.0 / st;
     const double z0 = r * ct * ist;
-    const double dz0dr = ct * ist - r * c * ist * ist;
     const double ir0 = rsqrt(r2 + z0 * z0);
     const double ar = z0 * ir0, ai = -z * ir0;
     const double br = y * ir0, bi = -x * ir0;
-    double fc = 1.0, dfcdr = 0.0;
+    // Their gradients and the switching function in the working precision G
+    // (they only feed the G recursions): FP64 runs at 1/64 of the FP32 rate.
+    const G gr = G(r), gir = G(ir), gz0 = G(z0), gir0 = G(ir0), gist = G(ist), gct = G(ct);
+    const G gar = G(ar), gai = G(ai), gbr = G(br), gbi = G(bi);
+    const G c = G(a.rfac0 * M_PI * a.inv_span);  // d theta0 / d r
+    const G dz0dr = gct * gist - gr * c * gist * gist;
+    G fc = G(1), dfcdr = G(0);
     if (a.switchflag && r > a.rmin0) {
-      double sw, cw;
-      sincospi((r - a.rmin0) * a.inv_span, &sw, &cw);
-      fc = 0.5 * (cw + 1.0);
-      dfcdr = -0.5 * M_PI * a.inv_span * sw;
+      G sw, cw;
+      sincospi_g(G((r - a.rmin0) * a.inv_span), &sw, &cw);
+      fc = G(0.5) * (cw + G(1));
+      dfcdr = G(-0.5 * M_PI * a.inv_span) * sw;
     }
-    const double rv[3] = {x, y, z};
+    const G rv[3] = {G(x), G(y), G(z)};
     for (int d = 0; d < 3; ++d) {
-      const double ud = rv[d] * ir;
+      const G ud = rv[d] * gir;
       dfc[d] = dfcdr * ud;
-      const double dz0 = dz0dr * ud;
-      const double dr0 = (r * ud + z0 * dz0) * ir0;
+      const G dz0 = dz0dr * ud;
+      const G dr0 = (gr * ud + gz0 * dz0) * gir0;
       // d a = (d(z0 - i z) - a d r0) / r0 ; d b = (d(y - i x) - b d r0) / r0
-      da[2 * d] = (dz0 - ar * dr0) * ir0;
-      da[2 * d + 1] = ((d == 2 ? -1.0 : 0.0) - ai * dr0) * ir0;
-      db[2 * d] = ((d == 1 ? 1.0 : 0.0) - br * dr0) * ir0;
-      db[2 * d + 1] = ((d == 0 ? -1.0 : 0.0) - bi * dr0) * ir0;
+      da[2 * d] = (dz0 - gar * dr0) * gir0;
+      da[2 * d + 1] = ((d == 2 ? G(-1) : G(0)) - gai * dr0) * gir0;
+      db[2 * d] = ((d == 1 ? G(1) : G(0)) - gbr * dr0) * gir0;
+      db[2 * d + 1] = ((d == 0 ? G(-1) : G(0)) - gbi * dr0) * gir0;
     }
     write_geom(g, gm, ar, ai, br, bi, fc, dfc, da, db);
   }
@@ -427,20 +416,17 @@ inline int blocks_for(long n, int t) { return (int)((n + t - 1) / t); }
 
 cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  pos4_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, pos, pos4);
-  return cudaGetLastError();
+  return launch_pdl(pos4_kernel, dim3(blocks_for(n, 256)), dim3(256), 0, s, n, pos, pos4);
 }
 
 cudaError_t launch_neigh_build(const NeighArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  neigh_build_kernel<false><<<blocks_for(a.n, kNbWarps), kNbWarps * 32, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(neigh_build_kernel<false>, dim3(blocks_for(a.n, kNbAtoms)), dim3(kNbWarps * 32), 0, s, a);
 }
 
 cudaError_t launch_neigh_build_batch(const NeighArgs& a, int ncta, cudaStream_t s) {
   if (ncta <= 0) return cudaSuccess;
-  neigh_build_kernel<true><<<ncta, kNbWarps * 32, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(neigh_build_kernel<true>, dim3(ncta), dim3(kNbWarps * 32), 0, s, a);
 }
 
 cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, double Ly,
@@ -448,16 +434,13 @@ cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, doub
                                 const signed char* uimg, int ucap, int* cnt, int* nbr,
                                 signed char* img, double* rij, int* flags, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  neigh_ingest_kernel<<<blocks_for((long)n * K, 256), 256, 0, s>>>(
-      n, K, pos, Lx, Ly, Lz, ucnt, uidx, uimg, ucap, cnt, nbr, img, rij, flags);
-  return cudaGetLastError();
+  return launch_pdl(neigh_ingest_kernel, dim3(blocks_for((long)n * K, 256)), dim3(256), 0, s, n, K, pos, Lx, Ly, Lz, ucnt, uidx, uimg, ucap, cnt, nbr, img, rij, flags);
 }
 
 template <typename G>
 cudaError_t launch_pairs(const WorkArgs& a, int* rev, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  pairs_kernel<G><<<blocks_for(a.n, kPairAtoms), kPairThreads, 0, s>>>(a, rev);
-  return cudaGetLastError();
+  return launch_pdl(pairs_kernel<G>, dim3(blocks_for(a.n, kPairAtoms)), dim3(kPairThreads), 0, s, a, rev);
 }
 template cudaError_t launch_pairs<float>(const WorkArgs&, int*, cudaStream_t);
 template cudaError_t launch_pairs<double>(const WorkArgs&, int*, cudaStream_t);

@@ -181,9 +181,35 @@ void HostTables::build(int J2) {
             }
           }
         }
-        // every output has at least the term of the (t, 0, t) triple, whose
-        // Clebsch-Gordan product is 1; flag the last term of the output
-        if (terms.size() > first) terms.back() |= (1u << 22);
+        // Group the output's terms by their first factor (index and
+        // conjugation flag, stable): compute_Y then forms
+        //   Y += U_t1[..] * sum_k coef_k U_t2,k[..]
+        // once per group.  Bit 23 ends a group, bit 22 the output; every
+        // output has at least the term of the (t, 0, t) triple, whose
+        // Clebsch-Gordan product is 1.
+        const size_t cnt = terms.size() - first;
+        if (cnt > 0) {
+          std::vector<size_t> ord(cnt);
+          for (size_t k = 0; k < cnt; ++k) ord[k] = k;
+          auto key = [&](size_t k) { return terms[first + k] & ((1023u) | (1u << 20)); };
+          std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return key(x) < key(y); });
+          std::vector<unsigned> tw(cnt);
+          std::vector<double> tc(cnt);
+          std::vector<int> tq(cnt);
+          for (size_t k = 0; k < cnt; ++k) {
+            tw[k] = terms[first + ord[k]];
+            tc[k] = term_cg[first + ord[k]];
+            tq[k] = term_trip[first + ord[k]];
+          }
+          const unsigned kmask = 1023u | (1u << 20);
+          for (size_t k = 0; k < cnt; ++k) {
+            const bool ge = (k + 1 == cnt) || ((tw[k] & kmask) != (tw[k + 1] & kmask));
+            terms[first + k] = tw[k] | (ge ? (1u << 23) : 0u);
+            term_cg[first + k] = tc[k];
+            term_trip[first + k] = tq[k];
+          }
+          terms.back() |= (1u << 22);
+        }
         term_out_first.push_back((int)first);
       }
   term_out_first.push_back((int)terms.size());
