@@ -212,8 +212,6 @@ def time_variant(torch, snap, w, precision, steps, warmup, flush, dev, profile=F
     s.sync()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(steps)]
-    if profile:
-        s.profile(True)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for k in range(steps):
@@ -225,7 +223,17 @@ def time_variant(torch, snap, w, precision, steps, warmup, flush, dev, profile=F
     wall = time.perf_counter() - t0
     s.sync()
     ms = [a.elapsed_time(b) for a, b in evs]
-    prof = s.profile_read() if profile else None
+    prof = None
+    if profile:
+        # stage times from a separate pass with events between the stages
+        # (they would otherwise perturb the timed steps above)
+        s.profile(True)
+        for k in range(min(steps, 20)):
+            flush.fill_(k & 0xff)
+            s.compute(pos, cfg.box, E, F, W, wait=False)
+        s.sync()
+        prof = s.profile_read()
+        s.profile(False)
     launches = s.launches_per_call()
     npairs = int(s.get_buffer(snap.BUF_NBR_CNT).sum())
     s.close()

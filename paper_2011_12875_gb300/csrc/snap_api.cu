@@ -16,6 +16,24 @@
 
 using snap::HostTables;
 
+// A captured single-configuration evaluation, replayed while the same call
+// repeats (same sizes, box, buffers, tunables and workspace).  A key is
+// captured the second time it is seen in a row, so one-off calls never pay
+// for capture and instantiation.
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<unsigned long long> key;   // of exec
+  std::vector<unsigned long long> seen;  // key of the previous uncaptured call
+  snap::WorkArgs args;                   // host-side state of the captured call
+  int launches = 0, n = 0, K = 0;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key.clear();
+    seen.clear();
+  }
+};
+
 struct snap_ctx {
   int twojmax = 0;
   double rcut = 0, rfac0 = 0, rmin0 = 0, wself = 1.0;
@@ -84,6 +102,11 @@ struct snap_ctx {
   cudaStream_t gstream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   const void* g_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long g_ws = -1;  // workspace generation the batch graph was captured with
+  // bumped whenever a device buffer that a captured graph refers to moves
+  long long ws_gen = 0;
+  // single-configuration graphs (snap_compute*, snap_compute_host)
+  GraphSlot gdev, ghost;
 
   // buffers of snap_compute_host
   int cap_host = 0;
@@ -142,6 +165,15 @@ int upload(snap_ctx* c, T** dst, const std::vector<T>& v) {
   return SNAP_OK;
 }
 
+// Overwrite an existing table of the same size in place (its address, which
+// captured graphs hold, stays valid); allocate it the first time.
+template <typename T>
+int upload_inplace(snap_ctx* c, T** dst, const std::vector<T>& v) {
+  if (!*dst) return upload(c, dst, v);
+  if (!v.empty()) SNAP_CUDA(c, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SNAP_OK;
+}
+
 // compute_Y term records (index word + coefficient in the working precision)
 int upload_yrec(snap_ctx* c) {
   const std::vector<double> coef = c->tab.term_coef(c->beta.data());
@@ -172,7 +204,7 @@ int upload_yrec(snap_ctx* c) {
       r[k].w = word(c->tab.terms[k]);
       r[k].c = (float)coef[k];
     }
-    return upload(c, reinterpret_cast<snap::YRec<float>**>(&c->d_yrec), r);
+    return upload_inplace(c, reinterpret_cast<snap::YRec<float>**>(&c->d_yrec), r);
   }
   std::vector<snap::YRec<double>> r(n);
   for (size_t k = 0; k < n; ++k) {
@@ -180,7 +212,7 @@ int upload_yrec(snap_ctx* c) {
     r[k].pad = 0;
     r[k].c = coef[k];
   }
-  return upload(c, reinterpret_cast<snap::YRec<double>**>(&c->d_yrec), r);
+  return upload_inplace(c, reinterpret_cast<snap::YRec<double>**>(&c->d_yrec), r);
 }
 
 // bispectrum term records (coefficients do not depend on beta)
@@ -245,6 +277,7 @@ int ensure_workspace(snap_ctx* c, int n, int K) {
   SNAP_CUDA(c, cudaMalloc(&c->d_vpart, sizeof(double) * 6 * (4 * nblk + 1)));
   c->cap_n = ncap;
   c->cap_nk = nkcap;
+  c->ws_gen += 1;
   return SNAP_OK;
 }
 
@@ -260,6 +293,14 @@ int ensure_slices(snap_ctx* c, int n) {
   }
   c->d_yslice = it->second;
   c->nslices = g.nslices;
+  c->ws_gen += 1;
+  return SNAP_OK;
+}
+
+int ensure_flags(snap_ctx* c) {
+  if (c->d_flags) return SNAP_OK;
+  SNAP_CUDA(c, cudaMalloc(&c->d_flags, 8 * sizeof(int)));
+  SNAP_CUDA(c, cudaMallocHost(&c->h_flags, 8 * sizeof(int)));
   return SNAP_OK;
 }
 
@@ -326,11 +367,8 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
     return fail(c, SNAP_ERR_ARG, "neighbour list: cnt, idx and img must all be given with 1 <= cap <= 64");
   const int K = user ? ucap : c->K;
   int rc = ensure_workspace(c, n, K);
+  if (!rc) rc = ensure_flags(c);
   if (rc) return rc;
-  if (!c->d_flags) {
-    SNAP_CUDA(c, cudaMalloc(&c->d_flags, 8 * sizeof(int)));
-    SNAP_CUDA(c, cudaMallocHost(&c->h_flags, 8 * sizeof(int)));
-  }
   rc = ensure_slices(c, n);
   if (rc) return rc;
   SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 8 * sizeof(int), s));
@@ -470,11 +508,8 @@ int prepare_batch(snap_ctx* c, int nconf, const int* natoms, const double* boxes
   }
   const int n = c->bat_total;
   int rc = ensure_workspace(c, n, c->K);
+  if (!rc) rc = ensure_flags(c);
   if (rc) return rc;
-  if (!c->d_flags) {
-    SNAP_CUDA(c, cudaMalloc(&c->d_flags, 8 * sizeof(int)));
-    SNAP_CUDA(c, cudaMallocHost(&c->h_flags, 8 * sizeof(int)));
-  }
   const int old_slices = c->nslices;
   rc = ensure_slices(c, n);
   if (rc) return rc;
@@ -552,6 +587,94 @@ int check_flags(snap_ctx* c) {
                     std::to_string(c->last_K));
   if (c->h_flags[1]) return fail(c, SNAP_ERR_NEIGH_ASYM, "neighbour list is not symmetric (missing reverse pair)");
   return SNAP_OK;
+}
+
+unsigned long long key_bits(double x) {
+  unsigned long long u;
+  std::memcpy(&u, &x, sizeof(u));
+  return u;
+}
+unsigned long long key_ptr(const void* p) { return (unsigned long long)(uintptr_t)p; }
+
+bool pinned_or_null(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+// Replay the slot's graph if the key matches; run directly the first time a
+// key is seen; capture (on the context's capture stream) and replay the
+// second time in a row.  run(stream) enqueues the whole evaluation and sets
+// the host-side state of the call (generation, last arguments and sizes).
+template <typename F>
+int graph_run(snap_ctx* c, GraphSlot& g, const std::vector<unsigned long long>& key, cudaStream_t s,
+              F&& run) {
+  if (!(g.exec && g.key == key)) {
+    if (g.seen != key) {
+      g.seen = key;
+      return run(s);
+    }
+    g.reset();
+    if (!c->gstream) SNAP_CUDA(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    const long long gen0 = c->generation;
+    SNAP_CUDA(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+    const int rc = run(c->gstream);
+    cudaError_t e = cudaStreamEndCapture(c->gstream, &graph);
+    c->generation = gen0;  // capturing evaluated nothing
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(c, SNAP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g.exec = nullptr;
+      return fail(c, SNAP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    g.key = key;
+    g.args = c->last_args;
+    g.n = c->last_n;
+    g.K = c->last_K;
+    g.launches = c->launches;
+  }
+  SNAP_CUDA(c, cudaGraphLaunch(g.exec, s));
+  c->generation += 1;
+  c->last_args = g.args;
+  c->have_last = true;
+  c->last_n = g.n;
+  c->last_K = g.K;
+  c->launches = g.launches;
+  return SNAP_OK;
+}
+
+// One energy + force evaluation on device buffers, through a cached CUDA
+// graph when the same call repeats (not while stage profiling is on).
+int compute_dev(snap_ctx* c, int n, const double* pos, const double* box, const int* ucnt,
+                const int* uidx, const signed char* uimg, int ucap, double* energy, double* forces,
+                double* virial, cudaStream_t s) {
+  const bool user = (ucnt || uidx || uimg);
+  auto run = [&](cudaStream_t st) {
+    return enqueue(c, n, pos, box, ucnt, uidx, uimg, ucap, energy, forces, virial, st);
+  };
+  if (c->prof_on || (user && (!ucnt || !uidx || !uimg || ucap < 1 || ucap > snap::kMaxNeighCap))) return run(s);
+  // every buffer exists before a capture (no allocation inside one)
+  const int K = user ? ucap : c->K;
+  int rc = ensure_workspace(c, n, K);
+  if (!rc) rc = ensure_flags(c);
+  if (!rc) rc = ensure_slices(c, n);
+  if (rc) return rc;
+  const std::vector<unsigned long long> key = {
+      1, (unsigned long long)c->ws_gen, (unsigned long long)n, (unsigned long long)K,
+      (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves, key_bits(box[0]),
+      key_bits(box[1]), key_bits(box[2]), key_ptr(pos), key_ptr(energy), key_ptr(forces),
+      key_ptr(virial), key_ptr(ucnt), key_ptr(uidx), key_ptr(uimg), (unsigned long long)ucap};
+  return graph_run(c, c->gdev, key, s, run);
 }
 
 }  // namespace
@@ -645,6 +768,13 @@ int snap_set_beta(snap_ctx* c, const double* beta) {
   if (!c || !beta) return fail(c, SNAP_ERR_ARG, "NULL argument");
   cudaDeviceSynchronize();
   c->beta.assign(beta, beta + 1 + c->tab.ncoeff);
+  // beta_0 is a kernel argument: captured graphs hold the old value
+  c->gdev.reset();
+  c->ghost.reset();
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
   return upload_yrec(c);
 }
 
@@ -669,7 +799,7 @@ int snap_compute(snap_ctx* c, int natoms, const double* pos, const double* box, 
     return SNAP_OK;
   }
   if (!pos || !forces) return fail(c, SNAP_ERR_ARG, "pos and forces are required");
-  int rc = enqueue(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, energy, forces, virial, s);
+  int rc = compute_dev(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, energy, forces, virial, s);
   if (rc) return rc;
   SNAP_CUDA(c, cudaStreamSynchronize(s));
   return check_flags(c);
@@ -687,7 +817,7 @@ int snap_compute_async(snap_ctx* c, int natoms, const double* pos, const double*
     return SNAP_OK;
   }
   if (!pos || !forces) return fail(c, SNAP_ERR_ARG, "pos and forces are required");
-  return enqueue(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, energy, forces, virial, s);
+  return compute_dev(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, energy, forces, virial, s);
 }
 
 int snap_sync(snap_ctx* c, void* stream) {
@@ -800,7 +930,7 @@ int snap_compute_batch(snap_ctx* c, int nconf, const int* natoms, const double* 
   if (rc) return rc;
   if (!use_graph) return launch_batch(c, pos, energy, forces, virial, s);
   const void* key[4] = {pos, energy, forces, virial};
-  const bool same = c->gexec && std::equal(key, key + 4, c->g_key);
+  const bool same = c->gexec && std::equal(key, key + 4, c->g_key) && c->g_ws == c->ws_gen;
   if (!same) {
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);
@@ -823,6 +953,7 @@ int snap_compute_batch(snap_ctx* c, int nconf, const int* natoms, const double* 
       return fail(c, SNAP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
     std::copy(key, key + 4, c->g_key);
+    c->g_ws = c->ws_gen;
   }
   SNAP_CUDA(c, cudaGraphLaunch(c->gexec, s));
   c->generation += 1;
@@ -922,15 +1053,41 @@ int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const dou
     SNAP_CUDA(c, cudaMalloc(&c->d_hW, sizeof(double) * 6));
     c->cap_host = natoms;
   }
-  SNAP_CUDA(c, cudaMemcpyAsync(c->d_hpos, pos_host, sizeof(double) * 3 * natoms, cudaMemcpyHostToDevice, s));
-  int rc = enqueue(c, natoms, c->d_hpos, box, nullptr, nullptr, nullptr, 0, energy_host ? c->d_hE : nullptr,
-                   c->d_hF, virial_host ? c->d_hW : nullptr, s);
+  auto run = [&](cudaStream_t st) -> int {
+    SNAP_CUDA(c, cudaMemcpyAsync(c->d_hpos, pos_host, sizeof(double) * 3 * natoms, cudaMemcpyHostToDevice, st));
+    int rc = enqueue(c, natoms, c->d_hpos, box, nullptr, nullptr, nullptr, 0, energy_host ? c->d_hE : nullptr,
+                     c->d_hF, virial_host ? c->d_hW : nullptr, st);
+    if (rc) return rc;
+    if (energy_host)
+      SNAP_CUDA(c, cudaMemcpyAsync(energy_host, c->d_hE, sizeof(double) * natoms, cudaMemcpyDeviceToHost, st));
+    SNAP_CUDA(c, cudaMemcpyAsync(forces_host, c->d_hF, sizeof(double) * 3 * natoms, cudaMemcpyDeviceToHost, st));
+    if (virial_host)
+      SNAP_CUDA(c, cudaMemcpyAsync(virial_host, c->d_hW, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
+    return SNAP_OK;
+  };
+  int rc = SNAP_OK;
+  if (c->prof_on) {
+    rc = run(s);
+  } else {
+    // every buffer exists before a capture (no allocation inside one)
+    rc = ensure_workspace(c, natoms, c->K);
+    if (!rc) rc = ensure_flags(c);
+    if (!rc) rc = ensure_slices(c, natoms);
+    if (rc) return rc;
+    const std::vector<unsigned long long> key = {
+        2, (unsigned long long)c->ws_gen, (unsigned long long)natoms, (unsigned long long)c->K,
+        (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves, key_bits(box[0]),
+        key_bits(box[1]), key_bits(box[2]), key_ptr(pos_host), key_ptr(energy_host),
+        key_ptr(forces_host), key_ptr(virial_host), key_ptr(c->d_hpos)};
+    // copies from and to pageable host memory cannot be captured
+    const bool replay = c->ghost.exec && c->ghost.key == key;
+    if (replay || (pinned_or_null(pos_host) && pinned_or_null(energy_host) && pinned_or_null(forces_host) &&
+                   pinned_or_null(virial_host)))
+      rc = graph_run(c, c->ghost, key, s, run);
+    else
+      rc = run(s);
+  }
   if (rc) return rc;
-  if (energy_host)
-    SNAP_CUDA(c, cudaMemcpyAsync(energy_host, c->d_hE, sizeof(double) * natoms, cudaMemcpyDeviceToHost, s));
-  SNAP_CUDA(c, cudaMemcpyAsync(forces_host, c->d_hF, sizeof(double) * 3 * natoms, cudaMemcpyDeviceToHost, s));
-  if (virial_host)
-    SNAP_CUDA(c, cudaMemcpyAsync(virial_host, c->d_hW, sizeof(double) * 6, cudaMemcpyDeviceToHost, s));
   SNAP_CUDA(c, cudaStreamSynchronize(s));
   return check_flags(c);
 }
@@ -1008,6 +1165,8 @@ int snap_destroy(snap_ctx* c) {
   dfree(c->d_ctamap);
   dfree(c->d_vatom);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gdev.reset();
+  c->ghost.reset();
   if (c->gstream) cudaStreamDestroy(c->gstream);
   for (auto* pool : {&c->prof_pending, &c->prof_free})
     for (auto& ev : *pool)

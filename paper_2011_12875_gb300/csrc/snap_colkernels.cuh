@@ -115,8 +115,6 @@ __device__ __forceinline__ void seed_column(c2<R> (&v)[N], bool take) {
 // the result does not depend on the launch shape.
 template <typename R, int J2>
 __global__ void __launch_bounds__(256) ui_col_kernel(WorkArgs a) {
-  pdl_wait();
-  pdl_trigger();
   using S = Shape<J2>;
   constexpr int NC = S::NC, P = S::P;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -209,8 +207,6 @@ __global__ void __launch_bounds__(256) ui_col_kernel(WorkArgs a) {
 template <typename R, int J2>
 __global__ void __launch_bounds__(256) tan_col_kernel(WorkArgs a, const double* __restrict__ gd,
                                                           void* dUout) {
-  pdl_wait();
-  pdl_trigger();
   using S = Shape<J2>;
   constexpr int NC = S::NC, P = S::P;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -336,8 +332,6 @@ __device__ __forceinline__ R shfl_down(R v) {
 
 template <typename R, int J2>
 __global__ void __launch_bounds__(256, 2) de_rev_col_kernel(WorkArgs a) {
-  pdl_wait();
-  pdl_trigger();
   using S_ = Shape<J2>;
   constexpr int NC = S_::NC, P = S_::P;
   const int NW = blockDim.x >> 5;
@@ -533,7 +527,7 @@ cudaError_t launch_ui_col_t(const WorkArgs& a, cudaStream_t s) {
   const int nw = col_fit_warps(a.col_warps, per);
   cudaError_t e = col_allow_smem(ui_col_kernel<R, J2>, per * nw);
   if (e != cudaSuccess) return e;
-  return launch_pdl(ui_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a);
+  return launch_k(ui_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a);
 }
 
 template <typename R, int J2>
@@ -543,7 +537,7 @@ cudaError_t launch_tan_col_t(const WorkArgs& a, const double* g, void* dU, cudaS
   const int nw = col_fit_warps(a.col_warps, per);
   cudaError_t e = col_allow_smem(tan_col_kernel<R, J2>, per * nw);
   if (e != cudaSuccess) return e;
-  return launch_pdl(tan_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a, g, dU);
+  return launch_k(tan_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a, g, dU);
 }
 
 template <typename R, int J2>
@@ -554,7 +548,7 @@ cudaError_t launch_de_rev_col_t(const WorkArgs& a, cudaStream_t s) {
   const int nw = col_fit_warps(a.col_warps, per);
   cudaError_t e = col_allow_smem(de_rev_col_kernel<R, J2>, per * nw);
   if (e != cudaSuccess) return e;
-  return launch_pdl(de_rev_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a);
+  return launch_k(de_rev_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a);
 }
 
 }  // namespace col

@@ -6,31 +6,13 @@
 
 namespace snap {
 
-// Programmatic dependent launch.  Every kernel of the library starts with
-// pdl_wait() (returns once the preceding kernel in the stream has completed
-// and its writes are visible; a no-op for a normal launch) followed by
-// pdl_trigger() (lets the next kernel be scheduled while this one runs), and
-// every launch goes through launch_pdl, so consecutive kernels overlap their
-// launch latency instead of leaving the GPU idle between them.
+// Kernel launch with the configuration as arguments (one place to change how
+// the library launches).
 #ifdef __CUDACC__
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                              cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-  if (e != cudaSuccess) return e;
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t s, Args... args) {
+  kernel<<<grid, block, smem, s>>>(static_cast<KArgs>(args)...);
   return cudaGetLastError();
 }
 #endif

@@ -77,8 +77,6 @@ __device__ __forceinline__ cx<R> prev_elem(const cx<R>* lay, int tp, int m, int 
 // and w_self is added on the diagonal (Eq. u).
 template <typename R, int NW>
 __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
-  pdl_wait();
-  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = a.H, L = a.lmax, J2 = a.twojmax;
   R* root = reinterpret_cast<R*>(smem);
@@ -224,11 +222,18 @@ struct YAcc {
 // `ul` points at lane 0's element 0 plus this lane (elements 256 B apart for
 // complex float, 512 B for complex double).  CP: the staged block is
 // [2][H][32] with the conjugate in its second half (no sign flips).
+template <typename R>
+__device__ __forceinline__ cx<R> y_second(unsigned w, const char* __restrict__ ul) {
+  constexpr int SH = sizeof(R) == 4 ? 0 : 1;
+  return *reinterpret_cast<const cx<R>*>(ul + ((w & 0x3FF00u) << SH));
+}
+
+// The rest of a term once its second factor u2 is loaded (loads of a batch of
+// terms are issued together, ahead of the arithmetic).
 template <typename R, bool CP>
-__device__ __forceinline__ void y_term(unsigned w, R c, const char* __restrict__ ul,
+__device__ __forceinline__ void y_term(unsigned w, R c, cx<R> u2, const char* __restrict__ ul,
                                        cx<R>* __restrict__ Yg, int lane, YAcc<R>& y) {
   constexpr int SH = sizeof(R) == 4 ? 0 : 1;
-  const cx<R> u2 = *reinterpret_cast<const cx<R>*>(ul + ((w & 0x3FF00u) << SH));
   const R i2 = CP ? u2.im : flip_sign(u2.im, w & 0x80000000u);
   y.ar += c * u2.re;
   y.ai += c * i2;
@@ -250,8 +255,6 @@ __device__ __forceinline__ void y_term(unsigned w, R c, const char* __restrict__
 
 template <typename R, bool STAGED, bool CP>
 __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
-  pdl_wait();
-  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long blk = blockIdx.x;
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   y.re = y.im = y.ar = y.ai = R(0);
   y.o = o0;
   const char* ul = reinterpret_cast<const char*>(us + lane);
-  auto term = [&](unsigned w, R c) { y_term<R, CP>(w, c, ul, Yg, lane, y); };
+  auto term = [&](unsigned w, R c) { y_term<R, CP>(w, c, y_second<R>(w, ul), ul, Yg, lane, y); };
   if constexpr (sizeof(R) == 4) {
     // two 8-byte records per 16-byte load
     if ((q & 1) && q < q1) {
@@ -309,10 +312,16 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
       uint4 v[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(rec + q) + k);
+      cx<R> u2[8];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        term(v[k].x, __uint_as_float(v[k].y));
-        term(v[k].z, __uint_as_float(v[k].w));
+        u2[2 * k] = y_second<R>(v[k].x, ul);
+        u2[2 * k + 1] = y_second<R>(v[k].z, ul);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        y_term<R, CP>(v[k].x, __uint_as_float(v[k].y), u2[2 * k], ul, Yg, lane, y);
+        y_term<R, CP>(v[k].z, __uint_as_float(v[k].w), u2[2 * k + 1], ul, Yg, lane, y);
       }
     }
   } else {
@@ -320,8 +329,12 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
       uint4 v[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(rec + q + k));
+      cx<R> u2[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) term(v[k].x, (R)__hiloint2double((int)v[k].w, (int)v[k].z));
+      for (int k = 0; k < 4; ++k) u2[k] = y_second<R>(v[k].x, ul);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        y_term<R, CP>(v[k].x, (R)__hiloint2double((int)v[k].w, (int)v[k].z), u2[k], ul, Yg, lane, y);
     }
   }
   for (; q < q1; ++q) term(rec[q].w, rec[q].c);
@@ -334,8 +347,6 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
 // summed per output element and each output is dotted with conj(U_t).
 template <typename R, bool STAGED>
 __global__ void __launch_bounds__(256) bi_kernel(WorkArgs a) {
-  pdl_wait();
-  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long blk = blockIdx.x;
@@ -398,8 +409,6 @@ __global__ void __launch_bounds__(256) bi_kernel(WorkArgs a) {
 // read from global memory.
 template <typename R, bool STAGED>
 __global__ void __launch_bounds__(256) dbi_kernel(WorkArgs a, const cx<R>* __restrict__ dUg, double* dB) {
-  pdl_wait();
-  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long blk = blockIdx.x;
@@ -464,8 +473,6 @@ __global__ void __launch_bounds__(256) dbi_kernel(WorkArgs a, const cx<R>* __res
 // gathered through the reverse-slot map like the forces (w = 1 gives -F).
 __global__ void __launch_bounds__(256) force_weighted_kernel(WorkArgs a, const double* __restrict__ wt,
                                                              double* __restrict__ grad) {
-  pdl_wait();
-  pdl_trigger();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long k = (long)blockIdx.x * 8 + warp;
   if (k >= a.n) return;
@@ -500,8 +507,6 @@ __global__ void __launch_bounds__(256) force_weighted_kernel(WorkArgs a, const d
 // <x, y> = Re(conj(x) y), which is Eq. (snapforce2) for this pair.
 template <typename R, int NW>
 __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
-  pdl_wait();
-  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = a.H, L = a.lmax, J2 = a.twojmax;
   R* root = reinterpret_cast<R*>(smem);
@@ -668,8 +673,6 @@ inline size_t force_smem(int K, bool vatom) {
 
 template <typename R>
 __global__ void __launch_bounds__(kFThreads) force_kernel(WorkArgs a) {
-  pdl_wait();
-  pdl_trigger();
   extern __shared__ __align__(16) double fsm[];  // g [kFAtoms*K][3], batch: + v [kFAtoms*K][6]
   __shared__ int off[kFAtoms + 1];
   __shared__ double ep[kFSlices][kFAtoms];
@@ -864,7 +867,7 @@ cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s) {
   const size_t sm = ui_smem<R>(a.H, a.lmax);
   cudaError_t e = allow_smem(ui_kernel<R, kUiWarps>, sm);
   if (e != cudaSuccess) return e;
-  return launch_pdl(ui_kernel<R, kUiWarps>, dim3(a.n), dim3(kUiWarps * 32), sm, s, a);
+  return launch_k(ui_kernel<R, kUiWarps>, dim3(a.n), dim3(kUiWarps * 32), sm, s, a);
 }
 
 bool yi_conjplane(int rsize, int H) { return (size_t)4 * H * 32 * rsize + 16 <= 100 * 1024; }
@@ -910,13 +913,13 @@ cudaError_t launch_yi(const WorkArgs& a, cudaStream_t s) {
   if (g.staged && g.conjplane) {
     cudaError_t e = allow_smem(yi_kernel<R, true, true>, g.smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(yi_kernel<R, true, true>, dim3(grid), dim3(g.threads), g.smem, s, a);
+    return launch_k(yi_kernel<R, true, true>, dim3(grid), dim3(g.threads), g.smem, s, a);
   } else if (g.staged) {
     cudaError_t e = allow_smem(yi_kernel<R, true, false>, g.smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(yi_kernel<R, true, false>, dim3(grid), dim3(g.threads), g.smem, s, a);
+    return launch_k(yi_kernel<R, true, false>, dim3(grid), dim3(g.threads), g.smem, s, a);
   }
-  return launch_pdl(yi_kernel<R, false, false>, dim3(grid), dim3(g.threads), 0, s, a);
+  return launch_k(yi_kernel<R, false, false>, dim3(grid), dim3(g.threads), 0, s, a);
 }
 
 template <typename R>
@@ -925,7 +928,7 @@ cudaError_t launch_de(const WorkArgs& a, cudaStream_t s) {
   const size_t sm = de_smem<R>(a.H, a.lmax);
   cudaError_t e = allow_smem(de_kernel<R, kDeWarps>, sm);
   if (e != cudaSuccess) return e;
-  return launch_pdl(de_kernel<R, kDeWarps>, dim3(a.n), dim3(kDeWarps * 32), sm, s, a);
+  return launch_k(de_kernel<R, kDeWarps>, dim3(a.n), dim3(kDeWarps * 32), sm, s, a);
 }
 
 template <typename R>
@@ -934,7 +937,7 @@ cudaError_t launch_force(const WorkArgs& a, cudaStream_t s) {
   const size_t sm = force_smem(a.K, a.vatom != nullptr);
   cudaError_t e = allow_smem(force_kernel<R>, sm);
   if (e != cudaSuccess) return e;
-  return launch_pdl(force_kernel<R>, dim3((unsigned)((a.n + kFAtoms - 1) / kFAtoms)), dim3(kFThreads), sm, s, a);
+  return launch_k(force_kernel<R>, dim3((unsigned)((a.n + kFAtoms - 1) / kFAtoms)), dim3(kFThreads), sm, s, a);
 }
 
 template <typename R>
@@ -946,9 +949,9 @@ cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s) {
   if (g.staged) {
     cudaError_t e = allow_smem(bi_kernel<R, true>, sm);
     if (e != cudaSuccess) return e;
-    return launch_pdl(bi_kernel<R, true>, dim3(grid), dim3(256), sm, s, a);
+    return launch_k(bi_kernel<R, true>, dim3(grid), dim3(256), sm, s, a);
   }
-  return launch_pdl(bi_kernel<R, false>, dim3(grid), dim3(256), 0, s, a);
+  return launch_k(bi_kernel<R, false>, dim3(grid), dim3(256), 0, s, a);
 }
 template cudaError_t launch_bi<float>(const WorkArgs&, cudaStream_t);
 template cudaError_t launch_bi<double>(const WorkArgs&, cudaStream_t);
@@ -963,16 +966,16 @@ cudaError_t launch_dbi(const WorkArgs& a, const void* dU, double* dB, cudaStream
   if (g.staged) {
     cudaError_t e = allow_smem(dbi_kernel<R, true>, sm);
     if (e != cudaSuccess) return e;
-    return launch_pdl(dbi_kernel<R, true>, dim3(grid), dim3(256), sm, s, a, d, dB);
+    return launch_k(dbi_kernel<R, true>, dim3(grid), dim3(256), sm, s, a, d, dB);
   }
-  return launch_pdl(dbi_kernel<R, false>, dim3(grid), dim3(256), 0, s, a, d, dB);
+  return launch_k(dbi_kernel<R, false>, dim3(grid), dim3(256), 0, s, a, d, dB);
 }
 template cudaError_t launch_dbi<float>(const WorkArgs&, const void*, double*, cudaStream_t);
 template cudaError_t launch_dbi<double>(const WorkArgs&, const void*, double*, cudaStream_t);
 
 cudaError_t launch_force_weighted(const WorkArgs& a, const double* w, double* grad, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  return launch_pdl(force_weighted_kernel, dim3((a.n + 7) / 8), dim3(256), 0, s, a, w, grad);
+  return launch_k(force_weighted_kernel, dim3((a.n + 7) / 8), dim3(256), 0, s, a, w, grad);
 }
 
 // Per-configuration virial: one CTA per configuration sums its atoms in a
@@ -980,8 +983,6 @@ cudaError_t launch_force_weighted(const WorkArgs& a, const double* w, double* gr
 __global__ void __launch_bounds__(256) virial_conf_kernel(const double* __restrict__ vatom,
                                                           const NeighConf* __restrict__ confs,
                                                           double* __restrict__ virial) {
-  pdl_wait();
-  pdl_trigger();
   __shared__ double red[256];
   const NeighConf c = confs[blockIdx.x];
   for (int k = 0; k < 6; ++k) {
@@ -1001,7 +1002,7 @@ __global__ void __launch_bounds__(256) virial_conf_kernel(const double* __restri
 cudaError_t launch_virial_conf(const double* vatom, const NeighConf* confs, int nconf, double* virial,
                                cudaStream_t s) {
   if (nconf <= 0) return cudaSuccess;
-  return launch_pdl(virial_conf_kernel, dim3(nconf), dim3(256), 0, s, vatom, confs, virial);
+  return launch_k(virial_conf_kernel, dim3(nconf), dim3(256), 0, s, vatom, confs, virial);
 }
 
 template cudaError_t launch_ui<float>(const WorkArgs&, cudaStream_t);

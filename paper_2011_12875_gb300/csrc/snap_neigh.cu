@@ -21,8 +21,6 @@ static_assert(kNbAtoms == kNeighAtomsPerCta, "batch CTA map and kernel disagree"
 constexpr unsigned kFull = 0xffffffffu;
 
 __global__ void pos4_kernel(int n, const double* __restrict__ pos, float4* __restrict__ pos4) {
-  pdl_wait();
-  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) pos4[i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], 0.f);
 }
@@ -57,8 +55,6 @@ __device__ __forceinline__ int pack_img(int x, int y, int z) {
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a) {
-  pdl_wait();
-  pdl_trigger();
   __shared__ int cand_j[kNbWarps][kCandCap];
   __shared__ int cand_s[kNbWarps][kCandCap];
   __shared__ int ncands[kNbWarps];
@@ -215,8 +211,6 @@ __global__ void neigh_ingest_kernel(int n, int K, const double* __restrict__ pos
                                     const int* __restrict__ uidx, const signed char* __restrict__ uimg,
                                     int ucap, int* cnt, int* nbr, signed char* img, double* rij,
                                     int* flags) {
-  pdl_wait();
-  pdl_trigger();
   const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long)n * K) return;
   const int i = (int)(q / K), s = (int)(q - (long)i * K);
@@ -302,8 +296,6 @@ __device__ void write_geom(G* g, G* gm, double ar, double ai, double br, double 
 
 template <typename G>
 __global__ void __launch_bounds__(kPairThreads) pairs_kernel(WorkArgs a, int* rev) {
-  pdl_wait();
-  pdl_trigger();
   __shared__ long qs[kPairAtoms * kMaxNeighCap];
   __shared__ long qm[kPairAtoms * kMaxNeighCap];
   __shared__ int ncanon;
@@ -416,17 +408,17 @@ inline int blocks_for(long n, int t) { return (int)((n + t - 1) / t); }
 
 cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  return launch_pdl(pos4_kernel, dim3(blocks_for(n, 256)), dim3(256), 0, s, n, pos, pos4);
+  return launch_k(pos4_kernel, dim3(blocks_for(n, 256)), dim3(256), 0, s, n, pos, pos4);
 }
 
 cudaError_t launch_neigh_build(const NeighArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  return launch_pdl(neigh_build_kernel<false>, dim3(blocks_for(a.n, kNbAtoms)), dim3(kNbWarps * 32), 0, s, a);
+  return launch_k(neigh_build_kernel<false>, dim3(blocks_for(a.n, kNbAtoms)), dim3(kNbWarps * 32), 0, s, a);
 }
 
 cudaError_t launch_neigh_build_batch(const NeighArgs& a, int ncta, cudaStream_t s) {
   if (ncta <= 0) return cudaSuccess;
-  return launch_pdl(neigh_build_kernel<true>, dim3(ncta), dim3(kNbWarps * 32), 0, s, a);
+  return launch_k(neigh_build_kernel<true>, dim3(ncta), dim3(kNbWarps * 32), 0, s, a);
 }
 
 cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, double Ly,
@@ -434,13 +426,13 @@ cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, doub
                                 const signed char* uimg, int ucap, int* cnt, int* nbr,
                                 signed char* img, double* rij, int* flags, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  return launch_pdl(neigh_ingest_kernel, dim3(blocks_for((long)n * K, 256)), dim3(256), 0, s, n, K, pos, Lx, Ly, Lz, ucnt, uidx, uimg, ucap, cnt, nbr, img, rij, flags);
+  return launch_k(neigh_ingest_kernel, dim3(blocks_for((long)n * K, 256)), dim3(256), 0, s, n, K, pos, Lx, Ly, Lz, ucnt, uidx, uimg, ucap, cnt, nbr, img, rij, flags);
 }
 
 template <typename G>
 cudaError_t launch_pairs(const WorkArgs& a, int* rev, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  return launch_pdl(pairs_kernel<G>, dim3(blocks_for(a.n, kPairAtoms)), dim3(kPairThreads), 0, s, a, rev);
+  return launch_k(pairs_kernel<G>, dim3(blocks_for(a.n, kPairAtoms)), dim3(kPairThreads), 0, s, a, rev);
 }
 template cudaError_t launch_pairs<float>(const WorkArgs&, int*, cudaStream_t);
 template cudaError_t launch_pairs<double>(const WorkArgs&, int*, cudaStream_t);

@@ -8,12 +8,15 @@ of the benchmark; the derivation is written out in the design notes.
 """
 from __future__ import annotations
 
+from functools import lru_cache
+
 
 def half_layer(t: int):
     """(ma, mb) of the half layout of layer t (mb <= t/2)."""
     return [(ma, mb) for mb in range(t // 2 + 1) for ma in range(t + 1)]
 
 
+@lru_cache(maxsize=None)
 def ui_pair(twojmax: int) -> int:
     """compute_U, one neighbour pair: the layer recursion and the f_c u_t sum.
     Each term of an element is conj(a or b) * u_{t-1} (6) scaled by its root
@@ -26,6 +29,7 @@ def ui_pair(twojmax: int) -> int:
     return f
 
 
+@lru_cache(maxsize=None)
 def de_pair(twojmax: int) -> int:
     """Fused dU + dE, one pair: forward recursion (as compute_U, with the
     Re(Y conj u) accumulation, 4) and the reverse pass: per element of layer
@@ -46,22 +50,30 @@ def de_pair(twojmax: int) -> int:
     return f + 30
 
 
+@lru_cache(maxsize=None)
 def yi_atom(twojmax: int) -> int:
-    """compute_Y, one atom: for each half element of each Z^t_{t1 t2}, the
-    double sum of CG-weighted products (8 per term: complex multiply 6, CG
-    scale-accumulate 2... counted as 6 + 4), the mb1 scale-accumulate (4) and
-    the beta-weighted add into Y (4)."""
+    """compute_Y, one atom.  For each half element (t, ma, mb) of Y, the terms
+    beta~ C(ma1,ma2) C(mb1,mb2) U_t1[ma1][mb1] U_t2[ma2][mb2] of every triple
+    (t1 >= t2) with output rank t, grouped by their first factor
+    U_t1[ma1][mb1]: Y += U_t1[ma1][mb1] * sum_k coef_k U_t2,k.  Per term a
+    real-by-complex scale-accumulate (4), per group a complex
+    multiply-accumulate (8).  Terms and groups are counted structurally (a
+    Clebsch-Gordan product that happens to vanish is still counted)."""
     f = 0
-    for t1 in range(twojmax + 1):
-        for t2 in range(t1 + 1):
-            for t in range(t1 - t2, min(twojmax, t1 + t2) + 1, 2):
-                dl = (t1 + t2 - t) // 2
-                for ma, mb in half_layer(t):
-                    na = min(t1, ma + dl) - max(0, ma + dl - t2) + 1
-                    nb = min(t1, mb + dl) - max(0, mb + dl - t2) + 1
-                    if na <= 0 or nb <= 0:
+    for t in range(twojmax + 1):
+        for ma, mb in half_layer(t):
+            groups = set()
+            nterm = 0
+            for t1 in range(twojmax + 1):
+                for t2 in range(t1 + 1):
+                    if not (t1 - t2 <= t <= min(twojmax, t1 + t2)) or (t1 + t2 - t) % 2:
                         continue
-                    f += nb * (na * 10 + 4) + 4
+                    dl = (t1 + t2 - t) // 2
+                    for mb1 in range(max(0, mb + dl - t2), min(t1, mb + dl) + 1):
+                        for ma1 in range(max(0, ma + dl - t2), min(t1, ma + dl) + 1):
+                            nterm += 1
+                            groups.add((t1, ma1, mb1))
+            f += 4 * nterm + 8 * len(groups)
     return f
 
 
