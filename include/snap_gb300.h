@@ -134,7 +134,7 @@ int snap_sync(snap_ctx* ctx, void* stream);
  * calls timed; it returns SNAP_NSTAGES.  snap_stage_name(k) names stage k.
  * snap_launches_per_call(ctx) is the number of kernels the last compute
  * launched. */
-#define SNAP_NSTAGES 6
+#define SNAP_NSTAGES 5
 int snap_profile(snap_ctx* ctx, int enable);
 int snap_profile_read(snap_ctx* ctx, double* ms, long long* calls, int nstages);
 const char* snap_stage_name(int stage);

@@ -331,6 +331,7 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.nbr = c->d_nbr;
   a.img = c->d_img;
   a.rev = c->d_rev;
+  a.rev_out = c->d_rev;
   a.rij = c->d_rij;
   a.geom = c->d_geom;
   a.U = c->d_U;
@@ -428,12 +429,11 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   a.B = B;
 
   const bool mixed = c->precision == SNAP_MIXED;
-  SNAP_CUDA(c, mixed ? snap::launch_pairs<float>(a, c->d_rev, s) : snap::launch_pairs<double>(a, c->d_rev, s));
-  SNAP_CUDA(c, mark());
   const bool colk = mixed && c->twojmax >= 1;  // register column-chain kernels
   SNAP_CUDA(c, colk ? snap::launch_ui_col<float>(a, s)
                     : (mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s)));
   SNAP_CUDA(c, mark());
+  c->launches += 1;
   c->generation += 1;
   c->last_args = a;
   c->have_last = (mode == 0);
@@ -460,7 +460,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   SNAP_CUDA(c, mark());
   SNAP_CUDA(c, mixed ? snap::launch_force<float>(a, s) : snap::launch_force<double>(a, s));
   SNAP_CUDA(c, mark());
-  c->launches += 5;
+  c->launches += 3;
   if (!ev.empty()) c->prof_pending.push_back(ev);
   SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
   c->last_n = n;
@@ -561,7 +561,6 @@ int launch_batch(snap_ctx* c, const double* pos, double* energy, double* forces,
   a.vatom = c->d_vatom;
   const bool mixed = c->precision == SNAP_MIXED;
   const bool colk = mixed && c->twojmax >= 1;
-  SNAP_CUDA(c, mixed ? snap::launch_pairs<float>(a, c->d_rev, s) : snap::launch_pairs<double>(a, c->d_rev, s));
   SNAP_CUDA(c, colk ? snap::launch_ui_col<float>(a, s)
                     : (mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s)));
   SNAP_CUDA(c, mixed ? snap::launch_yi<float>(a, s) : snap::launch_yi<double>(a, s));
@@ -570,7 +569,7 @@ int launch_batch(snap_ctx* c, const double* pos, double* energy, double* forces,
   SNAP_CUDA(c, mixed ? snap::launch_force<float>(a, s) : snap::launch_force<double>(a, s));
   if (virial) SNAP_CUDA(c, snap::launch_virial_conf(c->d_vatom, c->d_confs, c->bat_nconf, virial, s));
   SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  c->launches = 7 + (virial ? 1 : 0);
+  c->launches = 6 + (virial ? 1 : 0);
   c->generation += 1;
   c->last_args = a;
   c->have_last = true;
@@ -861,7 +860,7 @@ int snap_profile_read(snap_ctx* c, double* ms, long long* calls, int nstages) {
 }
 
 const char* snap_stage_name(int stage) {
-  static const char* names[SNAP_NSTAGES] = {"neighbor_build", "pair_geometry", "compute_ui",
+  static const char* names[SNAP_NSTAGES] = {"neighbor_build", "compute_ui",
                                             "compute_yi", "fused_dE", "energy_force_virial"};
   return (stage >= 0 && stage < SNAP_NSTAGES) ? names[stage] : "";
 }

@@ -17,6 +17,7 @@
 #pragma once
 #include <type_traits>
 
+#include "snap_geom.cuh"
 #include "snap_internal.h"
 
 namespace snap {
@@ -107,7 +108,8 @@ __device__ __forceinline__ void seed_column(c2<R> (&v)[N], bool take) {
 }
 
 // ------------------------------------------------------------- compute_U
-// Warp = one atom (the CTA's warps are independent atoms, so no CTA-wide
+// First the atom's slot geometry and reverse-slot map (snap_geom.cuh), then
+// the recursion.  Warp = one atom (the CTA's warps are independent atoms, so no CTA-wide
 // barrier and no idle warps when the pair count is not a multiple of the
 // CTA's pairs); the warp takes P pairs at a time.  Pair group g sums f_c u_t
 // of pairs g, g + P, ... into its own shared-memory copy of Ulisttot (no two
@@ -125,6 +127,8 @@ __global__ void __launch_bounds__(256) ui_col_kernel(WorkArgs a) {
   c2<R>* acc = reinterpret_cast<c2<R>*>(smem) + (size_t)warp * P * H;  // [P][H]
   const int g = lane / NC, mb = lane - g * NC;
   const bool grp = g < P;
+  // the atom's slot geometry and reverse map (dense lanes: one slot each)
+  geo::atom_slots<R>(a, (int)i, lane, 32);
   for (int e = lane; e < P * H; e += 32) acc[e] = mk<R>(0, 0);
   __syncwarp();
   c2<R>* my = acc + (grp ? g : 0) * H;

@@ -98,6 +98,7 @@ struct WorkArgs {
   const int* nbr;
   const signed char* img;
   const int* rev;
+  int* rev_out;  // the same table, written by compute_U
   double* rij;
   void* geom;  // R [N][K][kGeomStride]: Cayley-Klein geometry in the working precision
   // Ulisttot and Y: complex (re, im interleaved), AoSoA [ceil(N/32)][H][32]
@@ -138,7 +139,6 @@ cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, doub
                                 const signed char* uimg, int ucap, int* cnt, int* nbr,
                                 signed char* img, double* rij, int* flags, cudaStream_t s);
 // reverse-slot map + geometry in the working precision G (one kernel)
-template <typename G> cudaError_t launch_pairs(const WorkArgs& a, int* rev, cudaStream_t s);
 
 // Launchers (snap_kernels.cu), R = float (mixed) or double (FP64)
 template <typename R> cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s);

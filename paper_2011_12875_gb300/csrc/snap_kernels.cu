@@ -9,6 +9,7 @@
 
 #include <algorithm>
 
+#include "snap_geom.cuh"
 #include "snap_internal.h"
 
 namespace snap {
@@ -67,7 +68,8 @@ __device__ __forceinline__ cx<R> prev_elem(const cx<R>* lay, int tp, int m, int 
 }
 
 // ------------------------------------------------------------- compute_U
-// One CTA per atom i, one warp per neighbour pair (lanes over the elements of
+// First the atom's slot geometry and reverse-slot map (snap_geom.cuh), then
+// the recursion.  One CTA per atom i, one warp per neighbour pair (lanes over the elements of
 // a layer), NW warps per CTA.  u_t of a pair follows the layer recursion
 // (Eq. hysphrecur): for mb <= t/2,
 //   u_t[ma][mb] = sqrt((t-ma)/(t-mb)) conj(a) u_{t-1}[ma][mb]
@@ -87,6 +89,8 @@ __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
   const R* rootg = reinterpret_cast<const R*>(a.rootpq);
   for (int e = threadIdx.x; e < kRootDim * kRootDim; e += blockDim.x) root[e] = rootg[e];
   for (int e = threadIdx.x; e < NW * H; e += blockDim.x) acc[e] = mk<R>(0, 0);
+  // the atom's slot geometry and reverse map (snap_geom.cuh)
+  geo::atom_slots<R>(a, i, threadIdx.x, blockDim.x);
   __syncthreads();
   cx<R>* myacc = acc + warp * H;
   cx<R>* b0 = buf + warp * 2 * L;
@@ -214,52 +218,55 @@ template <typename R>
 struct YAcc {
   R re, im;  // the output element
   R ar, ai;  // sum of coef * second factor over the current group
-  int o;
 };
 
-// One term of an output: acc += coef * U2; at the end of a group (terms with
-// one first factor U1), Y += U1 * acc; at the end of an output, store Y.
-// `ul` points at lane 0's element 0 plus this lane (elements 256 B apart for
-// complex float, 512 B for complex double).  CP: the staged block is
-// [2][H][32] with the conjugate in its second half (no sign flips).
+// Byte offset of a record's second (first) factor from lane 0's element 0:
+// elements are 256 B apart for complex float, 512 B for complex double.
 template <typename R>
-__device__ __forceinline__ cx<R> y_second(unsigned w, const char* __restrict__ ul) {
-  constexpr int SH = sizeof(R) == 4 ? 0 : 1;
-  return *reinterpret_cast<const cx<R>*>(ul + ((w & 0x3FF00u) << SH));
+__device__ __forceinline__ unsigned y_off2(unsigned w) {
+  return (w & 0x3FF00u) << (sizeof(R) == 4 ? 0 : 1);
+}
+template <typename R>
+__device__ __forceinline__ unsigned y_off1(unsigned w) {
+  return ((w >> 10) & 0x3FF00u) << (sizeof(R) == 4 ? 0 : 1);
 }
 
-// The rest of a term once its second factor u2 is loaded (loads of a batch of
-// terms are issued together, ahead of the arithmetic).
+// The rest of a term once its second factor u2 is loaded: acc += coef * u2;
+// at the end of a group (terms with one first factor U1), Y += U1 * acc; at
+// the end of an output, store Y.  `ul` points at lane 0's element 0 plus this
+// lane.  CP: the staged block is [2][H][32] with the conjugate in its second
+// half (no sign flips).
 template <typename R, bool CP>
 __device__ __forceinline__ void y_term(unsigned w, R c, cx<R> u2, const char* __restrict__ ul,
-                                       cx<R>* __restrict__ Yg, int lane, YAcc<R>& y) {
-  constexpr int SH = sizeof(R) == 4 ? 0 : 1;
+                                       cx<R>* __restrict__ Yg, int lane, int& o, YAcc<R>& y) {
   const R i2 = CP ? u2.im : flip_sign(u2.im, w & 0x80000000u);
   y.ar += c * u2.re;
   y.ai += c * i2;
   if (w & (1u << 28)) {
-    const cx<R> u1 = *reinterpret_cast<const cx<R>*>(ul + (((w >> 10) & 0x3FF00u) << SH));
+    const cx<R> u1 = *reinterpret_cast<const cx<R>*>(ul + y_off1<R>(w));
     const R i1 = CP ? u1.im : flip_sign(u1.im, (w << 1) & 0x80000000u);
     y.re += u1.re * y.ar - i1 * y.ai;
     y.im += u1.re * y.ai + i1 * y.ar;
     y.ar = R(0);
     y.ai = R(0);
     if (w & (1u << 29)) {
-      Yg[y.o * 32 + lane] = mk<R>(y.re, y.im);
+      Yg[o * 32 + lane] = mk<R>(y.re, y.im);
       y.re = R(0);
       y.im = R(0);
-      ++y.o;
+      ++o;
     }
   }
 }
 
+// CTA = one 32-atom block x one ysplit-th of the outputs; U of the block
+// staged by a TMA bulk copy.
 template <typename R, bool STAGED, bool CP>
 __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long blk = blockIdx.x;
+  const long blk0 = blockIdx.x;
   const int H = a.H;
-  const cx<R>* us = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
+  const cx<R>* us = reinterpret_cast<const cx<R>*>(a.U) + blk0 * H * 32;
   if (STAGED) {
     cx<R>* su = reinterpret_cast<cx<R>*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(su + (CP ? 2 : 1) * H * 32);
@@ -293,17 +300,19 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   if (slice >= a.nslices) return;
   const int o0 = a.yslice[slice], o1 = a.yslice[slice + 1];
   if (o0 >= o1) return;
-  cx<R>* Yg = reinterpret_cast<cx<R>*>(a.Y) + blk * H * 32;
+  cx<R>* Yg = reinterpret_cast<cx<R>*>(a.Y) + blk0 * H * 32;
   const YRec<R>* __restrict__ rec = reinterpret_cast<const YRec<R>*>(a.yrec);
   const int q1 = a.yfirst[o1];
   int q = a.yfirst[o0];
+  int o = o0;
   YAcc<R> y;
   y.re = y.im = y.ar = y.ai = R(0);
-  y.o = o0;
   const char* ul = reinterpret_cast<const char*>(us + lane);
-  auto term = [&](unsigned w, R c) { y_term<R, CP>(w, c, y_second<R>(w, ul), ul, Yg, lane, y); };
+  auto load2 = [&](unsigned w) { return *reinterpret_cast<const cx<R>*>(ul + y_off2<R>(w)); };
+  auto term = [&](unsigned w, R c) { y_term<R, CP>(w, c, load2(w), ul, Yg, lane, o, y); };
   if constexpr (sizeof(R) == 4) {
-    // two 8-byte records per 16-byte load
+    // two 8-byte records per 16-byte load; the second factors of a batch are
+    // loaded ahead of its arithmetic
     if ((q & 1) && q < q1) {
       term(rec[q].w, rec[q].c);
       ++q;
@@ -315,13 +324,13 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
       cx<R> u2[8];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        u2[2 * k] = y_second<R>(v[k].x, ul);
-        u2[2 * k + 1] = y_second<R>(v[k].z, ul);
+        u2[2 * k] = load2(v[k].x);
+        u2[2 * k + 1] = load2(v[k].z);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        y_term<R, CP>(v[k].x, __uint_as_float(v[k].y), u2[2 * k], ul, Yg, lane, y);
-        y_term<R, CP>(v[k].z, __uint_as_float(v[k].w), u2[2 * k + 1], ul, Yg, lane, y);
+        y_term<R, CP>(v[k].x, __uint_as_float(v[k].y), u2[2 * k], ul, Yg, lane, o, y);
+        y_term<R, CP>(v[k].z, __uint_as_float(v[k].w), u2[2 * k + 1], ul, Yg, lane, o, y);
       }
     }
   } else {
@@ -331,10 +340,10 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
       for (int k = 0; k < 4; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(rec + q + k));
       cx<R> u2[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) u2[k] = y_second<R>(v[k].x, ul);
+      for (int k = 0; k < 4; ++k) u2[k] = load2(v[k].x);
 #pragma unroll
       for (int k = 0; k < 4; ++k)
-        y_term<R, CP>(v[k].x, (R)__hiloint2double((int)v[k].w, (int)v[k].z), u2[k], ul, Yg, lane, y);
+        y_term<R, CP>(v[k].x, (R)__hiloint2double((int)v[k].w, (int)v[k].z), u2[k], ul, Yg, lane, o, y);
     }
   }
   for (; q < q1; ++q) term(rec[q].w, rec[q].c);
@@ -875,16 +884,16 @@ bool yi_conjplane(int rsize, int H) { return (size_t)4 * H * 32 * rsize + 16 <= 
 YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves) {
   YiGeometry g;
   g.nblk = (n + 31) / 32;
-  const size_t stage = (size_t)2 * H * 32 * rsize + 16;  // complex [H][32] + mbarrier
-  g.staged = stage <= 200 * 1024;
+  const size_t block = (size_t)2 * H * 32 * rsize;  // one staged [H][32] complex block
+  g.staged = block + 16 <= 200 * 1024;
   g.conjplane = yi_conjplane(rsize, H);
-  g.smem = g.staged ? (g.conjplane ? 2 * stage - 16 : stage) : 0;
+  g.smem = g.staged ? (g.conjplane ? 2 : 1) * block + 16 : 0;
   g.threads = (g.smem > 100 * 1024) ? 1024 : (g.smem > 60 * 1024 ? 512 : 256);
   int cps = 2048 / g.threads;
   if (g.staged) cps = std::max(1, std::min(cps, (int)((227 * 1024) / g.smem)));
-  // Split each 32-atom block's outputs into ysplit CTAs.  CTAs of one launch
-  // take about equal time, so the launch lasts ceil(CTAs / resident) CTA
-  // lifetimes; pick the split that minimises
+  // Split each CTA's outputs into ysplit CTAs.  CTAs of one launch take about
+  // equal time, so the launch lasts ceil(CTAs / resident) CTA lifetimes;
+  // pick the split that minimises
   //   ceil(nblk ysplit / resident) (1 / ysplit + c),
   // c = the fixed per-CTA cost (staging U) relative to a whole block's terms,
   // taken as 0.02 / waves (the tunable: more waves, finer splits).
@@ -913,13 +922,14 @@ cudaError_t launch_yi(const WorkArgs& a, cudaStream_t s) {
   if (g.staged && g.conjplane) {
     cudaError_t e = allow_smem(yi_kernel<R, true, true>, g.smem);
     if (e != cudaSuccess) return e;
-    return launch_k(yi_kernel<R, true, true>, dim3(grid), dim3(g.threads), g.smem, s, a);
-  } else if (g.staged) {
+    return launch_k(yi_kernel<R, true, true>, grid, dim3(g.threads), g.smem, s, a);
+  }
+  if (g.staged) {
     cudaError_t e = allow_smem(yi_kernel<R, true, false>, g.smem);
     if (e != cudaSuccess) return e;
-    return launch_k(yi_kernel<R, true, false>, dim3(grid), dim3(g.threads), g.smem, s, a);
+    return launch_k(yi_kernel<R, true, false>, grid, dim3(g.threads), g.smem, s, a);
   }
-  return launch_k(yi_kernel<R, false, false>, dim3(grid), dim3(g.threads), 0, s, a);
+  return launch_k(yi_kernel<R, false, false>, grid, dim3(g.threads), 0, s, a);
 }
 
 template <typename R>

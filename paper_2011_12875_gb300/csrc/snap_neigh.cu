@@ -1,11 +1,11 @@
-// snap_neigh.cu -- neighbour list, reverse-slot map and per-slot FP64
-// Cayley-Klein geometry.
+// snap_neigh.cu -- neighbour list.
 //
 // The neighbour list is the build_neighborlist stage of the SNAP algorithm
 // (arXiv:2011.12875, Sec. II-B and Listing 2): for every atom i, every atom k
 // and periodic image s with |r_k + s L - r_i| < R_cut.  Here it is built on
-// the device into a fixed-capacity [N][K] table.  The reverse-slot map lets
-// the force stage gather dE_k/dr_ki instead of scattering with atomics.
+// the device into a fixed-capacity [N][K] table with exact FP64 separations
+// (the slot geometry and reverse-slot map are derived from it in
+// snap_geom.cuh).
 #include <math.h>
 
 #include "snap_internal.h"
@@ -240,168 +240,6 @@ __global__ void neigh_ingest_kernel(int n, int K, const double* __restrict__ pos
   rij[3 * q + 2] = sep1(i, k, pos[3 * i + 2], pos[3 * k + 2], iz, Lz);
 }
 
-// Reverse-slot map and FP64 Cayley-Klein geometry, once per unordered pair.
-//
-// rev[i][s] is the slot of the opposite pair (k, i, -s) in k's list (the
-// force gather reads dE_k/dr_ki through it).  The geometry of a slot
-// (Sec. II-A: the neighbour vector mapped to the 3-sphere, with constants
-// from the paper's SNAP reference): theta0 = rfac0 pi (r - rmin0)/(rcut -
-// rmin0), z0 = r cot theta0, r0 = sqrt(r^2 + z0^2), a = (z0 - i z)/r0,
-// b = (y - i x)/r0, the cosine switching function f_c, and the derivatives
-// of a, b and f_c with respect to r.  For the opposite vector -r the same
-// quantities are a' = conj(a), b' = -b, grad f_c' = -grad f_c,
-// da'/dr = -conj(da/dr), db'/dr = db/dr, exactly, so only one slot of each
-// pair is evaluated (in FP64) and both are written (in the working
-// precision G).  A CTA collects the canonical slots of kPairAtoms atoms in
-// shared memory first, so the FP64 work runs on dense lanes.
-constexpr int kPairAtoms = 2;
-constexpr int kPairThreads = 64;
-
-__device__ __forceinline__ void sincospi_g(float x, float* s, float* c) { sincospif(x, s, c); }
-__device__ __forceinline__ void sincospi_g(double x, double* s, double* c) { sincospi(x, s, c); }
-
-template <typename G>
-__device__ void write_geom(G* g, G* gm, double ar, double ai, double br, double bi, G fc,
-                           const G* dfc, const G* da, const G* db) {
-  G v[kGeomStride];
-  v[0] = G(ar);
-  v[1] = G(ai);
-  v[2] = G(br);
-  v[3] = G(bi);
-  v[4] = fc;
-  for (int d = 0; d < 3; ++d) {
-    v[5 + d] = dfc[d];
-    v[8 + 2 * d] = da[2 * d];
-    v[9 + 2 * d] = da[2 * d + 1];
-    v[14 + 2 * d] = db[2 * d];
-    v[15 + 2 * d] = db[2 * d + 1];
-  }
-  for (int e = 0; e < kGeomStride; ++e) g[e] = v[e];
-  if (!gm) return;
-  // opposite vector: a -> conj(a), b -> -b, grad f_c -> -grad f_c,
-  // da -> -conj(da), db -> db (negation is exact in any precision)
-  gm[0] = v[0];
-  gm[1] = -v[1];
-  gm[2] = -v[2];
-  gm[3] = -v[3];
-  gm[4] = v[4];
-  for (int d = 0; d < 3; ++d) {
-    gm[5 + d] = -v[5 + d];
-    gm[8 + 2 * d] = -v[8 + 2 * d];
-    gm[9 + 2 * d] = v[9 + 2 * d];
-    gm[14 + 2 * d] = v[14 + 2 * d];
-    gm[15 + 2 * d] = v[15 + 2 * d];
-  }
-}
-
-template <typename G>
-__global__ void __launch_bounds__(kPairThreads) pairs_kernel(WorkArgs a, int* rev) {
-  __shared__ long qs[kPairAtoms * kMaxNeighCap];
-  __shared__ long qm[kPairAtoms * kMaxNeighCap];
-  __shared__ int ncanon;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  if (threadIdx.x == 0) ncanon = 0;
-  __syncthreads();
-  constexpr int per_warp = kPairAtoms / (kPairThreads / 32);
-  for (int aa = 0; aa < per_warp; ++aa) {
-    const int i = blockIdx.x * kPairAtoms + warp * per_warp + aa;
-    if (i >= a.n) break;
-    const int cnt = a.cnt[i];
-    for (int s0 = 0; s0 < cnt; s0 += 32) {
-      const int s = s0 + lane;
-      bool canon = false;
-      long q = 0, q2 = -1;
-      if (s < cnt) {
-        q = (long)i * a.K + s;
-        const int k = a.nbr[q];
-        const int sx = a.img[3 * q], sy = a.img[3 * q + 1], sz = a.img[3 * q + 2];
-        const int ck = a.cnt[k];
-        int found = -1;
-        // all of k's slots are read with independent loads (no early exit)
-        const int* kn = a.nbr + (long)k * a.K;
-        for (int t0 = 0; t0 < ck; t0 += 8) {
-          int nb[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) nb[u] = (t0 + u < ck) ? kn[t0 + u] : -1;
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            if (nb[u] == i && found < 0) {
-              const long p = (long)k * a.K + t0 + u;
-              if (a.img[3 * p] == -sx && a.img[3 * p + 1] == -sy && a.img[3 * p + 2] == -sz) found = t0 + u;
-            }
-          }
-        }
-        rev[q] = found;
-        if (found < 0) atomicMax(&a.flags[1], 1);
-        const bool pos = sx > 0 || (sx == 0 && (sy > 0 || (sy == 0 && sz > 0)));
-        canon = found < 0 || i < k || (i == k && pos);
-        if (found >= 0) q2 = (long)k * a.K + found;
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, canon);
-      int base = 0;
-      if (lane == 0) base = atomicAdd(&ncanon, __popc(m));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (canon) {
-        const int p = base + __popc(m & lt);
-        qs[p] = q;
-        qm[p] = q2;
-      }
-    }
-  }
-  __syncthreads();
-  const int nc = ncanon;
-  for (int p = threadIdx.x; p < nc; p += blockDim.x) {
-    const long q = qs[p], q2 = qm[p];
-    G* g = reinterpret_cast<G*>(a.geom) + q * kGeomStride;
-    G* gm = q2 >= 0 ? reinterpret_cast<G*>(a.geom) + q2 * kGeomStride : nullptr;
-    const double x = a.rij[3 * q], y = a.rij[3 * q + 1], z = a.rij[3 * q + 2];
-    const double r2 = x * x + y * y + z * z;
-    const double ir = rsqrt(r2);
-    const double r = r2 * ir;
-    G dfc[3] = {0, 0, 0}, da[6] = {0, 0, 0, 0, 0, 0}, db[6] = {0, 0, 0, 0, 0, 0};
-    if (!(r < a.rcut)) {  // outside the cutoff (caller lists): no contribution
-      write_geom(g, gm, 1.0, 0.0, 0.0, 0.0, G(0), dfc, da, db);
-      continue;
-    }
-    // The Cayley-Klein parameters in FP64 (Sec. II-A): theta0, z0 = r cot theta0,
-    // r0 = sqrt(r^2 + z0^2), a = (z0 - i z) / r0, b = (y - i x) / r0.
-    double st, ct;
-    sincospi(a.rfac0 * (r - a.rmin0) * a.inv_span, &st, &ct);
-    const double ist = 1.0 / st;
-    const double z0 = r * ct * ist;
-    const double ir0 = rsqrt(r2 + z0 * z0);
-    const double ar = z0 * ir0, ai = -z * ir0;
-    const double br = y * ir0, bi = -x * ir0;
-    // Their gradients and the switching function in the working precision G
-    // (they only feed the G recursions): FP64 runs at 1/64 of the FP32 rate.
-    const G gr = G(r), gir = G(ir), gz0 = G(z0), gir0 = G(ir0), gist = G(ist), gct = G(ct);
-    const G gar = G(ar), gai = G(ai), gbr = G(br), gbi = G(bi);
-    const G c = G(a.rfac0 * M_PI * a.inv_span);  // d theta0 / d r
-    const G dz0dr = gct * gist - gr * c * gist * gist;
-    G fc = G(1), dfcdr = G(0);
-    if (a.switchflag && r > a.rmin0) {
-      G sw, cw;
-      sincospi_g(G((r - a.rmin0) * a.inv_span), &sw, &cw);
-      fc = G(0.5) * (cw + G(1));
-      dfcdr = G(-0.5 * M_PI * a.inv_span) * sw;
-    }
-    const G rv[3] = {G(x), G(y), G(z)};
-    for (int d = 0; d < 3; ++d) {
-      const G ud = rv[d] * gir;
-      dfc[d] = dfcdr * ud;
-      const G dz0 = dz0dr * ud;
-      const G dr0 = (gr * ud + gz0 * dz0) * gir0;
-      // d a = (d(z0 - i z) - a d r0) / r0 ; d b = (d(y - i x) - b d r0) / r0
-      da[2 * d] = (dz0 - gar * dr0) * gir0;
-      da[2 * d + 1] = ((d == 2 ? G(-1) : G(0)) - gai * dr0) * gir0;
-      db[2 * d] = ((d == 1 ? G(1) : G(0)) - gbr * dr0) * gir0;
-      db[2 * d + 1] = ((d == 0 ? G(-1) : G(0)) - gbi * dr0) * gir0;
-    }
-    write_geom(g, gm, ar, ai, br, bi, fc, dfc, da, db);
-  }
-}
-
 inline int blocks_for(long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
@@ -429,12 +267,5 @@ cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, doub
   return launch_k(neigh_ingest_kernel, dim3(blocks_for((long)n * K, 256)), dim3(256), 0, s, n, K, pos, Lx, Ly, Lz, ucnt, uidx, uimg, ucap, cnt, nbr, img, rij, flags);
 }
 
-template <typename G>
-cudaError_t launch_pairs(const WorkArgs& a, int* rev, cudaStream_t s) {
-  if (a.n <= 0) return cudaSuccess;
-  return launch_k(pairs_kernel<G>, dim3(blocks_for(a.n, kPairAtoms)), dim3(kPairThreads), 0, s, a, rev);
-}
-template cudaError_t launch_pairs<float>(const WorkArgs&, int*, cudaStream_t);
-template cudaError_t launch_pairs<double>(const WorkArgs&, int*, cudaStream_t);
 
 }  // namespace snap

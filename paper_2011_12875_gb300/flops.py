@@ -78,13 +78,12 @@ def yi_atom(twojmax: int) -> int:
 
 
 def step(twojmax: int, natoms: int, npairs: int) -> dict:
-    """Flops of one step by kernel (the FP64 geometry and force stages are
-    small and counted separately)."""
+    """Flops of one step by stage, keyed by the library's stage names."""
     H = sum(len(half_layer(t)) for t in range(twojmax + 1))
     return {
-        "compute_ui": ui_pair(twojmax) * npairs,
+        # compute_U includes the slot geometry (FP64 core, about 150 flops a slot)
+        "compute_ui": (ui_pair(twojmax) + 150) * npairs,
         "compute_yi": yi_atom(twojmax) * natoms,
         "fused_dE": de_pair(twojmax) * npairs,
-        "force_virial": natoms * 4 * H + npairs * 30,
-        "ck_geometry": npairs * 150,
+        "energy_force_virial": natoms * 4 * H + npairs * 30,
     }

@@ -44,7 +44,7 @@ EXPORTS = ("snap_num_coeff", "snap_create", "snap_set_beta", "snap_set_neigh_cap
            "snap_bispectrum_deriv", "snap_force_weighted", "snap_generation",
            "snap_compute_batch", "snap_set_tuning", "snap_get_tuning", "snap_autotune",
            "snap_neighbors_noalloc")
-NSTAGES = 6
+NSTAGES = 5
 
 _lib = None
 
