@@ -199,6 +199,7 @@ def run_reference(args):
 def time_variant(torch, snap, w, precision, steps, warmup, flush, dev, profile=False):
     """Device time of `steps` evaluations (CUDA events on the compute stream,
     L2 flushed between steps outside the events)."""
+    import numpy as np
     cfg, beta = w.config(), w.beta()
     s = snap.Snap(w.twojmax, beta, precision=precision)
     pos = torch.tensor(cfg.pos, dtype=torch.float64, device=dev)
@@ -235,10 +236,12 @@ def time_variant(torch, snap, w, precision, steps, warmup, flush, dev, profile=F
         prof = s.profile_read()
         s.profile(False)
     launches = s.launches_per_call()
-    npairs = int(s.get_buffer(snap.BUF_NBR_CNT).sum())
+    cnt = s.get_buffer(snap.BUF_NBR_CNT)
+    npairs = int(cnt.sum())
+    hist = {int(k): int(v) for k, v in enumerate(np.bincount(cnt)) if v}
     s.close()
     return {"ms": ms, "wall": wall, "prof": prof, "launches": launches, "npairs": npairs,
-            "natoms": n}
+            "natoms": n, "neighbor_hist": hist}
 
 
 def e2e_host(snap, torch, w, precision, steps):
@@ -431,11 +434,14 @@ def main():
         "dtype": "f32 recursions + f64 geometry/accumulation" if hprec == snap.MIXED else "f64",
         "data": "synthetic BCC (a=3.1803 A, +-0.1 A displacements, seeded beta)",
         "config": {"workload": head.name, "natoms": r["natoms"], "twojmax": head.twojmax,
-                   "neighbors": r["npairs"] / r["natoms"], "precision": args.precision,
+                   "neighbors": r["npairs"] / r["natoms"], "neighbor_hist": r["neighbor_hist"],
+                   "precision": args.precision,
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": r["launches"] * args.steps,
         "stages": stages,
+        # the same steps without the neighbour build (its profiled time taken off)
+        "value_excl_neighbor_build": world * r["natoms"] / ((t_max - stages["neighbor_build"]["ms_per_call"]) * 1e-3),
         "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved,
                      "peak": hpeak, "unit": "TFLOP/s", "frac": achieved / hpeak,
                      "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
