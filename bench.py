@@ -333,8 +333,30 @@ def next_rows(torch, snap, inputs, flush, dev, args):
         "batched_no_graph_ms": t_nograph, "per_config_loop_ms": t_loop,
         "per_config_loop_atom_steps_per_s": total / (t_loop * 1e-3),
         "speedup_vs_loop": t_loop / t_graph,
-        "default_tuning": {"col_warps": default_tuning[0], "yi_waves": default_tuning[1], "graph_ms": t_default},
-        "autotuned": {"col_warps": tuned[0], "yi_waves": tuned[1], "autotune_median_ms": best_ms}}
+        "default_tuning": {"col_warps": default_tuning[0], "yi_waves": default_tuning[1],
+                           "yi_layout": default_tuning[2], "graph_ms": t_default},
+        "autotuned": {"col_warps": tuned[0], "yi_waves": tuned[1], "yi_layout": tuned[2],
+                      "autotune_median_ms": best_ms}}
+    # --- compute_Y layouts on the headline workload: warp of 32 atoms (AoSoA)
+    # vs warp per atom, stage time and whole step
+    w = inputs.WORKLOADS["bcc10_2j8"]
+    cfg = w.config()
+    lay = {}
+    for layout, tag in ((0, "warp_of_32_atoms"), (1, "warp_per_atom")):
+        s = snap.Snap(8, w.beta(), precision=snap.MIXED)
+        s.set_tuning(4, 2, layout)
+        p_ = torch.tensor(cfg.pos, device=dev)
+        for _ in range(3):
+            s.compute(p_, cfg.box, wait=False)
+        t = _events_time(torch, lambda: s.compute(p_, cfg.box, wait=False), 10, flush, dev)
+        s.profile(True)
+        for _ in range(10):
+            s.compute(p_, cfg.box, wait=False)
+        pr = s.profile_read()
+        s.profile(False)
+        s.close()
+        lay[tag] = {"step_ms": t, "compute_yi_ms": pr["compute_yi"][0] / max(pr["compute_yi"][1], 1)}
+    out["compute_y_layout_2000_2j8_mixed"] = lay
     # --- bispectrum output, 2000 atoms, 2J = 8
     w = inputs.WORKLOADS["bcc10_2j8"]
     cfg = w.config()

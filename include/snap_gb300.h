@@ -190,17 +190,24 @@ int snap_compute_batch(snap_ctx* ctx, int nconf, const int* natoms, const double
                        const double* pos, double* energy, double* forces, double* virial,
                        int use_graph, void* stream);
 
-/* Launch-shape tunables: col_warps (2, 4 or 8 warps per CTA of the register
- * column-chain kernels; each warp computes one atom, so this is atoms per CTA,
- * halved where the CTA's shared memory would pass 227 KB) and yi_waves (1..8,
- * fineness of the compute_Y split: the slices per 32-atom block minimise
- * ceil(CTAs / resident CTAs) * (1/slices + 0.02/yi_waves)).  Neither changes
- * a result bit.  snap_autotune times every combination of
- * col_warps in {2, 4, 8} and yi_waves in {1, 2, 4} on the given batch
- * (reps timed calls each, CUDA events on `stream`), keeps the fastest, and
- * reports its median time in *best_ms.  Synchronous. */
-int snap_set_tuning(snap_ctx* ctx, int col_warps, int yi_waves);
-int snap_get_tuning(const snap_ctx* ctx, int* col_warps, int* yi_waves);
+/* Launch-shape tunables:
+ *  col_warps (2, 4 or 8): warps per CTA of the register column-chain kernels;
+ *    each warp computes one atom, so this is atoms per CTA (halved where the
+ *    CTA's shared memory would pass 227 KB);
+ *  yi_waves (1..8): fineness of the compute_Y split; the slices per 32-atom
+ *    block minimise ceil(CTAs / resident CTAs) * (1/slices + 0.02/yi_waves);
+ *  yi_layout: 0 = compute_Y with a warp of 32 atoms (lanes = atoms, the
+ *    block's Ulisttot staged by TMA; the paper's AoSoA layout, Sec. V-B),
+ *    1 = a warp per atom (its Ulisttot staged in shared memory, lanes over
+ *    output elements), the layout the paper compares it with.
+ * col_warps and yi_waves change no result bit; yi_layout changes the
+ * compute_Y kernel and may change rounding.  snap_autotune times every
+ * combination of col_warps in {2, 4, 8} with yi_waves in {1, 2, 4} (layout 0)
+ * or layout 1 on the given batch (reps timed calls each, CUDA events on
+ * `stream`), keeps the fastest, and reports its median time in *best_ms.
+ * Synchronous. */
+int snap_set_tuning(snap_ctx* ctx, int col_warps, int yi_waves, int yi_layout);
+int snap_get_tuning(const snap_ctx* ctx, int* col_warps, int* yi_waves, int* yi_layout);
 int snap_autotune(snap_ctx* ctx, int nconf, const int* natoms, const double* boxes,
                   const double* pos, double* energy, double* forces, double* virial, int reps,
                   double* best_ms, void* stream);

@@ -45,6 +45,7 @@ struct snap_ctx {
   int K = 32;
   int col_warps = 4;  // tunables (snap_set_tuning / snap_autotune)
   int yi_waves = 2;
+  int yi_layout = 0;
   int last_nmax = 0;
   int last_n = 0, last_K = 0;
   std::string err;
@@ -59,6 +60,8 @@ struct snap_ctx {
   int* d_bgfirst = nullptr;
   void* d_root = nullptr;
   int* d_yslice = nullptr;
+  int* d_ysched = nullptr;  // lane schedule of the warp-per-atom compute_Y
+  int ysched_m = 0;
   int nslices = -1;
   std::map<int, int*> yslice_cache;  // compute_Y slice tables by slice count
 
@@ -343,6 +346,9 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.yrec = c->d_yrec;
   a.yfirst = c->d_yfirst;
   a.yslice = c->d_yslice;
+  a.yi_layout = c->yi_layout;
+  a.ysched = c->d_ysched;
+  a.ysched_m = c->ysched_m;
   a.nslices = c->nslices;
   a.nsm = c->nsm;
   a.col_warps = c->col_warps;
@@ -670,8 +676,9 @@ int compute_dev(snap_ctx* c, int n, const double* pos, const double* box, const 
   if (rc) return rc;
   const std::vector<unsigned long long> key = {
       1, (unsigned long long)c->ws_gen, (unsigned long long)n, (unsigned long long)K,
-      (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves, key_bits(box[0]),
-      key_bits(box[1]), key_bits(box[2]), key_ptr(pos), key_ptr(energy), key_ptr(forces),
+      (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves,
+      (unsigned long long)c->yi_layout, key_bits(box[0]), key_bits(box[1]), key_bits(box[2]),
+      key_ptr(pos), key_ptr(energy), key_ptr(forces),
       key_ptr(virial), key_ptr(ucnt), key_ptr(uidx), key_ptr(uimg), (unsigned long long)ucap};
   return graph_run(c, c->gdev, key, s, run);
 }
@@ -748,6 +755,7 @@ int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switch
   }
   int rc = upload(c, &c->d_half_tmm, c->tab.half_tmm);
   if (!rc) rc = upload(c, &c->d_yfirst, c->tab.term_out_first);
+  if (!rc) rc = upload(c, &c->d_ysched, c->tab.lane_outputs(32, &c->ysched_m));
   if (!rc) rc = upload_r(c, &c->d_root, c->tab.rootpq);
   if (!rc) rc = upload_yrec(c);
   if (!rc) rc = upload_brec(c);
@@ -959,14 +967,16 @@ int snap_compute_batch(snap_ctx* c, int nconf, const int* natoms, const double* 
   return SNAP_OK;
 }
 
-int snap_set_tuning(snap_ctx* c, int col_warps, int yi_waves) {
+int snap_set_tuning(snap_ctx* c, int col_warps, int yi_waves, int yi_layout) {
   if (!c) return SNAP_ERR_ARG;
   if (col_warps != 2 && col_warps != 4 && col_warps != 8)
     return fail(c, SNAP_ERR_ARG, "col_warps must be 2, 4 or 8");
   if (yi_waves < 1 || yi_waves > 8) return fail(c, SNAP_ERR_ARG, "yi_waves must be in 1..8");
-  if (c->col_warps != col_warps || c->yi_waves != yi_waves) {
+  if (yi_layout != 0 && yi_layout != 1) return fail(c, SNAP_ERR_ARG, "yi_layout must be 0 or 1");
+  if (c->col_warps != col_warps || c->yi_waves != yi_waves || c->yi_layout != yi_layout) {
     c->col_warps = col_warps;
     c->yi_waves = yi_waves;
+    c->yi_layout = yi_layout;
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);
       c->gexec = nullptr;
@@ -975,10 +985,11 @@ int snap_set_tuning(snap_ctx* c, int col_warps, int yi_waves) {
   return SNAP_OK;
 }
 
-int snap_get_tuning(const snap_ctx* c, int* col_warps, int* yi_waves) {
+int snap_get_tuning(const snap_ctx* c, int* col_warps, int* yi_waves, int* yi_layout) {
   if (!c) return SNAP_ERR_ARG;
   if (col_warps) *col_warps = c->col_warps;
   if (yi_waves) *yi_waves = c->yi_waves;
+  if (yi_layout) *yi_layout = c->yi_layout;
   return SNAP_OK;
 }
 
@@ -991,14 +1002,18 @@ int snap_autotune(snap_ctx* c, int nconf, const int* natoms, const double* boxes
   const int cw[3] = {2, 4, 8};
   const int yw[3] = {1, 2, 4};
   double best = 1e300;
-  int bc = c->col_warps, by = c->yi_waves;
+  int bc = c->col_warps, by = c->yi_waves, bl = c->yi_layout;
   cudaEvent_t e0, e1;
   SNAP_CUDA(c, cudaEventCreate(&e0));
   SNAP_CUDA(c, cudaEventCreate(&e1));
   int rc = SNAP_OK;
+  // combinations: col_warps x (yi_waves of the warp-of-atoms compute_Y, or
+  // the warp-per-atom compute_Y, which has no split)
   for (int a = 0; a < 3 && !rc; ++a)
-    for (int b = 0; b < 3 && !rc; ++b) {
-      rc = snap_set_tuning(c, cw[a], yw[b]);
+    for (int b = 0; b < 4 && !rc; ++b) {
+      const int lay = b == 3 ? 1 : 0;
+      const int wav = b == 3 ? c->yi_waves : yw[b];
+      rc = snap_set_tuning(c, cw[a], wav, lay);
       if (rc) break;
       std::vector<float> ms;
       for (int it = 0; it < reps + 2 && !rc; ++it) {
@@ -1017,13 +1032,14 @@ int snap_autotune(snap_ctx* c, int nconf, const int* natoms, const double* boxes
       if (med < best) {
         best = med;
         bc = cw[a];
-        by = yw[b];
+        by = wav;
+        bl = lay;
       }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  rc = snap_set_tuning(c, bc, by);
+  rc = snap_set_tuning(c, bc, by, bl);
   if (best_ms) *best_ms = best;
   SNAP_CUDA(c, cudaStreamSynchronize(s));
   return rc ? rc : check_flags(c);
@@ -1075,8 +1091,9 @@ int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const dou
     if (rc) return rc;
     const std::vector<unsigned long long> key = {
         2, (unsigned long long)c->ws_gen, (unsigned long long)natoms, (unsigned long long)c->K,
-        (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves, key_bits(box[0]),
-        key_bits(box[1]), key_bits(box[2]), key_ptr(pos_host), key_ptr(energy_host),
+        (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves,
+        (unsigned long long)c->yi_layout, key_bits(box[0]), key_bits(box[1]), key_bits(box[2]),
+        key_ptr(pos_host), key_ptr(energy_host),
         key_ptr(forces_host), key_ptr(virial_host), key_ptr(c->d_hpos)};
     // copies from and to pageable host memory cannot be captured
     const bool replay = c->ghost.exec && c->ghost.key == key;
@@ -1146,6 +1163,7 @@ int snap_destroy(snap_ctx* c) {
   dfree(c->d_half_tmm);
   dfree(c->d_yrec);
   dfree(c->d_yfirst);
+  dfree(c->d_ysched);
   dfree(c->d_brec);
   dfree(c->d_bout);
   dfree(c->d_bfirst);

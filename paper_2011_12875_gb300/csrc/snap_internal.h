@@ -116,6 +116,9 @@ struct WorkArgs {
   const int* yfirst;      // [H+1] first term of each output element
   const int* yslice;
   int nslices;
+  int yi_layout;          // 0: warp of 32 atoms (AoSoA), 1: warp per atom
+  const int* ysched;      // [32][ysched_m] outputs of each lane (warp-per-atom layout)
+  int ysched_m;
   int nsm;
   int col_warps;  // warps per CTA of the column-chain kernels (tunable)
   int yi_waves;   // compute_Y waves per SM (tunable)

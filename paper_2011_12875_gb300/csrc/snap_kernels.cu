@@ -349,6 +349,59 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   for (; q < q1; ++q) term(rec[q].w, rec[q].c);
 }
 
+// ------------------------------------------- compute_Y, one atom per warp
+// The alternative layout to the warp of atoms (the paper compares the two,
+// Sec. V-B): warp = one atom, its Ulisttot and conj(Ulisttot) staged in shared
+// memory as a [2][H] block, lanes over output elements (dealt to the lanes in
+// decreasing term count, snake order, so their loads balance); each lane walks
+// its outputs' term records in the same grouped order as yi_kernel.
+constexpr int kYaWarps = 8;
+
+template <typename R>
+__global__ void __launch_bounds__(kYaWarps * 32) yi_atom_kernel(WorkArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long i = (long)blockIdx.x * kYaWarps + warp;
+  if (i >= a.n) return;  // whole warp
+  const int H = a.H;
+  cx<R>* ua = reinterpret_cast<cx<R>*>(smem) + (size_t)warp * 2 * H;
+  const long base = (i >> 5) * (long)H * 32 + (i & 31);
+  const cx<R>* Ug = reinterpret_cast<const cx<R>*>(a.U) + base;
+  for (int e = lane; e < H; e += 32) {
+    const cx<R> v = Ug[(long)e * 32];
+    ua[e] = v;
+    ua[H + e] = mk<R>(v.re, -v.im);
+  }
+  __syncwarp();
+  cx<R>* Yg = reinterpret_cast<cx<R>*>(a.Y) + base;
+  const YRec<R>* __restrict__ rec = reinterpret_cast<const YRec<R>*>(a.yrec);
+  const int m = a.ysched_m;
+  for (int k = 0; k < m; ++k) {
+    const int o = a.ysched[lane * m + k];
+    if (o < 0) break;
+    YAcc<R> y;
+    y.re = y.im = y.ar = y.ai = R(0);
+    const int q1 = a.yfirst[o + 1];
+    for (int q = a.yfirst[o]; q < q1; ++q) {
+      const unsigned w = rec[q].w;
+      const R c = rec[q].c;
+      // elements of the factors in the [2][H] block: the staged-conjugate
+      // record format indexes it directly, the other one sets the sign bits
+      const cx<R> u2 = ua[(int)((w >> 8) & 1023u) + (int)(w >> 31) * H];
+      y.ar += c * u2.re;
+      y.ai += c * u2.im;
+      if (w & (1u << 28)) {
+        const cx<R> u1 = ua[(int)((w >> 18) & 1023u) + (int)((w >> 30) & 1u) * H];
+        y.re += u1.re * y.ar - u1.im * y.ai;
+        y.im += u1.re * y.ai + u1.im * y.ar;
+        y.ar = R(0);
+        y.ai = R(0);
+      }
+    }
+    Yg[(long)o * 32] = mk<R>(y.re, y.im);
+  }
+}
+
 // ------------------------------------------------------- bispectrum B_l
 // Descriptor output (Sec. II-A, Eq. z): B_l = Re Z^t_{t1t2} : conj(U_t) for
 // every canonical component l, for 32 atoms per warp (lanes = atoms, U staged
@@ -916,6 +969,13 @@ YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves) {
 template <typename R>
 cudaError_t launch_yi(const WorkArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
+  if (a.yi_layout == 1) {
+    const size_t sm = sizeof(cx<R>) * 2 * (size_t)a.H * kYaWarps;
+    cudaError_t e = allow_smem(yi_atom_kernel<R>, sm);
+    if (e != cudaSuccess) return e;
+    return launch_k(yi_atom_kernel<R>, dim3((unsigned)((a.n + kYaWarps - 1) / kYaWarps)),
+                    dim3(kYaWarps * 32), sm, s, a);
+  }
   const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm, a.yi_waves);
   if (g.nslices != a.nslices) return cudaErrorInvalidValue;
   dim3 grid(g.nblk, g.ysplit);

@@ -299,6 +299,22 @@ std::vector<int> HostTables::bslices(int nslices) const {
   return b;
 }
 
+std::vector<int> HostTables::lane_outputs(int lanes, int* m) const {
+  std::vector<int> ord(H);
+  for (int o = 0; o < H; ++o) ord[o] = o;
+  auto nterm = [&](int o) { return term_out_first[o + 1] - term_out_first[o]; };
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return nterm(x) > nterm(y); });
+  const int mm = (H + lanes - 1) / lanes;
+  std::vector<int> t((size_t)lanes * mm, -1);
+  for (int k = 0; k < H; ++k) {
+    const int round = k / lanes, pos = k % lanes;
+    const int lane = (round & 1) ? lanes - 1 - pos : pos;
+    t[(size_t)lane * mm + round] = ord[k];
+  }
+  *m = mm;
+  return t;
+}
+
 std::vector<int> HostTables::slices(int nslices) const {
   // nslices contiguous runs of output elements with about equal term counts;
   // entry k is the first output of run k (entry nslices = H)

@@ -36,6 +36,9 @@ struct HostTables {
   std::vector<double> beta_weights(const double* beta) const;
   std::vector<double> term_coef(const double* beta) const;
   std::vector<int> slices(int nslices) const;
+  // outputs dealt to `lanes` lanes in decreasing term count, snake order:
+  // [lanes][m] output indices, -1 past a lane's last; m returned in *m
+  std::vector<int> lane_outputs(int lanes, int* m) const;
   std::vector<int> bslices(int nslices) const;
 };
 

@@ -99,9 +99,9 @@ def load(path: str | None = None):
     L.snap_generation.restype = ctypes.c_longlong
     L.snap_compute_batch.argtypes = [p, i, p, p, p, p, p, p, i, p]
     L.snap_compute_batch.restype = i
-    L.snap_set_tuning.argtypes = [p, i, i]
+    L.snap_set_tuning.argtypes = [p, i, i, i]
     L.snap_set_tuning.restype = i
-    L.snap_get_tuning.argtypes = [p, p, p]
+    L.snap_get_tuning.argtypes = [p, p, p, p]
     L.snap_get_tuning.restype = i
     L.snap_autotune.argtypes = [p, i, p, p, p, p, p, p, i, p, p]
     L.snap_autotune.restype = i
@@ -314,13 +314,16 @@ class Snap:
         self._batch_keep = (na, bx)
         return energy, forces, virial
 
-    def set_tuning(self, col_warps: int, yi_waves: int):
-        self._check(self._lib.snap_set_tuning(self._h, col_warps, yi_waves))
+    def set_tuning(self, col_warps: int, yi_waves: int, yi_layout: int = 0):
+        """Launch-shape tunables (see snap_set_tuning); yi_layout 0 = warp of
+        32 atoms, 1 = warp per atom."""
+        self._check(self._lib.snap_set_tuning(self._h, col_warps, yi_waves, yi_layout))
 
     def get_tuning(self):
-        a, b = ctypes.c_int(), ctypes.c_int()
-        self._check(self._lib.snap_get_tuning(self._h, ctypes.byref(a), ctypes.byref(b)))
-        return a.value, b.value
+        """(col_warps, yi_waves, yi_layout)."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.snap_get_tuning(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
 
     def autotune(self, pos, natoms, boxes, reps: int = 5, stream=None):
         """Pick the fastest launch shape for this batch; returns its median ms."""

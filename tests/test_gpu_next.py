@@ -217,12 +217,15 @@ def test_autotune_keeps_results(snapmod):
     P = torch.tensor(pos, device="cuda:0")
     E0, F0, _ = [x.cpu().numpy() for x in s.compute_batch(P, natoms, boxes, use_graph=False)]
     ms = s.autotune(P, natoms, boxes, reps=3)
-    cw, yw = s.get_tuning()
-    assert ms > 0 and cw in (2, 4, 8) and yw in (1, 2, 4)
+    cw, yw, yl = s.get_tuning()
+    assert ms > 0 and cw in (2, 4, 8) and yw in (1, 2, 4) and yl in (0, 1)
     E1, F1, _ = [x.cpu().numpy() for x in s.compute_batch(P, natoms, boxes, use_graph=True)]
-    # tunables change only launch shapes: the same per-atom arithmetic in the
-    # same order, so the same bits
-    assert np.array_equal(E1, E0) and np.array_equal(F1, F0)
+    if yl == 0:
+        # launch shapes only: the same per-atom arithmetic in the same order,
+        # so the same bits
+        assert np.array_equal(E1, E0) and np.array_equal(F1, F0)
+    else:
+        assert rel_err(E1, E0) < 1e-6 and rel_err(F1, F0) < 1e-5
     s.close()
 
 
@@ -249,3 +252,28 @@ def test_tuning_changes_no_bit(snapmod, prec, twojmax):
             for x, y in zip(run(), ref):
                 assert np.array_equal(x, y), (cw, yw)
     s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("twojmax", [1, 2, 5, 8, 14])
+def test_warp_per_atom_compute_y_parity(snapmod, prec, twojmax):
+    """compute_Y with a warp per atom (yi_layout 1): E, F, W against the
+    oracle at the tolerances of the warp-of-atoms layout, and against that
+    layout itself."""
+    cfg = inputs.bcc(2, disp=0.15, seed=32)
+    beta = inputs.beta(twojmax)
+    _, ref = O.evaluate(O.Params(twojmax), beta, cfg.pos, cfg.box)
+    s = snapmod.Snap(twojmax, beta, precision=prec)
+    pos = torch.tensor(cfg.pos, device="cuda:0")
+    E0, F0, W0 = [x.cpu().numpy().copy() for x in s.compute(pos, cfg.box)]
+    s.set_tuning(4, 2, 1)
+    E1, F1, W1 = [x.cpu().numpy().copy() for x in s.compute(pos, cfg.box)]
+    Y1 = s.get_buffer(snapmod.BUF_YLIST).copy()
+    s.set_tuning(4, 2, 0)
+    s.compute(pos, cfg.box)
+    Y0 = s.get_buffer(snapmod.BUF_YLIST).copy()
+    s.close()
+    tolE, tolF = (FP64_TOL, FP64_TOL) if prec == 0 else (2e-5, 2e-4)
+    assert rel_err(E1, ref.E) <= tolE and rel_err(F1, ref.F) <= tolF and rel_err(W1, ref.W) <= tolF
+    assert rel_err(Y1, Y0) <= (1e-13 if prec == 0 else 1e-6)
+    assert rel_err(E1, E0) <= (1e-13 if prec == 0 else 1e-6)
