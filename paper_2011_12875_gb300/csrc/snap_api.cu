@@ -54,6 +54,7 @@ struct snap_ctx {
   int* d_half_tmm = nullptr;
   void* d_yrec = nullptr;
   int* d_yfirst = nullptr;
+  unsigned short* d_yruns = nullptr;
   void* d_brec = nullptr;
   int* d_bout = nullptr;
   int* d_bfirst = nullptr;
@@ -345,6 +346,7 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.half_tmm = c->d_half_tmm;
   a.yrec = c->d_yrec;
   a.yfirst = c->d_yfirst;
+  a.yruns = c->d_yruns;
   a.yslice = c->d_yslice;
   a.yi_layout = c->yi_layout;
   a.ysched = c->d_ysched;
@@ -743,7 +745,7 @@ int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switch
   c->rmin0 = rmin0;
   c->switchflag = switchflag;
   c->precision = precision;
-  c->tab.build(twojmax);
+  c->tab.build(twojmax, precision == SNAP_MIXED);
   c->beta.assign(beta, beta + 1 + c->tab.ncoeff);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -755,6 +757,7 @@ int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switch
   }
   int rc = upload(c, &c->d_half_tmm, c->tab.half_tmm);
   if (!rc) rc = upload(c, &c->d_yfirst, c->tab.term_out_first);
+  if (!rc) rc = upload(c, &c->d_yruns, c->tab.term_runs);
   if (!rc) rc = upload(c, &c->d_ysched, c->tab.lane_outputs(32, &c->ysched_m));
   if (!rc) rc = upload_r(c, &c->d_root, c->tab.rootpq);
   if (!rc) rc = upload_yrec(c);
@@ -1163,6 +1166,7 @@ int snap_destroy(snap_ctx* c) {
   dfree(c->d_half_tmm);
   dfree(c->d_yrec);
   dfree(c->d_yfirst);
+  dfree(c->d_yruns);
   dfree(c->d_ysched);
   dfree(c->d_brec);
   dfree(c->d_bout);

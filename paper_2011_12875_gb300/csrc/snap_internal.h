@@ -18,6 +18,7 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
 #endif
 
 constexpr int kMaxTwoJ = 14;
+constexpr int kYGroupMax = 8;  // longest compute_Y term group (longer ones are cut)
 constexpr int kMaxNeighCap = 64;
 constexpr int kRootDim = 16;     // rootpq table is kRootDim x kRootDim
 constexpr int kGeomStride = 20;  // doubles per neighbour slot, see PairGeom
@@ -114,6 +115,7 @@ struct WorkArgs {
   const int* half_tmm;
   const void* yrec;       // compute_Y term records (see snap_tables.cpp)
   const int* yfirst;      // [H+1] first term of each output element
+  const void* yruns;      // [H][kYGroupMax] u16: groups of 1..kYGroupMax terms per output
   const int* yslice;
   int nslices;
   int yi_layout;          // 0: warp of 32 atoms (AoSoA), 1: warp per atom

@@ -8,6 +8,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "snap_geom.cuh"
 #include "snap_internal.h"
@@ -231,11 +234,51 @@ __device__ __forceinline__ unsigned y_off1(unsigned w) {
   return ((w >> 10) & 0x3FF00u) << (sizeof(R) == 4 ? 0 : 1);
 }
 
-// The rest of a term once its second factor u2 is loaded: acc += coef * u2;
-// at the end of a group (terms with one first factor U1), Y += U1 * acc; at
-// the end of an output, store Y.  `ul` points at lane 0's element 0 plus this
-// lane.  CP: the staged block is [2][H][32] with the conjugate in its second
-// half (no sign flips).
+// B consecutive groups of K terms from record q: every record and both
+// factors are loaded ahead of the arithmetic (no branch inside), then per
+// group acc = sum_k coef_k U2,k and Y += U1 * acc.  `ul` points at lane 0's
+// element 0 plus this lane.  CP: the staged block is [2][H][32] with the
+// conjugate in its second half (no sign flips).
+template <typename R, bool CP, int K, int B>
+__device__ __forceinline__ void y_groups(const YRec<R>* __restrict__ rec, int q, const char* __restrict__ ul,
+                                         R& yre, R& yim) {
+  unsigned w[B * K];
+  R c[B * K];
+#pragma unroll
+  for (int j = 0; j < B * K; ++j) {
+    if constexpr (sizeof(R) == 4) {
+      const uint2 r = __ldg(reinterpret_cast<const uint2*>(rec + q + j));
+      w[j] = r.x;
+      c[j] = __uint_as_float(r.y);
+    } else {
+      const uint4 r = __ldg(reinterpret_cast<const uint4*>(rec + q + j));
+      w[j] = r.x;
+      c[j] = (R)__hiloint2double((int)r.w, (int)r.z);
+    }
+  }
+  cx<R> u2[B * K], u1[B];
+#pragma unroll
+  for (int j = 0; j < B * K; ++j) u2[j] = *reinterpret_cast<const cx<R>*>(ul + y_off2<R>(w[j]));
+#pragma unroll
+  for (int b = 0; b < B; ++b) u1[b] = *reinterpret_cast<const cx<R>*>(ul + y_off1<R>(w[b * K]));
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    R ar = R(0), ai = R(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int j = b * K + k;
+      ar += c[j] * u2[j].re;
+      ai += c[j] * (CP ? u2[j].im : flip_sign(u2[j].im, w[j] & 0x80000000u));
+    }
+    const R i1 = CP ? u1[b].im : flip_sign(u1[b].im, (w[b * K] << 1) & 0x80000000u);
+    yre += u1[b].re * ar - i1 * ai;
+    yim += u1[b].re * ai + i1 * ar;
+  }
+}
+
+// FP64 path: one term at a time with the group-end and output-end bits of
+// the record (FP64 arithmetic, not the integer work around it, bounds that
+// path, and this loop keeps its registers low).
 template <typename R, bool CP>
 __device__ __forceinline__ void y_term(unsigned w, R c, cx<R> u2, const char* __restrict__ ul,
                                        cx<R>* __restrict__ Yg, int lane, int& o, YAcc<R>& y) {
@@ -258,10 +301,19 @@ __device__ __forceinline__ void y_term(unsigned w, R c, cx<R> u2, const char* __
   }
 }
 
+// All groups of K terms of one output (a run of `ng` groups from record q).
+template <typename R, bool CP, int K>
+__device__ __forceinline__ void y_run(const YRec<R>* __restrict__ rec, int& q, int ng,
+                                      const char* __restrict__ ul, R& yre, R& yim) {
+  constexpr int B = K >= 8 ? 1 : 8 / K;  // groups per step: about 8 records
+  for (; ng >= B; ng -= B, q += B * K) y_groups<R, CP, K, B>(rec, q, ul, yre, yim);
+  for (; ng > 0; --ng, q += K) y_groups<R, CP, K, 1>(rec, q, ul, yre, yim);
+}
+
 // CTA = one 32-atom block x one ysplit-th of the outputs; U of the block
 // staged by a TMA bulk copy.
 template <typename R, bool STAGED, bool CP>
-__global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
+__global__ void __launch_bounds__(STAGED ? 1024 : 256, 1) yi_kernel(WorkArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long blk0 = blockIdx.x;
@@ -302,51 +354,48 @@ __global__ void __launch_bounds__(1024) yi_kernel(WorkArgs a) {
   if (o0 >= o1) return;
   cx<R>* Yg = reinterpret_cast<cx<R>*>(a.Y) + blk0 * H * 32;
   const YRec<R>* __restrict__ rec = reinterpret_cast<const YRec<R>*>(a.yrec);
-  const int q1 = a.yfirst[o1];
-  int q = a.yfirst[o0];
-  int o = o0;
-  YAcc<R> y;
-  y.re = y.im = y.ar = y.ai = R(0);
   const char* ul = reinterpret_cast<const char*>(us + lane);
-  auto load2 = [&](unsigned w) { return *reinterpret_cast<const cx<R>*>(ul + y_off2<R>(w)); };
-  auto term = [&](unsigned w, R c) { y_term<R, CP>(w, c, load2(w), ul, Yg, lane, o, y); };
-  if constexpr (sizeof(R) == 4) {
-    // two 8-byte records per 16-byte load; the second factors of a batch are
-    // loaded ahead of its arithmetic
-    if ((q & 1) && q < q1) {
-      term(rec[q].w, rec[q].c);
-      ++q;
-    }
-    for (; q + 8 <= q1; q += 8) {
-      uint4 v[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(rec + q) + k);
-      cx<R> u2[8];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        u2[2 * k] = load2(v[k].x);
-        u2[2 * k + 1] = load2(v[k].z);
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        y_term<R, CP>(v[k].x, __uint_as_float(v[k].y), u2[2 * k], ul, Yg, lane, o, y);
-        y_term<R, CP>(v[k].z, __uint_as_float(v[k].w), u2[2 * k + 1], ul, Yg, lane, o, y);
-      }
-    }
-  } else {
+  if constexpr (sizeof(R) == 8) {
+    // FP64: the terms of the slice in order, four records per batch
+    int q = a.yfirst[o0];
+    const int q1 = a.yfirst[o1];
+    int o = o0;
+    YAcc<R> y;
+    y.re = y.im = y.ar = y.ai = R(0);
     for (; q + 4 <= q1; q += 4) {
       uint4 v[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(rec + q + k));
       cx<R> u2[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) u2[k] = load2(v[k].x);
+      for (int k = 0; k < 4; ++k) u2[k] = *reinterpret_cast<const cx<R>*>(ul + y_off2<R>(v[k].x));
 #pragma unroll
       for (int k = 0; k < 4; ++k)
         y_term<R, CP>(v[k].x, (R)__hiloint2double((int)v[k].w, (int)v[k].z), u2[k], ul, Yg, lane, o, y);
     }
+    for (; q < q1; ++q)
+      y_term<R, CP>(rec[q].w, rec[q].c, *reinterpret_cast<const cx<R>*>(ul + y_off2<R>(rec[q].w)), ul, Yg,
+                    lane, o, y);
+    return;
   }
-  for (; q < q1; ++q) term(rec[q].w, rec[q].c);
+  // FP32: per output, its runs of 1-, 2-, ... 8-term groups (branch-free
+  // bodies of known length)
+  const uint4* runs = reinterpret_cast<const uint4*>(a.yruns);  // 8 u16 counts per output
+  static_assert(kYGroupMax == 8, "one 16-byte run header per output");
+  for (int o = o0; o < o1; ++o) {
+    int q = a.yfirst[o];
+    const uint4 h = __ldg(runs + o);
+    R yre = R(0), yim = R(0);
+    y_run<R, CP, 1>(rec, q, (int)(h.x & 0xffffu), ul, yre, yim);
+    y_run<R, CP, 2>(rec, q, (int)(h.x >> 16), ul, yre, yim);
+    y_run<R, CP, 3>(rec, q, (int)(h.y & 0xffffu), ul, yre, yim);
+    y_run<R, CP, 4>(rec, q, (int)(h.y >> 16), ul, yre, yim);
+    y_run<R, CP, 5>(rec, q, (int)(h.z & 0xffffu), ul, yre, yim);
+    y_run<R, CP, 6>(rec, q, (int)(h.z >> 16), ul, yre, yim);
+    y_run<R, CP, 7>(rec, q, (int)(h.w & 0xffffu), ul, yre, yim);
+    y_run<R, CP, 8>(rec, q, (int)(h.w >> 16), ul, yre, yim);
+    Yg[o * 32 + lane] = mk<R>(yre, yim);
+  }
 }
 
 // ------------------------------------------- compute_Y, one atom per warp
@@ -932,6 +981,13 @@ cudaError_t launch_ui(const WorkArgs& a, cudaStream_t s) {
   return launch_k(ui_kernel<R, kUiWarps>, dim3(a.n), dim3(kUiWarps * 32), sm, s, a);
 }
 
+template <typename R, bool STAGED, bool CP>
+cudaError_t yi_occupancy(const YiGeometry& g, int* ctas) {
+  cudaError_t e = STAGED ? allow_smem(yi_kernel<R, STAGED, CP>, g.smem) : cudaSuccess;
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, yi_kernel<R, STAGED, CP>, g.threads, g.smem);
+}
+
 bool yi_conjplane(int rsize, int H) { return (size_t)4 * H * 32 * rsize + 16 <= 100 * 1024; }
 
 YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves) {
@@ -944,14 +1000,44 @@ YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves) {
   g.threads = (g.smem > 100 * 1024) ? 1024 : (g.smem > 60 * 1024 ? 512 : 256);
   int cps = 2048 / g.threads;
   if (g.staged) cps = std::max(1, std::min(cps, (int)((227 * 1024) / g.smem)));
+  // the instance's real residency (registers can limit it further), queried
+  // once per (precision, H)
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> occ_cache;
+  int occ = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = occ_cache.find({rsize, H});
+    if (it != occ_cache.end()) {
+      occ = it->second;
+    } else {
+      cudaError_t oe;
+      if (rsize == 4)
+        oe = g.staged ? (g.conjplane ? yi_occupancy<float, true, true>(g, &occ)
+                                     : yi_occupancy<float, true, false>(g, &occ))
+                      : yi_occupancy<float, false, false>(g, &occ);
+      else
+        oe = g.staged ? (g.conjplane ? yi_occupancy<double, true, true>(g, &occ)
+                                     : yi_occupancy<double, true, false>(g, &occ))
+                      : yi_occupancy<double, false, false>(g, &occ);
+      if (oe != cudaSuccess) {
+        cudaGetLastError();
+        occ = 0;
+      } else {
+        occ_cache[{rsize, H}] = occ;
+      }
+    }
+  }
+  if (occ > 0) cps = std::min(cps, occ);
   // Split each CTA's outputs into ysplit CTAs.  CTAs of one launch take about
   // equal time, so the launch lasts ceil(CTAs / resident) CTA lifetimes;
   // pick the split that minimises
   //   ceil(nblk ysplit / resident) (1 / ysplit + c),
   // c = the fixed per-CTA cost (staging U) relative to a whole block's terms,
-  // taken as 0.02 / waves (the tunable: more waves, finer splits).
+  // taken as 0.02 / waves (the tunable: more waves, finer splits), and a
+  // tenth of that without staging.
   const long resident = (long)nsm * cps;
-  const double c = 0.02 / std::max(1, waves);
+  const double c = (g.staged ? 0.02 : 0.002) / std::max(1, waves);
   double best = 1e300;
   g.ysplit = 1;
   for (int ys = 1; ys <= 64; ++ys) {

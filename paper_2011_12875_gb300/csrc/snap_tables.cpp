@@ -10,6 +10,7 @@
 #include "snap_tables.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <map>
 
@@ -77,7 +78,7 @@ int count_coeff(int twojmax) {
   return n;
 }
 
-void HostTables::build(int J2) {
+void HostTables::build(int J2, bool size_runs) {
   twojmax = J2;
   H = half_size(J2);
   lmax = half_layer_size(J2);
@@ -141,6 +142,7 @@ void HostTables::build(int J2) {
   term_cg.clear();
   term_trip.clear();
   term_out_first.clear();
+  term_runs.clear();
   auto half_elem = [&](int tt, int xa, int xb, int& idx, int& conj, double& sgn) {
     if (2 * xb <= tt) {
       idx = half_base(tt) + xb * (tt + 1) + xa;
@@ -184,10 +186,15 @@ void HostTables::build(int J2) {
         // Group the output's terms by their first factor (index and
         // conjugation flag, stable): compute_Y then forms
         //   Y += U_t1[..] * sum_k coef_k U_t2,k[..]
-        // once per group.  Bit 23 ends a group, bit 22 the output; every
-        // output has at least the term of the (t, 0, t) triple, whose
-        // Clebsch-Gordan product is 1.
+        // once per group.  Groups longer than kYGroupMax are cut into chunks,
+        // and with size_runs the chunks are ordered by length (stable), so an
+        // output is a run of 1-term groups, then of 2-term groups, ...;
+        // term_runs counts them.  Without it the groups keep the order of
+        // their first factor.  Bit 23 ends a group, bit 22 the output; every output has at
+        // least the term of the (t, 0, t) triple, whose Clebsch-Gordan
+        // product is 1.
         const size_t cnt = terms.size() - first;
+        std::array<unsigned short, kYGroupMax> runs{};
         if (cnt > 0) {
           std::vector<size_t> ord(cnt);
           for (size_t k = 0; k < cnt; ++k) ord[k] = k;
@@ -202,14 +209,30 @@ void HostTables::build(int J2) {
             tq[k] = term_trip[first + ord[k]];
           }
           const unsigned kmask = 1023u | (1u << 20);
-          for (size_t k = 0; k < cnt; ++k) {
-            const bool ge = (k + 1 == cnt) || ((tw[k] & kmask) != (tw[k + 1] & kmask));
-            terms[first + k] = tw[k] | (ge ? (1u << 23) : 0u);
-            term_cg[first + k] = tc[k];
-            term_trip[first + k] = tq[k];
+          struct Chunk {
+            size_t b, n;
+          };
+          std::vector<Chunk> ch;
+          for (size_t k = 0; k < cnt;) {
+            size_t e = k + 1;
+            while (e < cnt && (tw[e] & kmask) == (tw[k] & kmask)) ++e;
+            for (size_t b = k; b < e; b += kYGroupMax) ch.push_back({b, std::min<size_t>(kYGroupMax, e - b)});
+            k = e;
+          }
+          if (size_runs)
+            std::stable_sort(ch.begin(), ch.end(), [](const Chunk& x, const Chunk& y) { return x.n < y.n; });
+          size_t pos = first;
+          for (const Chunk& c : ch) {
+            runs[c.n - 1] += 1;
+            for (size_t j = 0; j < c.n; ++j, ++pos) {
+              terms[pos] = tw[c.b + j] | (j + 1 == c.n ? (1u << 23) : 0u);
+              term_cg[pos] = tc[c.b + j];
+              term_trip[pos] = tq[c.b + j];
+            }
           }
           terms.back() |= (1u << 22);
         }
+        term_runs.insert(term_runs.end(), runs.begin(), runs.end());
         term_out_first.push_back((int)first);
       }
   term_out_first.push_back((int)terms.size());

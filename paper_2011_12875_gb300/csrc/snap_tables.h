@@ -23,6 +23,9 @@ struct HostTables {
   std::vector<double> term_cg;
   std::vector<int> term_trip;
   std::vector<int> term_out_first;  // [H+1] first term of every output
+  // [H][kYGroupMax]: number of groups of 1, 2, ... kYGroupMax terms of each
+  // output (they follow one another in that order)
+  std::vector<unsigned short> term_runs;
   // bispectrum terms (records as above, coefficient without beta), the U
   // element of each output group, and the first term of each component
   std::vector<unsigned> bterms;
@@ -32,7 +35,9 @@ struct HostTables {
   std::vector<int> bgroup_first;  // [ncoeff+1] first output group of each component
   std::vector<double> rootpq;
 
-  void build(int twojmax);
+  // size_runs: order each output's term groups by length (the run layout of
+  // the FP32 compute_Y); otherwise by first factor
+  void build(int twojmax, bool size_runs = true);
   std::vector<double> beta_weights(const double* beta) const;
   std::vector<double> term_coef(const double* beta) const;
   std::vector<int> slices(int nslices) const;
