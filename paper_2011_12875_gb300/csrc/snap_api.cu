@@ -202,15 +202,16 @@ int upload_yrec(snap_ctx* c) {
     return (e2 << 8) | (e1 << 18) | (((w >> 23) & 1u) << 28) | (((w >> 22) & 1u) << 29) |
            (c1 << 30) | (c2 << 31);
   };
+  // kYRecPad zero records past the end: compute_Y prefetches that far ahead
   if (c->precision == SNAP_MIXED) {
-    std::vector<snap::YRec<float>> r(n);
+    std::vector<snap::YRec<float>> r(n + snap::kYRecPad);
     for (size_t k = 0; k < n; ++k) {
       r[k].w = word(c->tab.terms[k]);
       r[k].c = (float)coef[k];
     }
     return upload_inplace(c, reinterpret_cast<snap::YRec<float>**>(&c->d_yrec), r);
   }
-  std::vector<snap::YRec<double>> r(n);
+  std::vector<snap::YRec<double>> r(n + snap::kYRecPad);
   for (size_t k = 0; k < n; ++k) {
     r[k].w = word(c->tab.terms[k]);
     r[k].pad = 0;

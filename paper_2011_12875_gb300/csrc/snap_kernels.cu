@@ -242,6 +242,8 @@ __device__ __forceinline__ unsigned y_off1(unsigned w) {
 template <typename R, bool CP, int K, int B>
 __device__ __forceinline__ void y_groups(const YRec<R>* __restrict__ rec, int q, const char* __restrict__ ul,
                                          R& yre, R& yim) {
+  // the record stream is read once per CTA: pull it into L1 ahead of use
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(rec + q + kYRecPad));
   unsigned w[B * K];
   R c[B * K];
 #pragma unroll
