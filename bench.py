@@ -151,6 +151,45 @@ def cpu_baseline(w, seconds=10.0):
             "sample": f"{sample}; {steps} steps in {el:.1f} s, workload {w.name}"}
 
 
+def accuracy_vs_oracle(torch, snap, inputs, dev):
+    """The GPU results, mixed and FP64, against the FP64 oracle (part of the
+    cpu_baseline leg, the bench step that runs the oracle): every atom of the
+    2000-atom 2J = 8 workload, and 16 seeded atoms of the 2000-atom 2J = 14
+    one (forces on an atom need its neighbours' dE/dr, so the oracle evaluates
+    those atoms and their neighbours).  Errors relative to the largest
+    magnitude of each quantity, and the largest absolute force error (eV/A
+    for beta in eV)."""
+    import numpy as np
+    from oracle import snap_oracle as O
+
+    def gpu(J, beta, cfg, prec):
+        s = snap.Snap(J, beta, precision=prec)
+        E, F, W = [x.cpu().numpy() for x in s.compute(torch.tensor(cfg.pos, device=dev), cfg.box)]
+        s.close()
+        return E, F, W
+
+    def err(a, b):
+        return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+    out = {}
+    w = inputs.WORKLOADS["bcc10_2j8"]
+    cfg, beta = w.config(), w.beta()
+    _, ref = O.evaluate(O.Params(8), beta, cfg.pos, cfg.box)
+    for prec, tag in ((snap.MIXED, "mixed"), (snap.FP64, "fp64")):
+        E, F, W = gpu(8, beta, cfg, prec)
+        out[f"2j8_{tag}"] = {"atoms": cfg.natoms, "energy_rel": err(E, ref.E), "force_rel": err(F, ref.F),
+                             "force_max_abs": float(np.abs(F - ref.F).max()), "virial_rel": err(W, ref.W)}
+    w = inputs.WORKLOADS["bcc10_2j14"]
+    cfg, beta = w.config(), w.beta()
+    atoms = np.sort(np.random.Generator(np.random.PCG64(77)).choice(cfg.natoms, 16, replace=False))
+    Fref, res, _ = O.forces_for_atoms(O.Params(14), beta, cfg.pos, cfg.box, atoms)
+    for prec, tag in ((snap.MIXED, "mixed"), (snap.FP64, "fp64")):
+        E, F, _ = gpu(14, beta, cfg, prec)
+        out[f"2j14_{tag}"] = {"atoms": int(len(atoms)), "energy_rel": err(E[atoms], res.E[atoms]),
+                              "force_rel": err(F[atoms], Fref), "force_max_abs": float(np.abs(F[atoms] - Fref).max())}
+    return out
+
+
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle timed on the host cores, each step
     a bounded sample (a fixed subset of centre atoms) of the workload."""
@@ -503,6 +542,7 @@ def main():
             line["next"] = next_rows(torch, snap, inputs, flush, dev, args)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(head)
+            line["accuracy_vs_oracle"] = accuracy_vs_oracle(torch, snap, inputs, dev)
         print(json.dumps(line), flush=True)
     if pg:
         pg.barrier()
