@@ -70,6 +70,7 @@ struct snap_ctx {
   long cap_nk = 0;
   int cap_n = 0;
   float4* d_pos4 = nullptr;
+  float4* d_tiles = nullptr;  // bounding boxes of 32-atom tiles
   int* d_cnt = nullptr;
   int* d_nbr = nullptr;
   signed char* d_img = nullptr;
@@ -242,6 +243,7 @@ int upload_brec(snap_ctx* c) {
 
 void free_workspace(snap_ctx* c) {
   dfree(c->d_pos4);
+  dfree(c->d_tiles);
   dfree(c->d_cnt);
   dfree(c->d_nbr);
   dfree(c->d_img);
@@ -267,6 +269,7 @@ int ensure_workspace(snap_ctx* c, int n, int K) {
   const long nblk = (ncap + 31) / 32;
   const size_t uy = (size_t)nblk * 32 * c->tab.H * 2 * c->rsize();
   SNAP_CUDA(c, cudaMalloc(&c->d_pos4, sizeof(float4) * ncap));
+  SNAP_CUDA(c, cudaMalloc(&c->d_tiles, sizeof(float4) * 2 * ((ncap + 31) / 32)));
   SNAP_CUDA(c, cudaMalloc(&c->d_cnt, sizeof(int) * ncap));
   SNAP_CUDA(c, cudaMalloc(&c->d_nbr, sizeof(int) * nkcap));
   SNAP_CUDA(c, cudaMalloc(&c->d_img, 3 * nkcap));
@@ -410,6 +413,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
     na.K = K;
     na.pos = pos;
     na.pos4 = c->d_pos4;
+    na.tiles = c->d_tiles;
     na.Lx = box[0];
     na.Ly = box[1];
     na.Lz = box[2];
@@ -425,7 +429,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
     na.img = c->d_img;
     na.rij = c->d_rij;
     na.flags = c->d_flags;
-    SNAP_CUDA(c, snap::launch_pos4(n, pos, c->d_pos4, s));
+    SNAP_CUDA(c, snap::launch_pos4(n, pos, c->d_pos4, s, c->d_tiles));
     SNAP_CUDA(c, snap::launch_neigh_build(na, s));
     c->launches += 2;
   }

@@ -81,6 +81,9 @@ struct NeighArgs {
   const int2* cta_map;
   const double* pos;     // [n][3]
   const float4* pos4;    // [n] FP32 copy for the coarse test
+  // [ceil(n/32)][2]: FP32 centre and half extent of each 32-atom tile, for
+  // skipping far tiles in the single-configuration build; nullptr: no skipping
+  const float4* tiles = nullptr;
   double Lx, Ly, Lz;
   int Sx, Sy, Sz;        // image shifts enumerated beyond the nearest image
   double rcut;
@@ -136,7 +139,7 @@ struct WorkArgs {
 };
 
 // Launchers (snap_neigh.cu)
-cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s);
+cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s, float4* tiles = nullptr);
 cudaError_t launch_neigh_build(const NeighArgs& a, cudaStream_t s);
 // batch: one launch over all configurations (ncta CTAs)
 cudaError_t launch_neigh_build_batch(const NeighArgs& a, int ncta, cudaStream_t s);

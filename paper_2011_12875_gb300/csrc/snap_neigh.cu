@@ -14,15 +14,46 @@ namespace snap {
 
 namespace {
 
-constexpr int kNbWarps = 8;                       // warps per CTA
-constexpr int kNbSplit = 4;                       // warps per centre atom
-constexpr int kNbAtoms = kNbWarps / kNbSplit;     // centre atoms per CTA
-static_assert(kNbAtoms == kNeighAtomsPerCta, "batch CTA map and kernel disagree");
+constexpr int kNbWarps = 8;  // warps per CTA
+// Warps per centre atom: a batch build scans every block of its
+// configuration, so four warps share the scan; a single-configuration build
+// skips far tiles and one warp per atom suffices.
+constexpr int kNbSplitBatch = 4;
+static_assert(kNbWarps / kNbSplitBatch == kNeighAtomsPerCta, "batch CTA map and kernel disagree");
 constexpr unsigned kFull = 0xffffffffu;
 
-__global__ void pos4_kernel(int n, const double* __restrict__ pos, float4* __restrict__ pos4) {
+// FP32 positions, and (when `tiles` is given) the bounding box of every tile
+// of 32 consecutive atoms as an FP32 centre and half extent, padded by 1e-4 A
+// for rounding.  Blocks are whole warps, one tile per warp.
+__global__ void pos4_kernel(int n, const double* __restrict__ pos, float4* __restrict__ pos4,
+                            float4* __restrict__ tiles) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) pos4[i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], 0.f);
+  const int lane = threadIdx.x & 31;
+  const bool ok = i < n;
+  float x = 0.f, y = 0.f, z = 0.f;
+  if (ok) {
+    x = (float)pos[3 * i];
+    y = (float)pos[3 * i + 1];
+    z = (float)pos[3 * i + 2];
+    pos4[i] = make_float4(x, y, z, 0.f);
+  }
+  if (!tiles) return;  // uniform over the grid
+  float lx = ok ? x : INFINITY, ly = ok ? y : INFINITY, lz = ok ? z : INFINITY;
+  float hx = ok ? x : -INFINITY, hy = ok ? y : -INFINITY, hz = ok ? z : -INFINITY;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lx = fminf(lx, __shfl_xor_sync(kFull, lx, o));
+    ly = fminf(ly, __shfl_xor_sync(kFull, ly, o));
+    lz = fminf(lz, __shfl_xor_sync(kFull, lz, o));
+    hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
+    hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o));
+    hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
+  }
+  if (lane == 0 && ok) {
+    const int t = i >> 5;
+    tiles[2 * t] = make_float4(0.5f * (lx + hx), 0.5f * (ly + hy), 0.5f * (lz + hz), 0.f);
+    tiles[2 * t + 1] = make_float4(0.5f * (hx - lx) + 1e-4f, 0.5f * (hy - ly) + 1e-4f, 0.5f * (hz - lz) + 1e-4f, 0.f);
+  }
 }
 
 // Exact FP64 separation r_k + s L - r_i, computed so that the pairs (i,k,s)
@@ -38,7 +69,7 @@ __device__ __forceinline__ double norm2(double x, double y, double z) {
   return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
 }
 
-// kNbSplit warps per centre atom i, each scanning one contiguous part of the
+// SPLIT warps per centre atom i, each scanning one contiguous part of the
 // candidate range: lanes test 32 atoms k at a time in FP32 with a margin (all
 // images in range) and the survivors are appended, in a fixed order
 // (32-block, image, lane), to the part's candidate list in shared memory.
@@ -53,17 +84,18 @@ __device__ __forceinline__ int pack_img(int x, int y, int z) {
   return (x + 128) | ((y + 128) << 8) | ((z + 128) << 16);
 }
 
-template <bool BATCH>
+template <bool BATCH, int SPLIT>
 __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a) {
+  constexpr int kAtoms = kNbWarps / SPLIT;
   __shared__ int cand_j[kNbWarps][kCandCap];
   __shared__ int cand_s[kNbWarps][kCandCap];
   __shared__ int ncands[kNbWarps];
   __shared__ int cmax;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int part = warp % kNbSplit, ai = warp / kNbSplit;
+  const int part = warp % SPLIT, ai = warp / SPLIT;
   const unsigned lt = (1u << lane) - 1u;
   // candidate range [j_lo, j_hi), box and image range of this CTA's atoms
-  int j_lo = 0, j_hi = a.n, i = blockIdx.x * kNbAtoms + ai;
+  int j_lo = 0, j_hi = a.n, i = blockIdx.x * kAtoms + ai;
   int Sx = a.Sx, Sy = a.Sy, Sz = a.Sz;
   double Ldx = a.Lx, Ldy = a.Ly, Ldz = a.Lz;
   if (BATCH) {
@@ -80,13 +112,14 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
     Sz = c.S[2];
   }
   if (threadIdx.x == 0) cmax = 0;
+  __syncthreads();  // before any warp's atomicMax on cmax
   const bool NEAREST = (Sx == 0 && Sy == 0 && Sz == 0);
   const bool active = i < j_hi;
-  // this warp's part of the candidate range, in 32-blocks
+  // this warp's part of the candidate range, in 32-blocks [b0, b1)
   const int nblk32 = (j_hi - j_lo + 31) / 32;
-  const int per = (nblk32 + kNbSplit - 1) / kNbSplit;
-  const int c0 = j_lo + 32 * min(nblk32, per * part);
-  const int c1 = min(j_hi, j_lo + 32 * min(nblk32, per * (part + 1)));
+  const int per = (nblk32 + SPLIT - 1) / SPLIT;
+  const int b0 = min(nblk32, per * part), b1 = min(nblk32, per * (part + 1));
+  const int c1 = min(j_hi, j_lo + 32 * b1);
   int* cj = cand_j[warp];
   int* cs = cand_s[warp];
   int ncand = 0;  // candidates of this part (warp-uniform, may pass kCandCap)
@@ -107,51 +140,71 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
     }
     ncand += __popc(m);
   };
+  // Far tiles are skipped: their minimum-image distance bound passes
+  // rcut + 0.02 A, so they hold no candidate of the rcut + 0.01 A test and the
+  // list is the same (single configuration, nearest image; tiles start at 0).
+  // Each lane tests one of the next 32 tiles, and the warp scans the tiles
+  // that pass, in order.
+  const bool cull = !BATCH && NEAREST && a.tiles != nullptr;
+  const float rcull2 = ((float)a.rcut + 2e-2f) * ((float)a.rcut + 2e-2f);
   if (active) {
-    for (int j0 = c0; j0 < c1; j0 += 32) {
-      const int j = j0 + lane;
-      const bool valid = j < c1;
-      const float4 pj = valid ? __ldg(a.pos4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float dx0 = pj.x - pi4.x, dy0 = pj.y - pi4.y, dz0 = pj.z - pi4.z;
-      // nearest-image shift counts, kept in float (int <-> float conversions
-      // run on a slow pipe and are only done for the rare candidates)
-      const float nxf = -rintf(dx0 * iLx), nyf = -rintf(dy0 * iLy), nzf = -rintf(dz0 * iLz);
-      const float bx = dx0 + nxf * Lx, by = dy0 + nyf * Ly, bz = dz0 + nzf * Lz;
-      if (NEAREST) {
-        // box > 2 (rcut + margin) in every direction: only the nearest image
-        const bool c = valid && (bx * bx + by * by + bz * bz < rc2f) && (j != i);
-        push(c, j, c ? pack_img((int)nxf, (int)nyf, (int)nzf) : 0);
-        continue;
+    for (int bb = b0; bb < b1; bb += 32) {
+      bool near = bb + lane < b1;
+      if (cull && near) {
+        const float4 tc = __ldg(a.tiles + 2 * (bb + lane)), th = __ldg(a.tiles + 2 * (bb + lane) + 1);
+        float ex = tc.x - pi4.x, ey = tc.y - pi4.y, ez = tc.z - pi4.z;
+        ex = fmaxf(fabsf(ex - Lx * rintf(ex * iLx)) - th.x, 0.f);
+        ey = fmaxf(fabsf(ey - Ly * rintf(ey * iLy)) - th.y, 0.f);
+        ez = fmaxf(fabsf(ez - Lz * rintf(ez * iLz)) - th.z, 0.f);
+        near = ex * ex + ey * ey + ez * ez <= rcull2;
       }
-      float sxf = -(float)Sx;
-      for (int sx = -Sx; sx <= Sx; ++sx, sxf += 1.f) {
-        float syf = -(float)Sy;
-        for (int sy = -Sy; sy <= Sy; ++sy, syf += 1.f) {
-          float szf = -(float)Sz;
-          for (int sz = -Sz; sz <= Sz; ++sz, szf += 1.f) {
-            const float fx = bx + sxf * Lx, fy = by + syf * Ly, fz = bz + szf * Lz;
-            bool c = valid && (fx * fx + fy * fy + fz * fz < rc2f);
-            int ix = 0, iy = 0, iz = 0;
-            if (c) {
-              ix = (int)(nxf + sxf);
-              iy = (int)(nyf + syf);
-              iz = (int)(nzf + szf);
-              c = !((j == i) && ix == 0 && iy == 0 && iz == 0);
+      for (unsigned tm = __ballot_sync(kFull, near); tm; tm &= tm - 1) {
+        const int j0 = j_lo + 32 * (bb + __ffs(tm) - 1);
+        const int j = j0 + lane;
+        const bool valid = j < c1;
+        const float4 pj = valid ? __ldg(a.pos4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float dx0 = pj.x - pi4.x, dy0 = pj.y - pi4.y, dz0 = pj.z - pi4.z;
+        // nearest-image shift counts, kept in float (int <-> float conversions
+        // run on a slow pipe and are only done for the rare candidates)
+        const float nxf = -rintf(dx0 * iLx), nyf = -rintf(dy0 * iLy), nzf = -rintf(dz0 * iLz);
+        const float bx = dx0 + nxf * Lx, by = dy0 + nyf * Ly, bz = dz0 + nzf * Lz;
+        if (NEAREST) {
+          // box > 2 (rcut + margin) in every direction: only the nearest image
+          const bool c = valid && (bx * bx + by * by + bz * bz < rc2f) && (j != i);
+          push(c, j, c ? pack_img((int)nxf, (int)nyf, (int)nzf) : 0);
+          continue;
+        }
+        float sxf = -(float)Sx;
+        for (int sx = -Sx; sx <= Sx; ++sx, sxf += 1.f) {
+          float syf = -(float)Sy;
+          for (int sy = -Sy; sy <= Sy; ++sy, syf += 1.f) {
+            float szf = -(float)Sz;
+            for (int sz = -Sz; sz <= Sz; ++sz, szf += 1.f) {
+              const float fx = bx + sxf * Lx, fy = by + syf * Ly, fz = bz + szf * Lz;
+              bool c = valid && (fx * fx + fy * fy + fz * fz < rc2f);
+              int ix = 0, iy = 0, iz = 0;
+              if (c) {
+                ix = (int)(nxf + sxf);
+                iy = (int)(nyf + syf);
+                iz = (int)(nzf + szf);
+                c = !((j == i) && ix == 0 && iy == 0 && iz == 0);
+              }
+              push(c, j, c ? pack_img(ix, iy, iz) : 0);
             }
-            push(c, j, c ? pack_img(ix, iy, iz) : 0);
           }
         }
       }
     }
   }
   if (lane == 0) ncands[warp] = ncand;
-  __syncthreads();
+  if (SPLIT > 1) __syncthreads();
+  else __syncwarp();
   if (active && part == 0) {
     // exact FP64 check of the concatenated candidate lists
-    int off[kNbSplit + 1];
+    int off[SPLIT + 1];
     off[0] = 0;
     bool over = false;
-    for (int p = 0; p < kNbSplit; ++p) {
+    for (int p = 0; p < SPLIT; ++p) {
       const int c = ncands[warp + p];
       over |= c > kCandCap;
       off[p + 1] = off[p] + min(c, kCandCap);
@@ -159,12 +212,12 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
     const double xi = a.pos[3 * i], yi = a.pos[3 * i + 1], zi = a.pos[3 * i + 2];
     const double rc2 = a.rcut * a.rcut;
     int count = 0;
-    for (int e0 = 0; e0 < off[kNbSplit]; e0 += 32) {
+    for (int e0 = 0; e0 < off[SPLIT]; e0 += 32) {
       const int e = e0 + lane;
       bool in = false;
       double ex = 0, ey = 0, ez = 0;
       int j = 0, ix = 0, iy = 0, iz = 0;
-      if (e < off[kNbSplit]) {
+      if (e < off[SPLIT]) {
         int p = 0;
         while (e >= off[p + 1]) ++p;
         j = cand_j[warp + p][e - off[p]];
@@ -244,19 +297,19 @@ inline int blocks_for(long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s) {
+cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s, float4* tiles) {
   if (n <= 0) return cudaSuccess;
-  return launch_k(pos4_kernel, dim3(blocks_for(n, 256)), dim3(256), 0, s, n, pos, pos4);
+  return launch_k(pos4_kernel, dim3(blocks_for(n, 256)), dim3(256), 0, s, n, pos, pos4, tiles);
 }
 
 cudaError_t launch_neigh_build(const NeighArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  return launch_k(neigh_build_kernel<false>, dim3(blocks_for(a.n, kNbAtoms)), dim3(kNbWarps * 32), 0, s, a);
+  return launch_k(neigh_build_kernel<false, 1>, dim3(blocks_for(a.n, kNbWarps)), dim3(kNbWarps * 32), 0, s, a);
 }
 
 cudaError_t launch_neigh_build_batch(const NeighArgs& a, int ncta, cudaStream_t s) {
   if (ncta <= 0) return cudaSuccess;
-  return launch_k(neigh_build_kernel<true>, dim3(ncta), dim3(kNbWarps * 32), 0, s, a);
+  return launch_k(neigh_build_kernel<true, kNbSplitBatch>, dim3(ncta), dim3(kNbWarps * 32), 0, s, a);
 }
 
 cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, double Ly,
