@@ -335,7 +335,9 @@ __device__ __forceinline__ R shfl_down(R v) {
 }
 
 template <typename R, int J2>
-__global__ void __launch_bounds__(256, 2) de_rev_col_kernel(WorkArgs a) {
+// FP32: 128 registers (two CTAs of 256 threads); FP64 may use them all (its
+// FP64 pipe saturates with few warps, and the columns are twice the size).
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) de_rev_col_kernel(WorkArgs a) {
   using S_ = Shape<J2>;
   constexpr int NC = S_::NC, P = S_::P;
   const int NW = blockDim.x >> 5;
