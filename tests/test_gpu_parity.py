@@ -108,6 +108,68 @@ def test_ragged_neighbour_counts(snapmod):
     full_check(snapmod, 6, cfg, snapmod.FP64)
 
 
+def reordered(cfg, seed, unwrap):
+    """The configuration with its atoms in a random order and, with unwrap,
+    each atom moved by a random whole number of box lengths per axis (the
+    same physical system)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    perm = rng.permutation(cfg.natoms)
+    pos = cfg.pos[perm].copy()
+    if unwrap:
+        pos += rng.integers(-2, 3, size=pos.shape) * cfg.box[None, :]
+    return inputs.Config(pos=np.ascontiguousarray(pos), box=cfg.box, name=cfg.name + "-reordered")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_random_atom_order(snapmod, prec):
+    """The neighbour build skips far 32-atom tiles by their bounding boxes:
+    with atoms in random order (tiles spread over the box) the neighbour
+    sets, U, Y, dE/dr, E, F and W still match the oracle."""
+    cfg = reordered(inputs.bcc(6, disp=0.15, seed=41), seed=42, unwrap=False)
+    full_check(snapmod, 4, cfg, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_unwrapped_positions(snapmod, prec):
+    """Positions moved by whole box lengths (outside [0, L), random order):
+    the same per-atom neighbour counts and, within the tolerances, the same E,
+    F and W as the oracle on the wrapped positions (the image indices of the
+    list differ by the wrap, so the sets are not compared)."""
+    base = inputs.bcc(6, disp=0.15, seed=41)
+    cfg = reordered(base, seed=42, unwrap=True)
+    wrapped = inputs.Config(pos=np.ascontiguousarray(np.mod(cfg.pos, cfg.box[None, :])), box=cfg.box)
+    beta = inputs.beta(4)
+    pairs, ref = O.evaluate(O.Params(4), beta, wrapped.pos, wrapped.box)
+    s, E, F, W = run_gpu(snapmod, 4, beta, cfg, prec)
+    cnt = s.get_buffer(snapmod.BUF_NBR_CNT).copy()
+    s.close()
+    assert np.array_equal(cnt, np.bincount(pairs.i, minlength=cfg.natoms))
+    tol = FP64_TOL if prec == snapmod.FP64 else None
+    assert rel_err(E, ref.E) <= (tol or MIXED_TOL["E"])
+    assert rel_err(F, ref.F) <= (tol or MIXED_TOL["F"])
+    assert rel_err(W, ref.W) <= (tol or MIXED_TOL["W"])
+
+
+def test_tile_culling_on_spatial_order_large(snapmod):
+    """2000 atoms in lattice order (compact tiles, most culled) and the same
+    atoms shuffled (no tile culled): identical per-atom results after undoing
+    the permutation, and the same neighbour counts."""
+    cfg = inputs.bcc(10, disp=0.1, seed=43)
+    rng = np.random.Generator(np.random.PCG64(44))
+    perm = rng.permutation(cfg.natoms)
+    shuffled = inputs.Config(pos=np.ascontiguousarray(cfg.pos[perm]), box=cfg.box, name="shuffled")
+    beta = inputs.beta(2)
+    s1, E1, F1, W1 = run_gpu(snapmod, 2, beta, cfg, snapmod.FP64)
+    c1 = s1.get_buffer(snapmod.BUF_NBR_CNT).copy()
+    s1.close()
+    s2, E2, F2, W2 = run_gpu(snapmod, 2, beta, shuffled, snapmod.FP64)
+    c2 = s2.get_buffer(snapmod.BUF_NBR_CNT).copy()
+    s2.close()
+    assert np.array_equal(c1[perm], c2)
+    assert rel_err(E2, E1[perm]) <= 1e-12 and rel_err(F2, F1[perm]) <= 1e-12
+    assert rel_err(W2, W1) <= 1e-12
+
+
 def test_switching_variants(snapmod):
     cfg = inputs.bcc(2, disp=0.1, seed=9)
     for p in (O.Params(4, rmin0=0.7), O.Params(4, switchflag=0), O.Params(5, rfac0=0.7, rcut=4.2)):
