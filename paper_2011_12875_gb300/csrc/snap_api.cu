@@ -371,10 +371,12 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
 // Enqueue the whole evaluation on stream s (no synchronisation).
 // mode 0: energy, forces, virial; mode 1: bispectrum components into B;
 // mode 2: derivative of the bispectrum along the displacement field g into B.
+// pos_stage: positions are in mapped host memory; the position kernel copies
+// them there (device) and the neighbour build reads the copy.
 int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int* ucnt,
             const int* uidx, const signed char* uimg, int ucap, double* energy, double* forces,
             double* virial, cudaStream_t s, int mode = 0, double* B = nullptr,
-            const double* g = nullptr) {
+            const double* g = nullptr, double* pos_stage = nullptr) {
   const bool user = (ucnt || uidx || uimg);
   if (user && (!ucnt || !uidx || !uimg || ucap < 1 || ucap > snap::kMaxNeighCap))
     return fail(c, SNAP_ERR_ARG, "neighbour list: cnt, idx and img must all be given with 1 <= cap <= 64");
@@ -429,7 +431,8 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
     na.img = c->d_img;
     na.rij = c->d_rij;
     na.flags = c->d_flags;
-    SNAP_CUDA(c, snap::launch_pos4(n, pos, c->d_pos4, s, c->d_tiles));
+    SNAP_CUDA(c, snap::launch_pos4(n, pos, c->d_pos4, s, c->d_tiles, pos_stage));
+    if (pos_stage) na.pos = pos_stage;
     SNAP_CUDA(c, snap::launch_neigh_build(na, s));
     c->launches += 2;
   }
@@ -1091,6 +1094,26 @@ int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const dou
       SNAP_CUDA(c, cudaMemcpyAsync(virial_host, c->d_hW, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
     return SNAP_OK;
   };
+  // With pinned (hence device-mapped) host buffers the kernels read the
+  // positions and write the results through the mapping: the position kernel
+  // stages the positions in device memory as it reads them, the force kernel
+  // writes energies, forces and virial straight to the caller's buffers.
+  const double* mpos = nullptr;
+  double *mE = nullptr, *mF = nullptr, *mW = nullptr;
+  auto mapped = [&]() -> bool {
+    auto dev = [](const void* h, void** d) {
+      if (!h) return true;
+      if (cudaHostGetDevicePointer(d, const_cast<void*>(h), 0) == cudaSuccess) return true;
+      cudaGetLastError();
+      return false;
+    };
+    return dev(pos_host, (void**)&mpos) && dev(energy_host, (void**)&mE) && dev(forces_host, (void**)&mF) &&
+           dev(virial_host, (void**)&mW);
+  };
+  auto run_mapped = [&](cudaStream_t st) -> int {
+    return enqueue(c, natoms, mpos, box, nullptr, nullptr, nullptr, 0, mE, mF, mW, st, 0, nullptr, nullptr,
+                   c->d_hpos);
+  };
   int rc = SNAP_OK;
   if (c->prof_on) {
     rc = run(s);
@@ -1106,11 +1129,13 @@ int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const dou
         (unsigned long long)c->yi_layout, key_bits(box[0]), key_bits(box[1]), key_bits(box[2]),
         key_ptr(pos_host), key_ptr(energy_host),
         key_ptr(forces_host), key_ptr(virial_host), key_ptr(c->d_hpos)};
-    // copies from and to pageable host memory cannot be captured
+    // pageable host memory is neither mapped nor capturable: plain copies (a
+    // key that matches the captured graph was checked when it was captured)
     const bool replay = c->ghost.exec && c->ghost.key == key;
-    if (replay || (pinned_or_null(pos_host) && pinned_or_null(energy_host) && pinned_or_null(forces_host) &&
-                   pinned_or_null(virial_host)))
-      rc = graph_run(c, c->ghost, key, s, run);
+    if (replay ||
+        (pinned_or_null(pos_host) && pinned_or_null(energy_host) && pinned_or_null(forces_host) &&
+         pinned_or_null(virial_host) && mapped()))
+      rc = graph_run(c, c->ghost, key, s, run_mapped);
     else
       rc = run(s);
   }

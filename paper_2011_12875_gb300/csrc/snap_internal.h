@@ -139,7 +139,8 @@ struct WorkArgs {
 };
 
 // Launchers (snap_neigh.cu)
-cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s, float4* tiles = nullptr);
+cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s, float4* tiles = nullptr,
+                        double* copy = nullptr);
 cudaError_t launch_neigh_build(const NeighArgs& a, cudaStream_t s);
 // batch: one launch over all configurations (ncta CTAs)
 cudaError_t launch_neigh_build_batch(const NeighArgs& a, int ncta, cudaStream_t s);

@@ -22,19 +22,27 @@ constexpr int kNbSplitBatch = 4;
 static_assert(kNbWarps / kNbSplitBatch == kNeighAtomsPerCta, "batch CTA map and kernel disagree");
 constexpr unsigned kFull = 0xffffffffu;
 
-// FP32 positions, and (when `tiles` is given) the bounding box of every tile
-// of 32 consecutive atoms as an FP32 centre and half extent, padded by 1e-4 A
-// for rounding.  Blocks are whole warps, one tile per warp.
+// FP32 positions, (when `tiles` is given) the bounding box of every tile of
+// 32 consecutive atoms as an FP32 centre and half extent, padded by 1e-4 A for
+// rounding, and (when `copy` is given) a device copy of the FP64 positions,
+// for positions read from mapped host memory.  Blocks are whole warps, one
+// tile per warp.
 __global__ void pos4_kernel(int n, const double* __restrict__ pos, float4* __restrict__ pos4,
-                            float4* __restrict__ tiles) {
+                            float4* __restrict__ tiles, double* __restrict__ copy) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool ok = i < n;
   float x = 0.f, y = 0.f, z = 0.f;
   if (ok) {
-    x = (float)pos[3 * i];
-    y = (float)pos[3 * i + 1];
-    z = (float)pos[3 * i + 2];
+    const double px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
+    if (copy) {
+      copy[3 * i] = px;
+      copy[3 * i + 1] = py;
+      copy[3 * i + 2] = pz;
+    }
+    x = (float)px;
+    y = (float)py;
+    z = (float)pz;
     pos4[i] = make_float4(x, y, z, 0.f);
   }
   if (!tiles) return;  // uniform over the grid
@@ -297,9 +305,10 @@ inline int blocks_for(long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s, float4* tiles) {
+cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s, float4* tiles,
+                        double* copy) {
   if (n <= 0) return cudaSuccess;
-  return launch_k(pos4_kernel, dim3(blocks_for(n, 256)), dim3(256), 0, s, n, pos, pos4, tiles);
+  return launch_k(pos4_kernel, dim3(blocks_for(n, 256)), dim3(256), 0, s, n, pos, pos4, tiles, copy);
 }
 
 cudaError_t launch_neigh_build(const NeighArgs& a, cudaStream_t s) {
