@@ -284,8 +284,10 @@ def time_variant(torch, snap, w, precision, steps, warmup, flush, dev, profile=F
 
 
 def e2e_host(snap, torch, w, precision, steps):
-    """Same metric through snap_compute_host: pinned host buffers, H2D of the
-    positions and D2H of energies, forces and virial inside every step."""
+    """Same metric through snap_compute_host with pinned host buffers: every
+    step moves the positions host -> device and the energies, forces and
+    virial device -> host inside the call (the library reads and writes them
+    through the host mapping of the pinned buffers), wall clock per call."""
     import numpy as np
     cfg, beta = w.config(), w.beta()
     n = cfg.natoms
