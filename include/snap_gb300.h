@@ -89,7 +89,10 @@ int snap_neigh_max(const snap_ctx* ctx);
 
 /* Energy, forces and virial of one configuration.
  *   natoms  : N >= 0 (N = 0 returns at once)
- *   pos     : device, [N][3] doubles (x, y, z)
+ *   pos     : device, [N][3] doubles (x, y, z).  Any position is accepted (no
+ *             wrapping into the box is needed), but the device neighbour builder
+ *             pre-screens pairs in FP32 with a 0.01 A margin, so |coordinates|
+ *             should stay below about 1e4 A.
  *   box     : HOST, 3 doubles: orthorhombic box lengths, periodic in x, y, z
  *   nbr_cnt, nbr_idx, nbr_img, nbr_cap :
  *             all NULL/0 -> the library builds the list on the device

@@ -73,6 +73,15 @@ __device__ __forceinline__ double sep1(int i, int k, double xi, double xk, int s
   return __dmul_rn((double)s, L);
 }
 
+// The same for |s| <= 1, where s L is exactly 0 or +-L: a select instead of
+// the int -> double conversion and the multiply (both on the FP64 pipe).
+__device__ __forceinline__ double sep1_near(int i, int k, double xi, double xk, int s, double L) {
+  const double sl = s == 0 ? 0.0 : (s > 0 ? L : -L);
+  if (i < k) return __dsub_rn(__dadd_rn(xk, sl), xi);
+  if (i > k) return -__dsub_rn(__dadd_rn(xi, -sl), xk);
+  return sl;
+}
+
 __device__ __forceinline__ double norm2(double x, double y, double z) {
   return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
 }
@@ -87,6 +96,8 @@ __device__ __forceinline__ double norm2(double x, double y, double z) {
 // pairs with a ballot: the list is deterministic and identical to a
 // sequential scan of all candidates.
 constexpr int kCandCap = 128;  // candidates per part (more: reported as overflow)
+
+constexpr int kSure = 1 << 24;  // candidate flag: certainly within rcut
 
 __device__ __forceinline__ int pack_img(int x, int y, int z) {
   return (x + 128) | ((y + 128) << 8) | ((z + 128) << 16);
@@ -137,6 +148,9 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
   const float iLx = 1.f / Lx, iLy = 1.f / Ly, iLz = 1.f / Lz;
   const float rcf = (float)a.rcut + 1e-2f;
   const float rc2f = rcf * rcf;
+  // below rcut - 0.01 A in FP32 the pair is certainly within rcut
+  const float rsf = fmaxf((float)a.rcut - 1e-2f, 0.f);
+  const float rs2f = rsf * rsf;
   auto push = [&](bool c, int j, int pk) {
     const unsigned m = __ballot_sync(kFull, c);
     if (c) {
@@ -178,8 +192,9 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
         const float bx = dx0 + nxf * Lx, by = dy0 + nyf * Ly, bz = dz0 + nzf * Lz;
         if (NEAREST) {
           // box > 2 (rcut + margin) in every direction: only the nearest image
-          const bool c = valid && (bx * bx + by * by + bz * bz < rc2f) && (j != i);
-          push(c, j, c ? pack_img((int)nxf, (int)nyf, (int)nzf) : 0);
+          const float d2 = bx * bx + by * by + bz * bz;
+          const bool c = valid && (d2 < rc2f) && (j != i);
+          push(c, j, c ? pack_img((int)nxf, (int)nyf, (int)nzf) | (d2 < rs2f ? kSure : 0) : 0);
           continue;
         }
         float sxf = -(float)Sx;
@@ -189,7 +204,8 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
             float szf = -(float)Sz;
             for (int sz = -Sz; sz <= Sz; ++sz, szf += 1.f) {
               const float fx = bx + sxf * Lx, fy = by + syf * Ly, fz = bz + szf * Lz;
-              bool c = valid && (fx * fx + fy * fy + fz * fz < rc2f);
+              const float d2 = fx * fx + fy * fy + fz * fz;
+              bool c = valid && (d2 < rc2f);
               int ix = 0, iy = 0, iz = 0;
               if (c) {
                 ix = (int)(nxf + sxf);
@@ -197,7 +213,7 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
                 iz = (int)(nzf + szf);
                 c = !((j == i) && ix == 0 && iy == 0 && iz == 0);
               }
-              push(c, j, c ? pack_img(ix, iy, iz) : 0);
+              push(c, j, c ? pack_img(ix, iy, iz) | (d2 < rs2f ? kSure : 0) : 0);
             }
           }
         }
@@ -222,22 +238,40 @@ __global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a)
     int count = 0;
     for (int e0 = 0; e0 < off[SPLIT]; e0 += 32) {
       const int e = e0 + lane;
-      bool in = false;
+      const bool have = e < off[SPLIT];
       double ex = 0, ey = 0, ez = 0;
-      int j = 0, ix = 0, iy = 0, iz = 0;
-      if (e < off[SPLIT]) {
+      int j = 0, ix = 0, iy = 0, iz = 0, pk = 0;
+      if (have) {
         int p = 0;
         while (e >= off[p + 1]) ++p;
         j = cand_j[warp + p][e - off[p]];
-        const int pk = cand_s[warp + p][e - off[p]];
+        pk = cand_s[warp + p][e - off[p]];
         ix = (pk & 0xff) - 128;
         iy = ((pk >> 8) & 0xff) - 128;
         iz = ((pk >> 16) & 0xff) - 128;
-        ex = sep1(i, j, xi, a.pos[3 * j], ix, Ldx);
-        ey = sep1(i, j, yi, a.pos[3 * j + 1], iy, Ldy);
-        ez = sep1(i, j, zi, a.pos[3 * j + 2], iz, Ldz);
-        in = norm2(ex, ey, ez) < rc2;
       }
+      // FP64 is spent only where needed, decided for the whole warp: the
+      // select shift when every image is within one box, the exact distance
+      // test unless every candidate is certainly inside
+      // (both votes are taken by all 32 lanes, outside any branch)
+      const bool all_near =
+          __all_sync(kFull, !have || (abs(ix) <= 1 && abs(iy) <= 1 && abs(iz) <= 1));
+      const bool sure = have && (pk & kSure);
+      const bool all_sure = __all_sync(kFull, !have || sure);
+      if (have) {
+        const double xj = a.pos[3 * j], yj = a.pos[3 * j + 1], zj = a.pos[3 * j + 2];
+        if (all_near) {
+          ex = sep1_near(i, j, xi, xj, ix, Ldx);
+          ey = sep1_near(i, j, yi, yj, iy, Ldy);
+          ez = sep1_near(i, j, zi, zj, iz, Ldz);
+        } else {
+          ex = sep1(i, j, xi, xj, ix, Ldx);
+          ey = sep1(i, j, yi, yj, iy, Ldy);
+          ez = sep1(i, j, zi, zj, iz, Ldz);
+        }
+      }
+      bool in = sure;
+      if (!all_sure) in = have && (sure || norm2(ex, ey, ez) < rc2);
       const unsigned m = __ballot_sync(kFull, in);
       if (in) {
         const int slot = count + __popc(m & lt);
