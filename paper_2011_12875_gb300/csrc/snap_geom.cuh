@@ -45,14 +45,19 @@ __device__ void slot_geom(const WorkArgs& a, long q) {
     for (int e = 0; e < kGeomStride; ++e) g[e] = v[e];
     return;
   }
+  // r0 = sqrt(r^2 + z0^2) = r / |sin theta0|, so with sr = |sin theta0| / r
+  //   a = z0 / r0 - i z / r0 = sign(sin theta0) cos theta0 - i z sr,
+  //   b = (y - i x) / r0     = y sr - i x sr
+  // (no division, one reciprocal square root; sr multiplies +-x, +-y, +-z, so
+  // the opposite slot still gets exactly conj(a) and -b)
   double st, ct;
   sincospi(a.rfac0 * (r - a.rmin0) * a.inv_span, &st, &ct);
-  const double ist = 1.0 / st;
-  const double z0 = r * ct * ist;
-  const double ir0 = rsqrt(r2 + z0 * z0);
-  const double ar = z0 * ir0, ai = -z * ir0;
-  const double br = y * ir0, bi = -x * ir0;
-  const G gr = G(r), gir = G(ir), gz0 = G(z0), gir0 = G(ir0), gist = G(ist), gct = G(ct);
+  const double sr = fabs(st) * ir;
+  const double ar = st < 0.0 ? -ct : ct, ai = -z * sr;
+  const double br = y * sr, bi = -x * sr;
+  // z0 = r cot theta0 and 1/r0 for the gradients, in the working precision
+  const G gr = G(r), gir = G(ir), gct = G(ct), gst = G(st);
+  const G gist = G(1) / gst, gz0 = gr * gct * gist, gir0 = G(sr);
   const G gar = G(ar), gai = G(ai), gbr = G(br), gbi = G(bi);
   const G c = G(a.rfac0 * M_PI * a.inv_span);  // d theta0 / d r
   const G dz0dr = gct * gist - gr * c * gist * gist;
