@@ -761,196 +761,200 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
 }
 
 // --------------------------------------------- energy, forces and virial
-// CTA = kFAtoms consecutive atoms, kFThreads threads.  FP64 runs at 1/64 of
-// the FP32 rate on this part, so the FP64 work is laid out dense:
+// CTA = kFAtoms consecutive atoms, kFThreads threads (a warp per two atoms).
+// FP64 runs at 1/64 of the FP32 rate on this part and a warp FP64
+// instruction costs the same whatever its active lanes, so the FP64 sums are
+// short trees on full warps instead of long chains on a few threads:
 //  * energy: E_i - beta_0 is a cubic form in U, so by Euler's relation
 //    E_i = beta_0 + (1/3) Re sum_t Y_t : conj(U_t) (full matrices; half layout
-//    with half_weight); kFSlices threads per atom take every kFSlices-th
-//    element in the working precision and their partials are added in FP64,
-//    in order;
-//  * forces: one thread per (atom, slot) forms
-//    g = dE_i/dr_ik - dE_k/dr_ki (the second term through the reverse-slot
-//    map, no atomics) and the virial products -dE_i/dr_ik,a r_ik,b; then one
-//    thread per (atom, component) adds its atom's g in slot order, so
-//    F_i = sum_k g in a fixed order;
-//  * virial: W_ab = -sum dE_i/dr_ik,a r_ik,b is reduced per CTA and the last
+//    with half_weight).  kFSlices slices per atom take every kFSlices-th
+//    element in the working precision (lanes over atoms: the U and Y reads
+//    are coalesced); the slices are added in FP64 by a fixed tree;
+//  * forces: lane l of an atom's kFLanes takes slots l, l + kFLanes, ...: it
+//    forms g = dE_i/dr_ik - dE_k/dr_ki (the second term through the
+//    reverse-slot map, no atomics), adds its g in slot order and accumulates
+//    the virial products -dE_i/dr_ik,a r_ik,b; the lane sums are then added
+//    by a fixed butterfly;
+//  * virial: W_ab is reduced per CTA by the same kind of tree and the last
 //    CTA to finish adds the CTA partials in a fixed order (batch mode: per
-//    atom, in slot order, reduced per configuration afterwards).
+//    atom, reduced per configuration afterwards).
+// Every sum has an order fixed by the slot and element indices alone, so the
+// per-atom results do not depend on launch shape or batching.
 constexpr int kFAtoms = 8;
 constexpr int kFThreads = 128;
-constexpr int kFSlices = kFThreads / kFAtoms;  // energy partials per atom
+constexpr int kFWarps = kFThreads / 32;
+constexpr int kFSlices = kFThreads / kFAtoms;  // energy slices per atom
+constexpr int kFLanes = 16;                    // lanes per atom in the force sums
+static_assert(kFWarps * 32 / kFLanes == kFAtoms, "a warp per two atoms");
 
-inline size_t force_smem(int K, bool vatom) {
-  return sizeof(double) * (size_t)kFAtoms * K * (vatom ? 9 : 3);
+// Sum of x[0..N) over each aligned group of G lanes (N <= G, both powers of
+// two).  A level with mask m first halves the components a lane carries (the
+// lane with bit m clear keeps the lower half and receives its partner's
+// lower half), so N components take N - 1 + log2(G / N) additions instead of
+// N log2(G).  Returns the total of component (lane mod G) / (G / N).
+template <int N, int G>
+__device__ __forceinline__ double tree_sum(double (&x)[N], int lane) {
+  static_assert(N >= 1 && N <= G && G <= 32 && (N & (N - 1)) == 0 && (G & (G - 1)) == 0, "");
+  int n = N;
+#pragma unroll
+  for (int m = G / 2; m >= 1; m >>= 1) {
+    if (n > 1) {
+      const bool up = lane & m;
+      const int h = n / 2;
+#pragma unroll
+      for (int j = 0; j < N / 2; ++j) {
+        if (j < h) {
+          const double send = up ? x[j] : x[j + h];
+          const double keep = up ? x[j + h] : x[j];
+          x[j] = keep + __shfl_xor_sync(kFull, send, m);
+        }
+      }
+      n = h;
+    } else {
+      x[0] += __shfl_xor_sync(kFull, x[0], m);
+    }
+  }
+  return x[0];
 }
+
+inline size_t force_smem(int, bool) { return 0; }
 
 template <typename R>
 __global__ void __launch_bounds__(kFThreads) force_kernel(WorkArgs a) {
-  extern __shared__ __align__(16) double fsm[];  // g [kFAtoms*K][3], batch: + v [kFAtoms*K][6]
-  __shared__ int off[kFAtoms + 1];
-  __shared__ double ep[kFSlices][kFAtoms];
+  __shared__ double ew[kFWarps][kFAtoms];  // energy: per warp, per atom
+  __shared__ double wv[kFWarps][8];        // virial: per warp, per component
   __shared__ bool last;
   const int K = a.K, H = a.H;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const long i0 = (long)blockIdx.x * kFAtoms;
   const int na = (int)min((long)kFAtoms, a.n - i0);
-  double* gs = fsm;
-  double* vsm = fsm + (size_t)kFAtoms * K * 3;
-  if (tid < 32) {  // slot offsets: inclusive scan of the clamped counts
-    int c = tid < na ? min(a.cnt[i0 + tid], K) : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(kFull, c, o);
-      if (tid >= o) c += t;
-    }
-    if (tid < kFAtoms) off[tid + 1] = c;
-    if (tid == 0) off[0] = 0;
-  }
-  // energy partials (lanes over atoms, so the U and Y reads are coalesced)
-  if (a.energy) {
-    const int ai = tid % kFAtoms, sl = tid / kFAtoms;
-    R e = R(0);
-    if (ai < na) {
-      const long i = i0 + ai;
-      const long blk = i >> 5;
-      const int li = (int)(i & 31);
-      const cx<R>* Ug = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32 + li;
-      const cx<R>* Yg = reinterpret_cast<const cx<R>*>(a.Y) + blk * H * 32 + li;
-#pragma unroll 4
-      for (int el = sl; el < H; el += kFSlices) {
-        const int p = __ldg(a.half_tmm + el);
-        const R w = (R)half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
-        const cx<R> u = Ug[el * 32], y = Yg[el * 32];
-        e += w * (y.re * u.re + y.im * u.im);
-      }
-    }
-    ep[sl][ai] = (double)e;
-  }
-  __syncthreads();
-  const int total = off[na];
-  double v[6] = {0, 0, 0, 0, 0, 0};
-  for (int p0 = tid; p0 < total; p0 += 2 * kFThreads) {
-    // two slots per pass: all first-level loads before the reverse-slot ones
-    long q[2];
-    bool ok[2];
-    int rv_[2], kn[2];
-    double d[2][3], r[2][3], dk[2][3];
+  // forces: lanes 16h .. 16h + 15 of warp w take atom 2w + h.  The first
+  // pass's slot loads go out before the count and the energy loads (every
+  // slot below K is in bounds; those at or past the count are discarded).
+  const int l = lane % kFLanes;
+  const int ai = 2 * w + lane / kFLanes;
+  const bool have = ai < na;
+  const long i = i0 + ai;
+  bool ok[2];
+  int rv[2], kn[2];
+  double d[2][3], r[2][3], dk[2][3];
+  auto load_slots = [&](int s0) {
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const int p = p0 + u * kFThreads;
-      ok[u] = p < total;
-      int lo = 0, hi = na - 1;  // atom of flat slot p: last k with off[k] <= p
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= p) lo = mid;
-        else hi = mid - 1;
-      }
-      q[u] = (i0 + lo) * K + (ok[u] ? p - off[lo] : 0);
-      rv_[u] = -1;
+      const int s = s0 + u * kFLanes + l;
+      rv[u] = -1;
       kn[u] = 0;
+#pragma unroll
       for (int c = 0; c < 3; ++c) d[u][c] = r[u][c] = dk[u][c] = 0.0;
-      if (ok[u]) {
-        rv_[u] = a.rev[q[u]];
-        kn[u] = a.nbr[q[u]];
+      if (have && s < K) {
+        const long q = i * K + s;
+        rv[u] = a.rev[q];
+        kn[u] = a.nbr[q];
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
-          d[u][c] = a.dedr[q[u] * 3 + c];
-          r[u][c] = a.rij[q[u] * 3 + c];
+          d[u][c] = a.dedr[q * 3 + c];
+          r[u][c] = a.rij[q * 3 + c];
         }
       }
     }
+  };
+  const int cnt_raw = have ? a.cnt[i] : 0;
+  load_slots(0);
+  // energy partials: lane = atom (8) x slice (4) of the warp's 4 slices
+  if (a.energy) {
+    const int ae = lane % kFAtoms, sl = (kFSlices / kFWarps) * w + lane / kFAtoms;
+    R e = R(0);
+    if (ae < na) {
+      const long ie = i0 + ae;
+      const long blk = ie >> 5;
+      const int li = (int)(ie & 31);
+      const cx<R>* Ug = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32 + li;
+      const cx<R>* Yg = reinterpret_cast<const cx<R>*>(a.Y) + blk * H * 32 + li;
+#pragma unroll 8
+      for (int el = sl; el < H; el += kFSlices) {
+        const int p = __ldg(a.half_tmm + el);
+        const R w8 = (R)half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
+        const cx<R> u = Ug[el * 32], y = Yg[el * 32];
+        e += w8 * (y.re * u.re + y.im * u.im);
+      }
+    }
+    double de = (double)e;
+    de += __shfl_xor_sync(kFull, de, 8);
+    de += __shfl_xor_sync(kFull, de, 16);
+    if (lane < kFAtoms) ew[w][lane] = de;
+  }
+  const int cnt = min(cnt_raw, K);
+  double f[4] = {0.0, 0.0, 0.0, 0.0};
+  double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int s0 = 0; s0 < cnt; s0 += 2 * kFLanes) {
+    // two slots per pass: the reverse-slot loads after the first-level ones
+    if (s0 > 0) load_slots(s0);
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
-      if (ok[u] && rv_[u] >= 0)
-        for (int c = 0; c < 3; ++c) dk[u][c] = a.dedr[((long)kn[u] * K + rv_[u]) * 3 + c];
+    for (int u = 0; u < 2; ++u) {
+      ok[u] = s0 + u * kFLanes + l < cnt;
+      if (ok[u] && rv[u] >= 0)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dk[u][c] = a.dedr[((long)kn[u] * K + rv[u]) * 3 + c];
+    }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (!ok[u]) continue;
-      const int p = p0 + u * kFThreads;
-      for (int c = 0; c < 3; ++c) gs[3 * p + c] = d[u][c] - dk[u][c];
-      const double vp[6] = {-d[u][0] * r[u][0], -d[u][1] * r[u][1], -d[u][2] * r[u][2],
-                            -d[u][0] * r[u][1], -d[u][0] * r[u][2], -d[u][1] * r[u][2]};
-      if (a.vatom) {
-        for (int c = 0; c < 6; ++c) vsm[6 * p + c] = vp[c];
-      } else {
-        for (int c = 0; c < 6; ++c) v[c] += vp[c];
-      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) f[c] += d[u][c] - dk[u][c];
+      v[0] = fma(-d[u][0], r[u][0], v[0]);
+      v[1] = fma(-d[u][1], r[u][1], v[1]);
+      v[2] = fma(-d[u][2], r[u][2], v[2]);
+      v[3] = fma(-d[u][0], r[u][1], v[3]);
+      v[4] = fma(-d[u][0], r[u][2], v[4]);
+      v[5] = fma(-d[u][1], r[u][2], v[5]);
     }
   }
-  __syncthreads();
-  if (tid < 3 * na) {
-    const int ai = tid / 3, c = tid - 3 * ai;
-    double f = 0.0;
-    for (int p = off[ai]; p < off[ai + 1]; ++p) f += gs[3 * p + c];
-    a.forces[3 * (i0 + ai) + c] = f;
-  }
-  if (a.energy && tid < na) {
-    double e = 0.0;
-    for (int sl = 0; sl < kFSlices; ++sl) e += ep[sl][tid];
-    a.energy[i0 + tid] = a.beta0 + e / 3.0;
-  }
+  const double fsum = tree_sum<4, kFLanes>(f, lane);  // component l / 4
+  if (have && l % 4 == 0 && l / 4 < 3) a.forces[3 * i + l / 4] = fsum;
   if (a.vatom) {  // batch mode: per-atom virial, reduced per configuration later
-    for (int t = tid; t < 6 * na; t += kFThreads) {
-      const int ai = t / 6, c = t - 6 * ai;
-      double w = 0.0;
-      for (int p = off[ai]; p < off[ai + 1]; ++p) w += vsm[6 * p + c];
-      a.vatom[6 * (i0 + ai) + c] = w;
-    }
-    return;
-  }
-  if (!a.virial) return;
-  // CTA partial of the virial: the threads' sums through shared memory,
-  // 16 strided FP64 chains per component, then those 16 in order
-  __shared__ double vt[6][kFThreads];
-  __shared__ double v16[6][16];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) vt[c][tid] = v[c];
-  __syncthreads();
-  if (tid < 96) {
-    const int c = tid >> 4, sub = tid & 15;
-    double t = 0.0;
-#pragma unroll
-    for (int k = sub; k < kFThreads; k += 16) t += vt[c][k];
-    v16[c][sub] = t;
+    const double vs = tree_sum<8, kFLanes>(v, lane);  // component l / 2
+    if (have && l % 2 == 0 && l / 2 < 6) a.vatom[6 * i + l / 2] = vs;
+  } else if (a.virial) {
+    const double vs = tree_sum<8, 32>(v, lane);  // component lane / 4
+    if (lane % 4 == 0) wv[w][lane / 4] = vs;
   }
   __syncthreads();
+  if (a.energy && tid < na) {
+    const double e = (ew[0][tid] + ew[1][tid]) + (ew[2][tid] + ew[3][tid]);
+    a.energy[i0 + tid] = a.beta0 + e * (1.0 / 3.0);
+  }
+  if (a.vatom || !a.virial) return;
   const int cta = blockIdx.x, ncta = gridDim.x;
   if (tid < 6) {
-    double t = 0.0;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) t += v16[tid][k];
-    a.vpart[6 * cta + tid] = t;
+    a.vpart[6 * cta + tid] = (wv[0][tid] + wv[1][tid]) + (wv[2][tid] + wv[3][tid]);
     __threadfence();
   }
   __syncthreads();
   if (tid == 0) last = (atomicAdd(&a.flags[4], 1) == ncta - 1);
   __syncthreads();
   if (!last) return;
-  // last CTA: 16 strided chains per component over the CTA partials (loads
-  // issued 8 at a time), then the 16 in order: a fixed order, so the virial
-  // is deterministic
+  // last CTA: thread t adds the CTA partials t, t + kFThreads, ... in order
+  // (loads issued four at a time), then the same trees: a fixed order, so
+  // the virial is deterministic
   __threadfence();
-  if (tid < 96) {
-    const int c = tid >> 4, sub = tid & 15;
-    double t = 0.0;
-    for (int b0 = sub; b0 < ncta; b0 += 16 * 8) {
-      double x[8];
+  double x[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b0 = tid; b0 < ncta; b0 += 4 * kFThreads) {
+    double y[4][6];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int b = b0 + 16 * k;
-        x[k] = b < ncta ? __ldcg(a.vpart + 6 * b + c) : 0.0;
-      }
+    for (int k = 0; k < 4; ++k) {
+      const int b = b0 + k * kFThreads;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) t += x[k];
+      for (int c = 0; c < 6; ++c) y[k][c] = b < ncta ? __ldcg(a.vpart + 6 * b + c) : 0.0;
     }
-    v16[c][sub] = t;
-  }
-  __syncthreads();
-  if (tid < 6) {
-    double t = 0.0;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) t += v16[tid][k];
-    a.virial[tid] = t;
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) x[c] += y[k][c];
   }
+  const double xs = tree_sum<8, 32>(x, lane);
+  if (lane % 4 == 0) wv[w][lane / 4] = xs;
+  __syncthreads();
+  if (tid < 6) a.virial[tid] = (wv[0][tid] + wv[1][tid]) + (wv[2][tid] + wv[3][tid]);
 }
 
 constexpr int kUiWarps = 4;
