@@ -13,6 +13,7 @@
 #include <array>
 #include <cmath>
 #include <map>
+#include <unordered_map>
 
 namespace snap {
 
@@ -156,11 +157,13 @@ void HostTables::build(int J2, bool size_runs) {
   };
   // triples grouped by output rank
   std::vector<std::vector<int>> by_t(J2 + 1);
+  std::unordered_map<unsigned long long, size_t> same_layer;  // (triple, word) -> term
   for (int q = 0; q < (int)ztrip.size(); ++q) by_t[ztrip[q].t].push_back(q);
   for (int t = 0; t <= J2; ++t)
     for (int mb = 0; 2 * mb <= t; ++mb)
       for (int ma = 0; ma <= t; ++ma) {
         const size_t first = terms.size();
+        same_layer.clear();
         for (int q : by_t[t]) {
           const ZTrip& z = ztrip[q];
           const int dl = (z.t1 + z.t2 - t) / 2;
@@ -176,12 +179,42 @@ void HostTables::build(int J2, bool size_runs) {
               double s1, s2;
               half_elem(z.t1, ma1, mb1, i1, c1, s1);
               half_elem(z.t2, ma2, mb2, i2, c2, s2);
-              terms.push_back((unsigned)i1 | ((unsigned)i2 << 10) | ((unsigned)c1 << 20) |
-                              ((unsigned)c2 << 21));
-              term_cg.push_back(ca * cb * s1 * s2);
+              // t1 == t2: the term with the factors swapped, (ma2, mb2) as
+              // the first, has the same coefficient and the same product, so
+              // the two are kept as one term, the stored element with the
+              // lower (index, conjugation) first, with the summed coefficient
+              if (z.t1 == z.t2 && (i2 < i1 || (i2 == i1 && c2 < c1))) {
+                std::swap(i1, i2);
+                std::swap(c1, c2);
+              }
+              const unsigned w = (unsigned)i1 | ((unsigned)i2 << 10) | ((unsigned)c1 << 20) |
+                                 ((unsigned)c2 << 21);
+              const double cgp = ca * cb * s1 * s2;
+              if (z.t1 == z.t2) {
+                const auto ins = same_layer.emplace(((unsigned long long)q << 32) | w, terms.size());
+                if (!ins.second) {
+                  term_cg[ins.first->second] += cgp;
+                  continue;
+                }
+              }
+              terms.push_back(w);
+              term_cg.push_back(cgp);
               term_trip.push_back(q);
             }
           }
+        }
+        {  // drop merged terms whose coefficients cancelled exactly
+          size_t o = first;
+          for (size_t k = first; k < terms.size(); ++k)
+            if (term_cg[k] != 0.0) {
+              terms[o] = terms[k];
+              term_cg[o] = term_cg[k];
+              term_trip[o] = term_trip[k];
+              ++o;
+            }
+          terms.resize(o);
+          term_cg.resize(o);
+          term_trip.resize(o);
         }
         // Group the output's terms by their first factor (index and
         // conjugation flag, stable): compute_Y then forms

@@ -50,12 +50,22 @@ def de_pair(twojmax: int) -> int:
     return f + 30
 
 
+def _half_elem(t: int, xa: int, xb: int):
+    """Stored (index, conjugated) of U_t[xa][xb] in the half layout."""
+    base = sum((tt // 2 + 1) * (tt + 1) for tt in range(t))
+    if 2 * xb <= t:
+        return (base + xb * (t + 1) + xa, 0)
+    return (base + (t - xb) * (t + 1) + (t - xa), 1)
+
+
 @lru_cache(maxsize=None)
 def yi_atom(twojmax: int) -> int:
     """compute_Y, one atom.  For each half element (t, ma, mb) of Y, the terms
     beta~ C(ma1,ma2) C(mb1,mb2) U_t1[ma1][mb1] U_t2[ma2][mb2] of every triple
     (t1 >= t2) with output rank t, grouped by their first factor
-    U_t1[ma1][mb1]: Y += U_t1[ma1][mb1] * sum_k coef_k U_t2,k.  Per term a
+    U_t1[ma1][mb1]: Y += U_t1[ma1][mb1] * sum_k coef_k U_t2,k.  When t1 == t2
+    the term with the factors swapped has the same coefficient, so the pair
+    is one term (the stored element with the lower index first).  Per term a
     real-by-complex scale-accumulate (4), per group a complex
     multiply-accumulate (8).  Terms and groups are counted structurally (a
     Clebsch-Gordan product that happens to vanish is still counted)."""
@@ -63,7 +73,7 @@ def yi_atom(twojmax: int) -> int:
     for t in range(twojmax + 1):
         for ma, mb in half_layer(t):
             groups = set()
-            nterm = 0
+            pairs = set()
             for t1 in range(twojmax + 1):
                 for t2 in range(t1 + 1):
                     if not (t1 - t2 <= t <= min(twojmax, t1 + t2)) or (t1 + t2 - t) % 2:
@@ -71,9 +81,13 @@ def yi_atom(twojmax: int) -> int:
                     dl = (t1 + t2 - t) // 2
                     for mb1 in range(max(0, mb + dl - t2), min(t1, mb + dl) + 1):
                         for ma1 in range(max(0, ma + dl - t2), min(t1, ma + dl) + 1):
-                            nterm += 1
-                            groups.add((t1, ma1, mb1))
-            f += 4 * nterm + 8 * len(groups)
+                            x1 = _half_elem(t1, ma1, mb1)
+                            x2 = _half_elem(t2, ma + dl - ma1, mb + dl - mb1)
+                            if t1 == t2 and x2 < x1:
+                                x1, x2 = x2, x1
+                            pairs.add((t1, t2, x1, x2))
+                            groups.add(x1)
+            f += 4 * len(pairs) + 8 * len(groups)
     return f
 
 
