@@ -238,7 +238,9 @@ int snap_compute_host(snap_ctx* ctx, int natoms, const double* pos_host,
  * Half layout: for t = 2j = 0..twojmax, the columns mb = 0..floor(t/2) of
  * the (t+1)x(t+1) matrix, each column ma = 0..t; element (t, ma, mb) at
  * snap_half_index(twojmax, t, ma, mb).  The other columns follow from
- * M[t-ma][t-mb] = (-1)^(ma+mb) conj(M[ma][mb]). */
+ * M[t-ma][t-mb] = (-1)^(ma+mb) conj(M[ma][mb]).  On the device, Y below the
+ * centre of the middle column (2 mb = t, ma > mb) is left at zero (no
+ * contraction reads it); SNAP_BUF_YLIST fills it in from that symmetry. */
 enum snap_buffer {
   SNAP_BUF_NBR_CNT = 0,
   SNAP_BUF_NBR_IDX = 1,

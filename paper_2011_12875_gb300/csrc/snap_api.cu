@@ -1185,6 +1185,23 @@ long long snap_get_buffer(snap_ctx* c, int which, void* dst, size_t bytes) {
           out[2 * (i * H + e)] = hv[2 * q];
           out[2 * (i * H + e) + 1] = hv[2 * q + 1];
         }
+      if (which == SNAP_BUF_YLIST) {
+        // compute_Y leaves the middle column below its centre (2 mb = t,
+        // ma > mb) at zero: no contraction reads it.  Fill it from the
+        // inversion symmetry Y[ma][mb] = (-1)^(ma+mb) conj(Y[t-ma][t-mb]).
+        for (int t = 0; t <= c->tab.twojmax; t += 2) {
+          const int mb = t / 2;
+          for (int ma = mb + 1; ma <= t; ++ma) {
+            const long e = snap_half_index(c->tab.twojmax, t, ma, mb);
+            const long m = snap_half_index(c->tab.twojmax, t, t - ma, mb);
+            const double sg = ((ma + mb) & 1) ? -1.0 : 1.0;
+            for (long i = 0; i < n; ++i) {
+              out[2 * (i * H + e)] = sg * out[2 * (i * H + m)];
+              out[2 * (i * H + e) + 1] = -sg * out[2 * (i * H + m) + 1];
+            }
+          }
+        }
+      }
       std::memcpy(dst, out.data(), std::min(size, bytes));
       return (long long)size;
     }

@@ -79,6 +79,66 @@ int count_coeff(int twojmax) {
   return n;
 }
 
+namespace {
+
+// Factor order of the terms [first, end) of one output.  A term's product is
+// symmetric in its two factors, and compute_Y groups the terms of an output
+// by their first factor (Y += U[e1] * sum_k c_k U[e2,k]), so fewer distinct
+// first factors mean fewer groups.  Choosing them is a vertex cover of the
+// graph whose vertices are the stored elements (index, conjugation) and
+// whose edges are the terms; the greedy cover takes, again and again, the
+// element with the most terms not yet covered (ties: the larger element) and
+// makes it the first factor of those terms.
+void orient_by_cover(std::vector<unsigned>& terms, size_t first) {
+  const size_t n = terms.size() - first;
+  if (n < 2) return;
+  auto e1 = [](unsigned w) { return (w & 1023u) << 1 | ((w >> 20) & 1u); };
+  auto e2 = [](unsigned w) { return ((w >> 10) & 1023u) << 1 | ((w >> 21) & 1u); };
+  std::unordered_map<unsigned, std::vector<size_t>> inc;  // element -> its terms
+  for (size_t k = first; k < terms.size(); ++k) {
+    const unsigned a = e1(terms[k]), b = e2(terms[k]);
+    inc[a].push_back(k);
+    if (b != a) inc[b].push_back(k);
+  }
+  std::unordered_map<unsigned, int> deg;
+  std::vector<std::pair<int, unsigned>> heap;  // (uncovered terms, element)
+  for (const auto& kv : inc) {
+    deg[kv.first] = (int)kv.second.size();
+    heap.push_back({(int)kv.second.size(), kv.first});
+  }
+  std::make_heap(heap.begin(), heap.end());
+  std::vector<char> covered(n, 0);
+  while (!heap.empty()) {
+    std::pop_heap(heap.begin(), heap.end());
+    const auto top = heap.back();
+    heap.pop_back();
+    const unsigned v = top.second;
+    if (top.first != deg[v]) {  // stale entry: push the current count back
+      if (deg[v] > 0) {
+        heap.push_back({deg[v], v});
+        std::push_heap(heap.begin(), heap.end());
+      }
+      continue;
+    }
+    if (top.first == 0) break;
+    for (size_t k : inc[v]) {
+      if (covered[k - first]) continue;
+      covered[k - first] = 1;
+      unsigned& w = terms[k];
+      const unsigned a = e1(w), b = e2(w);
+      if (a != v) {  // v is the second factor: swap the two factors
+        w = ((w >> 10) & 1023u) | ((w & 1023u) << 10) | (((w >> 21) & 1u) << 20) |
+            (((w >> 20) & 1u) << 21) | (w & ~((1u << 22) - 1));
+      }
+      const unsigned o = (a == v) ? b : a;
+      if (o != v) --deg[o];
+    }
+    deg[v] = 0;
+  }
+}
+
+}  // namespace
+
 void HostTables::build(int J2, bool size_runs) {
   twojmax = J2;
   H = half_size(J2);
@@ -164,7 +224,13 @@ void HostTables::build(int J2, bool size_runs) {
       for (int ma = 0; ma <= t; ++ma) {
         const size_t first = terms.size();
         same_layer.clear();
+        // Below the centre of the middle column (2 mb = t, ma > mb) Y is the
+        // mirror of the element above it, and the contractions that read Y
+        // (energy, dE/dr) give it weight 0: one zero term there (Y = 0), and
+        // the host export fills in the mirror.
+        const bool mirrored = 2 * mb == t && ma > mb;
         for (int q : by_t[t]) {
+          if (mirrored) break;
           const ZTrip& z = ztrip[q];
           const int dl = (z.t1 + z.t2 - t) / 2;
           for (int mb1 = std::max(0, mb + dl - z.t2); mb1 <= std::min(z.t1, mb + dl); ++mb1) {
@@ -216,6 +282,12 @@ void HostTables::build(int J2, bool size_runs) {
           term_cg.resize(o);
           term_trip.resize(o);
         }
+        if (mirrored) {
+          terms.push_back(0u);
+          term_cg.push_back(0.0);
+          term_trip.push_back(by_t[t].front());
+        }
+        orient_by_cover(terms, first);
         // Group the output's terms by their first factor (index and
         // conjugation flag, stable): compute_Y then forms
         //   Y += U_t1[..] * sum_k coef_k U_t2,k[..]
@@ -224,8 +296,8 @@ void HostTables::build(int J2, bool size_runs) {
         // output is a run of 1-term groups, then of 2-term groups, ...;
         // term_runs counts them.  Without it the groups keep the order of
         // their first factor.  Bit 23 ends a group, bit 22 the output; every output has at
-        // least the term of the (t, 0, t) triple, whose Clebsch-Gordan
-        // product is 1.
+        // least one term: the term of the (t, 0, t) triple, whose
+        // Clebsch-Gordan product is 1, or the zero term of a mirrored output.
         const size_t cnt = terms.size() - first;
         std::array<unsigned short, kYGroupMax> runs{};
         if (cnt > 0) {

@@ -8,6 +8,7 @@ of the benchmark; the derivation is written out in the design notes.
 """
 from __future__ import annotations
 
+import heapq
 from functools import lru_cache
 
 
@@ -50,29 +51,68 @@ def de_pair(twojmax: int) -> int:
     return f + 30
 
 
-def _half_elem(t: int, xa: int, xb: int):
-    """Stored (index, conjugated) of U_t[xa][xb] in the half layout."""
+def _half_elem(t: int, xa: int, xb: int) -> int:
+    """Stored element of U_t[xa][xb] in the half layout, as 2 index + conj."""
     base = sum((tt // 2 + 1) * (tt + 1) for tt in range(t))
     if 2 * xb <= t:
-        return (base + xb * (t + 1) + xa, 0)
-    return (base + (t - xb) * (t + 1) + (t - xa), 1)
+        return 2 * (base + xb * (t + 1) + xa)
+    return 2 * (base + (t - xb) * (t + 1) + (t - xa)) + 1
+
+
+def _cover_size(edges) -> int:
+    """Groups of one output: the greedy vertex cover of its terms (edges
+    between stored elements) that takes the element with the most uncovered
+    terms first (ties: the larger element), as the library's tables do."""
+    inc = {}
+    for k, (a, b) in enumerate(edges):
+        inc.setdefault(a, []).append(k)
+        if b != a:
+            inc.setdefault(b, []).append(k)
+    deg = {v: len(ks) for v, ks in inc.items()}
+    heap = [(-d, -v) for v, d in deg.items()]
+    heapq.heapify(heap)
+    covered = [False] * len(edges)
+    groups = 0
+    while heap:
+        d, v = heapq.heappop(heap)
+        d, v = -d, -v
+        if d != deg[v]:
+            if deg[v] > 0:
+                heapq.heappush(heap, (-deg[v], -v))
+            continue
+        if d == 0:
+            break
+        groups += 1
+        for k in inc[v]:
+            if covered[k]:
+                continue
+            covered[k] = True
+            a, b = edges[k]
+            o = b if a == v else a
+            if o != v:
+                deg[o] -= 1
+        deg[v] = 0
+    return groups
 
 
 @lru_cache(maxsize=None)
 def yi_atom(twojmax: int) -> int:
     """compute_Y, one atom.  For each half element (t, ma, mb) of Y, the terms
     beta~ C(ma1,ma2) C(mb1,mb2) U_t1[ma1][mb1] U_t2[ma2][mb2] of every triple
-    (t1 >= t2) with output rank t, grouped by their first factor
-    U_t1[ma1][mb1]: Y += U_t1[ma1][mb1] * sum_k coef_k U_t2,k.  When t1 == t2
-    the term with the factors swapped has the same coefficient, so the pair
-    is one term (the stored element with the lower index first).  Per term a
-    real-by-complex scale-accumulate (4), per group a complex
-    multiply-accumulate (8).  Terms and groups are counted structurally (a
-    Clebsch-Gordan product that happens to vanish is still counted)."""
+    (t1 >= t2) with output rank t.  When t1 == t2 the term with the factors
+    swapped has the same coefficient, so the pair is one term.  Outputs below
+    the centre of the middle column (2 mb = t, ma > mb) are mirrors that no
+    contraction reads, and are not computed.  The terms of an output are
+    grouped by a shared factor, Y += U[e] * sum_k coef_k U[e_k], the factors
+    chosen by a greedy vertex cover.  Per term a real-by-complex
+    scale-accumulate (4), per group a complex multiply-accumulate (8).  Terms
+    are counted structurally (a Clebsch-Gordan product that happens to vanish
+    is still counted)."""
     f = 0
     for t in range(twojmax + 1):
         for ma, mb in half_layer(t):
-            groups = set()
+            if 2 * mb == t and ma > mb:
+                continue
             pairs = set()
             for t1 in range(twojmax + 1):
                 for t2 in range(t1 + 1):
@@ -83,11 +123,8 @@ def yi_atom(twojmax: int) -> int:
                         for ma1 in range(max(0, ma + dl - t2), min(t1, ma + dl) + 1):
                             x1 = _half_elem(t1, ma1, mb1)
                             x2 = _half_elem(t2, ma + dl - ma1, mb + dl - mb1)
-                            if t1 == t2 and x2 < x1:
-                                x1, x2 = x2, x1
-                            pairs.add((t1, t2, x1, x2))
-                            groups.add(x1)
-            f += 4 * len(pairs) + 8 * len(groups)
+                            pairs.add((min(x1, x2), max(x1, x2)) if t1 == t2 else (x1, x2))
+            f += 4 * len(pairs) + 8 * _cover_size(sorted(pairs))
     return f
 
 
