@@ -203,7 +203,7 @@ int upload_yrec(snap_ctx* c) {
     return (e2 << 8) | (e1 << 18) | (((w >> 23) & 1u) << 28) | (((w >> 22) & 1u) << 29) |
            (c1 << 30) | (c2 << 31);
   };
-  // kYRecPad zero records past the end: compute_Y prefetches that far ahead
+  // kYRecPad zero records past the end: compute_Y reads up to that far ahead
   if (c->precision == SNAP_MIXED) {
     std::vector<snap::YRec<float>> r(n + snap::kYRecPad);
     for (size_t k = 0; k < n; ++k) {

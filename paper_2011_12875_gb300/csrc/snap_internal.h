@@ -19,7 +19,8 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
 
 constexpr int kMaxTwoJ = 14;
 constexpr int kYGroupMax = 8;  // longest compute_Y term group (longer ones are cut)
-constexpr int kYRecPad = 64;   // zero records after the compute_Y term list (prefetch distance)
+constexpr int kYRecPad = 256;  // zero records after the compute_Y term list (read-ahead)
+constexpr int kYRecPrefetch = 64;  // compute_Y's L1 prefetch distance without the record ring
 constexpr int kMaxNeighCap = 64;
 constexpr int kRootDim = 16;     // rootpq table is kRootDim x kRootDim
 constexpr int kGeomStride = 20;  // doubles per neighbour slot, see PairGeom

@@ -234,26 +234,109 @@ __device__ __forceinline__ unsigned y_off1(unsigned w) {
   return ((w >> 10) & 0x3FF00u) << (sizeof(R) == 4 ? 0 : 1);
 }
 
+// Term records of compute_Y read straight from global memory (pulled into
+// L1 ahead of use: the stream is read once per CTA).
+template <typename R>
+struct YRecGlobal {
+  static constexpr bool kShared = false;
+  const YRec<R>* __restrict__ rec;
+  __device__ __forceinline__ void at(int q) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(rec + q + kYRecPrefetch));
+  }
+  __device__ __forceinline__ const YRec<R>* ptr(int q) const { return rec + q; }
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Term records of compute_Y streamed through a per-warp ring in shared
+// memory: chunks of kYChunk records copied by cp.async (16 bytes a lane),
+// kYRingChunks of them resident or in flight, and the first kYGroupMax
+// records of the chunk in slot 0 mirrored past the ring's end, so that a
+// step of up to kYGroupMax records never wraps.  While the warp's steps
+// start in chunk c, chunks c and c + 1 are complete (a step may run into
+// c + 1) and c + 2, c + 3 are in flight.  A record is then a broadcast
+// shared-memory load instead of a global load through the L1 tags.
+constexpr int kYChunk = 32;
+constexpr int kYRingChunks = 4;
+constexpr int kYRingLen = kYChunk * kYRingChunks + kYGroupMax;
+static_assert(kYChunk % 2 == 0 && kYGroupMax % 2 == 0 && kYGroupMax <= kYChunk, "16-byte copies");
+static_assert(kYChunk * kYRingChunks <= kYRecPad, "ring reads stay in the padding");
+
+// Byte offset of the record rings in compute_Y's dynamic shared memory:
+// after the staged plane(s) of complex float and the 16-byte barrier slot.
+__host__ __device__ constexpr size_t yi_ring_offset(int H, bool cp) {
+  return (size_t)(cp ? 2 : 1) * H * 32 * sizeof(cx<float>) + 16;
+}
+
+struct YRecRing {
+  static constexpr bool kShared = true;
+  YRec<float>* buf;         // [kYRingLen] of this warp
+  const YRec<float>* base;  // global record qs (qs even: 16-byte aligned)
+  int qs, cross, lane;
+  __device__ __forceinline__ void issue(int c) {  // chunk c into slot c % kYRingChunks
+    const int slot = (c % kYRingChunks) * kYChunk;
+    const YRec<float>* g = base + c * kYChunk;
+    if (lane < kYChunk / 2) {
+      cp_async16(buf + slot + 2 * lane, g + 2 * lane);
+    } else if (slot == 0 && lane < (kYChunk + kYGroupMax) / 2) {
+      const int m = lane - kYChunk / 2;
+      cp_async16(buf + kYChunk * kYRingChunks + 2 * m, g + 2 * m);
+    }
+    cp_async_commit();
+  }
+  __device__ __forceinline__ void init(const YRec<float>* rec, int q0, int ln, YRec<float>* b) {
+    buf = b;
+    lane = ln;
+    qs = q0 & ~1;
+    base = rec + qs;
+    cross = qs + kYChunk;
+#pragma unroll
+    for (int c = 0; c < kYRingChunks; ++c) issue(c);
+    cp_async_wait<kYRingChunks - 2>();
+    __syncwarp();
+  }
+  // before a step that starts at record q (steps advance by < kYChunk)
+  __device__ __forceinline__ void at(int q) {
+    if (q >= cross) {
+      issue((cross - qs) / kYChunk - 1 + kYRingChunks);  // into the slot just left
+      cp_async_wait<kYRingChunks - 2>();
+      __syncwarp();
+      cross += kYChunk;
+    }
+  }
+  __device__ __forceinline__ const YRec<float>* ptr(int q) const {
+    return buf + ((q - qs) & (kYChunk * kYRingChunks - 1));
+  }
+};
+
 // B consecutive groups of K terms from record q: every record and both
 // factors are loaded ahead of the arithmetic (no branch inside), then per
 // group acc = sum_k coef_k U2,k and Y += U1 * acc.  `ul` points at lane 0's
 // element 0 plus this lane.  CP: the staged block is [2][H][32] with the
 // conjugate in its second half (no sign flips).
-template <typename R, bool CP, int K, int B>
-__device__ __forceinline__ void y_groups(const YRec<R>* __restrict__ rec, int q, const char* __restrict__ ul,
-                                         R& yre, R& yim) {
-  // the record stream is read once per CTA: pull it into L1 ahead of use
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(rec + q + kYRecPad));
+template <typename R, bool CP, int K, int B, typename Src>
+__device__ __forceinline__ void y_groups(Src& src, int q, const char* __restrict__ ul, R& yre, R& yim) {
+  src.at(q);
+  const YRec<R>* rp = src.ptr(q);
   unsigned w[B * K];
   R c[B * K];
 #pragma unroll
   for (int j = 0; j < B * K; ++j) {
     if constexpr (sizeof(R) == 4) {
-      const uint2 r = __ldg(reinterpret_cast<const uint2*>(rec + q + j));
+      const uint2 r = Src::kShared ? *reinterpret_cast<const uint2*>(rp + j)
+                                   : __ldg(reinterpret_cast<const uint2*>(rp + j));
       w[j] = r.x;
       c[j] = __uint_as_float(r.y);
     } else {
-      const uint4 r = __ldg(reinterpret_cast<const uint4*>(rec + q + j));
+      const uint4 r = __ldg(reinterpret_cast<const uint4*>(rp + j));
       w[j] = r.x;
       c[j] = (R)__hiloint2double((int)r.w, (int)r.z);
     }
@@ -304,12 +387,37 @@ __device__ __forceinline__ void y_term(unsigned w, R c, cx<R> u2, const char* __
 }
 
 // All groups of K terms of one output (a run of `ng` groups from record q).
-template <typename R, bool CP, int K>
-__device__ __forceinline__ void y_run(const YRec<R>* __restrict__ rec, int& q, int ng,
-                                      const char* __restrict__ ul, R& yre, R& yim) {
+template <typename R, bool CP, int K, typename Src>
+__device__ __forceinline__ void y_run(Src& src, int& q, int ng, const char* __restrict__ ul, R& yre, R& yim) {
   constexpr int B = K >= 8 ? 1 : 8 / K;  // groups per step: about 8 records
-  for (; ng >= B; ng -= B, q += B * K) y_groups<R, CP, K, B>(rec, q, ul, yre, yim);
-  for (; ng > 0; --ng, q += K) y_groups<R, CP, K, 1>(rec, q, ul, yre, yim);
+  static_assert(B * K <= kYGroupMax, "a step fits the record ring's mirror");
+  for (; ng >= B; ng -= B, q += B * K) y_groups<R, CP, K, B>(src, q, ul, yre, yim);
+  for (; ng > 0; --ng, q += K) y_groups<R, CP, K, 1>(src, q, ul, yre, yim);
+}
+
+// One warp's outputs [o0, o1): per output its runs of 1-, 2-, ... 8-term
+// groups (branch-free bodies of known length).  The records of consecutive
+// outputs are consecutive, and the next output's run header is loaded while
+// the current one is computed.
+template <typename R, bool CP, typename Src>
+__device__ __forceinline__ void y_outputs(Src& src, const uint4* __restrict__ runs, int q, int o0, int o1,
+                                          const char* __restrict__ ul, cx<R>* __restrict__ Yg, int lane) {
+  static_assert(kYGroupMax == 8, "one 16-byte run header per output");
+  uint4 h = __ldg(runs + o0);
+  for (int o = o0; o < o1; ++o) {
+    const uint4 hn = __ldg(runs + min(o + 1, o1 - 1));
+    R yre = R(0), yim = R(0);
+    y_run<R, CP, 1>(src, q, (int)(h.x & 0xffffu), ul, yre, yim);
+    y_run<R, CP, 2>(src, q, (int)(h.x >> 16), ul, yre, yim);
+    y_run<R, CP, 3>(src, q, (int)(h.y & 0xffffu), ul, yre, yim);
+    y_run<R, CP, 4>(src, q, (int)(h.y >> 16), ul, yre, yim);
+    y_run<R, CP, 5>(src, q, (int)(h.z & 0xffffu), ul, yre, yim);
+    y_run<R, CP, 6>(src, q, (int)(h.z >> 16), ul, yre, yim);
+    y_run<R, CP, 7>(src, q, (int)(h.w & 0xffffu), ul, yre, yim);
+    y_run<R, CP, 8>(src, q, (int)(h.w >> 16), ul, yre, yim);
+    Yg[o * 32 + lane] = mk<R>(yre, yim);
+    h = hn;
+  }
 }
 
 // CTA = one 32-atom block x one ysplit-th of the outputs; U of the block
@@ -378,25 +486,21 @@ __global__ void __launch_bounds__(STAGED ? 1024 : 256, 1) yi_kernel(WorkArgs a) 
     for (; q < q1; ++q)
       y_term<R, CP>(rec[q].w, rec[q].c, *reinterpret_cast<const cx<R>*>(ul + y_off2<R>(rec[q].w)), ul, Yg,
                     lane, o, y);
-    return;
-  }
-  // FP32: per output, its runs of 1-, 2-, ... 8-term groups (branch-free
-  // bodies of known length)
-  const uint4* runs = reinterpret_cast<const uint4*>(a.yruns);  // 8 u16 counts per output
-  static_assert(kYGroupMax == 8, "one 16-byte run header per output");
-  for (int o = o0; o < o1; ++o) {
-    int q = a.yfirst[o];
-    const uint4 h = __ldg(runs + o);
-    R yre = R(0), yim = R(0);
-    y_run<R, CP, 1>(rec, q, (int)(h.x & 0xffffu), ul, yre, yim);
-    y_run<R, CP, 2>(rec, q, (int)(h.x >> 16), ul, yre, yim);
-    y_run<R, CP, 3>(rec, q, (int)(h.y & 0xffffu), ul, yre, yim);
-    y_run<R, CP, 4>(rec, q, (int)(h.y >> 16), ul, yre, yim);
-    y_run<R, CP, 5>(rec, q, (int)(h.z & 0xffffu), ul, yre, yim);
-    y_run<R, CP, 6>(rec, q, (int)(h.z >> 16), ul, yre, yim);
-    y_run<R, CP, 7>(rec, q, (int)(h.w & 0xffffu), ul, yre, yim);
-    y_run<R, CP, 8>(rec, q, (int)(h.w >> 16), ul, yre, yim);
-    Yg[o * 32 + lane] = mk<R>(yre, yim);
+  } else {
+    // FP32: the records through the warp's ring in shared memory (staged
+    // CTAs; the ring sits after the staged planes and their barrier)
+    const uint4* runs = reinterpret_cast<const uint4*>(a.yruns);  // 8 u16 counts per output
+    const int q0 = a.yfirst[o0];
+    if constexpr (STAGED) {
+      YRec<float>* rb = reinterpret_cast<YRec<float>*>(smem + yi_ring_offset(H, CP)) + warp * kYRingLen;
+      YRecRing src;
+      src.init(rec, q0, lane, rb);
+      y_outputs<R, CP>(src, runs, q0, o0, o1, ul, Yg, lane);
+      cp_async_wait<0>();  // no copy outlives the warp
+    } else {
+      YRecGlobal<R> src{rec};
+      y_outputs<R, CP>(src, runs, q0, o0, o1, ul, Yg, lane);
+    }
   }
 }
 
@@ -1004,6 +1108,8 @@ YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves) {
   g.conjplane = yi_conjplane(rsize, H);
   g.smem = g.staged ? (g.conjplane ? 2 : 1) * block + 16 : 0;
   g.threads = (g.smem > 100 * 1024) ? 1024 : (g.smem > 60 * 1024 ? 512 : 256);
+  // FP32 staged CTAs: a term-record ring per warp after the planes
+  if (g.staged && rsize == 4) g.smem += (size_t)(g.threads / 32) * kYRingLen * sizeof(YRec<float>);
   int cps = 2048 / g.threads;
   if (g.staged) cps = std::max(1, std::min(cps, (int)((227 * 1024) / g.smem)));
   // the instance's real residency (registers can limit it further), queried
