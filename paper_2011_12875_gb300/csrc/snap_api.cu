@@ -183,25 +183,27 @@ int upload_inplace(snap_ctx* c, T** dst, const std::vector<T>& v) {
 int upload_yrec(snap_ctx* c) {
   const std::vector<double> coef = c->tab.term_coef(c->beta.data());
   const size_t n = c->tab.terms.size();
-  // Kernel word: bits 8-17 the second factor's element, 18-27 the first's
-  // (each times 256 is the byte offset of the element's [32] lanes of
-  // complex float), bit 28 ends a group, 29 an output, 30 / 31 conjugate the
-  // first / second factor (the sign bit of its imaginary part).  With a
-  // staged conjugate plane the elements run over 2H (element + H for a
-  // conjugated read) and the conjugation bits are clear.
+  // Kernel word (the formats are described with yrec_plane_format): the
+  // element offsets in units of 256 B (one element's [32] lanes of complex
+  // float; the FP64 kernel doubles them), the group-end and output-end bits
+  // and, without a staged conjugate plane, the conjugation flags (the sign
+  // bit of the factor's imaginary part).  With the plane the elements run
+  // over 2H (element + H for a conjugated read).
   const bool cp = snap::yi_conjplane((int)c->rsize(), c->tab.H);
+  const bool pf = snap::yrec_plane_format((int)c->rsize(), c->tab.H);
   const unsigned H = (unsigned)c->tab.H;
   if ((cp ? 2 * H : H) > 1024u) return fail(c, SNAP_ERR_ARG, "compute_Y element index exceeds 10 bits");
   auto word = [&](unsigned w) -> unsigned {
     unsigned e1 = w & 1023u, e2 = (w >> 10) & 1023u;
     unsigned c1 = (w >> 20) & 1u, c2 = (w >> 21) & 1u;
+    const unsigned ge = (w >> 23) & 1u, oe = (w >> 22) & 1u;
     if (cp) {
       e1 += c1 * H;
       e2 += c2 * H;
       c1 = c2 = 0;
     }
-    return (e2 << 8) | (e1 << 18) | (((w >> 23) & 1u) << 28) | (((w >> 22) & 1u) << 29) |
-           (c1 << 30) | (c2 << 31);
+    if (pf) return (e2 << 22) | e1 | (ge << 12) | (oe << 13);
+    return (e2 << 8) | (e1 << 18) | (ge << 28) | (oe << 29) | (c1 << 30) | (c2 << 31);
   };
   // kYRecPad zero records past the end: compute_Y reads up to that far ahead
   if (c->precision == SNAP_MIXED) {

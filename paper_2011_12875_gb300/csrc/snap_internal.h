@@ -165,7 +165,18 @@ struct YiGeometry {
   bool conjplane;  // a conjugated copy of the block is staged too (records index it)
 };
 // Whether compute_Y stages U and its conjugate (records in the 2H-index format).
-bool yi_conjplane(int rsize, int H);
+__host__ __device__ inline bool yi_conjplane(int rsize, int H) {
+  return (size_t)4 * H * 32 * rsize + 16 <= 100 * 1024;
+}
+// compute_Y term record word.  FP32 with the conjugate plane: bits 14-31 the
+// byte offset of the second factor's [32] lanes (element times 256, the
+// element over the 2H plane), bits 0-9 the first factor's element, bit 12
+// ends a group, bit 13 an output.  Otherwise: bits 8-17 the second factor's
+// element, 18-27 the first's, bit 28 ends a group, 29 an output, 30 / 31
+// conjugate the first / second factor (no conjugation bits with the plane).
+__host__ __device__ inline bool yrec_plane_format(int rsize, int H) {
+  return rsize == 4 && yi_conjplane(rsize, H);
+}
 YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves);
 
 // Per-configuration virial: sum of vatom over each configuration's atoms.

@@ -224,13 +224,17 @@ struct YAcc {
 };
 
 // Byte offset of a record's second (first) factor from lane 0's element 0:
-// elements are 256 B apart for complex float, 512 B for complex double.
-template <typename R>
+// elements are 256 B apart for complex float, 512 B for complex double.  PF:
+// the FP32 conjugate-plane word, whose top bits are the second factor's
+// offset itself (one shift).
+template <typename R, bool PF>
 __device__ __forceinline__ unsigned y_off2(unsigned w) {
+  if constexpr (PF) return w >> 14;
   return (w & 0x3FF00u) << (sizeof(R) == 4 ? 0 : 1);
 }
-template <typename R>
+template <typename R, bool PF>
 __device__ __forceinline__ unsigned y_off1(unsigned w) {
+  if constexpr (PF) return (w & 0x3FFu) << 8;
   return ((w >> 10) & 0x3FF00u) << (sizeof(R) == 4 ? 0 : 1);
 }
 
@@ -341,11 +345,12 @@ __device__ __forceinline__ void y_groups(Src& src, int q, const char* __restrict
       c[j] = (R)__hiloint2double((int)r.w, (int)r.z);
     }
   }
+  constexpr bool PF = sizeof(R) == 4 && CP;
   cx<R> u2[B * K], u1[B];
 #pragma unroll
-  for (int j = 0; j < B * K; ++j) u2[j] = *reinterpret_cast<const cx<R>*>(ul + y_off2<R>(w[j]));
+  for (int j = 0; j < B * K; ++j) u2[j] = *reinterpret_cast<const cx<R>*>(ul + y_off2<R, PF>(w[j]));
 #pragma unroll
-  for (int b = 0; b < B; ++b) u1[b] = *reinterpret_cast<const cx<R>*>(ul + y_off1<R>(w[b * K]));
+  for (int b = 0; b < B; ++b) u1[b] = *reinterpret_cast<const cx<R>*>(ul + y_off1<R, PF>(w[b * K]));
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     R ar = R(0), ai = R(0);
@@ -371,7 +376,7 @@ __device__ __forceinline__ void y_term(unsigned w, R c, cx<R> u2, const char* __
   y.ar += c * u2.re;
   y.ai += c * i2;
   if (w & (1u << 28)) {
-    const cx<R> u1 = *reinterpret_cast<const cx<R>*>(ul + y_off1<R>(w));
+    const cx<R> u1 = *reinterpret_cast<const cx<R>*>(ul + y_off1<R, false>(w));
     const R i1 = CP ? u1.im : flip_sign(u1.im, (w << 1) & 0x80000000u);
     y.re += u1.re * y.ar - i1 * y.ai;
     y.im += u1.re * y.ai + i1 * y.ar;
@@ -478,13 +483,13 @@ __global__ void __launch_bounds__(STAGED ? 1024 : 256, 1) yi_kernel(WorkArgs a) 
       for (int k = 0; k < 4; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(rec + q + k));
       cx<R> u2[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) u2[k] = *reinterpret_cast<const cx<R>*>(ul + y_off2<R>(v[k].x));
+      for (int k = 0; k < 4; ++k) u2[k] = *reinterpret_cast<const cx<R>*>(ul + y_off2<R, false>(v[k].x));
 #pragma unroll
       for (int k = 0; k < 4; ++k)
         y_term<R, CP>(v[k].x, (R)__hiloint2double((int)v[k].w, (int)v[k].z), u2[k], ul, Yg, lane, o, y);
     }
     for (; q < q1; ++q)
-      y_term<R, CP>(rec[q].w, rec[q].c, *reinterpret_cast<const cx<R>*>(ul + y_off2<R>(rec[q].w)), ul, Yg,
+      y_term<R, CP>(rec[q].w, rec[q].c, *reinterpret_cast<const cx<R>*>(ul + y_off2<R, false>(rec[q].w)), ul, Yg,
                     lane, o, y);
   } else {
     // FP32: the records through the warp's ring in shared memory (staged
@@ -530,6 +535,7 @@ __global__ void __launch_bounds__(kYaWarps * 32) yi_atom_kernel(WorkArgs a) {
   __syncwarp();
   cx<R>* Yg = reinterpret_cast<cx<R>*>(a.Y) + base;
   const YRec<R>* __restrict__ rec = reinterpret_cast<const YRec<R>*>(a.yrec);
+  const bool pf = yrec_plane_format((int)sizeof(R), H);
   const int m = a.ysched_m;
   for (int k = 0; k < m; ++k) {
     const int o = a.ysched[lane * m + k];
@@ -541,12 +547,14 @@ __global__ void __launch_bounds__(kYaWarps * 32) yi_atom_kernel(WorkArgs a) {
       const unsigned w = rec[q].w;
       const R c = rec[q].c;
       // elements of the factors in the [2][H] block: the staged-conjugate
-      // record format indexes it directly, the other one sets the sign bits
-      const cx<R> u2 = ua[(int)((w >> 8) & 1023u) + (int)(w >> 31) * H];
+      // record formats index it directly, the other one sets the sign bits
+      const int e2 = pf ? (int)(w >> 22) : (int)((w >> 8) & 1023u) + (int)(w >> 31) * H;
+      const cx<R> u2 = ua[e2];
       y.ar += c * u2.re;
       y.ai += c * u2.im;
-      if (w & (1u << 28)) {
-        const cx<R> u1 = ua[(int)((w >> 18) & 1023u) + (int)((w >> 30) & 1u) * H];
+      if (w & (pf ? (1u << 12) : (1u << 28))) {
+        const int e1 = pf ? (int)(w & 1023u) : (int)((w >> 18) & 1023u) + (int)((w >> 30) & 1u) * H;
+        const cx<R> u1 = ua[e1];
         y.re += u1.re * y.ar - u1.im * y.ai;
         y.im += u1.re * y.ai + u1.im * y.ar;
         y.ar = R(0);
@@ -1098,7 +1106,6 @@ cudaError_t yi_occupancy(const YiGeometry& g, int* ctas) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, yi_kernel<R, STAGED, CP>, g.threads, g.smem);
 }
 
-bool yi_conjplane(int rsize, int H) { return (size_t)4 * H * 32 * rsize + 16 <= 100 * 1024; }
 
 YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves) {
   YiGeometry g;
