@@ -526,11 +526,15 @@ inline int col_fit_warps(int nw, size_t per_warp) {
   return nw;
 }
 
+// compute_U takes half the tunable's warps per CTA (at least 2): with one
+// atom per warp, the smaller CTAs spread over the SMs more evenly (2000 atoms
+// at 2J8: 41.0 -> 37.0 us against 4-warp CTAs), while the fused dE kernel
+// keeps the tunable itself (its 4- and 8-warp CTAs are faster at 2J14).
 template <typename R, int J2>
 cudaError_t launch_ui_col_t(const WorkArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const size_t per = sizeof(c2<R>) * (size_t)Shape<J2>::P * a.H;
-  const int nw = col_fit_warps(a.col_warps, per);
+  const int nw = col_fit_warps(a.col_warps > 2 ? a.col_warps / 2 : 2, per);
   cudaError_t e = col_allow_smem(ui_col_kernel<R, J2>, per * nw);
   if (e != cudaSuccess) return e;
   return launch_k(ui_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a);
