@@ -259,6 +259,20 @@ long long snap_get_buffer(snap_ctx* ctx, int which, void* dst_host, size_t bytes
 int snap_half_index(int twojmax, int t, int ma, int mb);
 int snap_half_size(int twojmax);
 
+/* compute_Y's term list for one atom, evaluated on the host in FP64 from the
+ * same tables the device walks (Sec. III, Eq. y: Y = sum over the Y triples
+ * of beta~ C C U_t1 U_t2, with the list's exact reductions: the two terms of
+ * a t1 == t2 triple with swapped factors kept as one, the factors of each
+ * output grouped, and the outputs below the centre of the middle column,
+ * 2 mb = t with ma > mb, left at zero).  No GPU work: a check of the tables.
+ *   precision: SNAP_FP64 or SNAP_MIXED (the table variant of that path)
+ *   beta:      double [snap_num_coeff(twojmax) + 1], beta_0 first
+ *   u:         double [H][2] (re, im), Ulisttot of the atom in half layout
+ *   y:         double [H][2] out, Y in half layout
+ * Returns SNAP_OK, or SNAP_ERR_ARG for a twojmax outside 0..14, an unknown
+ * precision or a NULL pointer. */
+int snap_yi_host(int twojmax, int precision, const double* beta, const double* u, double* y);
+
 /* Neighbour list for callers that cannot allocate device memory -- for
  * example code running inside a CUDA graph capture, where cudaMalloc is not
  * allowed, or programs whose device memory belongs to another allocator.

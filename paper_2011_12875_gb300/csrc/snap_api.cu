@@ -716,6 +716,33 @@ int snap_half_index(int twojmax, int t, int ma, int mb) {
   return snap::half_base(t) + mb * (t + 1) + ma;
 }
 
+int snap_yi_host(int twojmax, int precision, const double* beta, const double* u, double* y) {
+  if (twojmax < 0 || twojmax > snap::kMaxTwoJ || (precision != SNAP_FP64 && precision != SNAP_MIXED) ||
+      !beta || !u || !y)
+    return SNAP_ERR_ARG;
+  snap::HostTables tab;
+  tab.build(twojmax, precision == SNAP_MIXED);
+  const std::vector<double> coef = tab.term_coef(beta);
+  auto fac = [&](unsigned idx, unsigned conj, double& re, double& im) {
+    re = u[2 * idx];
+    im = conj ? -u[2 * idx + 1] : u[2 * idx + 1];
+  };
+  for (int o = 0; o < tab.H; ++o) {
+    double yr = 0.0, yi = 0.0;
+    for (int k = tab.term_out_first[o]; k < tab.term_out_first[o + 1]; ++k) {
+      const unsigned w = tab.terms[k];
+      double ar, ai, br, bi;
+      fac(w & 1023u, (w >> 20) & 1u, ar, ai);
+      fac((w >> 10) & 1023u, (w >> 21) & 1u, br, bi);
+      yr += coef[k] * (ar * br - ai * bi);
+      yi += coef[k] * (ar * bi + ai * br);
+    }
+    y[2 * o] = yr;
+    y[2 * o + 1] = yi;
+  }
+  return SNAP_OK;
+}
+
 int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switchflag,
                 const double* beta, int precision, snap_ctx** out) {
   if (!out) {

@@ -43,7 +43,7 @@ EXPORTS = ("snap_num_coeff", "snap_create", "snap_set_beta", "snap_set_neigh_cap
            "snap_stage_name", "snap_launches_per_call", "snap_compute_bispectrum",
            "snap_bispectrum_deriv", "snap_force_weighted", "snap_generation",
            "snap_compute_batch", "snap_set_tuning", "snap_get_tuning", "snap_autotune",
-           "snap_neighbors_noalloc")
+           "snap_neighbors_noalloc", "snap_yi_host")
 NSTAGES = 5
 
 _lib = None
@@ -113,6 +113,8 @@ def load(path: str | None = None):
     L.snap_half_index.restype = i
     L.snap_half_size.argtypes = [i]
     L.snap_half_size.restype = i
+    L.snap_yi_host.argtypes = [i, i, p, p, p]
+    L.snap_yi_host.restype = i
     L.snap_destroy.argtypes = [p]
     L.snap_destroy.restype = i
     L.snap_last_error.argtypes = [p]
@@ -131,6 +133,19 @@ def half_size(twojmax: int) -> int:
 
 def half_index(twojmax: int, t: int, ma: int, mb: int) -> int:
     return load().snap_half_index(twojmax, t, ma, mb)
+
+
+def yi_host(twojmax: int, beta, u_half, precision: int = MIXED) -> np.ndarray:
+    """compute_Y's term list for one atom on the host in FP64 (snap_yi_host):
+    u_half [H][2] -> Y [H][2], half layout.  No GPU work."""
+    H = half_size(twojmax)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    u = np.ascontiguousarray(u_half, dtype=np.float64).reshape(H, 2)
+    y = np.zeros((H, 2))
+    rc = load().snap_yi_host(twojmax, precision, _np_ptr(beta), _np_ptr(u), _np_ptr(y))
+    if rc != 0:
+        raise SnapError(rc, "snap_yi_host: invalid argument")
+    return y
 
 
 def _np_ptr(a: np.ndarray):
