@@ -14,7 +14,9 @@ namespace snap {
 
 namespace {
 
-constexpr int kNbWarps = 8;  // warps per CTA
+constexpr int kNbWarps = 8;        // warps per CTA of the batch build
+constexpr int kNbWarpsSingle = 2;  // warps (= atoms) per CTA of a single configuration: small
+                                   // CTAs spread the one-warp atoms evenly over the SMs
 // Warps per centre atom: a batch build scans every block of its
 // configuration, so four warps share the scan; a single-configuration build
 // skips far tiles and one warp per atom suffices.
@@ -103,12 +105,12 @@ __device__ __forceinline__ int pack_img(int x, int y, int z) {
   return (x + 128) | ((y + 128) << 8) | ((z + 128) << 16);
 }
 
-template <bool BATCH, int SPLIT>
-__global__ void __launch_bounds__(kNbWarps * 32) neigh_build_kernel(NeighArgs a) {
-  constexpr int kAtoms = kNbWarps / SPLIT;
-  __shared__ int cand_j[kNbWarps][kCandCap];
-  __shared__ int cand_s[kNbWarps][kCandCap];
-  __shared__ int ncands[kNbWarps];
+template <bool BATCH, int SPLIT, int NW>
+__global__ void __launch_bounds__(NW * 32) neigh_build_kernel(NeighArgs a) {
+  constexpr int kAtoms = NW / SPLIT;
+  __shared__ int cand_j[NW][kCandCap];
+  __shared__ int cand_s[NW][kCandCap];
+  __shared__ int ncands[NW];
   __shared__ int cmax;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int part = warp % SPLIT, ai = warp / SPLIT;
@@ -347,12 +349,13 @@ cudaError_t launch_pos4(int n, const double* pos, float4* pos4, cudaStream_t s, 
 
 cudaError_t launch_neigh_build(const NeighArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  return launch_k(neigh_build_kernel<false, 1>, dim3(blocks_for(a.n, kNbWarps)), dim3(kNbWarps * 32), 0, s, a);
+  return launch_k(neigh_build_kernel<false, 1, kNbWarpsSingle>, dim3(blocks_for(a.n, kNbWarpsSingle)),
+                  dim3(kNbWarpsSingle * 32), 0, s, a);
 }
 
 cudaError_t launch_neigh_build_batch(const NeighArgs& a, int ncta, cudaStream_t s) {
   if (ncta <= 0) return cudaSuccess;
-  return launch_k(neigh_build_kernel<true, kNbSplitBatch>, dim3(ncta), dim3(kNbWarps * 32), 0, s, a);
+  return launch_k(neigh_build_kernel<true, kNbSplitBatch, kNbWarps>, dim3(ncta), dim3(kNbWarps * 32), 0, s, a);
 }
 
 cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, double Ly,
