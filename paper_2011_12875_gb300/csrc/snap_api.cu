@@ -360,6 +360,7 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.nslices = c->nslices;
   a.nsm = c->nsm;
   a.col_warps = c->col_warps;
+  a.de_maxcnt = (c->last_nmax > 0 && c->last_nmax <= K) ? c->last_nmax : K;
   a.yi_waves = c->yi_waves;
   a.ncoeff = c->tab.ncoeff;
   a.brec = c->d_brec;

@@ -15,6 +15,7 @@
 // one warp shuffle per element.  This file is included by one translation
 // unit per working precision.
 #pragma once
+#include <algorithm>
 #include <type_traits>
 
 #include "snap_geom.cuh"
@@ -316,6 +317,9 @@ __global__ void __launch_bounds__(256) tan_col_kernel(WorkArgs a, const double* 
   }
 }
 
+template <typename R>
+constexpr int de_max_warps() { return sizeof(R) == 4 ? 16 : 8; }
+
 // --------------------------------------- fused dU + dE/dr, reverse mode
 // Same lane layout; warp = one atom, with its weighted Y_i in shared memory.
 // For one pair, S(a, b) = Re sum_t Y_t : conj(u_t) is a real function of the
@@ -334,27 +338,40 @@ __device__ __forceinline__ R shfl_down(R v) {
   return __shfl_down_sync(kFull, v, 1);
 }
 
+//
+// FP32: 128 registers (up to 16 warps a CTA); FP64 may use them all, up to 8
+// warps (its FP64 pipe saturates with few warps, and the columns are twice
+// the size).
+//
+// CTA = A consecutive atoms and NW warps (A is a launch parameter, planned
+// by launch_de_rev_col_t).  The CTA's pairs, atom after atom, are taken in
+// passes of P pairs; warp w takes passes w, w + NW, ...  Every pass but the
+// CTA's last is full whatever the atoms' counts, and with A below NW x
+// (passes per warp) x P / (pairs per atom) no warp takes more passes than
+// planned (the time of a CTA is that of its longest chain of passes).  A
+// pair's arithmetic does not depend on its pass or its warp.
 template <typename R, int J2>
-// FP32: 128 registers (two CTAs of 256 threads); FP64 may use them all (its
-// FP64 pipe saturates with few warps, and the columns are twice the size).
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) de_rev_col_kernel(WorkArgs a) {
+__global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(WorkArgs a, int A) {
   using S_ = Shape<J2>;
   constexpr int NC = S_::NC, P = S_::P;
   const int NW = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = a.H;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long i = (long)blockIdx.x * NW + warp;  // warp = one atom
-  if (i >= a.n) return;                          // whole warp
-  c2<R>* Yw = reinterpret_cast<c2<R>*>(smem) + (size_t)warp * H;  // [NW][H]
-  c2<R>* ust = reinterpret_cast<c2<R>*>(smem) + (size_t)NW * H;   // [NW*P][H] forward columns
+  const long i0 = (long)blockIdx.x * A;  // the CTA's atoms i0 .. i0 + na - 1
+  const int na = (int)min((long)A, a.n - i0);
+  c2<R>* Ywa = reinterpret_cast<c2<R>*>(smem);                    // [A][H] weighted Y
+  c2<R>* ust = Ywa + (size_t)A * H;                              // [NW*P][H] forward columns
   R* red = reinterpret_cast<R*>(ust + (size_t)NW * P * H);       // [NW][32][5]
+  int* coff = reinterpret_cast<int*>(red + (size_t)NW * 32 * 5);  // [A+1] first pair of each atom
   const int g = lane / NC, mb = lane - g * NC;
   const bool grp = g < P;
-  {
+  for (int al = warp; al < na; al += NW) {  // weighted Y of the CTA's atoms
+    const long i = i0 + al;
     const c2<R>* Yg = reinterpret_cast<const c2<R>*>(a.Y);
     const long blk = i >> 5;
     const int li = (int)(i & 31);
+    c2<R>* Yw = Ywa + (size_t)al * H;
     for (int e = lane; e < H; e += 32) {
       const int p = a.half_tmm[e];
       const R w = (R)hweight(tmm_t(p), tmm_ma(p), tmm_mb(p));
@@ -362,17 +379,41 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) de_rev_col_kernel
       Yw[e] = mk<R>(w * y.re, w * y.im);
     }
   }
-  __syncwarp();
+  if (warp == 0) {  // exclusive offsets of the atoms' pairs (inclusive scan, 32 at a time)
+    int carry = 0;
+    if (lane == 0) coff[0] = 0;
+    for (int b = 0; b < na; b += 32) {
+      int c = b + lane < na ? a.cnt[i0 + b + lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(kFull, c, o);
+        if (lane >= o) c += u;
+      }
+      if (b + lane < na) coff[b + lane + 1] = carry + c;
+      carry += __shfl_sync(kFull, c, 31);
+    }
+  }
+  __syncthreads();
+  const int total = coff[na];
   c2<R>* my = ust + (warp * P + (grp ? g : 0)) * H;
   R rs[J2 + 1];
 #pragma unroll
   for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
   R* myred = red + (warp * 32 + lane) * 5;
-  const int cnt = a.cnt[i];
-  for (int s0 = 0; s0 < cnt; s0 += P) {
-    const int s = s0 + g;
-    const bool ok = grp && s < cnt;
-    const long slot = i * a.K + (ok ? s : 0);
+  for (int s0 = warp * P; s0 < total; s0 += NW * P) {
+    const int f = s0 + g;
+    const bool ok = grp && f < total;
+    // the pair's atom: the last al with coff[al] <= f (empty atoms skipped)
+    const int fk = min(f, total - 1);
+    int lo = 0, hi = na - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (coff[mid] <= fk) lo = mid;
+      else hi = mid - 1;
+    }
+    const long i = i0 + lo;
+    const c2<R>* Yw = Ywa + (size_t)lo * H;
+    const long slot = i * a.K + (ok ? f - coff[lo] : 0);
     const R* gm = reinterpret_cast<const R*>(a.geom) + slot * kGeomStride;
     c2<R> ka = mk<R>(1, 0), kb = mk<R>(0, 0);  // a and b
     if (ok) {
@@ -550,15 +591,90 @@ cudaError_t launch_tan_col_t(const WorkArgs& a, const double* g, void* dU, cudaS
   return launch_k(tan_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a, g, dU);
 }
 
+// Launch plan of the fused dE kernel: warps per CTA (NW) and atoms per CTA
+// (A) for atoms of `maxcnt` pairs, from the kernel's registers, the shared
+// memory of a plan and the SM count.
+//  * A plan's cost is (waves of CTAs) x (passes of its longest warp); the
+//    search minimises it, ties going to fewer warps in all.
+//  * The reference shape is a warp per atom in CTAs of `nw0` warps.  In one or
+//    two waves its cost is counted the same way; over more waves its small
+//    CTAs even out and it costs about (all passes) / (resident warps).
+//  * The searched plan is taken when it costs 3% less than the reference
+//    (measured at 2J8 and 2J14 on 2000 atoms, a 64-configuration batch, and
+//    16000 atoms at 2J14, where the reference stays ahead).
+struct DePlan {
+  int nw, A;
+  size_t smem;
+};
+inline DePlan de_plan(int n, int maxcnt, int P, size_t per_warp, size_t per_atom, int regs, int nsm,
+                      int max_warps, int nw0) {
+  const int ralloc = (regs + 7) / 8 * 8;
+  auto shape = [&](int nw, int A, size_t* smem, long* waves, long* ppw) -> bool {
+    *smem = (size_t)A * per_atom + (size_t)nw * per_warp + sizeof(int) * (A + 1);
+    if (*smem > (size_t)227 * 1024) return false;
+    const int cps = std::min({65536 / (ralloc * nw * 32), (int)((228 * 1024) / (*smem + 1024)), 64 / nw, 32});
+    if (cps < 1) return false;
+    const long ctas = (n + A - 1) / A;
+    *waves = (ctas + (long)nsm * cps - 1) / ((long)nsm * cps);
+    *ppw = ((((long)A * maxcnt + P - 1) / P) + nw - 1) / nw;
+    return true;
+  };
+  DePlan ref{nw0, nw0, 0};
+  double ref_cost = 1e300;
+  {
+    long waves, ppw;
+    size_t smem;
+    if (shape(nw0, nw0, &smem, &waves, &ppw)) {
+      ref.smem = smem;
+      const long slots = (long)nsm * std::max(1, (int)std::min<long>(
+                                                  {65536L / (ralloc * nw0 * 32), (long)((228 * 1024) / (smem + 1024)),
+                                                   64L / nw0, 32L})) * nw0;
+      const long per_atom_passes = (maxcnt + P - 1) / P;
+      ref_cost = waves <= 2 ? (double)(waves * per_atom_passes)
+                            : (double)n * per_atom_passes / (double)slots;
+    }
+  }
+  DePlan best{0, 0, 0};
+  long best_cost = -1, best_warps = 0;
+  for (int nw = 2; nw <= max_warps; nw *= 2) {
+    for (int A = 1; A <= 256; ++A) {
+      long waves, ppw;
+      size_t smem;
+      if (!shape(nw, A, &smem, &waves, &ppw)) break;
+      const long cost = waves * ppw;
+      const long warps = (long)((n + A - 1) / A) * nw;
+      if (best_cost < 0 || cost < best_cost || (cost == best_cost && warps < best_warps)) {
+        best_cost = cost;
+        best_warps = warps;
+        best = DePlan{nw, A, smem};
+      }
+    }
+  }
+  if (best_cost < 0 || (ref.smem != 0 && (double)best_cost > 0.97 * ref_cost)) return ref;
+  return best;
+}
+
 template <typename R, int J2>
 cudaError_t launch_de_rev_col_t(const WorkArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  // per warp: Yw [H], forward columns [P][H], lane partials [32][5]
-  const size_t per = sizeof(c2<R>) * (size_t)(1 + Shape<J2>::P) * a.H + sizeof(R) * 32 * 5;
-  const int nw = col_fit_warps(a.col_warps, per);
-  cudaError_t e = col_allow_smem(de_rev_col_kernel<R, J2>, per * nw);
+  // per warp: forward columns [P][H], lane partials [32][5]; per atom: Yw [H] and its offset
+  const size_t per_warp = sizeof(c2<R>) * (size_t)Shape<J2>::P * a.H + sizeof(R) * 32 * 5;
+  const size_t per_atom = sizeof(c2<R>) * (size_t)a.H;
+  static int regs = 0;  // per instantiation
+  if (regs == 0) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, de_rev_col_kernel<R, J2>);
+    if (e != cudaSuccess) return e;
+    regs = fa.numRegs;
+  }
+  const int nw0 = std::min(col_fit_warps(a.col_warps, per_warp + per_atom), de_max_warps<R>());
+  const DePlan p = de_plan(a.n, std::max(1, a.de_maxcnt), Shape<J2>::P, per_warp, per_atom, regs,
+                           std::max(1, a.nsm), de_max_warps<R>(), nw0);
+  if (p.smem == 0) return cudaErrorInvalidConfiguration;  // no plan fits (not reached for 2J <= 14)
+  cudaError_t e = col_allow_smem(de_rev_col_kernel<R, J2>, p.smem);
   if (e != cudaSuccess) return e;
-  return launch_k(de_rev_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a);
+  return launch_k(de_rev_col_kernel<R, J2>, dim3((unsigned)((a.n + p.A - 1) / p.A)), dim3(p.nw * 32), p.smem, s,
+                  a, p.A);
 }
 
 }  // namespace col

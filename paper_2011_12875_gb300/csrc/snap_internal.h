@@ -128,6 +128,7 @@ struct WorkArgs {
   int ysched_m;
   int nsm;
   int col_warps;  // warps per CTA of the column-chain kernels (tunable)
+  int de_maxcnt;  // neighbour count the fused dE launch is planned for (last seen maximum, else K)
   int yi_waves;   // compute_Y waves per SM (tunable)
   // bispectrum output
   int ncoeff;
