@@ -47,6 +47,7 @@ struct snap_ctx {
   int yi_waves = 2;
   int yi_layout = 0;
   int last_nmax = 0;
+  int seen_nmax = 0;  // largest neighbour count seen: the fused dE launch is planned for it
   int last_n = 0, last_K = 0;
   std::string err;
 
@@ -108,6 +109,7 @@ struct snap_ctx {
   cudaGraphExec_t gexec = nullptr;
   const void* g_key[4] = {nullptr, nullptr, nullptr, nullptr};
   long long g_ws = -1;  // workspace generation the batch graph was captured with
+  int g_demax = -1;     // neighbour count its fused dE launch was planned for
   // bumped whenever a device buffer that a captured graph refers to moves
   long long ws_gen = 0;
   // single-configuration graphs (snap_compute*, snap_compute_host)
@@ -322,6 +324,11 @@ bool box_ok(const double* box) {
 }
 
 // Kernel arguments for n atoms with capacity K (workspace and tables).
+// Neighbour count the fused dE launch is planned for: the largest count the
+// context has seen (monotone, so a captured graph is re-captured at most a
+// few times as it grows), else the capacity.
+int de_maxcnt(const snap_ctx* c, int K) { return (c->seen_nmax > 0 && c->seen_nmax <= K) ? c->seen_nmax : K; }
+
 snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   snap::WorkArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -360,7 +367,7 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.nslices = c->nslices;
   a.nsm = c->nsm;
   a.col_warps = c->col_warps;
-  a.de_maxcnt = (c->last_nmax > 0 && c->last_nmax <= K) ? c->last_nmax : K;
+  a.de_maxcnt = de_maxcnt(c, K);
   a.yi_waves = c->yi_waves;
   a.ncoeff = c->tab.ncoeff;
   a.brec = c->d_brec;
@@ -600,6 +607,7 @@ int launch_batch(snap_ctx* c, const double* pos, double* energy, double* forces,
 
 int check_flags(snap_ctx* c) {
   c->last_nmax = c->h_flags[0];
+  c->seen_nmax = std::max(c->seen_nmax, c->last_nmax);
   if (c->h_flags[3]) return fail(c, SNAP_ERR_TIMEOUT, "a bounded device wait (TMA staging) gave up");
   if (c->h_flags[2]) return fail(c, SNAP_ERR_ARG, "neighbour list: count outside 0..cap or index outside 0..N-1");
   if (c->h_flags[0] > c->last_K)
@@ -695,7 +703,8 @@ int compute_dev(snap_ctx* c, int n, const double* pos, const double* box, const 
       (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves,
       (unsigned long long)c->yi_layout, key_bits(box[0]), key_bits(box[1]), key_bits(box[2]),
       key_ptr(pos), key_ptr(energy), key_ptr(forces),
-      key_ptr(virial), key_ptr(ucnt), key_ptr(uidx), key_ptr(uimg), (unsigned long long)ucap};
+      key_ptr(virial), key_ptr(ucnt), key_ptr(uidx), key_ptr(uimg), (unsigned long long)ucap,
+      (unsigned long long)de_maxcnt(c, K)};
   return graph_run(c, c->gdev, key, s, run);
 }
 
@@ -981,7 +990,8 @@ int snap_compute_batch(snap_ctx* c, int nconf, const int* natoms, const double* 
   if (rc) return rc;
   if (!use_graph) return launch_batch(c, pos, energy, forces, virial, s);
   const void* key[4] = {pos, energy, forces, virial};
-  const bool same = c->gexec && std::equal(key, key + 4, c->g_key) && c->g_ws == c->ws_gen;
+  const int demax = de_maxcnt(c, c->K);
+  const bool same = c->gexec && std::equal(key, key + 4, c->g_key) && c->g_ws == c->ws_gen && c->g_demax == demax;
   if (!same) {
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);
@@ -1005,6 +1015,7 @@ int snap_compute_batch(snap_ctx* c, int nconf, const int* natoms, const double* 
     }
     std::copy(key, key + 4, c->g_key);
     c->g_ws = c->ws_gen;
+    c->g_demax = demax;
   }
   SNAP_CUDA(c, cudaGraphLaunch(c->gexec, s));
   c->generation += 1;
@@ -1158,7 +1169,8 @@ int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const dou
         (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves,
         (unsigned long long)c->yi_layout, key_bits(box[0]), key_bits(box[1]), key_bits(box[2]),
         key_ptr(pos_host), key_ptr(energy_host),
-        key_ptr(forces_host), key_ptr(virial_host), key_ptr(c->d_hpos)};
+        key_ptr(forces_host), key_ptr(virial_host), key_ptr(c->d_hpos),
+        (unsigned long long)de_maxcnt(c, c->K)};
     // pageable host memory is neither mapped nor capturable: plain copies (a
     // key that matches the captured graph was checked when it was captured)
     const bool replay = c->ghost.exec && c->ghost.key == key;
