@@ -197,7 +197,9 @@ int snap_compute_batch(snap_ctx* ctx, int nconf, const int* natoms, const double
  *  col_warps (2, 4 or 8): warps per CTA of the register column-chain kernels
  *    (compute_U takes half of it, at least 2); each warp computes one atom,
  *    so this is atoms per CTA (halved where the CTA's shared memory would
- *    pass 227 KB);
+ *    pass 227 KB).  The fused dE kernel plans its own CTA shape (atoms and
+ *    warps per CTA) from the system size and the largest neighbour count
+ *    seen, and falls back to this shape when the plan gains nothing;
  *  yi_waves (1..8): fineness of the compute_Y split; the slices per 32-atom
  *    block minimise ceil(CTAs / resident CTAs) * (1/slices + 0.02/yi_waves);
  *  yi_layout: 0 = compute_Y with a warp of 32 atoms (lanes = atoms, the

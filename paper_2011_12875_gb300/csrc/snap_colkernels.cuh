@@ -16,6 +16,7 @@
 // unit per working precision.
 #pragma once
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "snap_geom.cuh"
@@ -660,16 +661,32 @@ cudaError_t launch_de_rev_col_t(const WorkArgs& a, cudaStream_t s) {
   // per warp: forward columns [P][H], lane partials [32][5]; per atom: Yw [H] and its offset
   const size_t per_warp = sizeof(c2<R>) * (size_t)Shape<J2>::P * a.H + sizeof(R) * 32 * 5;
   const size_t per_atom = sizeof(c2<R>) * (size_t)a.H;
-  static int regs = 0;  // per instantiation
-  if (regs == 0) {
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, de_rev_col_kernel<R, J2>);
-    if (e != cudaSuccess) return e;
-    regs = fa.numRegs;
-  }
+  // the kernel's registers and the last plan, per instantiation (the plan
+  // search is a few hundred candidate shapes; repeated calls reuse it)
+  static std::mutex mu;
+  static int regs = 0;
+  static long long last_key[4] = {-1, -1, -1, -1};
+  static DePlan last_plan{0, 0, 0};
   const int nw0 = std::min(col_fit_warps(a.col_warps, per_warp + per_atom), de_max_warps<R>());
-  const DePlan p = de_plan(a.n, std::max(1, a.de_maxcnt), Shape<J2>::P, per_warp, per_atom, regs,
-                           std::max(1, a.nsm), de_max_warps<R>(), nw0);
+  const int maxcnt = std::max(1, a.de_maxcnt), nsm = std::max(1, a.nsm);
+  DePlan p;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (regs == 0) {
+      cudaFuncAttributes fa;
+      cudaError_t e = cudaFuncGetAttributes(&fa, de_rev_col_kernel<R, J2>);
+      if (e != cudaSuccess) return e;
+      regs = fa.numRegs;
+    }
+    const long long key[4] = {a.n, maxcnt, ((long long)nsm << 32) | nw0, a.H};
+    if (std::equal(key, key + 4, last_key)) {
+      p = last_plan;
+    } else {
+      p = de_plan(a.n, maxcnt, Shape<J2>::P, per_warp, per_atom, regs, nsm, de_max_warps<R>(), nw0);
+      std::copy(key, key + 4, last_key);
+      last_plan = p;
+    }
+  }
   if (p.smem == 0) return cudaErrorInvalidConfiguration;  // no plan fits (not reached for 2J <= 14)
   cudaError_t e = col_allow_smem(de_rev_col_kernel<R, J2>, p.smem);
   if (e != cudaSuccess) return e;
