@@ -107,6 +107,23 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(pg, x: float, dev) -> float:
+    """The largest x over the ranks of process group module `pg` (x itself
+    without one): the job's time is its slowest rank's."""
+    if not pg:
+        return x
+    import torch
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, natoms: int, ms: float) -> float:
+    """Atom-steps/s of the whole job: every rank evaluates its own replica of
+    `natoms` atoms per step, and a step lasts `ms` (the slowest rank's)."""
+    return world * natoms / (ms * 1e-3)
+
+
 def read_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
     summary (a line 'traffic <kernel> <workload> <bytes>'), else None."""
@@ -474,12 +491,8 @@ def main():
     clocks = sampler.stop()
     ms_mean = statistics.mean(r["ms"])
     ms_med = statistics.median(r["ms"])
-    t_max = ms_mean
-    if pg:
-        t = torch.tensor([ms_mean], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * r["natoms"] / (t_max * 1e-3)
+    t_max = max_over_ranks(pg, ms_mean, dev)
+    value = job_throughput(world, r["natoms"], t_max)
 
     # roofline of the dominant kernel (largest share of the step)
     prof = r["prof"]
@@ -514,8 +527,15 @@ def main():
                      "traffic": read_traffic(dom, head.name)},
         "clocks": clocks,
     }
+    # end to end through host buffers, on every rank; the job's step is the
+    # slowest rank's
+    if pg:
+        pg.barrier()
+    e2e = e2e_host(snap, torch, head, hprec, min(args.steps, 300))
+    e2e["ms_per_step"] = max_over_ranks(pg, e2e["ms_per_step"], dev)
+    e2e["value"] = job_throughput(world, r["natoms"], e2e["ms_per_step"])
     if rank == 0:
-        line["e2e"] = e2e_host(snap, torch, head, hprec, min(args.steps, 300))
+        line["e2e"] = e2e
         if not args.no_variants:
             variants = {}
             for name, prec, tag in (("bcc10_2j8", snap.FP64, "fp64_2j8_2000"),
