@@ -322,7 +322,8 @@ template <typename R>
 constexpr int de_max_warps() { return sizeof(R) == 4 ? 16 : 8; }
 
 // --------------------------------------- fused dU + dE/dr, reverse mode
-// Same lane layout; warp = one atom, with its weighted Y_i in shared memory.
+// Same lane layout (P pairs a warp, a lane per column); the CTA's atoms have
+// their weighted Y_i in shared memory (launch shape below).
 // For one pair, S(a, b) = Re sum_t Y_t : conj(u_t) is a real function of the
 // Cayley-Klein parameters; its gradient comes from one
 // forward pass of the recursion (each lane stores its column of every layer
@@ -339,7 +340,6 @@ __device__ __forceinline__ R shfl_down(R v) {
   return __shfl_down_sync(kFull, v, 1);
 }
 
-//
 // FP32: 128 registers (up to 16 warps a CTA); FP64 may use them all, up to 8
 // warps (its FP64 pipe saturates with few warps, and the columns are twice
 // the size).
