@@ -195,6 +195,31 @@ def test_batch_equals_per_configuration(snapmod, prec, use_graph):
     s.close()
 
 
+def test_large_batch_equals_per_configuration(snapmod):
+    """The 64-configuration batch of the benchmark (54 to 2000 atoms each,
+    about 45,000 in all): the fused dE launch is planned with tens of atoms a
+    CTA there (its per-CTA pair offsets take several 32-atom chunks), and the
+    results are still those of one snap_compute per configuration."""
+    cfgs = inputs.batch(64)
+    natoms = np.array([c.natoms for c in cfgs])
+    boxes = np.array([c.box for c in cfgs])
+    s = snapmod.Snap(8, inputs.beta(8), precision=1)
+    P = torch.tensor(np.concatenate([c.pos for c in cfgs]), device="cuda:0")
+    # the first call is planned for the capacity, the second for the counts
+    # it has seen (tens of atoms a CTA)
+    runs = [[x.cpu().numpy().copy() for x in s.compute_batch(P, natoms, boxes, use_graph=False)]
+            for _ in range(2)]
+    start = 0
+    for k, c in enumerate(cfgs):
+        e1, f1, w1 = [x.cpu().numpy() for x in s.compute(torch.tensor(c.pos, device="cuda:0"), c.box)]
+        sl = slice(start, start + c.natoms)
+        for E, F, W in runs:
+            assert np.array_equal(E[sl], e1) and np.array_equal(F[sl], f1), k
+            np.testing.assert_allclose(W[k], w1, rtol=1e-12, atol=1e-12 * np.abs(w1).max())
+        start += c.natoms
+    s.close()
+
+
 def test_batch_parity_with_oracle(snapmod):
     cfgs, pos, natoms, boxes = batch_of([3, 4, 2])
     beta = inputs.beta(8)
