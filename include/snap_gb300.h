@@ -47,7 +47,7 @@ enum snap_status {
   SNAP_OK = 0,
   SNAP_ERR_ARG = -1,            /* invalid argument (message says which) */
   SNAP_ERR_NEIGH_OVERFLOW = -2, /* an atom has more neighbours than the capacity */
-  SNAP_ERR_BOX = -3,            /* box length <= 0 or not finite */
+  SNAP_ERR_BOX = -3,            /* box length <= 0 or not finite, or too short against rcut */
   SNAP_ERR_CUDA = -4,           /* a CUDA call failed (message has the CUDA error) */
   SNAP_ERR_TIMEOUT = -5,        /* a bounded device wait gave up */
   SNAP_ERR_NOMEM = -6,          /* device or host allocation failed */
@@ -93,7 +93,12 @@ int snap_neigh_max(const snap_ctx* ctx);
  *             wrapping into the box is needed), but the device neighbour builder
  *             pre-screens pairs in FP32 with a 0.01 A margin, so |coordinates|
  *             should stay below about 1e4 A.
- *   box     : HOST, 3 doubles: orthorhombic box lengths, periodic in x, y, z
+ *   box     : HOST, 3 doubles: orthorhombic box lengths, periodic in x, y, z,
+ *             finite and > 0.  A box so short against rcut that the device
+ *             neighbour build would enumerate more than 4096 periodic images
+ *             per atom (or shifts beyond 100 along one axis) returns
+ *             SNAP_ERR_BOX before anything is launched (such a box holds more
+ *             images of one atom within rcut than any neighbour capacity).
  *   nbr_cnt, nbr_idx, nbr_img, nbr_cap :
  *             all NULL/0 -> the library builds the list on the device
  *             (every k, image s with |r_k + s L - r_i| < rcut, k != i or
@@ -275,17 +280,22 @@ int snap_half_size(int twojmax);
  * precision or a NULL pointer. */
 int snap_yi_host(int twojmax, int precision, const double* beta, const double* u, double* y);
 
-/* Neighbour list for callers that cannot allocate device memory -- for
- * example code running inside a CUDA graph capture, where cudaMalloc is not
- * allowed, or programs whose device memory belongs to another allocator.
+/* Neighbour list for callers that cannot call cudaMalloc.  Such callers
+ * include host programs that hand the GPU's memory to their own allocator or
+ * pool (reserved up front, so there may be no room outside it, and libraries
+ * must not take memory the pool counts on), and callers on a latency-critical
+ * path, where cudaMalloc may synchronise the device and stall other streams.
  * The paper has no counterpart: this is a deployment variant of the device
  * builder used by snap_compute, and it builds the same list (same order).
  * It allocates nothing: its scratch is a fixed 1 MiB device array inside the
  * library, held by every GPU that loads the library until the process exits.
  *   natoms  : 0..65536 (more returns SNAP_ERR_ARG)
  *   pos     : device, [natoms][3] doubles
- *   box     : HOST, 3 box lengths (periodic, orthorhombic)
- *   rcut    : cutoff, > 0
+ *   box     : HOST, 3 box lengths (periodic, orthorhombic), finite and > 0;
+ *             SNAP_ERR_BOX also for a box so short against rcut that the
+ *             build would enumerate more than 4096 periodic images per atom
+ *             (or shifts beyond 100 along one axis)
+ *   rcut    : cutoff, finite and > 0 (else SNAP_ERR_ARG)
  *   cap     : slots per atom, 1..64
  *   cnt, nbr, img, rij : device outputs, [natoms], [natoms][cap],
  *             [natoms][cap][3] signed char image shifts, [natoms][cap][3]
@@ -293,10 +303,11 @@ int snap_yi_host(int twojmax, int precision, const double* beta, const double* u
  *   max_count : device, 1 int, receives the largest count (a value above cap
  *             means the list overflowed), or NULL
  *   stream  : cudaStream_t (void*); the call only enqueues work.
- * The first call on a device looks up the device address of the scratch
- * array; make that first call before any stream capture.  All calls share
- * the one array: calls that may overlap on the GPU (different streams, or
- * several host threads) race and must be serialised by the caller. */
+ * Set-up: the first valid call on a device (natoms = 0 included) looks up the
+ * device address of the scratch array, so make it before any stream capture.
+ * All calls share the one array and each call clears its counters; calls
+ * that may overlap on the GPU (different streams, or several host threads)
+ * race and must be serialised by the caller. */
 int snap_neighbors_noalloc(int natoms, const double* pos, const double* box, double rcut,
                            int cap, int* cnt, int* nbr, signed char* img, double* rij,
                            int* max_count, void* stream);

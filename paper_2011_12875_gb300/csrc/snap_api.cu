@@ -323,6 +323,19 @@ bool box_ok(const double* box) {
   return true;
 }
 
+// A box the device neighbour build can enumerate (snap::image_shifts): each
+// length finite and > 0, and not so short against rcut that the image loop
+// would run away.  SNAP_OK or SNAP_ERR_BOX with the reason.
+int check_box(snap_ctx* c, const double* box) {
+  if (!box_ok(box)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+  int S[3];
+  if (!snap::image_shifts(box, c->rcut, S))
+    return fail(c, SNAP_ERR_BOX, "box too short for rcut: the neighbour build would enumerate more than " +
+                                     std::to_string(snap::kMaxImageLoop) + " periodic images per atom (or shifts beyond " +
+                                     std::to_string(snap::kMaxImageShift) + " along one axis)");
+  return SNAP_OK;
+}
+
 // Kernel arguments for n atoms with capacity K (workspace and tables).
 // Neighbour count the fused dE launch is planned for: the largest count the
 // context has seen (monotone, so a captured graph is re-captured at most a
@@ -430,8 +443,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
     na.Ly = box[1];
     na.Lz = box[2];
     int S[3];
-    for (int d = 0; d < 3; ++d)
-      S[d] = (box[d] > 2.0 * (c->rcut + 0.05)) ? 0 : (int)std::ceil(c->rcut / box[d]) + 1;
+    if (!snap::image_shifts(box, c->rcut, S)) return check_box(c, box);
     na.Sx = S[0];
     na.Sy = S[1];
     na.Sz = S[2];
@@ -515,10 +527,8 @@ int prepare_batch(snap_ctx* c, int nconf, const int* natoms, const double* boxes
       snap::NeighConf& f = confs[k];
       f.start = start;
       f.n = natoms[k];
-      for (int d = 0; d < 3; ++d) {
-        f.L[d] = boxes[3 * k + d];
-        f.S[d] = (f.L[d] > 2.0 * (c->rcut + 0.05)) ? 0 : (int)std::ceil(c->rcut / f.L[d]) + 1;
-      }
+      for (int d = 0; d < 3; ++d) f.L[d] = boxes[3 * k + d];
+      if (!snap::image_shifts(f.L, c->rcut, f.S)) return check_box(c, f.L);
       for (int o = 0; o < f.n; o += snap::kNeighAtomsPerCta) map.push_back(make_int2(k, o));
       start += f.n;
     }
@@ -852,7 +862,7 @@ int snap_compute(snap_ctx* c, int natoms, const double* pos, const double* box, 
                  double* forces, double* virial, void* stream) {
   if (!c) return SNAP_ERR_ARG;
   if (natoms < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
-  if (!box_ok(box)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+  if (int rb = check_box(c, box)) return rb;
   cudaStream_t s = (cudaStream_t)stream;
   if (natoms == 0) {
     if (virial) SNAP_CUDA(c, cudaMemsetAsync(virial, 0, 6 * sizeof(double), s));
@@ -870,7 +880,7 @@ int snap_compute_async(snap_ctx* c, int natoms, const double* pos, const double*
                        int nbr_cap, double* energy, double* forces, double* virial, void* stream) {
   if (!c) return SNAP_ERR_ARG;
   if (natoms < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
-  if (!box_ok(box)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+  if (int rb = check_box(c, box)) return rb;
   cudaStream_t s = (cudaStream_t)stream;
   if (natoms == 0) {
     if (virial) SNAP_CUDA(c, cudaMemsetAsync(virial, 0, 6 * sizeof(double), s));
@@ -933,7 +943,7 @@ int snap_compute_bispectrum(snap_ctx* c, int natoms, const double* pos, const do
                             int nbr_cap, double* B, void* stream) {
   if (!c) return SNAP_ERR_ARG;
   if (natoms < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
-  if (!box_ok(box)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+  if (int rb = check_box(c, box)) return rb;
   if (natoms == 0) return SNAP_OK;
   if (!pos || !B) return fail(c, SNAP_ERR_ARG, "pos and B are required");
   cudaStream_t s = (cudaStream_t)stream;
@@ -949,7 +959,7 @@ int snap_bispectrum_deriv(snap_ctx* c, int natoms, const double* pos, const doub
                           int nbr_cap, const double* g, double* dB, void* stream) {
   if (!c) return SNAP_ERR_ARG;
   if (natoms < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
-  if (!box_ok(box)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+  if (int rb = check_box(c, box)) return rb;
   if (natoms == 0) return SNAP_OK;
   if (!pos || !g || !dB) return fail(c, SNAP_ERR_ARG, "pos, g and dB are required");
   cudaStream_t s = (cudaStream_t)stream;
@@ -979,7 +989,7 @@ int snap_compute_batch(snap_ctx* c, int nconf, const int* natoms, const double* 
   long total = 0;
   for (int k = 0; k < nconf; ++k) {
     if (natoms[k] < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
-    if (!box_ok(boxes + 3 * k)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+    if (int rb = check_box(c, boxes + 3 * k)) return rb;
     total += natoms[k];
   }
   if (total > (1L << 30)) return fail(c, SNAP_ERR_ARG, "batch too large");
@@ -1104,7 +1114,7 @@ int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const dou
                       double* energy_host, double* forces_host, double* virial_host, void* stream) {
   if (!c) return SNAP_ERR_ARG;
   if (natoms < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
-  if (!box_ok(box)) return fail(c, SNAP_ERR_BOX, "box lengths must be finite and > 0");
+  if (int rb = check_box(c, box)) return rb;
   if (natoms == 0) {
     if (virial_host) std::memset(virial_host, 0, 6 * sizeof(double));
     return SNAP_OK;

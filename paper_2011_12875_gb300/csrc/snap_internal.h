@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace snap {
 
 // Kernel launch with the configuration as arguments (one place to change how
@@ -70,6 +72,30 @@ struct NeighConf {
   double L[3];
   int S[3];
 };
+
+// Image shifts the device neighbour build enumerates beyond the nearest
+// image, per axis: none when the box is longer than 2 (rcut + 0.05 A), else
+// ceil(rcut / L) + 1.  The build loops over (2 Sx + 1)(2 Sy + 1)(2 Sz + 1)
+// images for every 32 candidates and stores shifts as signed bytes, so a box
+// that needs more than kMaxImageLoop images in all, or more than kMaxImageShift
+// along one axis, is refused (false): such a box holds more images of a
+// single atom within rcut than any neighbour capacity.  rcut and the box
+// lengths must be finite and positive.
+constexpr int kMaxImageLoop = 4096;
+constexpr int kMaxImageShift = 100;
+inline bool image_shifts(const double* L, double rcut, int S[3]) {
+  if (!(rcut > 0.0 && rcut < 1e30)) return false;
+  long loop = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (!(L[d] > 0.0 && L[d] < 1e300)) return false;
+    const double q = rcut / L[d];
+    if (!(q < (double)kMaxImageShift)) return false;
+    S[d] = (L[d] > 2.0 * (rcut + 0.05)) ? 0 : (int)std::ceil(q) + 1;
+    if (S[d] > kMaxImageShift) return false;
+    loop *= 2L * S[d] + 1;
+  }
+  return loop <= kMaxImageLoop;
+}
 
 // centre atoms per CTA of the device neighbour build
 constexpr int kNeighAtomsPerCta = 2;

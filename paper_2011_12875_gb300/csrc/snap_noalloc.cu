@@ -1,13 +1,16 @@
 // snap_noalloc.cu -- neighbour-list build that allocates nothing.
 //
-// Some callers cannot allocate device memory: code running while a CUDA
-// graph is being captured (cudaMalloc is not allowed there), and host
-// programs whose device memory is owned by another allocator or pool and
-// must not be touched by libraries.  For them this file offers one entry
-// point that builds the same neighbour list as snap_compute's device builder
-// with the caller's output buffers only.  Its scratch (an FP32 copy of the
-// positions and a few counters) lives in the fixed array below, which every
-// GPU that loads the library holds until the process exits.
+// Some callers cannot call cudaMalloc.  A host program that hands the GPU's
+// memory to its own allocator or pool (an MD engine or a training framework
+// that reserves HBM up front) may have no room left outside that pool, and it
+// may forbid libraries to take memory the pool counts on.  A caller on a
+// latency-critical path cannot afford cudaMalloc either: it may synchronise
+// the device and stall work queued on other streams.  For them this file
+// offers one entry point that builds the same neighbour list as
+// snap_compute's device builder into the caller's output buffers only.  Its
+// scratch (an FP32 copy of the positions and a few counters) lives in the
+// fixed array below, which every GPU that loads the library holds until the
+// process exits.
 #include <cmath>
 #include <mutex>
 
@@ -54,20 +57,23 @@ extern "C" int snap_neighbors_noalloc(int natoms, const double* pos, const doubl
                                       void* stream) {
   if (natoms < 0 || natoms > kNoAllocMaxAtoms) return SNAP_ERR_ARG;
   if (cap < 1 || cap > snap::kMaxNeighCap) return SNAP_ERR_ARG;
-  if (!(rcut > 0.0)) return SNAP_ERR_ARG;
+  if (!(std::isfinite(rcut) && rcut > 0.0)) return SNAP_ERR_ARG;
   if (!box) return SNAP_ERR_BOX;
-  for (int d = 0; d < 3; ++d)
-    if (!(box[d] > 0.0 && box[d] < 1e300)) return SNAP_ERR_BOX;
-  if (natoms == 0) return SNAP_OK;
-  if (!pos || !cnt || !nbr || !img || !rij) return SNAP_ERR_ARG;
+  // bounded image range (the build's image loop and its signed-byte shifts)
+  int S[3];
+  if (!snap::image_shifts(box, rcut, S)) return SNAP_ERR_BOX;
+  // the set-up (the scratch array's device address) runs on every valid
+  // call, also one with no atoms, so a first call with natoms = 0 does it too
   unsigned char* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return SNAP_ERR_CUDA;
+  if (natoms == 0) return SNAP_OK;
+  if (!pos || !cnt || !nbr || !img || !rij) return SNAP_ERR_ARG;
   float4* pos4 = reinterpret_cast<float4*>(base);
   int* flags = reinterpret_cast<int*>(base + sizeof(float4) * kNoAllocMaxAtoms);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the counters keep the previous call's values: clear them
   if (cudaMemsetAsync(flags, 0, 4 * sizeof(int), s) != cudaSuccess) return SNAP_ERR_CUDA;
-  snap::NeighArgs na;
+  snap::NeighArgs na{};
   na.n = natoms;
   na.K = cap;
   na.pos = pos;
@@ -75,9 +81,6 @@ extern "C" int snap_neighbors_noalloc(int natoms, const double* pos, const doubl
   na.Lx = box[0];
   na.Ly = box[1];
   na.Lz = box[2];
-  int S[3];
-  for (int d = 0; d < 3; ++d)
-    S[d] = (box[d] > 2.0 * (rcut + 0.05)) ? 0 : (int)std::ceil(rcut / box[d]) + 1;
   na.Sx = S[0];
   na.Sy = S[1];
   na.Sz = S[2];

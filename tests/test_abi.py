@@ -85,3 +85,33 @@ def test_create_without_gpu_reports_cuda_error(lib):
     with pytest.raises(snap.SnapError) as ei:
         snap.Snap(8, np.zeros(56))
     assert ei.value.code == snap.ERR_CUDA
+
+
+def test_noalloc_refuses_bad_boxes_and_cutoffs_before_the_gpu(lib):
+    """The allocation-free neighbour list checks its box and cutoff on the
+    host: a box so short against rcut that the image loop would run away, a
+    non-finite box and a non-finite or non-positive rcut are refused before
+    any CUDA call (this runs without a GPU)."""
+    import numpy as np
+    from paper_2011_12875_gb300 import snap
+    p, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.snap_neighbors_noalloc.argtypes = [i, p, p, d, i, p, p, p, p, p, p]
+    lib.snap_neighbors_noalloc.restype = i
+
+    def call(box, rcut, n=4):
+        b = np.ascontiguousarray(box, dtype=np.float64)
+        return lib.snap_neighbors_noalloc(n, None, b.ctypes.data_as(p), rcut, 32,
+                                          None, None, None, None, None, None)
+    # 0.01 A box against a 4.7 A cutoff: 471 shifts a side
+    assert call([0.01, 0.01, 0.01], 4.7) == snap.ERR_BOX
+    # short along one axis only: more than 100 shifts
+    assert call([0.04, 50.0, 50.0], 4.7) == snap.ERR_BOX
+    # 0.5 A box: 11 shifts a side, 23^3 images per atom (> 4096)
+    assert call([0.5, 0.5, 0.5], 4.7) == snap.ERR_BOX
+    assert call([np.inf, 5.0, 5.0], 4.7) == snap.ERR_BOX
+    assert call([np.nan, 5.0, 5.0], 4.7) == snap.ERR_BOX
+    assert call([5.0, 0.0, 5.0], 4.7) == snap.ERR_BOX
+    for rc in (np.inf, -np.inf, np.nan, 0.0, -1.0):
+        assert call([5.0, 5.0, 5.0], rc) == snap.ERR_ARG, rc
+    # finite but absurd: every box is too short for it
+    assert call([5.0, 5.0, 5.0], 1e300) == snap.ERR_BOX

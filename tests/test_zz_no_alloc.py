@@ -1,9 +1,9 @@
 """snap_neighbors_noalloc: the neighbour-list entry point for callers that
-cannot allocate device memory (for example inside a CUDA graph capture, or
-under another owner's allocator).  It must produce the same list as the
-existing entry point (snap_compute's device builder, read back with
-snap_get_buffer), call after call, although all calls share one fixed scratch
-array inside the library.
+cannot call cudaMalloc (a host program whose device memory belongs to its own
+pool, or a caller on a latency-critical path where cudaMalloc may synchronise
+the device).  It must produce the same list as the existing entry point
+(snap_compute's device builder, read back with snap_get_buffer), call after
+call, although all calls share one fixed scratch array inside the library.
 
 This file is collected last on purpose, and it also passes alone in a fresh
 process.
@@ -104,3 +104,15 @@ def test_noalloc_reports_overflow_and_rejects_oversized_input(lib):
     rc = lib.snap_neighbors_noalloc(65537, None, box.ctypes.data_as(ctypes.c_void_p), 4.7, 32,
                                     None, None, None, None, None, None)
     assert rc == -1  # SNAP_ERR_ARG: more atoms than the fixed scratch holds
+    p = box.ctypes.data_as(ctypes.c_void_p)
+    for bad_rcut in (float("inf"), float("nan"), 0.0):
+        assert lib.snap_neighbors_noalloc(4, None, p, bad_rcut, 32, None, None, None, None, None,
+                                          None) == -1
+    tiny = np.array([0.01, 0.01, 0.01])
+    assert lib.snap_neighbors_noalloc(4, None, tiny.ctypes.data_as(ctypes.c_void_p), 4.7, 32, None,
+                                      None, None, None, None, None) == -3  # SNAP_ERR_BOX
+    # an empty call is valid (it does the set-up) and the next call still matches
+    assert lib.snap_neighbors_noalloc(0, None, p, inputs.RCUT, 32, None, None, None, None, None,
+                                      None) == 0
+    again = noalloc_lists(lib, cfg, 32)
+    assert again[4] == 26
