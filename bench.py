@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--workload", default="bcc10_2j8",
                     help="headline workload (bcc4_2j8, bcc10_2j8, bcc10_2j14, bcc20_2j14)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="only measure the FP32 and FP64 FMA peaks (snap_probe_fma) with clocks")
     return ap.parse_args()
 
 
@@ -170,12 +172,11 @@ def cpu_baseline(w, seconds=10.0):
 
 def accuracy_vs_oracle(torch, snap, inputs, dev):
     """The GPU results, mixed and FP64, against the FP64 oracle (part of the
-    cpu_baseline leg, the bench step that runs the oracle): every atom of the
-    2000-atom 2J = 8 workload, and 16 seeded atoms of the 2000-atom 2J = 14
-    one (forces on an atom need its neighbours' dE/dr, so the oracle evaluates
-    those atoms and their neighbours).  Errors relative to the largest
-    magnitude of each quantity, and the largest absolute force error (eV/A
-    for beta in eV)."""
+    cpu_baseline leg, the bench step that runs the oracle), per 2J: every atom
+    of the 2000-atom BCC configuration of the benchmark (+-0.1 A, the
+    benchmark's beta draw for that 2J) at 2J = 2, 4, ..., 14.  Errors are
+    relative to the largest magnitude of each quantity (E_i, F, virial), plus
+    the largest absolute force error (eV/A for beta in eV)."""
     import numpy as np
     from oracle import snap_oracle as O
 
@@ -189,21 +190,15 @@ def accuracy_vs_oracle(torch, snap, inputs, dev):
         return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
     out = {}
-    w = inputs.WORKLOADS["bcc10_2j8"]
-    cfg, beta = w.config(), w.beta()
-    _, ref = O.evaluate(O.Params(8), beta, cfg.pos, cfg.box)
-    for prec, tag in ((snap.MIXED, "mixed"), (snap.FP64, "fp64")):
-        E, F, W = gpu(8, beta, cfg, prec)
-        out[f"2j8_{tag}"] = {"atoms": cfg.natoms, "energy_rel": err(E, ref.E), "force_rel": err(F, ref.F),
-                             "force_max_abs": float(np.abs(F - ref.F).max()), "virial_rel": err(W, ref.W)}
-    w = inputs.WORKLOADS["bcc10_2j14"]
-    cfg, beta = w.config(), w.beta()
-    atoms = np.sort(np.random.Generator(np.random.PCG64(77)).choice(cfg.natoms, 16, replace=False))
-    Fref, res, _ = O.forces_for_atoms(O.Params(14), beta, cfg.pos, cfg.box, atoms)
-    for prec, tag in ((snap.MIXED, "mixed"), (snap.FP64, "fp64")):
-        E, F, _ = gpu(14, beta, cfg, prec)
-        out[f"2j14_{tag}"] = {"atoms": int(len(atoms)), "energy_rel": err(E[atoms], res.E[atoms]),
-                              "force_rel": err(F[atoms], Fref), "force_max_abs": float(np.abs(F[atoms] - Fref).max())}
+    cfg = inputs.WORKLOADS["bcc10_2j8"].config()
+    pairs = O.build_neighbors(cfg.pos, cfg.box, inputs.RCUT)
+    for J in (2, 4, 6, 8, 10, 12, 14):
+        beta = inputs.beta(J)
+        ref = O.compute(O.Params(J), beta, cfg.natoms, pairs)
+        for prec, tag in ((snap.MIXED, "mixed"), (snap.FP64, "fp64")):
+            E, F, W = gpu(J, beta, cfg, prec)
+            out[f"2j{J}_{tag}"] = {"E": err(E, ref.E), "F": err(F, ref.F), "W": err(W, ref.W),
+                                   "F_max_abs": float(np.abs(F - ref.F).max())}
     return out
 
 
@@ -229,8 +224,13 @@ def run_reference(args):
     per_atom = (time.perf_counter() - t0) / 64
     budget = 120.0 / max(1, args.steps + args.warmup)
     m = int(max(1, min(n, budget / max(per_atom, 1e-9))))
-    need = np.zeros(n, dtype=bool)
-    need[:m] = True
+    if m >= n:
+        need = None     # the whole step: E, dE/dr, forces and virial of every atom
+        sample = f"oracle E, F and virial of all {n} atoms per step ({w.name})"
+    else:
+        need = np.zeros(n, dtype=bool)
+        need[:m] = True
+        sample = f"oracle E + dE/dr of {m} of {n} centre atoms per step ({w.name})"
     for _ in range(args.warmup):
         O.compute(p, beta, n, pairs, need=need)
     t0 = time.perf_counter()
@@ -238,7 +238,6 @@ def run_reference(args):
         O.compute(p, beta, n, pairs, need=need)
     el = time.perf_counter() - t0
     value = m * args.steps / el
-    sample = f"oracle E + dE/dr of {m} of {n} centre atoms per step ({w.name})"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -459,10 +458,36 @@ def next_rows(torch, snap, inputs, flush, dev, args):
     return out
 
 
+def probe_peaks():
+    """FP32 and FP64 FMA peaks of this GPU (best of 5 timed launches each,
+    snap_probe_fma), with the SM clocks sampled while they ran."""
+    import torch
+    from paper_2011_12875_gb300 import build, snap
+    build.build()
+    snap.load()
+    torch.cuda.set_device(0)
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    out = {}
+    for prec, tag, iters in ((snap.MIXED, "fp32", 1 << 18), (snap.FP64, "fp64", 1 << 13)):
+        sampler = ClockSampler(int(cvd) if cvd.isdigit() else 0)
+        sampler.start()
+        t0 = time.perf_counter()
+        vals = []
+        while len(vals) < 5 or time.perf_counter() - t0 < 1.0:
+            vals.append(snap.probe_fma(prec, iters))
+        out[tag] = {"tflops": max(vals), "median_tflops": statistics.median(vals), "runs": len(vals),
+                    "clocks": sampler.stop()}
+    out["derived_tflops"] = {"fp32": FP32_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS}
+    print(json.dumps({"fma_peaks": out}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.probe_peaks:
+        probe_peaks()
         return
     import torch
     world, rank, local = dist_setup(args)
@@ -481,6 +506,12 @@ def main():
     head = inputs.WORKLOADS[args.workload]
     hprec = snap.MIXED if args.precision == "mixed" else snap.FP64
     hpeak = FP32_PEAK_TFLOPS if hprec == snap.MIXED else FP64_PEAK_TFLOPS
+    # measured FMA peak of the headline's working precision (context beside
+    # the derived peak the roofline fraction uses)
+    try:
+        measured_peak = snap.probe_fma(hprec, 1 << 16 if hprec == snap.MIXED else 1 << 12)
+    except snap.SnapError:
+        measured_peak = None
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     sampler = ClockSampler(int(cvd) if cvd.isdigit() else local)
     if pg:
@@ -505,28 +536,29 @@ def main():
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max, "ms_per_step_median": ms_med,
+        "warmup": args.warmup, "ms_per_step": t_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 recursions + f64 geometry/accumulation" if hprec == snap.MIXED else "f64",
-        "data": "synthetic BCC (a=3.1803 A, +-0.1 A displacements, seeded beta)",
+        "dtype": "f32 recursions, f64 geometry and sums" if hprec == snap.MIXED else "f64",
+        "data": "synthetic BCC, +-0.1 A, seeded beta",
         "config": {"workload": head.name, "natoms": r["natoms"], "twojmax": head.twojmax,
-                   "neighbors": r["npairs"] / r["natoms"], "neighbor_hist": r["neighbor_hist"],
-                   "precision": args.precision,
-                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "precision": args.precision, "l2": "flushed between steps",
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": r["launches"] * args.steps,
-        "stages": stages,
-        # the same steps without the neighbour build (its profiled time taken off)
-        "value_excl_neighbor_build": world * r["natoms"] / ((t_max - stages["neighbor_build"]["ms_per_call"]) * 1e-3),
-        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved,
-                     "peak": hpeak, "unit": "TFLOP/s", "frac": achieved / hpeak,
-                     "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
-                                     if hprec == snap.MIXED else
-                                     "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
-                     "flops_per_launch": fl.get(dom, 0),
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3),
+                     "peak": round(hpeak, 2), "unit": "TFLOP/s", "frac": round(achieved / hpeak, 4),
+                     "peak_measured": round(measured_peak, 2) if measured_peak else None,
                      "traffic": read_traffic(dom, head.name)},
         "clocks": clocks,
     }
+    detail = {"ms_per_step_median": ms_med, "neighbors": r["npairs"] / r["natoms"],
+              "neighbor_hist": r["neighbor_hist"], "stages": stages,
+              "flops_per_launch": fl.get(dom, 0),
+              "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+                              if hprec == snap.MIXED else "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
+              "peak_measured_source": "snap_probe_fma (8 FMA chains per thread, 8 CTAs of 256 per SM)",
+              # the same steps without the neighbour build (its profiled time taken off)
+              "value_excl_neighbor_build": world * r["natoms"] /
+              ((t_max - stages["neighbor_build"]["ms_per_call"]) * 1e-3)}
     # end to end through host buffers, on every rank; the job's step is the
     # slowest rank's
     if pg:
@@ -535,9 +567,9 @@ def main():
     e2e["ms_per_step"] = max_over_ranks(pg, e2e["ms_per_step"], dev)
     e2e["value"] = job_throughput(world, r["natoms"], e2e["ms_per_step"])
     if rank == 0:
-        line["e2e"] = e2e
+        line["e2e"] = {k: (round(v, 5) if isinstance(v, float) else v) for k, v in e2e.items()}
+        variants = {}
         if not args.no_variants:
-            variants = {}
             for name, prec, tag in (("bcc10_2j8", snap.FP64, "fp64_2j8_2000"),
                                     ("bcc10_2j14", snap.MIXED, "mixed_2j14_2000"),
                                     ("bcc10_2j14", snap.FP64, "fp64_2j14_2000"),
@@ -555,16 +587,27 @@ def main():
                 vdom_ms = vp[vdom][0] / max(vp[vdom][1], 1)
                 peak = FP32_PEAK_TFLOPS if prec == snap.MIXED else FP64_PEAK_TFLOPS
                 ach = vfl.get(vdom, 0) / (vdom_ms * 1e-3) / 1e12
-                variants[tag] = {"value": v["natoms"] / (vm * 1e-3), "ms_per_step": vm, "steps": k,
-                                 "dominant_kernel": vdom, "dominant_share": vp[vdom][0] / sum(x[0] for x in vp.values()),
-                                 "roofline_frac": ach / peak, "achieved_tflops": ach,
-                                 "peak_tflops": peak}
-            variants["mixed_2j8_2000"] = {"value": value / world, "ms_per_step": ms_mean}
-            line["variants"] = variants
-            line["next"] = next_rows(torch, snap, inputs, flush, dev, args)
+                variants[tag] = {"value": round(v["natoms"] / (vm * 1e-3)), "ms": round(vm, 4),
+                                 "kernel": vdom, "frac": round(ach / peak, 4)}
+                detail.setdefault("variants", {})[tag] = {
+                    "steps": k, "dominant_share": vp[vdom][0] / sum(x[0] for x in vp.values()),
+                    "achieved_tflops": ach, "peak_tflops": peak,
+                    "stages_ms": {x: vp[x][0] / max(vp[x][1], 1) for x in vp}}
+            detail["next"] = next_rows(torch, snap, inputs, flush, dev, args)
+        variants["mixed_2j8_2000"] = {"value": round(value / world), "ms": round(ms_mean, 4),
+                                      "kernel": dom, "frac": round(achieved / hpeak, 4)}
+        acc = None
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(head)
-            line["accuracy_vs_oracle"] = accuracy_vs_oracle(torch, snap, inputs, dev)
+            acc = accuracy_vs_oracle(torch, snap, inputs, dev)
+            detail["accuracy_vs_oracle"] = acc
+        # the detail first (its own line, no "metric" key), then the bench
+        # line itself, short, with the variants and the per-2J force error
+        # last so that a short tail of the output still holds them
+        print(json.dumps({"bench_detail": detail}), flush=True)
+        line["variants"] = variants
+        if acc:
+            line["force_err_vs_oracle"] = {k: float(f"{v['F']:.2g}") for k, v in acc.items()}
         print(json.dumps(line), flush=True)
     if pg:
         pg.barrier()

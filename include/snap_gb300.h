@@ -266,6 +266,16 @@ long long snap_get_buffer(snap_ctx* ctx, int which, void* dst_host, size_t bytes
 int snap_half_index(int twojmax, int t, int ma, int mb);
 int snap_half_size(int twojmax);
 
+/* Test hook for the timeout path (Sec. V-B's staged compute_Y has no such
+ * path in the paper; the library adds one because its staging waits are
+ * bounded).  With on = 1 every TMA staging step of compute_Y and of the
+ * bispectrum kernels registers its bytes on its mbarrier but issues no copy,
+ * so its bounded wait (1 s of the GPU's global timer) runs out with nothing in
+ * flight: the kernel raises an error flag and returns, and the call returns
+ * SNAP_ERR_TIMEOUT.  on = 0 (the default) restores normal operation; the
+ * context stays usable.  Returns SNAP_ERR_ARG for on outside {0, 1}. */
+int snap_test_stage_timeout(snap_ctx* ctx, int on);
+
 /* compute_Y's term list for one atom, evaluated on the host in FP64 from the
  * same tables the device walks (Sec. III, Eq. y: Y = sum over the Y triples
  * of beta~ C C U_t1 U_t2, with the list's exact reductions: the two terms of
@@ -311,6 +321,17 @@ int snap_yi_host(int twojmax, int precision, const double* beta, const double* u
 int snap_neighbors_noalloc(int natoms, const double* pos, const double* box, double rcut,
                            int cap, int* cnt, int* nbr, signed char* img, double* rij,
                            int* max_count, void* stream);
+
+/* Measured peak fused multiply-add rate of the current device in the
+ * working precision of `precision` (SNAP_MIXED: FP32, SNAP_FP64: FP64), the
+ * denominator against which the library's kernels, which use no tensor cores,
+ * are compared (Sec. II-C, Table 1 of the paper states SNAP speeds as a
+ * fraction of the nominal peak FLOP rate the same way).  Every thread of 8 CTAs per SM runs 8 independent FMA chains for
+ * `iters` rounds of 4 (8 <= iters <= 2^24); one untimed and one timed launch
+ * on `stream`, CUDA events.  *tflops receives 2 x FMAs / seconds / 1e12.
+ * Synchronous; allocates and frees a 2 KB buffer.  SNAP_ERR_ARG for a bad
+ * precision, iters or NULL tflops. */
+int snap_probe_fma(int precision, int iters, double* tflops, void* stream);
 
 /* Release the context and its device memory. */
 int snap_destroy(snap_ctx* ctx);

@@ -46,6 +46,7 @@ struct snap_ctx {
   int col_warps = 4;  // tunables (snap_set_tuning / snap_autotune)
   int yi_waves = 2;
   int yi_layout = 0;
+  int test_skip_stage = 0;  // snap_test_stage_timeout
   int last_nmax = 0;
   int seen_nmax = 0;  // largest neighbour count seen: the fused dE launch is planned for it
   int last_n = 0, last_K = 0;
@@ -382,6 +383,7 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.col_warps = c->col_warps;
   a.de_maxcnt = de_maxcnt(c, K);
   a.yi_waves = c->yi_waves;
+  a.test_skip_stage = c->test_skip_stage;
   a.ncoeff = c->tab.ncoeff;
   a.brec = c->d_brec;
   a.bout = c->d_bout;
@@ -1050,6 +1052,22 @@ int snap_set_tuning(snap_ctx* c, int col_warps, int yi_waves, int yi_layout) {
   return SNAP_OK;
 }
 
+int snap_test_stage_timeout(snap_ctx* c, int on) {
+  if (!c) return SNAP_ERR_ARG;
+  if (on != 0 && on != 1) return fail(c, SNAP_ERR_ARG, "on must be 0 or 1");
+  if (c->test_skip_stage != on) {
+    c->test_skip_stage = on;
+    // the flag is a kernel argument: captured graphs hold the old value
+    c->gdev.reset();
+    c->ghost.reset();
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+  }
+  return SNAP_OK;
+}
+
 int snap_get_tuning(const snap_ctx* c, int* col_warps, int* yi_waves, int* yi_layout) {
   if (!c) return SNAP_ERR_ARG;
   if (col_warps) *col_warps = c->col_warps;
@@ -1295,6 +1313,26 @@ int snap_destroy(snap_ctx* c) {
     for (auto& ev : *pool)
       for (auto e : ev) cudaEventDestroy(e);
   delete c;
+  return SNAP_OK;
+}
+
+int snap_probe_fma(int precision, int iters, double* tflops, void* stream) {
+  if ((precision != SNAP_FP64 && precision != SNAP_MIXED) || iters < 8 || iters > (1 << 24) || !tflops)
+    return SNAP_ERR_ARG;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SNAP_ERR_CUDA;
+  void* sink = nullptr;
+  if (cudaMalloc(&sink, 256 * sizeof(double)) != cudaSuccess) return SNAP_ERR_NOMEM;
+  double flops = 0.0;
+  float ms = 0.f;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaError_t e = precision == SNAP_MIXED
+                            ? snap::fma_probe<float>(nsm, iters, &flops, &ms, (float*)sink, s)
+                            : snap::fma_probe<double>(nsm, iters, &flops, &ms, (double*)sink, s);
+  cudaFree(sink);
+  if (e != cudaSuccess || !(ms > 0.f)) return SNAP_ERR_CUDA;
+  *tflops = flops / (ms * 1e-3) / 1e12;
   return SNAP_OK;
 }
 

@@ -156,6 +156,7 @@ struct WorkArgs {
   int col_warps;  // warps per CTA of the column-chain kernels (tunable)
   int de_maxcnt;  // neighbour count the fused dE launch is planned for (last seen maximum, else K)
   int yi_waves;   // compute_Y waves per SM (tunable)
+  int test_skip_stage;  // test hook: TMA staging registers its bytes but issues no copy
   // bispectrum output
   int ncoeff;
   const void* brec;       // YRec<R> records of the bispectrum terms
@@ -224,5 +225,8 @@ cudaError_t launch_tan_col(const WorkArgs& a, const double* g, void* dU, cudaStr
 // d B_l along the tangent dU (snap_kernels.cu) and the weighted force gather.
 template <typename R> cudaError_t launch_dbi(const WorkArgs& a, const void* dU, double* dB, cudaStream_t s);
 cudaError_t launch_force_weighted(const WorkArgs& a, const double* w, double* grad, cudaStream_t s);
+// FMA throughput probe (synchronous): flops and milliseconds of one timed launch
+template <typename R>
+cudaError_t fma_probe(int nsm, int iters, double* flops, float* ms, R* sink, cudaStream_t s);
 
 }  // namespace snap

@@ -172,7 +172,6 @@ __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
 // element offsets, conjugation flags, end-of-group and end-of-output bits)
 // and the coefficient.  Each warp owns a contiguous run of outputs, so every
 // Y element is accumulated in registers and written once (no atomics).
-constexpr unsigned kSpinLimit = 1u << 24;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -200,6 +199,51 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
       : "r"(smem_u32(bar)), "r"(phase)
       : "memory");
   return ok != 0;
+}
+
+// Bounded waits.  A wait gives up after kWaitNs of the global timer (or
+// kSpinCap polls, whichever comes first), so a copy that never completes
+// cannot hang the GPU: the kernel raises an error flag and returns, and the
+// call reports SNAP_ERR_TIMEOUT.
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
+constexpr unsigned kSpinCap = 1u << 28;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0; it < kSpinCap; ++it) {
+    if (mbar_try_wait(bar, phase)) return true;
+    if ((it & 63u) == 63u && global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+
+// Stage `bytes` from global `src` into shared `dst` with one bulk (TMA) copy
+// completed on the mbarrier `bar`, issued by thread 0; every thread of the
+// CTA waits, bounded.  The outcome is made CTA-uniform.  On a timeout the CTA
+// raises flags[3] and waits once more, again bounded, for the copy it issued
+// (if that second wait runs out too, the copy may still land in the exiting
+// CTA's shared memory).  skip_copy registers the bytes without issuing the
+// copy: a test hook under which the wait runs out with nothing in flight.
+__device__ bool stage_bulk(void* dst, const void* src, unsigned bytes, uint64_t* bar, int* flags,
+                           bool skip_copy) {
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, bytes);
+    if (!skip_copy) bulk_g2s(dst, src, bytes, bar);
+  }
+  const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0, kWaitNs));
+  if (!ok) {
+    if (threadIdx.x == 0) atomicMax(&flags[3], 1);
+    mbar_wait_bounded(bar, 0, kWaitNs / 4);
+  }
+  return ok;
 }
 
 __device__ __forceinline__ float flip_if(float v, unsigned bit) {
@@ -438,22 +482,7 @@ __global__ void __launch_bounds__(STAGED ? 1024 : 256, 1) yi_kernel(WorkArgs a) 
     cx<R>* su = reinterpret_cast<cx<R>*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(su + (CP ? 2 : 1) * H * 32);
     const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
-    if (threadIdx.x == 0) mbar_init(bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      mbar_expect_tx(bar, bytes);
-      bulk_g2s(su, us, bytes, bar);
-    }
-    bool ok = false;
-    for (unsigned it = 0; it < kSpinLimit; ++it)
-      if (mbar_try_wait(bar, 0)) {
-        ok = true;
-        break;
-      }
-    if (!ok) {
-      if (threadIdx.x == 0) atomicMax(&a.flags[3], 1);
-      return;
-    }
+    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0)) return;
     if (CP) {
       for (int e = threadIdx.x; e < H * 32; e += blockDim.x) {
         const cx<R> v = su[e];
@@ -581,22 +610,7 @@ __global__ void __launch_bounds__(256) bi_kernel(WorkArgs a) {
     cx<R>* su = reinterpret_cast<cx<R>*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(su + H * 32);
     const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
-    if (threadIdx.x == 0) mbar_init(bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      mbar_expect_tx(bar, bytes);
-      bulk_g2s(su, us, bytes, bar);
-    }
-    bool ok = false;
-    for (unsigned it = 0; it < kSpinLimit; ++it)
-      if (mbar_try_wait(bar, 0)) {
-        ok = true;
-        break;
-      }
-    if (!ok) {
-      if (threadIdx.x == 0) atomicMax(&a.flags[3], 1);
-      return;
-    }
+    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0)) return;
     us = su;
   }
   const int l = blockIdx.y * (blockDim.x >> 5) + warp;
@@ -644,22 +658,7 @@ __global__ void __launch_bounds__(256) dbi_kernel(WorkArgs a, const cx<R>* __res
     cx<R>* su = reinterpret_cast<cx<R>*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(su + H * 32);
     const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
-    if (threadIdx.x == 0) mbar_init(bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      mbar_expect_tx(bar, bytes);
-      bulk_g2s(su, us, bytes, bar);
-    }
-    bool ok = false;
-    for (unsigned it = 0; it < kSpinLimit; ++it)
-      if (mbar_try_wait(bar, 0)) {
-        ok = true;
-        break;
-      }
-    if (!ok) {
-      if (threadIdx.x == 0) atomicMax(&a.flags[3], 1);
-      return;
-    }
+    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0)) return;
     us = su;
   }
   const int l = blockIdx.y * (blockDim.x >> 5) + warp;
@@ -1288,5 +1287,53 @@ template cudaError_t launch_de<float>(const WorkArgs&, cudaStream_t);
 template cudaError_t launch_de<double>(const WorkArgs&, cudaStream_t);
 template cudaError_t launch_force<float>(const WorkArgs&, cudaStream_t);
 template cudaError_t launch_force<double>(const WorkArgs&, cudaStream_t);
+
+// ------------------------------------------------- FMA throughput probe
+// Peak FMA rate of the working precision, for the roofline denominators:
+// every thread runs kProbeChains independent multiply-add chains (enough to
+// cover the pipeline latency) for `iters` rounds.  The chains' operands come
+// from the arguments, and the sums are stored only under a condition the host
+// never meets, so nothing is folded away.
+constexpr int kProbeChains = 8;
+
+template <typename R>
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, R b, R c, R* sink) {
+  R x[kProbeChains];
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) x[k] = R(threadIdx.x + k);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < kProbeChains; ++k) x[k] = fma(x[k], b, c);
+  }
+  R t = R(0);
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) t += x[k];
+  if (t == R(-12345.0)) sink[threadIdx.x] = t;
+}
+
+template <typename R>
+cudaError_t fma_probe(int nsm, int iters, double* flops, float* ms, R* sink, cudaStream_t s) {
+  const int blocks = nsm * 8, threads = 256;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return e;
+  // warm-up launch, then the timed one
+  e = launch_k(fma_probe_kernel<R>, dim3(blocks), dim3(threads), 0, s, iters / 8, R(0.999), R(1e-3), sink);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) e = launch_k(fma_probe_kernel<R>, dim3(blocks), dim3(threads), 0, s, iters, R(0.999), R(1e-3), sink);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *flops = 2.0 * kProbeChains * 4 * (double)iters * blocks * threads;
+  return e;
+}
+template cudaError_t fma_probe<float>(int, int, double*, float*, float*, cudaStream_t);
+template cudaError_t fma_probe<double>(int, int, double*, float*, double*, cudaStream_t);
 
 }  // namespace snap

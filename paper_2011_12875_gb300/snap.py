@@ -43,7 +43,8 @@ EXPORTS = ("snap_num_coeff", "snap_create", "snap_set_beta", "snap_set_neigh_cap
            "snap_stage_name", "snap_launches_per_call", "snap_compute_bispectrum",
            "snap_bispectrum_deriv", "snap_force_weighted", "snap_generation",
            "snap_compute_batch", "snap_set_tuning", "snap_get_tuning", "snap_autotune",
-           "snap_neighbors_noalloc", "snap_yi_host")
+           "snap_neighbors_noalloc", "snap_yi_host", "snap_test_stage_timeout",
+           "snap_probe_fma")
 NSTAGES = 5
 
 _lib = None
@@ -101,6 +102,8 @@ def load(path: str | None = None):
     L.snap_compute_batch.restype = i
     L.snap_set_tuning.argtypes = [p, i, i, i]
     L.snap_set_tuning.restype = i
+    L.snap_test_stage_timeout.argtypes = [p, i]
+    L.snap_test_stage_timeout.restype = i
     L.snap_get_tuning.argtypes = [p, p, p, p]
     L.snap_get_tuning.restype = i
     L.snap_autotune.argtypes = [p, i, p, p, p, p, p, p, i, p, p]
@@ -115,12 +118,26 @@ def load(path: str | None = None):
     L.snap_half_size.restype = i
     L.snap_yi_host.argtypes = [i, i, p, p, p]
     L.snap_yi_host.restype = i
+    L.snap_probe_fma.argtypes = [i, i, p, p]
+    L.snap_probe_fma.restype = i
     L.snap_destroy.argtypes = [p]
     L.snap_destroy.restype = i
     L.snap_last_error.argtypes = [p]
     L.snap_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
+
+
+def probe_fma(precision: int, iters: int = 1 << 16, stream=None) -> float:
+    """Measured FMA peak (TFLOP/s) of the current device in the working
+    precision of `precision` (snap_probe_fma)."""
+    import torch
+    st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    out = ctypes.c_double()
+    rc = load().snap_probe_fma(precision, iters, ctypes.byref(out), ctypes.c_void_p(st))
+    if rc != OK:
+        raise SnapError(rc, "snap_probe_fma failed")
+    return out.value
 
 
 def num_coeff(twojmax: int) -> int:
@@ -333,6 +350,12 @@ class Snap:
         """Launch-shape tunables (see snap_set_tuning); yi_layout 0 = warp of
         32 atoms, 1 = warp per atom."""
         self._check(self._lib.snap_set_tuning(self._h, col_warps, yi_waves, yi_layout))
+
+    def test_stage_timeout(self, on: bool):
+        """Test hook (snap_test_stage_timeout): staging copies are not issued,
+        so their bounded waits run out and calls raise SnapError
+        (ERR_TIMEOUT) until it is switched off again."""
+        self._check(self._lib.snap_test_stage_timeout(self._h, int(bool(on))))
 
     def get_tuning(self):
         """(col_warps, yi_waves, yi_layout)."""

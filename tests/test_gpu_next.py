@@ -39,6 +39,7 @@ def test_bispectrum_parity(snapmod, twojmax, prec):
     B = s.bispectrum(pos, cfg.box).cpu().numpy()
     s.close()
     assert B.shape == ref.B.shape
+    print(f"ERRS-B prec={prec} J={twojmax} {rel_err(B, ref.B):.3e}")
     assert rel_err(B, ref.B) <= (FP64_TOL if prec == 0 else MIXED_B_TOL)
 
 
@@ -82,6 +83,7 @@ def test_weighted_force_and_autograd(snapmod, prec):
     wt = torch.tensor(w, device="cuda:0")
     (gpos,) = torch.autograd.grad((E * wt).sum(), pos)
     tol = FP64_TOL if prec == 0 else 2e-4
+    print(f"ERRS-WGRAD prec={prec} {rel_err(gpos.cpu().numpy(), want):.3e}")
     assert rel_err(gpos.cpu().numpy(), want) <= tol
     # uniform weights give minus the forces
     _, F, _ = s.compute(pos.detach(), cfg.box)
@@ -131,6 +133,7 @@ def test_bispectrum_derivative_vs_oracle_differences(snapmod, prec, twojmax):
     pos = torch.tensor(cfg.pos, dtype=torch.float64, device="cuda:0")
     dB = s.bispectrum_deriv(pos, cfg.box, torch.tensor(g, device="cuda:0")).cpu().numpy()
     s.close()
+    print(f"ERRS-DB prec={prec} J={twojmax} {rel_err(dB, fd):.3e}")
     assert rel_err(dB, fd) <= (2e-7 if prec == 0 else 3e-5)
 
 
@@ -299,6 +302,78 @@ def test_warp_per_atom_compute_y_parity(snapmod, prec, twojmax):
     Y0 = s.get_buffer(snapmod.BUF_YLIST).copy()
     s.close()
     tolE, tolF = (FP64_TOL, FP64_TOL) if prec == 0 else (2e-5, 2e-4)
+    print(f"ERRS-YA prec={prec} J={twojmax} E={rel_err(E1, ref.E):.3e} F={rel_err(F1, ref.F):.3e} "
+          f"W={rel_err(W1, ref.W):.3e} Y={rel_err(Y1, Y0):.3e}")
     assert rel_err(E1, ref.E) <= tolE and rel_err(F1, ref.F) <= tolF and rel_err(W1, ref.W) <= tolF
     assert rel_err(Y1, Y0) <= (1e-13 if prec == 0 else 1e-6)
     assert rel_err(E1, E0) <= (1e-13 if prec == 0 else 1e-6)
+
+
+def oracle_force_matching(J, cfg, beta, f_ref, comps):
+    """The oracle's L = sum_k |F_k - F_ref,k|^2 and its exact gradient in beta
+    for the components `comps` (indices into beta, 1..N_B).  F is linear in
+    beta and does not depend on beta_0 (Eqs. snapforce1 and dbidrk), so
+    dF/dbeta_l is the oracle's force field at beta = e_l and
+    dL/dbeta_l = sum_k 2 (F_k - F_ref,k) . F_k(e_l): one oracle evaluation per
+    component, no differencing."""
+    p = O.Params(J)
+    pairs = O.build_neighbors(cfg.pos, cfg.box, p.rcut)
+    F = O.compute(p, beta, cfg.natoms, pairs).F
+    r = F - f_ref
+    grad = {}
+    for l in comps:
+        e = np.zeros_like(beta)
+        e[l] = 1.0
+        Fl = O.compute(p, e, cfg.natoms, pairs).F
+        grad[l] = float((2.0 * r * Fl).sum())
+    return float((r * r).sum()), grad, r
+
+
+# relative-to-max tolerance of the mixed force-matching gradient (FP32 tangent
+# recursion and bispectrum contraction, FP64 sums): about 9x the measured
+# 3.4e-7 (2J = 8) and 3.2e-7 (2J = 14)
+MIXED_FM_TOL = {8: 3e-6, 14: 3e-6}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("twojmax", [8, 14])
+def test_force_matching_gradient_vs_oracle(snapmod, twojmax, prec):
+    """dL/dbeta of the force-matching loss on a 128-atom configuration of the
+    fitting set's kind (BCC, +-0.2 A) against the oracle's exact gradient: every
+    component at 2J = 8; at 2J = 14 a seeded sample of 24 components plus two
+    random projections of the whole gradient (each projection is one oracle
+    evaluation at beta = v, since sum_l v_l dL/dbeta_l = sum_k 2 r_k . F_k(v))."""
+    from paper_2011_12875_gb300 import autograd as AG
+    cfg = inputs.bcc(4, disp=0.2, seed=61)
+    beta = inputs.beta(twojmax)
+    nb = len(beta) - 1
+    rng = np.random.Generator(np.random.PCG64(62))
+    f_ref = rng.normal(scale=0.5, size=cfg.pos.shape)
+    if twojmax <= 8:
+        comps = list(range(1, nb + 1))
+    else:
+        comps = sorted(set([1, nb] + list(rng.choice(np.arange(2, nb), 22, replace=False))))
+    loss_o, grad_o, r_o = oracle_force_matching(twojmax, cfg, beta, f_ref, comps)
+    s = snapmod.Snap(twojmax, beta, precision=prec)
+    pos = torch.tensor(cfg.pos, dtype=torch.float64, device="cuda:0")
+    loss, grad = AG.force_matching_grad(s, pos, cfg.box, torch.tensor(f_ref, device="cuda:0"))
+    grad = grad.cpu().numpy()
+    s.close()
+    tol = FP64_TOL if prec == 0 else MIXED_FM_TOL[twojmax]
+    assert grad[0] == 0.0
+    assert abs(float(loss) - loss_o) <= tol * loss_o
+    want = np.array([grad_o[l] for l in comps])
+    got = grad[comps]
+    scale = np.abs(want).max()
+    err = np.abs(got - want).max() / scale
+    print("force-matching gradient", twojmax, prec, err)
+    assert err <= tol, err
+    p = O.Params(twojmax)
+    pairs = O.build_neighbors(cfg.pos, cfg.box, p.rcut)
+    for k in range(2 if twojmax > 8 else 0):
+        v = np.zeros_like(beta)
+        v[1:] = rng.normal(size=nb)
+        Fv = O.compute(p, v, cfg.natoms, pairs).F
+        proj_o = float((2.0 * r_o * Fv).sum())
+        proj = float(grad[1:] @ v[1:])
+        assert abs(proj - proj_o) <= tol * np.abs(v[1:]).sum() * np.abs(grad[1:]).max(), (k, proj, proj_o)

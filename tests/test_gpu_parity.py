@@ -3,7 +3,8 @@
 FP64 path: 1e-10 relative (to the largest magnitude of each quantity) on
 Ulisttot, Y, dE/dr per pair, E_i, F and the virial; neighbour lists exact.
 Mixed path (FP32 recursions, FP64 geometry and accumulation): the tolerances
-below, measured per quantity and per 2J (Table MIXED_TOL).
+below, per quantity and per 2J (table MIXED_TOL, derived from measured
+errors).
 """
 import numpy as np
 import pytest
@@ -16,9 +17,31 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
-# relative-to-max tolerance of the mixed path: (U, Y, dedr, E, F, W)
+# Relative-to-max tolerance of the mixed path (FP32 recursions, FP64
+# Cayley-Klein parameters and sums), per 2J and per result: Ulisttot, Y,
+# dE_i/dr_ik per pair, E_i, F and W.  Each limit is 8x the largest error
+# measured against the oracle at that 2J or a neighbouring one (the 16-atom
+# small-box configuration below at every 2J, 54 and 432 atoms where tested,
+# and all 2000 atoms of the benchmark configuration at every even 2J), rounded
+# up to 1, 2 or 5 x 10^k.  The measured values are tabulated in the design
+# notes; they are FP32 rounding (about 1e-7 on U, growing to about 1e-6 on Y,
+# dE/dr and F with the depth of the recursion).
 MIXED_TOL = {
-    "U": 2e-6, "Y": 2e-5, "dedr": 2e-4, "E": 2e-5, "F": 2e-4, "W": 2e-4,
+    0: {"U": 2e-06, "Y": 5e-06, "dedr": 5e-06, "E": 5e-06, "F": 2e-05, "W": 5e-07},
+    1: {"U": 2e-06, "Y": 5e-06, "dedr": 1e-05, "E": 1e-05, "F": 2e-05, "W": 5e-07},
+    2: {"U": 2e-06, "Y": 5e-06, "dedr": 1e-05, "E": 1e-05, "F": 1e-05, "W": 5e-07},
+    3: {"U": 2e-06, "Y": 5e-06, "dedr": 1e-05, "E": 1e-05, "F": 2e-05, "W": 1e-06},
+    4: {"U": 2e-06, "Y": 5e-06, "dedr": 5e-06, "E": 5e-06, "F": 2e-05, "W": 1e-06},
+    5: {"U": 2e-06, "Y": 5e-06, "dedr": 5e-06, "E": 5e-06, "F": 2e-05, "W": 2e-06},
+    6: {"U": 1e-06, "Y": 5e-06, "dedr": 5e-06, "E": 5e-06, "F": 2e-05, "W": 2e-06},
+    7: {"U": 1e-06, "Y": 2e-05, "dedr": 1e-05, "E": 1e-05, "F": 2e-05, "W": 5e-06},
+    8: {"U": 1e-06, "Y": 2e-05, "dedr": 1e-05, "E": 1e-05, "F": 1e-05, "W": 1e-05},
+    9: {"U": 1e-06, "Y": 2e-05, "dedr": 1e-05, "E": 1e-05, "F": 2e-05, "W": 1e-05},
+    10: {"U": 1e-06, "Y": 1e-05, "dedr": 1e-05, "E": 5e-06, "F": 2e-05, "W": 1e-05},
+    11: {"U": 1e-06, "Y": 1e-05, "dedr": 1e-05, "E": 5e-06, "F": 5e-05, "W": 5e-06},
+    12: {"U": 1e-06, "Y": 1e-05, "dedr": 1e-05, "E": 5e-06, "F": 5e-05, "W": 5e-06},
+    13: {"U": 1e-06, "Y": 2e-05, "dedr": 2e-05, "E": 5e-05, "F": 5e-05, "W": 5e-06},
+    14: {"U": 1e-06, "Y": 2e-05, "dedr": 2e-05, "E": 5e-05, "F": 2e-05, "W": 5e-06},
 }
 
 
@@ -62,8 +85,9 @@ def full_check(snapmod, twojmax, cfg, precision, beta=None, tol=None, params=Non
         "F": rel_err(F, ref.F), "W": rel_err(W, ref.W),
     }
     s.close()
+    print(f"ERRS prec={precision} J={twojmax} n={n}", " ".join(f"{k}={v:.3e}" for k, v in errs.items()))
     for key, e in errs.items():
-        lim = FP64_TOL if precision == snapmod.FP64 else (tol or MIXED_TOL)[key]
+        lim = FP64_TOL if precision == snapmod.FP64 else (tol or MIXED_TOL[twojmax])[key]
         assert e <= lim, (key, e, errs)
     return errs
 
@@ -145,9 +169,9 @@ def test_unwrapped_positions(snapmod, prec):
     s.close()
     assert np.array_equal(cnt, np.bincount(pairs.i, minlength=cfg.natoms))
     tol = FP64_TOL if prec == snapmod.FP64 else None
-    assert rel_err(E, ref.E) <= (tol or MIXED_TOL["E"])
-    assert rel_err(F, ref.F) <= (tol or MIXED_TOL["F"])
-    assert rel_err(W, ref.W) <= (tol or MIXED_TOL["W"])
+    assert rel_err(E, ref.E) <= (tol or MIXED_TOL[4]["E"])
+    assert rel_err(F, ref.F) <= (tol or MIXED_TOL[4]["F"])
+    assert rel_err(W, ref.W) <= (tol or MIXED_TOL[4]["W"])
 
 
 def test_tile_culling_on_spatial_order_large(snapmod):
@@ -201,19 +225,24 @@ def test_full_size_workloads(snapmod, name, prec, natoms_sample):
     s, E, F, W = run_gpu(snapmod, w.twojmax, beta, cfg, prec)
     s.close()
     n = cfg.natoms
-    tol = FP64_TOL if prec == 0 else MIXED_TOL["F"]
+    mt = MIXED_TOL[w.twojmax]
+    tol = FP64_TOL if prec == 0 else mt["F"]
     if natoms_sample >= n:
         _, ref = O.evaluate(p, beta, cfg.pos, cfg.box)
-        assert rel_err(E, ref.E) <= (FP64_TOL if prec == 0 else MIXED_TOL["E"])
+        print(f"ERRS-FULL prec={prec} {name} E={rel_err(E, ref.E):.3e} F={rel_err(F, ref.F):.3e} "
+              f"W={rel_err(W, ref.W):.3e}")
+        assert rel_err(E, ref.E) <= (FP64_TOL if prec == 0 else mt["E"])
         assert rel_err(F, ref.F) <= tol
-        assert rel_err(W, ref.W) <= (FP64_TOL if prec == 0 else MIXED_TOL["W"])
+        assert rel_err(W, ref.W) <= (FP64_TOL if prec == 0 else mt["W"])
     else:
         g = np.random.Generator(np.random.PCG64(77))
         atoms = np.sort(g.choice(n, natoms_sample, replace=False))
         Fs, res, _ = O.forces_for_atoms(p, beta, cfg.pos, cfg.box, atoms)
         scale = np.abs(F).max()
+        print(f"ERRS-SAMPLE prec={prec} {name} F={np.abs(F[atoms] - Fs).max() / scale:.3e} "
+              f"E={np.abs(E[atoms] - res.E[atoms]).max() / np.abs(res.E[atoms]).max():.3e}")
         assert np.abs(F[atoms] - Fs).max() <= tol * scale
-        etol = FP64_TOL if prec == 0 else MIXED_TOL["E"]
+        etol = FP64_TOL if prec == 0 else mt["E"]
         assert np.abs(E[atoms] - res.E[atoms]).max() <= etol * np.abs(res.E[atoms]).max()
     assert np.abs(F.sum(0)).max() <= (1e-9 if prec == 0 else 1e-5) * np.abs(F).max() * np.sqrt(n)
 
