@@ -355,6 +355,12 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.rfac0 = c->rfac0;
   a.rmin0 = c->rmin0;
   a.inv_span = 1.0 / (c->rcut - c->rmin0);
+  a.th_scale = c->rfac0 * a.inv_span;
+  a.th_scale_f = (float)a.th_scale;
+  a.dth_f = (float)(M_PI * a.th_scale);
+  a.inv_span_f = (float)a.inv_span;
+  a.rmin0_f = (float)c->rmin0;
+  a.dfc_f = (float)(-0.5 * M_PI * a.inv_span);
   a.wself = c->wself;
   a.beta0 = c->beta[0];
   a.switchflag = c->switchflag;

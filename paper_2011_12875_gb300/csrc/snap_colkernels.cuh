@@ -109,96 +109,230 @@ __device__ __forceinline__ void seed_column(c2<R> (&v)[N], bool take) {
   }
 }
 
-// ------------------------------------------------------------- compute_U
-// First the atom's slot geometry and reverse-slot map (snap_geom.cuh), then
-// the recursion.  Warp = one atom (the CTA's warps are independent atoms, so no CTA-wide
-// barrier and no idle warps when the pair count is not a multiple of the
-// CTA's pairs); the warp takes P pairs at a time.  Pair group g sums f_c u_t
-// of pairs g, g + P, ... into its own shared-memory copy of Ulisttot (no two
-// lanes write one address) and the P copies are added in a fixed order, so
-// the result does not depend on the launch shape.
+// ------------------------------------------- scaled layer recursion
+// With u_t[ma][mb] = S_t(ma, mb) v_t[ma][mb], S_t(ma, mb) =
+// sqrt((t - ma)! ma! / (t - mb)!), the recursion of Eq. (hysphrecur) becomes
+//   v_t[ma] = conj(a) v_{t-1}[ma] - conj(b) v_{t-1}[ma-1]
+// (S_t(ma, mb) = sqrt((t-ma)/(t-mb)) S_{t-1}(ma, mb) = sqrt(ma/(t-mb))
+// S_{t-1}(ma-1, mb) absorbs both root factors): 8 real operations an element
+// instead of 12.  S splits into sqrt((t - ma)! ma!), a constant of the
+// unrolled element, and 1 / sqrt((t - mb)!), one value per lane and layer.
+// The mirror that seeds column mc at layer 2 mc - 1 picks up S's ratio
+// between the two columns, 1 / sqrt(mc).
+__host__ __device__ constexpr double c_fact(int n) { return n <= 1 ? 1.0 : n * c_fact(n - 1); }
+__host__ __device__ constexpr double c_sqrt_iter(double x, double y, int k) {
+  return k == 0 ? y : c_sqrt_iter(x, 0.5 * (y + x / y), k - 1);
+}
+// square root of x >= 1 by Newton's iteration from x (64 steps: converged
+// for every argument below 2^64)
+__host__ __device__ constexpr double c_sqrt(double x) { return x <= 1.0 ? 1.0 : c_sqrt_iter(x, x, 64); }
+template <int T, int MA>
+__host__ __device__ constexpr double v_scale() { return c_sqrt(c_fact(T - MA) * c_fact(MA)); }
+
+// One layer of the scaled recursion on a lane's column, in place, ma
+// descending; A = conj(a), B = conj(b).
+template <typename R, int T, int N>
+__device__ __forceinline__ void v_layer(c2<R> (&v)[N], const c2<R> A, const c2<R> B) {
+  static_assert(T < N, "column too short");
+  c2<R> w = mk<R>(-(B.re * v[T - 1].re - B.im * v[T - 1].im), -(B.re * v[T - 1].im + B.im * v[T - 1].re));
+  v[T] = w;
+#pragma unroll
+  for (int ma = T - 1; ma >= 1; --ma) {
+    w.re = (A.re * v[ma].re - A.im * v[ma].im) - (B.re * v[ma - 1].re - B.im * v[ma - 1].im);
+    w.im = (A.re * v[ma].im + A.im * v[ma].re) - (B.re * v[ma - 1].im + B.im * v[ma - 1].re);
+    v[ma] = w;
+  }
+  v[0] = mk<R>(A.re * v[0].re - A.im * v[0].im, A.re * v[0].im + A.im * v[0].re);
+}
+
+// Seed of column T / 2 (lanes with take) for layer T - 1 in the scaled form:
+// the mirror of the column one lane below, times 1 / sqrt(T / 2).
+template <typename R, int T, int N>
+__device__ __forceinline__ void v_seed(c2<R> (&v)[N], bool take) {
+  constexpr int mc = T / 2;
+  constexpr double qd = 1.0 / c_sqrt(double(mc));
+  const R q = R(qd);
+  c2<R> src[T];
+#pragma unroll
+  for (int k = 0; k < T; ++k) {
+    src[k].re = shfl_up(v[k].re);
+    src[k].im = shfl_up(v[k].im);
+  }
+  if (take) {
+#pragma unroll
+    for (int m = 0; m < T; ++m) {
+      const R sq = (((T - 1 - m) + (mc - 1)) & 1) ? -q : q;
+      v[m] = mk<R>(sq * src[T - 1 - m].re, -sq * src[T - 1 - m].im);
+    }
+  }
+}
+
+// 1 / sqrt((t - mb)!) for t = 0..J2 (0 below mb), once per warp.
 template <typename R, int J2>
-__global__ void __launch_bounds__(256) ui_col_kernel(WorkArgs a) {
+__device__ __forceinline__ void v_gscale(R (&gs)[J2 + 1], int mb) {
+  R f = R(1);
+  const R mbr = R(mb);
+#pragma unroll
+  for (int t = 0; t <= J2; ++t) {
+    if (t > mb) f *= R(t) - mbr;
+    gs[t] = (t >= mb) ? R(1) / sqrt(f) : R(0);
+  }
+}
+
+// ------------------------------------------------------------- compute_U
+// An atom's pairs are taken in passes of P pairs (a lane per column of a
+// pair); f_c u_t of a pass is summed over its pair groups in two steps:
+//  * LV levels of shuffles first add the groups g, g + 1, ..., g + 2^LV - 1
+//    on the lanes of group g (a multiple of 2^LV), which leaves
+//    CPW = ceil(P / 2^LV) partial sums of each element;
+//  * those lanes store their partial sums (CPW copies of the half matrix) in
+//    the warp's scratch, and after the pass each lane adds the copies of the
+//    elements e = lane, lane + 32, ... to the warp's running sum.
+// LV is the fewest levels that keep the scratch under 4 KB in FP32 (2J = 8:
+// one level, three copies) and none in FP64, whose pipe, not the shuffles'
+// latency, bounds that path.  Q warps share an atom (warp q takes passes q,
+// q + Q, ...), and the atom's Ulisttot is the sum of the Q running sums plus
+// w_self on the diagonal.  Q, LV and P are constants of the instance, so the
+// order of every sum is fixed by the slot indices alone.
+template <typename R, int J2>
+struct UiPlan {
+  static constexpr int NC = Shape<J2>::NC, P = Shape<J2>::P;
+  static constexpr int HH = half_size(J2);
+  static constexpr int kMaxLv = P > 16 ? 5 : P > 8 ? 4 : P > 4 ? 3 : P > 2 ? 2 : P > 1 ? 1 : 0;
+  static constexpr int copies(int lv) { return (P + (1 << lv) - 1) >> lv; }
+  static constexpr int pick(int lv) {
+    return (sizeof(R) == 8 || lv >= kMaxLv || copies(lv) * HH * (int)sizeof(c2<R>) <= 4096) ? lv : pick(lv + 1);
+  }
+  static constexpr int LV = pick(0);
+  static constexpr int CPW = copies(LV);
+  static constexpr int Q = (26 + P - 1) / P >= 2 ? 2 : 1;  // warps per atom
+  static constexpr int A = Q == 1 ? 2 : 1;                  // atoms per CTA
+  static constexpr size_t warp_bytes = sizeof(c2<R>) * (size_t)(CPW + 1) * HH;
+};
+
+// Sum of v over the pair groups g, g + 1, ..., g + 2^LV - 1 (on the lanes of
+// writer groups; lanes past the warp add nothing).
+template <int LV, int NC, typename R>
+__device__ __forceinline__ R group_sum(R v, int lane) {
+#pragma unroll
+  for (int l = 0; l < LV; ++l) {
+    const R o = __shfl_down_sync(kFull, v, NC << l);
+    if (lane + (NC << l) < 32) v += o;
+  }
+  return v;
+}
+
+// First the atom's slot geometry (a, b, f_c also kept in shared memory) and
+// reverse-slot map (snap_geom.cuh): geometry on the atom's first warp,
+// reverse map on its second, dense lanes.  Then the recursion of UiPlan.
+// Resident CTAs an SM the register allocation is sized for: 16 two-warp CTAs
+// (64 registers) in FP32 up to 2J = 8, 8 above and in FP64.
+template <typename R, int J2>
+constexpr int ui_min_ctas() { return sizeof(R) == 8 ? 8 : (J2 <= 8 ? 16 : 8); }
+
+template <typename R, int J2>
+__global__ void __launch_bounds__(64, ui_min_ctas<R, J2>()) ui_col_kernel(WorkArgs a) {
   using S = Shape<J2>;
-  constexpr int NC = S::NC, P = S::P;
+  using UP = UiPlan<R, J2>;
+  constexpr int NC = S::NC, P = S::P, LV = UP::LV, CPW = UP::CPW, Q = UP::Q, A = UP::A, H = UP::HH;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int H = a.H;
+  const int K = a.K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long i = (long)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (i >= a.n) return;  // whole warp
-  c2<R>* acc = reinterpret_cast<c2<R>*>(smem) + (size_t)warp * P * H;  // [P][H]
+  const int al = warp / Q, wq = warp - al * Q;
+  const long i0 = (long)blockIdx.x * A;
+  const long i = i0 + al;
+  const bool have = i < a.n;  // warp-uniform
+  c2<R>* scr = reinterpret_cast<c2<R>*>(smem) + (size_t)warp * (CPW + 1) * H;  // [CPW][H] scratch
+  c2<R>* run = scr + (size_t)CPW * H;                                          // [H] running sum
+  R* abf = reinterpret_cast<R*>(smem + (size_t)A * Q * UP::warp_bytes);         // [A][K][5]
+  R* myabf = abf + (size_t)al * K * 5;
+  const int cnt = have ? a.cnt[i] : 0;
+  if (have) {
+    if (wq == 0)
+      for (int s = lane; s < cnt; s += 32) geo::slot_geom<R>(a, i * K + s, myabf + 5 * s);
+    if (wq == (Q > 1 ? 1 : 0))
+      for (int s = lane; s < cnt; s += 32) {
+        const long q = i * K + s;
+        const int r = geo::slot_rev(a, (int)i, q);
+        a.rev_out[q] = r;
+        if (r < 0) atomicMax(&a.flags[1], 1);
+      }
+  }
+  for (int e = lane; e < H; e += 32) run[e] = mk<R>(0, 0);
+  __syncthreads();
   const int g = lane / NC, mb = lane - g * NC;
   const bool grp = g < P;
-  // the atom's slot geometry and reverse map (dense lanes: one slot each)
-  geo::atom_slots<R>(a, (int)i, lane, 32);
-  for (int e = lane; e < P * H; e += 32) acc[e] = mk<R>(0, 0);
-  __syncwarp();
-  c2<R>* my = acc + (grp ? g : 0) * H;
-  R rs[J2 + 1];
-#pragma unroll
-  for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
-  const int cnt = a.cnt[i];
-  for (int s0 = 0; s0 < cnt; s0 += P) {
-    const int s = s0 + g;
+  const bool writer = grp && (g & ((1 << LV) - 1)) == 0;
+  c2<R>* my = scr + (size_t)(writer ? (g >> LV) : 0) * H;
+  // 1 / sqrt((t - mb)!) of every layer, once per warp
+  R gs[J2 + 1];
+  v_gscale<R, J2>(gs, mb);
+  const int npass = (cnt + P - 1) / P;
+  for (int pass = wq; pass < npass; pass += Q) {
+    const int s = pass * P + g;
     const bool ok = grp && s < cnt;
     c2<R> ca = mk<R>(1, 0), cb = mk<R>(0, 0);
     R fc = 0;
     if (ok) {
-      const R* gm = reinterpret_cast<const R*>(a.geom) + ((long)i * a.K + s) * kGeomStride;
+      const R* gm = myabf + 5 * s;
       ca = mk<R>(gm[0], -gm[1]);  // conj(a)
       cb = mk<R>(gm[2], -gm[3]);  // conj(b)
       fc = gm[4];
     }
-    c2<R> u[J2 + 1];
+    c2<R> v[J2 + 1];
 #pragma unroll
-    for (int k = 0; k <= J2; ++k) u[k] = mk<R>(0, 0);
-    if (mb == 0) u[0] = mk<R>(1, 0);
-    if (ok && mb == 0) my[0].re += fc;
+    for (int k = 0; k <= J2; ++k) v[k] = mk<R>(0, 0);
+    if (mb == 0) v[0] = mk<R>(1, 0);
+    {
+      const R v0 = group_sum<LV, NC>(mb == 0 ? fc : R(0), lane);
+      if (writer && mb == 0) my[0] = mk<R>(v0, 0);
+    }
     static_for<1, J2>([&](auto tc) {
       constexpr int t = decltype(tc)::value;
-      if constexpr ((t & 1) == 0) seed_column<R, t>(u, mb == t / 2);
-      const R r = rs[t];
-      const c2<R> A = mk<R>(r * ca.re, r * ca.im), B = mk<R>(r * cb.re, r * cb.im);
-      // in place, ma descending: u[ma] <- sqrt(t-ma) A u[ma] - sqrt(ma) B u[ma-1]
-#pragma unroll
-      for (int ma = t; ma >= 0; --ma) {
-        c2<R> v = mk<R>(0, 0);
-        if (ma < t) {
-          const R c = sqrt_int<R>(t - ma);
-          v.re = c * (A.re * u[ma].re - A.im * u[ma].im);
-          v.im = c * (A.re * u[ma].im + A.im * u[ma].re);
-        }
-        if (ma > 0) {
-          const R c = sqrt_int<R>(ma);
-          v.re -= c * (B.re * u[ma - 1].re - B.im * u[ma - 1].im);
-          v.im -= c * (B.re * u[ma - 1].im + B.im * u[ma - 1].re);
-        }
-        u[ma] = v;
-      }
-      if (ok && 2 * mb <= t) {
-        c2<R>* dst = my + half_base(t) + mb * (t + 1);
-#pragma unroll
-        for (int ma = 0; ma <= t; ++ma) {
-          dst[ma].re += fc * u[ma].re;
-          dst[ma].im += fc * u[ma].im;
-        }
-      }
+      if constexpr ((t & 1) == 0) v_seed<R, t>(v, mb == t / 2);
+      v_layer<R, t>(v, ca, cb);
+      // f_c u_t = f_c S_t v_t, S_t = sqrt((t-ma)! ma!) / sqrt((t-mb)!)
+      const R fg = fc * gs[t];
+      c2<R>* dst = my + half_base(t) + mb * (t + 1);
+      static_for<0, t>([&](auto mc_) {
+        constexpr int ma = decltype(mc_)::value;
+        constexpr double sc = v_scale<t, ma>();
+        const R w = fg * R(sc);
+        const R vr = group_sum<LV, NC>(w * v[ma].re, lane);
+        const R vi = group_sum<LV, NC>(w * v[ma].im, lane);
+        if (writer && 2 * mb <= t) dst[ma] = mk<R>(vr, vi);
+      });
     });
+    __syncwarp();
+    for (int e = lane; e < H; e += 32) {
+      c2<R> v = run[e];
+#pragma unroll
+      for (int c = 0; c < CPW; ++c) {
+        const c2<R> w = scr[(size_t)c * H + e];
+        v.re += w.re;
+        v.im += w.im;
+      }
+      run[e] = v;
+    }
+    __syncwarp();
   }
-  __syncwarp();
+  __syncthreads();
   c2<R>* Ug = reinterpret_cast<c2<R>*>(a.U);
-  const long blk = i >> 5;
-  const int li = (int)(i & 31);
-  for (int e = lane; e < H; e += 32) {
+  for (int idx = threadIdx.x; idx < A * H; idx += blockDim.x) {
+    const int a2 = idx / H, e = idx - a2 * H;
+    const long ii = i0 + a2;
+    if (ii >= a.n) break;
+    const c2<R>* rr = reinterpret_cast<const c2<R>*>(smem) + (size_t)a2 * Q * (CPW + 1) * H + (size_t)CPW * H + e;
     R sr = 0, si = 0;
 #pragma unroll
-    for (int c = 0; c < P; ++c) {
-      sr += acc[c * H + e].re;
-      si += acc[c * H + e].im;
+    for (int q = 0; q < Q; ++q) {
+      const c2<R> v = rr[(size_t)q * (CPW + 1) * H];
+      sr += v.re;
+      si += v.im;
     }
     const int p = a.half_tmm[e];
     if (tmm_ma(p) == tmm_mb(p)) sr += (R)a.wself;
-    Ug[(blk * H + e) * 32 + li] = mk<R>(sr, si);
+    Ug[((ii >> 5) * H + e) * 32 + (ii & 31)] = mk<R>(sr, si);
   }
 }
 
@@ -568,18 +702,16 @@ inline int col_fit_warps(int nw, size_t per_warp) {
   return nw;
 }
 
-// compute_U takes half the tunable's warps per CTA (at least 2): with one
-// atom per warp, the smaller CTAs spread over the SMs more evenly (2000 atoms
-// at 2J8: 41.0 -> 37.0 us against 4-warp CTAs), while the fused dE kernel
-// keeps the tunable itself (its 4- and 8-warp CTAs are faster at 2J14).
 template <typename R, int J2>
 cudaError_t launch_ui_col_t(const WorkArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const size_t per = sizeof(c2<R>) * (size_t)Shape<J2>::P * a.H;
-  const int nw = col_fit_warps(a.col_warps > 2 ? a.col_warps / 2 : 2, per);
-  cudaError_t e = col_allow_smem(ui_col_kernel<R, J2>, per * nw);
+  using UP = UiPlan<R, J2>;
+  if (a.H != UP::HH) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)UP::A * (UP::Q * UP::warp_bytes + sizeof(R) * 5 * (size_t)a.K);
+  cudaError_t e = col_allow_smem(ui_col_kernel<R, J2>, smem);
   if (e != cudaSuccess) return e;
-  return launch_k(ui_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a);
+  return launch_k(ui_col_kernel<R, J2>, dim3((unsigned)((a.n + UP::A - 1) / UP::A)), dim3(UP::A * UP::Q * 32),
+                  smem, s, a);
 }
 
 template <typename R, int J2>

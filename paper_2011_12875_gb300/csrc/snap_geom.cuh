@@ -24,13 +24,18 @@
 namespace snap {
 namespace geo {
 
-__device__ __forceinline__ void sincospi_g(float x, float* s, float* c) { sincospif(x, s, c); }
-__device__ __forceinline__ void sincospi_g(double x, double* s, double* c) { sincospi(x, s, c); }
-
 // Geometry of slot q into geom[q][0..kGeomStride): a (2), b (2), f_c,
 // grad f_c (3), da/dr_d (3 x 2), db/dr_d (3 x 2).
+// With `abf` given, a (2), b (2) and f_c are also written there (the
+// compute_U kernel keeps its atom's in shared memory).
+//
+// FP64 work is kept to what the Cayley-Klein parameters need: r, theta0,
+// sin/cos theta0, a and b.  In the mixed path (G = float) everything else --
+// f_c and the gradients, which only feed the FP32 recursions -- is computed
+// in FP32 from the rounded separation, so an FP64 instruction (1/64 of the
+// FP32 rate here, whatever its active lanes) is spent only on those.
 template <typename G>
-__device__ void slot_geom(const WorkArgs& a, long q) {
+__device__ void slot_geom(const WorkArgs& a, long q, G* abf = nullptr) {
   G* g = reinterpret_cast<G*>(a.geom) + q * kGeomStride;
   const double x = a.rij[3 * q], y = a.rij[3 * q + 1], z = a.rij[3 * q + 2];
   const double r2 = x * x + y * y + z * z;
@@ -43,6 +48,9 @@ __device__ void slot_geom(const WorkArgs& a, long q) {
     v[0] = G(1);
 #pragma unroll
     for (int e = 0; e < kGeomStride; ++e) g[e] = v[e];
+    if (abf)
+#pragma unroll
+      for (int e = 0; e < 5; ++e) abf[e] = v[e];
     return;
   }
   // r0 = sqrt(r^2 + z0^2) = r / |sin theta0|, so with sr = |sin theta0| / r
@@ -51,29 +59,47 @@ __device__ void slot_geom(const WorkArgs& a, long q) {
   // (no division, one reciprocal square root; sr multiplies +-x, +-y, +-z, so
   // the opposite slot still gets exactly conj(a) and -b)
   double st, ct;
-  sincospi(a.rfac0 * (r - a.rmin0) * a.inv_span, &st, &ct);
+  sincospi((r - a.rmin0) * a.th_scale, &st, &ct);
   const double sr = fabs(st) * ir;
   const double ar = st < 0.0 ? -ct : ct, ai = -z * sr;
   const double br = y * sr, bi = -x * sr;
-  // z0 = r cot theta0 and 1/r0 for the gradients, in the working precision
-  const G gr = G(r), gir = G(ir), gct = G(ct), gst = G(st);
-  const G gist = G(1) / gst, gz0 = gr * gct * gist, gir0 = G(sr);
   const G gar = G(ar), gai = G(ai), gbr = G(br), gbi = G(bi);
-  const G c = G(a.rfac0 * M_PI * a.inv_span);  // d theta0 / d r
-  const G dz0dr = gct * gist - gr * c * gist * gist;
-  G fc = G(1), dfcdr = G(0);
-  if (a.switchflag && r > a.rmin0) {
-    G sw, cw;
-    sincospi_g(G((r - a.rmin0) * a.inv_span), &sw, &cw);
-    fc = G(0.5) * (cw + G(1));
-    dfcdr = G(-0.5 * M_PI * a.inv_span) * sw;
+  const G rv[3] = {G(x), G(y), G(z)};
+  G gr, gir, gct, gst, c, fc = G(1), dfcdr = G(0);
+  if constexpr (sizeof(G) == 4) {
+    // the gradient factors in FP32 from the rounded separation
+    const float fr2 = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+    gir = rsqrtf(fr2);
+    gr = fr2 * gir;
+    sincospif((gr - a.rmin0_f) * a.th_scale_f, &gst, &gct);
+    c = a.dth_f;
+    if (a.switchflag && gr > a.rmin0_f) {
+      float sw, cw;
+      sincospif((gr - a.rmin0_f) * a.inv_span_f, &sw, &cw);
+      fc = 0.5f * (cw + 1.0f);
+      dfcdr = a.dfc_f * sw;
+    }
+  } else {
+    gr = r;
+    gir = ir;
+    gct = ct;
+    gst = st;
+    c = M_PI * a.th_scale;  // d theta0 / d r
+    if (a.switchflag && r > a.rmin0) {
+      double sw, cw;
+      sincospi((r - a.rmin0) * a.inv_span, &sw, &cw);
+      fc = 0.5 * (cw + 1.0);
+      dfcdr = -0.5 * M_PI * a.inv_span * sw;
+    }
   }
+  // z0 = r cot theta0, 1/r0 = |sin theta0| / r
+  const G gist = G(1) / gst, gz0 = gr * gct * gist, gir0 = fabs(gst) * gir;
+  const G dz0dr = gct * gist - gr * c * gist * gist;
   v[0] = gar;
   v[1] = gai;
   v[2] = gbr;
   v[3] = gbi;
   v[4] = fc;
-  const G rv[3] = {G(x), G(y), G(z)};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const G ud = rv[d] * gir;
@@ -88,6 +114,9 @@ __device__ void slot_geom(const WorkArgs& a, long q) {
   }
 #pragma unroll
   for (int e = 0; e < kGeomStride; ++e) g[e] = v[e];
+  if (abf)
+#pragma unroll
+    for (int e = 0; e < 5; ++e) abf[e] = v[e];
 }
 
 // Slot of (k, i, -img) in k's list, or -1.  All of k's slots are read with

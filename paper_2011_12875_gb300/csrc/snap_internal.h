@@ -125,6 +125,11 @@ struct WorkArgs {
   int n, K, twojmax, H, lmax;
   double rcut, rfac0, rmin0, wself, beta0;
   double inv_span;  // 1 / (rcut - rmin0)
+  double th_scale;  // rfac0 / (rcut - rmin0): theta0 / pi = th_scale (r - rmin0)
+  // FP32 copies for the mixed path's slot gradients (no FP64 work per slot):
+  // th_scale, d theta0 / d r = pi th_scale, 1 / (rcut - rmin0), rmin0 and
+  // the switching derivative's factor -pi / (2 (rcut - rmin0))
+  float th_scale_f, dth_f, inv_span_f, rmin0_f, dfc_f;
   int switchflag;
   const int* cnt;
   const int* nbr;
