@@ -62,6 +62,7 @@ struct snap_ctx {
   int* d_bfirst = nullptr;
   int* d_bgfirst = nullptr;
   void* d_root = nullptr;
+  void* d_hscale = nullptr;
   int* d_yslice = nullptr;
   int* d_ysched = nullptr;  // lane schedule of the warp-per-atom compute_Y
   int ysched_m = 0;
@@ -396,6 +397,7 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.bfirst = c->d_bfirst;
   a.bgfirst = c->d_bgfirst;
   a.rootpq = c->d_root;
+  a.hscale = c->d_hscale;
   return a;
 }
 
@@ -828,6 +830,7 @@ int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switch
   if (!rc) rc = upload(c, &c->d_yruns, c->tab.term_runs);
   if (!rc) rc = upload(c, &c->d_ysched, c->tab.lane_outputs(32, &c->ysched_m));
   if (!rc) rc = upload_r(c, &c->d_root, c->tab.rootpq);
+  if (!rc) rc = upload_r(c, &c->d_hscale, c->tab.half_scale);
   if (!rc) rc = upload_yrec(c);
   if (!rc) rc = upload_brec(c);
   if (!rc) rc = upload(c, &c->d_bout, c->tab.bout);
@@ -1299,6 +1302,7 @@ int snap_destroy(snap_ctx* c) {
   dfree(c->d_bfirst);
   dfree(c->d_bgfirst);
   dfree(c->d_root);
+  dfree(c->d_hscale);
   for (auto& kv : c->yslice_cache) cudaFree(kv.second);
   c->yslice_cache.clear();
   c->d_yslice = nullptr;

@@ -264,9 +264,6 @@ __global__ void __launch_bounds__(64, ui_min_ctas<R, J2>()) ui_col_kernel(WorkAr
   const bool grp = g < P;
   const bool writer = grp && (g & ((1 << LV) - 1)) == 0;
   c2<R>* my = scr + (size_t)(writer ? (g >> LV) : 0) * H;
-  // 1 / sqrt((t - mb)!) of every layer, once per warp
-  R gs[J2 + 1];
-  v_gscale<R, J2>(gs, mb);
   const int npass = (cnt + P - 1) / P;
   for (int pass = wq; pass < npass; pass += Q) {
     const int s = pass * P + g;
@@ -279,29 +276,27 @@ __global__ void __launch_bounds__(64, ui_min_ctas<R, J2>()) ui_col_kernel(WorkAr
       cb = mk<R>(gm[2], -gm[3]);  // conj(b)
       fc = gm[4];
     }
+    // the scaled column times f_c (the recursion is linear, so f_c rides
+    // along from layer 0); S is applied once, to the atom's sums
     c2<R> v[J2 + 1];
 #pragma unroll
     for (int k = 0; k <= J2; ++k) v[k] = mk<R>(0, 0);
-    if (mb == 0) v[0] = mk<R>(1, 0);
+    if (mb == 0) v[0] = mk<R>(fc, 0);
     {
-      const R v0 = group_sum<LV, NC>(mb == 0 ? fc : R(0), lane);
+      const R v0 = group_sum<LV, NC>(v[0].re, lane);
       if (writer && mb == 0) my[0] = mk<R>(v0, 0);
     }
     static_for<1, J2>([&](auto tc) {
       constexpr int t = decltype(tc)::value;
       if constexpr ((t & 1) == 0) v_seed<R, t>(v, mb == t / 2);
       v_layer<R, t>(v, ca, cb);
-      // f_c u_t = f_c S_t v_t, S_t = sqrt((t-ma)! ma!) / sqrt((t-mb)!)
-      const R fg = fc * gs[t];
       c2<R>* dst = my + half_base(t) + mb * (t + 1);
-      static_for<0, t>([&](auto mc_) {
-        constexpr int ma = decltype(mc_)::value;
-        constexpr double sc = v_scale<t, ma>();
-        const R w = fg * R(sc);
-        const R vr = group_sum<LV, NC>(w * v[ma].re, lane);
-        const R vi = group_sum<LV, NC>(w * v[ma].im, lane);
+#pragma unroll
+      for (int ma = 0; ma <= t; ++ma) {
+        const R vr = group_sum<LV, NC>(v[ma].re, lane);
+        const R vi = group_sum<LV, NC>(v[ma].im, lane);
         if (writer && 2 * mb <= t) dst[ma] = mk<R>(vr, vi);
-      });
+      }
     });
     __syncwarp();
     for (int e = lane; e < H; e += 32) {
@@ -330,6 +325,9 @@ __global__ void __launch_bounds__(64, ui_min_ctas<R, J2>()) ui_col_kernel(WorkAr
       sr += v.re;
       si += v.im;
     }
+    const R sc = reinterpret_cast<const R*>(a.hscale)[e];
+    sr *= sc;
+    si *= sc;
     const int p = a.half_tmm[e];
     if (tmm_ma(p) == tmm_mb(p)) sr += (R)a.wself;
     Ug[((ii >> 5) * H + e) * 32 + (ii & 31)] = mk<R>(sr, si);

@@ -170,6 +170,7 @@ struct WorkArgs {
   const int* bgfirst;     // [ncoeff+1] first output group of each component
   double* B;              // [N][ncoeff]
   const void* rootpq;
+  const void* hscale;  // R [H]: S_t(ma, mb) of the scaled recursion (u = S v)
 };
 
 // Launchers (snap_neigh.cu)

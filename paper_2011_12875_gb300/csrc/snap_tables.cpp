@@ -393,6 +393,15 @@ void HostTables::build(int J2, bool size_runs) {
   bcomp_first.push_back((int)bterms.size());
   bgroup_first.push_back((int)bout.size());
 
+  half_scale.assign(H, 0.0);
+  for (int e = 0; e < H; ++e) {
+    const int t = tmm_t(half_tmm[e]), ma = tmm_ma(half_tmm[e]), mb = tmm_mb(half_tmm[e]);
+    long double f = 1.0L;
+    for (int k = 2; k <= t - ma; ++k) f *= k;
+    for (int k = 2; k <= ma; ++k) f *= k;
+    for (int k = 2; k <= t - mb; ++k) f /= k;
+    half_scale[e] = (double)std::sqrt(f);
+  }
   rootpq.assign(kRootDim * kRootDim, 0.0);
   for (int p = 0; p < kRootDim; ++p)
     for (int q = 1; q < kRootDim; ++q) rootpq[p * kRootDim + q] = std::sqrt((double)p / (double)q);

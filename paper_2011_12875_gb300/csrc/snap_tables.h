@@ -34,6 +34,9 @@ struct HostTables {
   std::vector<int> bcomp_first;
   std::vector<int> bgroup_first;  // [ncoeff+1] first output group of each component
   std::vector<double> rootpq;
+  // [H]: S_t(ma, mb) = sqrt((t - ma)! ma! / (t - mb)!) of every half-layout
+  // element, the factor between the scaled recursion's v and u
+  std::vector<double> half_scale;
 
   // size_runs: order each output's term groups by length (the run layout of
   // the FP32 compute_Y); otherwise by first factor
