@@ -555,10 +555,7 @@ def main():
               "flops_per_launch": fl.get(dom, 0),
               "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
                               if hprec == snap.MIXED else "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
-              "peak_measured_source": "snap_probe_fma (8 FMA chains per thread, 8 CTAs of 256 per SM)",
-              # the same steps without the neighbour build (its profiled time taken off)
-              "value_excl_neighbor_build": world * r["natoms"] /
-              ((t_max - stages["neighbor_build"]["ms_per_call"]) * 1e-3)}
+              "peak_measured_source": "snap_probe_fma (8 FMA chains per thread, 8 CTAs of 256 per SM)"}
     # end to end through host buffers, on every rank; the job's step is the
     # slowest rank's
     if pg:

@@ -79,6 +79,7 @@ struct snap_ctx {
   signed char* d_img = nullptr;
   double* d_rij = nullptr;
   int* d_rev = nullptr;
+  int* d_key = nullptr;  // pair keys of the neighbour table (reverse-slot search)
   double* d_geom = nullptr;
   double* d_dedr = nullptr;
   void* d_U = nullptr;  // complex AoSoA [ceil(N/32)][H][32]
@@ -255,6 +256,7 @@ void free_workspace(snap_ctx* c) {
   dfree(c->d_img);
   dfree(c->d_rij);
   dfree(c->d_rev);
+  dfree(c->d_key);
   dfree(c->d_geom);
   dfree(c->d_dedr);
   dfree(c->d_U);
@@ -281,6 +283,7 @@ int ensure_workspace(snap_ctx* c, int n, int K) {
   SNAP_CUDA(c, cudaMalloc(&c->d_img, 3 * nkcap));
   SNAP_CUDA(c, cudaMalloc(&c->d_rij, sizeof(double) * 3 * nkcap));
   SNAP_CUDA(c, cudaMalloc(&c->d_rev, sizeof(int) * nkcap));
+  SNAP_CUDA(c, cudaMalloc(&c->d_key, sizeof(int) * nkcap));
   SNAP_CUDA(c, cudaMalloc(&c->d_geom, sizeof(double) * snap::kGeomStride * nkcap));
   SNAP_CUDA(c, cudaMalloc(&c->d_dedr, sizeof(double) * 3 * nkcap));
   SNAP_CUDA(c, cudaMalloc(&c->d_U, uy));
@@ -370,6 +373,7 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.img = c->d_img;
   a.rev = c->d_rev;
   a.rev_out = c->d_rev;
+  a.key = c->d_key;
   a.rij = c->d_rij;
   a.geom = c->d_geom;
   a.U = c->d_U;
@@ -438,12 +442,30 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   c->launches = 0;
   SNAP_CUDA(c, mark());
 
+  snap::WorkArgs a = make_args(c, n, K);
+  a.energy = energy;
+  a.forces = forces;
+  a.virial = virial;
+  a.B = B;
+  const bool mixed = c->precision == SNAP_MIXED;
+  // register column-chain kernels: FP32 for 2J >= 1; FP64 up to 2J = 8 (above,
+  // the FP64 columns need all 255 registers and the occupancy loss costs more
+  // than the layout gains: fused dE 6.1 vs 4.6 ms at 2J = 14, 2000 atoms)
+  const bool colk = c->twojmax >= 1 && (mixed || c->twojmax <= 8);
+  auto launch_u = [&]() -> cudaError_t {
+    return colk ? (mixed ? snap::launch_ui_col<float>(a, s) : snap::launch_ui_col<double>(a, s))
+                : (mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s));
+  };
   if (user) {
     SNAP_CUDA(c, snap::launch_neigh_ingest(n, K, pos, box[0], box[1], box[2], ucnt, uidx, uimg, ucap,
-                                           c->d_cnt, c->d_nbr, c->d_img, c->d_rij, c->d_flags, s));
+                                           c->d_cnt, c->d_nbr, c->d_img, c->d_rij, c->d_key, c->d_flags, s));
+    c->launches += 1;
+    SNAP_CUDA(c, mark());
+    SNAP_CUDA(c, launch_u());
     c->launches += 1;
   } else {
     snap::NeighArgs na;
+    std::memset(&na, 0, sizeof(na));
     na.n = n;
     na.K = K;
     na.pos = pos;
@@ -462,29 +484,24 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
     na.nbr = c->d_nbr;
     na.img = c->d_img;
     na.rij = c->d_rij;
+  na.key = c->d_key;
+    na.key = c->d_key;
     na.flags = c->d_flags;
     SNAP_CUDA(c, snap::launch_pos4(n, pos, c->d_pos4, s, c->d_tiles, pos_stage));
     if (pos_stage) na.pos = pos_stage;
-    SNAP_CUDA(c, snap::launch_neigh_build(na, s));
-    c->launches += 2;
+    c->launches += 1;
+    SNAP_CUDA(c, mark());
+    if (colk) {
+      // the neighbour build fused with compute_U
+      SNAP_CUDA(c, mixed ? snap::launch_neigh_u<float>(na, a, 0, s) : snap::launch_neigh_u<double>(na, a, 0, s));
+      c->launches += 1;
+    } else {
+      SNAP_CUDA(c, snap::launch_neigh_build(na, s));
+      SNAP_CUDA(c, launch_u());
+      c->launches += 2;
+    }
   }
   SNAP_CUDA(c, mark());
-
-  snap::WorkArgs a = make_args(c, n, K);
-  a.energy = energy;
-  a.forces = forces;
-  a.virial = virial;
-  a.B = B;
-
-  const bool mixed = c->precision == SNAP_MIXED;
-  // register column-chain kernels: FP32 for 2J >= 1; FP64 up to 2J = 8 (above,
-  // the FP64 columns need all 255 registers and the occupancy loss costs more
-  // than the layout gains: fused dE 6.1 vs 4.6 ms at 2J = 14, 2000 atoms)
-  const bool colk = c->twojmax >= 1 && (mixed || c->twojmax <= 8);
-  SNAP_CUDA(c, colk ? (mixed ? snap::launch_ui_col<float>(a, s) : snap::launch_ui_col<double>(a, s))
-                    : (mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s)));
-  SNAP_CUDA(c, mark());
-  c->launches += 1;
   c->generation += 1;
   c->last_args = a;
   c->have_last = (mode == 0);
@@ -600,9 +617,8 @@ int launch_batch(snap_ctx* c, const double* pos, double* energy, double* forces,
   na.nbr = c->d_nbr;
   na.img = c->d_img;
   na.rij = c->d_rij;
+  na.key = c->d_key;
   na.flags = c->d_flags;
-  SNAP_CUDA(c, snap::launch_pos4(n, pos, c->d_pos4, s));
-  SNAP_CUDA(c, snap::launch_neigh_build_batch(na, c->bat_ncta, s));
   snap::WorkArgs a = make_args(c, n, c->K);
   a.energy = energy;
   a.forces = forces;
@@ -610,15 +626,24 @@ int launch_batch(snap_ctx* c, const double* pos, double* energy, double* forces,
   a.vatom = c->d_vatom;
   const bool mixed = c->precision == SNAP_MIXED;
   const bool colk = c->twojmax >= 1 && (mixed || c->twojmax <= 8);
-  SNAP_CUDA(c, colk ? (mixed ? snap::launch_ui_col<float>(a, s) : snap::launch_ui_col<double>(a, s))
-                    : (mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s)));
+  SNAP_CUDA(c, snap::launch_pos4(n, pos, c->d_pos4, s));
+  int nl = 1;
+  if (colk) {
+    SNAP_CUDA(c, mixed ? snap::launch_neigh_u<float>(na, a, c->bat_ncta, s)
+                       : snap::launch_neigh_u<double>(na, a, c->bat_ncta, s));
+    nl += 1;
+  } else {
+    SNAP_CUDA(c, snap::launch_neigh_build_batch(na, c->bat_ncta, s));
+    SNAP_CUDA(c, mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s));
+    nl += 2;
+  }
   SNAP_CUDA(c, mixed ? snap::launch_yi<float>(a, s) : snap::launch_yi<double>(a, s));
   SNAP_CUDA(c, colk ? (mixed ? snap::launch_de_col<float>(a, s) : snap::launch_de_col<double>(a, s))
                     : (mixed ? snap::launch_de<float>(a, s) : snap::launch_de<double>(a, s)));
   SNAP_CUDA(c, mixed ? snap::launch_force<float>(a, s) : snap::launch_force<double>(a, s));
   if (virial) SNAP_CUDA(c, snap::launch_virial_conf(c->d_vatom, c->d_confs, c->bat_nconf, virial, s));
   SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  c->launches = 6 + (virial ? 1 : 0);
+  c->launches = nl + 3 + (virial ? 1 : 0);
   c->generation += 1;
   c->last_args = a;
   c->have_last = true;
@@ -942,7 +967,7 @@ int snap_profile_read(snap_ctx* c, double* ms, long long* calls, int nstages) {
 }
 
 const char* snap_stage_name(int stage) {
-  static const char* names[SNAP_NSTAGES] = {"neighbor_build", "compute_ui",
+  static const char* names[SNAP_NSTAGES] = {"neighbor_prep", "neighbor_compute_ui",
                                             "compute_yi", "fused_dE", "energy_force_virial"};
   return (stage >= 0 && stage < SNAP_NSTAGES) ? names[stage] : "";
 }

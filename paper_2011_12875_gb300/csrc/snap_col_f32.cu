@@ -41,4 +41,15 @@ cudaError_t launch_tan_col<float>(const WorkArgs& a, const double* g, void* dU, 
   }
 }
 
+template <>
+cudaError_t launch_neigh_u<float>(const NeighArgs& na, const WorkArgs& a, int ncta, cudaStream_t s) {
+  switch (a.twojmax) {
+#define SNAP_CASE(J) \
+  case J: return col::launch_neigh_u_t<float, J>(na, a, ncta, s);
+    SNAP_CASE(1) SNAP_CASE(2) SNAP_CASE(3) SNAP_CASE(4) SNAP_CASE(5) SNAP_CASE(6) SNAP_CASE(7) SNAP_CASE(8) SNAP_CASE(9) SNAP_CASE(10) SNAP_CASE(11) SNAP_CASE(12) SNAP_CASE(13) SNAP_CASE(14)
+#undef SNAP_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace snap

@@ -42,4 +42,15 @@ cudaError_t launch_tan_col<double>(const WorkArgs& a, const double* g, void* dU,
   }
 }
 
+template <>
+cudaError_t launch_neigh_u<double>(const NeighArgs& na, const WorkArgs& a, int ncta, cudaStream_t s) {
+  switch (a.twojmax) {
+#define SNAP_CASE(J) \
+  case J: return col::launch_neigh_u_t<double, J>(na, a, ncta, s);
+    SNAP_CASE(1) SNAP_CASE(2) SNAP_CASE(3) SNAP_CASE(4) SNAP_CASE(5) SNAP_CASE(6) SNAP_CASE(7) SNAP_CASE(8)
+#undef SNAP_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace snap

@@ -21,6 +21,7 @@
 
 #include "snap_geom.cuh"
 #include "snap_internal.h"
+#include "snap_neigh.cuh"
 
 namespace snap {
 namespace col {
@@ -222,44 +223,17 @@ __device__ __forceinline__ R group_sum(R v, int lane) {
   return v;
 }
 
-// First the atom's slot geometry (a, b, f_c also kept in shared memory) and
-// reverse-slot map (snap_geom.cuh): geometry on the atom's first warp,
-// reverse map on its second, dense lanes.  Then the recursion of UiPlan.
-// Resident CTAs an SM the register allocation is sized for: 16 two-warp CTAs
-// (64 registers) in FP32 up to 2J = 8, 8 above and in FP64.
+// The passes of one warp of an atom (warp wq of its Q): abf = the atom's
+// [K][5] (a, b, f_c) in shared memory, scr = the warp's [CPW + 1][H] scratch
+// (CPW partial sums of a pass, then the warp's running sum).
 template <typename R, int J2>
-constexpr int ui_min_ctas() { return sizeof(R) == 8 ? 8 : (J2 <= 8 ? 16 : 8); }
-
-template <typename R, int J2>
-__global__ void __launch_bounds__(64, ui_min_ctas<R, J2>()) ui_col_kernel(WorkArgs a) {
+__device__ __forceinline__ void u_passes(const R* __restrict__ abf, int cnt, int wq, int lane,
+                                         c2<R>* __restrict__ scr) {
   using S = Shape<J2>;
   using UP = UiPlan<R, J2>;
-  constexpr int NC = S::NC, P = S::P, LV = UP::LV, CPW = UP::CPW, Q = UP::Q, A = UP::A, H = UP::HH;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int K = a.K;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int al = warp / Q, wq = warp - al * Q;
-  const long i0 = (long)blockIdx.x * A;
-  const long i = i0 + al;
-  const bool have = i < a.n;  // warp-uniform
-  c2<R>* scr = reinterpret_cast<c2<R>*>(smem) + (size_t)warp * (CPW + 1) * H;  // [CPW][H] scratch
-  c2<R>* run = scr + (size_t)CPW * H;                                          // [H] running sum
-  R* abf = reinterpret_cast<R*>(smem + (size_t)A * Q * UP::warp_bytes);         // [A][K][5]
-  R* myabf = abf + (size_t)al * K * 5;
-  const int cnt = have ? a.cnt[i] : 0;
-  if (have) {
-    if (wq == 0)
-      for (int s = lane; s < cnt; s += 32) geo::slot_geom<R>(a, i * K + s, myabf + 5 * s);
-    if (wq == (Q > 1 ? 1 : 0))
-      for (int s = lane; s < cnt; s += 32) {
-        const long q = i * K + s;
-        const int r = geo::slot_rev(a, (int)i, q);
-        a.rev_out[q] = r;
-        if (r < 0) atomicMax(&a.flags[1], 1);
-      }
-  }
+  constexpr int NC = S::NC, P = S::P, LV = UP::LV, CPW = UP::CPW, Q = UP::Q, H = UP::HH;
+  c2<R>* run = scr + (size_t)CPW * H;
   for (int e = lane; e < H; e += 32) run[e] = mk<R>(0, 0);
-  __syncthreads();
   const int g = lane / NC, mb = lane - g * NC;
   const bool grp = g < P;
   const bool writer = grp && (g & ((1 << LV) - 1)) == 0;
@@ -271,7 +245,7 @@ __global__ void __launch_bounds__(64, ui_min_ctas<R, J2>()) ui_col_kernel(WorkAr
     c2<R> ca = mk<R>(1, 0), cb = mk<R>(0, 0);
     R fc = 0;
     if (ok) {
-      const R* gm = myabf + 5 * s;
+      const R* gm = abf + 5 * s;
       ca = mk<R>(gm[0], -gm[1]);  // conj(a)
       cb = mk<R>(gm[2], -gm[3]);  // conj(b)
       fc = gm[4];
@@ -311,13 +285,19 @@ __global__ void __launch_bounds__(64, ui_min_ctas<R, J2>()) ui_col_kernel(WorkAr
     }
     __syncwarp();
   }
-  __syncthreads();
+}
+
+// Ulisttot of atom i from its Q warps' running sums (ascr = the atom's
+// [Q][CPW + 1][H] scratch): their sum in warp order, times S, plus w_self on
+// the diagonal; elements e0, e0 + estride, ...
+template <typename R, int J2>
+__device__ __forceinline__ void u_store(const WorkArgs& a, const c2<R>* __restrict__ ascr, long i, int e0,
+                                        int estride) {
+  using UP = UiPlan<R, J2>;
+  constexpr int CPW = UP::CPW, Q = UP::Q, H = UP::HH;
   c2<R>* Ug = reinterpret_cast<c2<R>*>(a.U);
-  for (int idx = threadIdx.x; idx < A * H; idx += blockDim.x) {
-    const int a2 = idx / H, e = idx - a2 * H;
-    const long ii = i0 + a2;
-    if (ii >= a.n) break;
-    const c2<R>* rr = reinterpret_cast<const c2<R>*>(smem) + (size_t)a2 * Q * (CPW + 1) * H + (size_t)CPW * H + e;
+  for (int e = e0; e < H; e += estride) {
+    const c2<R>* rr = ascr + (size_t)CPW * H + e;
     R sr = 0, si = 0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -330,8 +310,89 @@ __global__ void __launch_bounds__(64, ui_min_ctas<R, J2>()) ui_col_kernel(WorkAr
     si *= sc;
     const int p = a.half_tmm[e];
     if (tmm_ma(p) == tmm_mb(p)) sr += (R)a.wself;
-    Ug[((ii >> 5) * H + e) * 32 + (ii & 31)] = mk<R>(sr, si);
+    Ug[((i >> 5) * H + e) * 32 + (i & 31)] = mk<R>(sr, si);
   }
+}
+
+// Resident CTAs an SM the register allocation is sized for: 16 two-warp CTAs
+// (64 registers) in FP32 up to 2J = 8, 8 above and in FP64.
+template <typename R, int J2>
+constexpr int ui_min_ctas() { return sizeof(R) == 8 ? 8 : (J2 <= 8 ? 16 : 8); }
+
+// compute_U for a neighbour table built elsewhere (caller-supplied lists):
+// CTA = A atoms of Q warps; the atom's first warp evaluates the slot
+// geometry from the stored separations (dense lanes), then the passes.
+template <typename R, int J2>
+__global__ void __launch_bounds__(64, ui_min_ctas<R, J2>()) ui_col_kernel(WorkArgs a) {
+  using UP = UiPlan<R, J2>;
+  constexpr int Q = UP::Q, A = UP::A;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = a.K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int al = warp / Q, wq = warp - al * Q;
+  const long i0 = (long)blockIdx.x * A;
+  const long i = i0 + al;
+  const bool have = i < a.n;  // warp-uniform
+  c2<R>* scr = reinterpret_cast<c2<R>*>(smem) + (size_t)warp * (UP::CPW + 1) * UP::HH;
+  R* myabf = reinterpret_cast<R*>(smem + (size_t)A * Q * UP::warp_bytes) + (size_t)al * K * 5;
+  const int cnt = have ? a.cnt[i] : 0;
+  if (have && wq == 0)
+    for (int s = lane; s < cnt; s += 32) geo::slot_geom<R>(a, i * K + s, myabf + 5 * s);
+  __syncthreads();
+  if (have) u_passes<R, J2>(myabf, cnt, wq, lane, scr);
+  __syncthreads();
+  for (int a2 = 0; a2 < A; ++a2) {
+    if (i0 + a2 >= a.n) break;
+    u_store<R, J2>(a, reinterpret_cast<const c2<R>*>(smem) + (size_t)a2 * Q * (UP::CPW + 1) * UP::HH, i0 + a2,
+                   threadIdx.x, blockDim.x);
+  }
+}
+
+// ---------------------------------------- neighbour build fused with compute_U
+// The neighbour build of snap_neigh.cuh (two atoms a CTA, SPLIT warps each)
+// and, in the same CTA, compute_U of those atoms: each stored pair's slot
+// geometry is evaluated on the lane that accepts it, from the exact FP64
+// separation in its registers (dense lanes, no reload), with a, b and f_c
+// kept in shared memory; then the first Q warps of each atom take its
+// passes.  One launch and one pass over the pairs instead of two.
+template <bool BATCH>
+struct NuShape {
+  static constexpr int SPLIT = BATCH ? 4 : 2;  // build warps per atom
+  static constexpr int NW = 2 * SPLIT;         // warps per CTA (two atoms)
+};
+
+template <typename R, int J2, bool BATCH>
+__global__ void __launch_bounds__(NuShape<BATCH>::NW * 32) neigh_u_kernel(NeighArgs na, WorkArgs a) {
+  using UP = UiPlan<R, J2>;
+  constexpr int SPLIT = NuShape<BATCH>::SPLIT, NW = NuShape<BATCH>::NW, Q = UP::Q;
+  static_assert(Q <= SPLIT, "an atom's passes run on its build warps");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = a.K;
+  R* abf = reinterpret_cast<R*>(smem + (size_t)2 * Q * UP::warp_bytes);  // [2][K][5]
+  nb::neigh_build_cta<BATCH, SPLIT, NW>(na, [&](int al, long i, int slot, long q, double ex, double ey,
+                                               double ez) {
+    (void)i;
+    geo::pair_geom<R>(a, q, ex, ey, ez, abf + ((size_t)al * K + slot) * 5);
+  });
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int al = warp / SPLIT, wq = warp - al * SPLIT;
+  long i, hi;
+  if (BATCH) {
+    const int2 m = na.cta_map[blockIdx.x];
+    const NeighConf c = na.confs[m.x];
+    i = c.start + m.y + al;
+    hi = c.start + c.n;
+  } else {
+    i = (long)blockIdx.x * 2 + al;
+    hi = na.n;
+  }
+  const bool have = i < hi;
+  c2<R>* ascr = reinterpret_cast<c2<R>*>(smem) + (size_t)al * Q * (UP::CPW + 1) * UP::HH;
+  if (have && wq < Q)
+    u_passes<R, J2>(abf + (size_t)al * K * 5, min(na.cnt[i], K), wq, lane,
+                    ascr + (size_t)wq * (UP::CPW + 1) * UP::HH);
+  __syncthreads();
+  if (have) u_store<R, J2>(a, ascr, i, wq * 32 + lane, SPLIT * 32);
 }
 
 // ------------------------------------------- tangent of Ulisttot along g
@@ -689,7 +750,11 @@ __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(W
 
 template <typename K>
 inline cudaError_t col_allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  // the default 48 KB limit covers static and dynamic shared memory together
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if (bytes + fa.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -710,6 +775,26 @@ cudaError_t launch_ui_col_t(const WorkArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   return launch_k(ui_col_kernel<R, J2>, dim3((unsigned)((a.n + UP::A - 1) / UP::A)), dim3(UP::A * UP::Q * 32),
                   smem, s, a);
+}
+
+// Fused neighbour build + compute_U: single configuration (ncta = 0: two
+// atoms a CTA in order) or a batch (ncta CTAs of na.cta_map).
+template <typename R, int J2>
+cudaError_t launch_neigh_u_t(const NeighArgs& na, const WorkArgs& a, int ncta, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  using UP = UiPlan<R, J2>;
+  if (a.H != UP::HH) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)2 * (UP::Q * UP::warp_bytes + sizeof(R) * 5 * (size_t)a.K);
+  if (ncta > 0) {
+    cudaError_t e = col_allow_smem(neigh_u_kernel<R, J2, true>, smem);
+    if (e != cudaSuccess) return e;
+    return launch_k(neigh_u_kernel<R, J2, true>, dim3((unsigned)ncta), dim3(NuShape<true>::NW * 32), smem, s, na,
+                    a);
+  }
+  cudaError_t e = col_allow_smem(neigh_u_kernel<R, J2, false>, smem);
+  if (e != cudaSuccess) return e;
+  return launch_k(neigh_u_kernel<R, J2, false>, dim3((unsigned)((a.n + 1) / 2)), dim3(NuShape<false>::NW * 32),
+                  smem, s, na, a);
 }
 
 template <typename R, int J2>

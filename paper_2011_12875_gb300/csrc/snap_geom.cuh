@@ -1,5 +1,6 @@
-// snap_geom.cuh -- per-slot Cayley-Klein geometry and reverse-slot map,
-// computed by the compute_U kernels for their own atom's neighbour slots.
+// snap_geom.cuh -- per-slot Cayley-Klein geometry (computed where the
+// slot's separation is at hand: the fused neighbour build, or the compute_U
+// kernels for caller-supplied lists) and the reverse-slot search.
 //
 // Geometry of a slot (Sec. II-A: the neighbour vector mapped to the
 // 3-sphere, with constants from the paper's SNAP reference):
@@ -15,7 +16,9 @@
 //
 // rev[i][s] is the slot of the opposite pair (k, i, -s) in k's list (the
 // force stage gathers dE_k/dr_ki through it instead of scattering with
-// atomics); a missing opposite pair raises flags[1].
+// atomics); a missing opposite pair raises flags[1].  The force kernel finds
+// it from the pair keys the neighbour build stores (find_rev_key) and keeps
+// it for the weighted gather.
 #pragma once
 #include <math.h>
 
@@ -35,9 +38,8 @@ namespace geo {
 // in FP32 from the rounded separation, so an FP64 instruction (1/64 of the
 // FP32 rate here, whatever its active lanes) is spent only on those.
 template <typename G>
-__device__ void slot_geom(const WorkArgs& a, long q, G* abf = nullptr) {
+__device__ void pair_geom(const WorkArgs& a, long q, double x, double y, double z, G* abf = nullptr) {
   G* g = reinterpret_cast<G*>(a.geom) + q * kGeomStride;
-  const double x = a.rij[3 * q], y = a.rij[3 * q + 1], z = a.rij[3 * q + 2];
   const double r2 = x * x + y * y + z * z;
   const double ir = rsqrt(r2);
   const double r = r2 * ir;
@@ -119,22 +121,42 @@ __device__ void slot_geom(const WorkArgs& a, long q, G* abf = nullptr) {
     for (int e = 0; e < 5; ++e) abf[e] = v[e];
 }
 
-// Slot of (k, i, -img) in k's list, or -1.  All of k's slots are read with
-// independent loads (no early exit).
-__device__ __forceinline__ int slot_rev(const WorkArgs& a, int i, long q) {
-  const int k = a.nbr[q];
+// The same for slot q from its stored separation.
+template <typename G>
+__device__ __forceinline__ void slot_geom(const WorkArgs& a, long q, G* abf = nullptr) {
+  pair_geom<G>(a, q, a.rij[3 * q], a.rij[3 * q + 1], a.rij[3 * q + 2], abf);
+}
+
+// Slot of (k, i, -img_q) in k's list (k = nbr[q]), or -1.  k's row of the
+// table is read with independent loads (16-byte loads when the capacity is a
+// multiple of 4, 32 entries a round), and the image of each entry equal to i
+// is checked (usually one).
+__device__ __forceinline__ int find_rev(const WorkArgs& a, int i, long q, int k) {
+  const int K = a.K;
+  const int ck = min(a.cnt[k], K);
+  const int* kn = a.nbr + (long)k * K;
   const int sx = a.img[3 * q], sy = a.img[3 * q + 1], sz = a.img[3 * q + 2];
-  const int ck = min(a.cnt[k], a.K);
-  const int* kn = a.nbr + (long)k * a.K;
   int found = -1;
-  for (int t0 = 0; t0 < ck; t0 += 8) {
-    int nb[8];
+  for (int t0 = 0; t0 < ck; t0 += 32) {
+    int nb[32];
+    if ((K & 3) == 0) {
+      const int4* row = reinterpret_cast<const int4*>(kn + t0);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) nb[u] = (t0 + u < ck) ? kn[t0 + u] : -1;
+      for (int u = 0; u < 8; ++u) {
+        const int4 v = (t0 + 4 * u < ck) ? __ldg(row + u) : make_int4(-1, -1, -1, -1);
+        nb[4 * u] = v.x;
+        nb[4 * u + 1] = v.y;
+        nb[4 * u + 2] = v.z;
+        nb[4 * u + 3] = v.w;
+      }
+    } else {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (nb[u] == i && found < 0) {
-        const long p = (long)k * a.K + t0 + u;
+      for (int u = 0; u < 32; ++u) nb[u] = (t0 + u < ck) ? __ldg(kn + t0 + u) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      if (nb[u] == i && t0 + u < ck && found < 0) {
+        const long p = (long)k * K + t0 + u;
         if (a.img[3 * p] == -sx && a.img[3 * p + 1] == -sy && a.img[3 * p + 2] == -sz) found = t0 + u;
       }
     }
@@ -142,17 +164,39 @@ __device__ __forceinline__ int slot_rev(const WorkArgs& a, int i, long q) {
   return found;
 }
 
-// Geometry and reverse slot of atom i's slots s = first, first + stride, ...
-template <typename G>
-__device__ void atom_slots(const WorkArgs& a, int i, int first, int stride) {
-  const int cnt = a.cnt[i];
-  for (int s = first; s < cnt; s += stride) {
-    const long q = (long)i * a.K + s;
-    const int r = slot_rev(a, i, q);
-    a.rev_out[q] = r;
-    if (r < 0) atomicMax(&a.flags[1], 1);
-    slot_geom<G>(a, q);
+// The same from the pair keys (pair_key): with key kq of slot q (k, s) the
+// reverse slot is the entry of k's row equal to i * 32 + 26 - (kq & 31), one
+// pass of 16-byte loads over the row; a slot without a key (an image shift
+// beyond one box) takes find_rev.
+__device__ __forceinline__ int find_rev_key(const WorkArgs& a, int i, long q, int k, int kq) {
+  const int K = a.K;
+  if (kq < 0 || (K & 3) != 0) return find_rev(a, i, q, k);
+  const int want = i * 32 + 26 - (kq & 31);
+  const int ck = min(a.cnt[k], K);
+  const int4* row = reinterpret_cast<const int4*>(a.key + (long)k * K);
+  int found = -1;
+  for (int t0 = 0; t0 < ck; t0 += 32) {
+    int4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (t0 + 4 * u < ck) ? __ldg(row + t0 / 4 + u) : make_int4(-1, -1, -1, -1);
+#pragma unroll
+    for (int u = 7; u >= 0; --u) {
+      const int b = t0 + 4 * u;
+      if (v[u].w == want && b + 3 < ck) found = b + 3;
+      if (v[u].z == want && b + 2 < ck) found = b + 2;
+      if (v[u].y == want && b + 1 < ck) found = b + 1;
+      if (v[u].x == want && b < ck) found = b;
+    }
+    if (found >= 0) break;
   }
+  return found;
+}
+
+// Geometry of atom i's slots s = first, first + stride, ...
+template <typename G>
+__device__ void atom_geom(const WorkArgs& a, int i, int first, int stride) {
+  const int cnt = a.cnt[i];
+  for (int s = first; s < cnt; s += stride) slot_geom<G>(a, (long)i * a.K + s);
 }
 
 }  // namespace geo

@@ -118,8 +118,19 @@ struct NeighArgs {
   int* nbr;
   signed char* img;
   double* rij;
+  int* key;  // [n][K] pair_key of every stored slot, or nullptr
   int* flags;
 };
+
+// Search key of a stored pair (k, image s): k * 32 + the image's code
+// (s_d + 1 in base 3) when every |s_d| <= 1 (and the atoms index below 2^26),
+// else -1.  The opposite pair (i, -s) has code 26 - code, so the force gather
+// finds the reverse slot with one pass over k's row of keys.
+__host__ __device__ constexpr int pair_key(int k, int ix, int iy, int iz, long n) {
+  return (ix >= -1 && ix <= 1 && iy >= -1 && iy <= 1 && iz >= -1 && iz <= 1 && n < (1L << 26))
+             ? k * 32 + (ix + 1) * 9 + (iy + 1) * 3 + (iz + 1)
+             : -1;
+}
 
 struct WorkArgs {
   int n, K, twojmax, H, lmax;
@@ -135,7 +146,8 @@ struct WorkArgs {
   const int* nbr;
   const signed char* img;
   const int* rev;
-  int* rev_out;  // the same table, written by compute_U
+  int* rev_out;  // the same table, written by the force kernel
+  const int* key;  // [N][K] pair_key of every slot
   double* rij;
   void* geom;  // R [N][K][kGeomStride]: Cayley-Klein geometry in the working precision
   // Ulisttot and Y: complex (re, im interleaved), AoSoA [ceil(N/32)][H][32]
@@ -182,7 +194,7 @@ cudaError_t launch_neigh_build_batch(const NeighArgs& a, int ncta, cudaStream_t 
 cudaError_t launch_neigh_ingest(int n, int K, const double* pos, double Lx, double Ly,
                                 double Lz, const int* ucnt, const int* uidx,
                                 const signed char* uimg, int ucap, int* cnt, int* nbr,
-                                signed char* img, double* rij, int* flags, cudaStream_t s);
+                                signed char* img, double* rij, int* key, int* flags, cudaStream_t s);
 // reverse-slot map + geometry in the working precision G (one kernel)
 
 // Launchers (snap_kernels.cu), R = float (mixed) or double (FP64)
@@ -224,6 +236,10 @@ template <typename R> cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s);
 // cudaErrorInvalidValue when no instance exists for the precision/2J.
 template <typename R> cudaError_t launch_ui_col(const WorkArgs& a, cudaStream_t s);
 template <typename R> cudaError_t launch_de_col(const WorkArgs& a, cudaStream_t s);
+// Neighbour build fused with compute_U (FP32: 1 <= twojmax <= 14; FP64: up
+// to 8): one configuration (ncta = 0) or a batch of ncta CTAs (na.confs).
+template <typename R>
+cudaError_t launch_neigh_u(const NeighArgs& na, const WorkArgs& a, int ncta, cudaStream_t s);
 // Tangent of Ulisttot along the displacement field g ([N][3], device); 0..14.
 template <typename R>
 cudaError_t launch_tan_col(const WorkArgs& a, const double* g, void* dU, cudaStream_t s);
@@ -231,6 +247,7 @@ cudaError_t launch_tan_col(const WorkArgs& a, const double* g, void* dU, cudaStr
 // d B_l along the tangent dU (snap_kernels.cu) and the weighted force gather.
 template <typename R> cudaError_t launch_dbi(const WorkArgs& a, const void* dU, double* dB, cudaStream_t s);
 cudaError_t launch_force_weighted(const WorkArgs& a, const double* w, double* grad, cudaStream_t s);
+
 // FMA throughput probe (synchronous): flops and milliseconds of one timed launch
 template <typename R>
 cudaError_t fma_probe(int nsm, int iters, double* flops, float* ms, R* sink, cudaStream_t s);

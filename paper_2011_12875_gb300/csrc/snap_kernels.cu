@@ -71,8 +71,8 @@ __device__ __forceinline__ cx<R> prev_elem(const cx<R>* lay, int tp, int m, int 
 }
 
 // ------------------------------------------------------------- compute_U
-// First the atom's slot geometry and reverse-slot map (snap_geom.cuh), then
-// the recursion.  One CTA per atom i, one warp per neighbour pair (lanes over the elements of
+// First the atom's slot geometry (snap_geom.cuh), then the recursion.  One
+// CTA per atom i, one warp per neighbour pair (lanes over the elements of
 // a layer), NW warps per CTA.  u_t of a pair follows the layer recursion
 // (Eq. hysphrecur): for mb <= t/2,
 //   u_t[ma][mb] = sqrt((t-ma)/(t-mb)) conj(a) u_{t-1}[ma][mb]
@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
   const R* rootg = reinterpret_cast<const R*>(a.rootpq);
   for (int e = threadIdx.x; e < kRootDim * kRootDim; e += blockDim.x) root[e] = rootg[e];
   for (int e = threadIdx.x; e < NW * H; e += blockDim.x) acc[e] = mk<R>(0, 0);
-  // the atom's slot geometry and reverse map (snap_geom.cuh)
-  geo::atom_slots<R>(a, i, threadIdx.x, blockDim.x);
+  // the atom's slot geometry (snap_geom.cuh)
+  geo::atom_geom<R>(a, i, threadIdx.x, blockDim.x);
   __syncthreads();
   cx<R>* myacc = acc + warp * H;
   cx<R>* b0 = buf + warp * 2 * L;
@@ -230,14 +230,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase,
 // (if that second wait runs out too, the copy may still land in the exiting
 // CTA's shared memory).  skip_copy registers the bytes without issuing the
 // copy: a test hook under which the wait runs out with nothing in flight.
+// `overlap()` runs on every thread while the copy is in flight.
+template <typename F>
 __device__ bool stage_bulk(void* dst, const void* src, unsigned bytes, uint64_t* bar, int* flags,
-                           bool skip_copy) {
+                           bool skip_copy, F&& overlap) {
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(bar, bytes);
     if (!skip_copy) bulk_g2s(dst, src, bytes, bar);
   }
+  overlap();
   const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0, kWaitNs));
   if (!ok) {
     if (threadIdx.x == 0) atomicMax(&flags[3], 1);
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(STAGED ? 1024 : 256, 1) yi_kernel(WorkArgs a) 
     cx<R>* su = reinterpret_cast<cx<R>*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(su + (CP ? 2 : 1) * H * 32);
     const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
-    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0)) return;
+    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0, [] {})) return;
     if (CP) {
       for (int e = threadIdx.x; e < H * 32; e += blockDim.x) {
         const cx<R> v = su[e];
@@ -610,7 +613,7 @@ __global__ void __launch_bounds__(256) bi_kernel(WorkArgs a) {
     cx<R>* su = reinterpret_cast<cx<R>*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(su + H * 32);
     const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
-    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0)) return;
+    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0, [] {})) return;
     us = su;
   }
   const int l = blockIdx.y * (blockDim.x >> 5) + warp;
@@ -658,7 +661,7 @@ __global__ void __launch_bounds__(256) dbi_kernel(WorkArgs a, const cx<R>* __res
     cx<R>* su = reinterpret_cast<cx<R>*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(su + H * 32);
     const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
-    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0)) return;
+    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0, [] {})) return;
     us = su;
   }
   const int l = blockIdx.y * (blockDim.x >> 5) + warp;
@@ -947,7 +950,7 @@ __global__ void __launch_bounds__(kFThreads) force_kernel(WorkArgs a) {
   const bool have = ai < na;
   const long i = i0 + ai;
   bool ok[2];
-  int rv[2], kn[2];
+  int rv[2], kn[2], ky[2];
   double d[2][3], r[2][3], dk[2][3];
   auto load_slots = [&](int s0) {
 #pragma unroll
@@ -955,12 +958,13 @@ __global__ void __launch_bounds__(kFThreads) force_kernel(WorkArgs a) {
       const int s = s0 + u * kFLanes + l;
       rv[u] = -1;
       kn[u] = 0;
+      ky[u] = -1;
 #pragma unroll
       for (int c = 0; c < 3; ++c) d[u][c] = r[u][c] = dk[u][c] = 0.0;
       if (have && s < K) {
         const long q = i * K + s;
-        rv[u] = a.rev[q];
         kn[u] = a.nbr[q];
+        ky[u] = a.key[q];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           d[u][c] = a.dedr[q * 3 + c];
@@ -998,11 +1002,22 @@ __global__ void __launch_bounds__(kFThreads) force_kernel(WorkArgs a) {
   double f[4] = {0.0, 0.0, 0.0, 0.0};
   double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int s0 = 0; s0 < cnt; s0 += 2 * kFLanes) {
-    // two slots per pass: the reverse-slot loads after the first-level ones
+    // two slots per pass: the reverse slot (a pass over the neighbour's row
+    // of pair keys, kept for the weighted gather) after the first-level
+    // loads, then its dE/dr
     if (s0 > 0) load_slots(s0);
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       ok[u] = s0 + u * kFLanes + l < cnt;
+      if (ok[u]) {
+        const long q = i * K + s0 + u * kFLanes + l;
+        rv[u] = geo::find_rev_key(a, (int)i, q, kn[u], ky[u]);
+        a.rev_out[q] = rv[u];
+        if (rv[u] < 0) atomicMax(&a.flags[1], 1);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
       if (ok[u] && rv[u] >= 0)
 #pragma unroll
         for (int c = 0; c < 3; ++c) dk[u][c] = a.dedr[((long)kn[u] * K + rv[u]) * 3 + c];
@@ -1082,7 +1097,11 @@ size_t de_smem(int H, int L) {
 
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  // the default 48 KB limit covers static and dynamic shared memory together
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if (bytes + fa.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 

@@ -19,14 +19,16 @@ def half_layer(t: int):
 
 @lru_cache(maxsize=None)
 def ui_pair(twojmax: int) -> int:
-    """compute_U, one neighbour pair: the layer recursion and the f_c u_t sum.
-    Each term of an element is conj(a or b) * u_{t-1} (6) scaled by its root
-    factor (2) and added (2); the element is then scaled by f_c and summed (4)."""
-    f = 2  # layer 0: f_c added to U_0
+    """compute_U, one neighbour pair, in the scaled form the library runs
+    (u = S v, v_t[ma] = conj(a) v_{t-1}[ma] - conj(b) v_{t-1}[ma-1], with f_c
+    carried in v from layer 0): a complex multiply (6) per term and the
+    subtraction of the two terms (2), and the element added to the pair sum
+    (2); S and w_self are applied once per atom, not per pair."""
+    f = 2  # layer 0: f_c added to the sum
     for t in range(1, twojmax + 1):
         for ma, mb in half_layer(t):
             nterm = (ma < t) + (ma > 0)
-            f += 10 * nterm + 4
+            f += 6 * nterm + 2 * (nterm - 1) + 2
     return f
 
 
@@ -132,8 +134,10 @@ def step(twojmax: int, natoms: int, npairs: int) -> dict:
     """Flops of one step by stage, keyed by the library's stage names."""
     H = sum(len(half_layer(t)) for t in range(twojmax + 1))
     return {
-        # compute_U includes the slot geometry (FP64 core, about 150 flops a slot)
-        "compute_ui": (ui_pair(twojmax) + 150) * npairs,
+        # the neighbour build fused with compute_U: the recursion and the slot
+        # geometry (FP64 core, about 150 flops a slot); the build's distance
+        # tests are not counted
+        "neighbor_compute_ui": (ui_pair(twojmax) + 150) * npairs,
         "compute_yi": yi_atom(twojmax) * natoms,
         "fused_dE": de_pair(twojmax) * npairs,
         "energy_force_virial": natoms * 4 * H + npairs * 30,
