@@ -568,7 +568,8 @@ __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(W
     c2<R>* Yw = Ywa + (size_t)al * H;
     for (int e = lane; e < H; e += 32) {
       const int p = a.half_tmm[e];
-      const R w = (R)hweight(tmm_t(p), tmm_ma(p), tmm_mb(p));
+      // the contraction weight times S of the scaled recursion (u = S v)
+      const R w = (R)hweight(tmm_t(p), tmm_ma(p), tmm_mb(p)) * reinterpret_cast<const R*>(a.hscale)[e];
       const c2<R> y = Yg[(blk * H + e) * 32 + li];
       Yw[e] = mk<R>(w * y.re, w * y.im);
     }
@@ -590,9 +591,6 @@ __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(W
   __syncthreads();
   const int total = coff[na];
   c2<R>* my = ust + (warp * P + (grp ? g : 0)) * H;
-  R rs[J2 + 1];
-#pragma unroll
-  for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
   R* myred = red + (warp * 32 + lane) * 5;
   for (int s0 = warp * P; s0 < total; s0 += NW * P) {
     const int f = s0 + g;
@@ -614,7 +612,7 @@ __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(W
       ka = mk<R>(gm[0], gm[1]);
       kb = mk<R>(gm[2], gm[3]);
     }
-    // ---- forward: u columns, stored per layer
+    // ---- forward: the scaled columns v, stored per layer
     c2<R> u[J2 + 1];
 #pragma unroll
     for (int k = 0; k <= J2; ++k) u[k] = mk<R>(0, 0);
@@ -624,27 +622,12 @@ __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(W
       Ssum = Yw[0].re;
       if (grp) my[0] = u[0];  // lanes past the last pair group own no storage
     }
+    // conj(a), conj(b)
+    const c2<R> ca = mk<R>(ka.re, -ka.im), cb = mk<R>(kb.re, -kb.im);
     static_for<1, J2>([&](auto tc) {
       constexpr int t = decltype(tc)::value;
-      if constexpr ((t & 1) == 0) seed_column<R, t>(u, mb == t / 2);
-      const R r = rs[t];
-      // conj(a) and conj(b) scaled by 1/sqrt(t - mb)
-      const c2<R> A = mk<R>(r * ka.re, -r * ka.im), B = mk<R>(r * kb.re, -r * kb.im);
-#pragma unroll
-      for (int ma = t; ma >= 0; --ma) {
-        c2<R> v = mk<R>(0, 0);
-        if (ma < t) {
-          const R c = sqrt_int<R>(t - ma);
-          v.re = c * (A.re * u[ma].re - A.im * u[ma].im);
-          v.im = c * (A.re * u[ma].im + A.im * u[ma].re);
-        }
-        if (ma > 0) {
-          const R c = sqrt_int<R>(ma);
-          v.re -= c * (B.re * u[ma - 1].re - B.im * u[ma - 1].im);
-          v.im -= c * (B.re * u[ma - 1].im + B.im * u[ma - 1].re);
-        }
-        u[ma] = v;
-      }
+      if constexpr ((t & 1) == 0) v_seed<R, t>(u, mb == t / 2);
+      v_layer<R, t>(u, ca, cb);
       if (grp && 2 * mb <= t) {
         c2<R>* dst = my + half_base(t) + mb * (t + 1);
         const c2<R>* yr = Yw + half_base(t) + mb * (t + 1);
@@ -681,16 +664,16 @@ __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(W
       }
       const bool act = grp && 2 * mb <= tp;
       const bool mir = even && act && (mb == mc - 1);
-      const R r = rs[t];
       const c2<R>* ucol = my + half_base(tp) + (act ? mb * (tp + 1) : 0);
       const c2<R>* yr = Yw + half_base(tp) + (act ? mb * (tp + 1) : 0);
-      const R rmc = even ? R(1) / sqrt_int<R>(t - mc) : R(0);
+      // the seed's factor 1 / sqrt(mc) (v_seed)
+      constexpr double qd = even ? 1.0 / c_sqrt(double(mc)) : 0.0;
+      const R qm = R(qd);
 #pragma unroll
       for (int m = 0; m <= tp; ++m) {
         const c2<R> uu = act ? ucol[m] : mk<R>(0, 0);
-        const R c1 = sqrt_int<R>(t - m) * r, c2v = sqrt_int<R>(m + 1) * r;
-        const c2<R> Av = mk<R>(c1 * lam[m].re, c1 * lam[m].im);
-        const c2<R> Bv = mk<R>(c2v * lam[m + 1].re, c2v * lam[m + 1].im);
+        const c2<R> Av = lam[m];
+        const c2<R> Bv = lam[m + 1];
         // g_a += conj(A) u ; g_b -= conj(B) u
         ga.re += Av.re * uu.re + Av.im * uu.im;
         ga.im += Av.re * uu.im - Av.im * uu.re;
@@ -704,11 +687,10 @@ __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(W
         if constexpr (even) {
           if (mir) {
             const int mp = tp - m;
-            const R d1 = sqrt_int<R>(t - mp) * rmc, d2 = sqrt_int<R>(mp + 1) * rmc;
-            const R sg = ((m + mc - 1) & 1) ? R(-1) : R(1);
+            const R sg = ((m + mc - 1) & 1) ? -qm : qm;
             const c2<R> v = mk<R>(sg * uu.re, -sg * uu.im);
-            const c2<R> A2 = mk<R>(d1 * recv[mp].re, d1 * recv[mp].im);
-            const c2<R> B2 = mk<R>(d2 * recv[mp + 1].re, d2 * recv[mp + 1].im);
+            const c2<R> A2 = recv[mp];
+            const c2<R> B2 = recv[mp + 1];
             ga.re += A2.re * v.re + A2.im * v.im;
             ga.im += A2.re * v.im - A2.im * v.re;
             gb.re -= B2.re * v.re + B2.im * v.im;
