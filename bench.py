@@ -430,21 +430,19 @@ def next_rows(torch, snap, inputs, flush, dev, args):
     from paper_2011_12875_gb300 import autograd as AG
     fit = inputs.fitting_set(32)
     rng = np.random.Generator(np.random.PCG64(99))
+    natoms_f = np.array([c.natoms for c in fit])
+    boxes_f = np.array([c.box for c in fit])
+    pos_f = torch.tensor(np.concatenate([c.pos for c in fit]), device=dev)
+    fref_f = torch.tensor(rng.normal(size=(int(natoms_f.sum()), 3)), device=dev)
     for J in (8, 14):
         s = snap.Snap(J, inputs.beta(J), precision=snap.MIXED)
-        data = [(torch.tensor(c.pos, device=dev), c.box,
-                 torch.tensor(rng.normal(size=c.pos.shape), device=dev)) for c in fit]
 
         def fm_step():
-            g = None
-            for p_, b_, fr in data:
-                _, gr = AG.force_matching_grad(s, p_, b_, fr)
-                g = gr if g is None else g + gr
-            return g
+            return AG.force_matching_grad_batch(s, pos_f, natoms_f, boxes_f, fref_f)[1]
         fm_step()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        reps = 3
+        reps = 10
         for _ in range(reps):
             fm_step()
         torch.cuda.synchronize(dev)
@@ -453,7 +451,8 @@ def next_rows(torch, snap, inputs, flush, dev, args):
         out[f"force_matching_step_2j{J}_mixed"] = {
             "configs": len(fit), "natoms_total": na, "seconds_per_step": el,
             "atom_steps_per_s": na / el,
-            "step": "per configuration: E, F; loss sum|F-F_ref|^2; dL/dbeta via snap_bispectrum_deriv"}
+            "step": "all 32 configurations batched: E, F (snap_compute_batch); loss sum|F-F_ref|^2; "
+                    "dL/dbeta via snap_bispectrum_deriv_batch"}
         s.close()
     return out
 

@@ -198,6 +198,16 @@ int snap_compute_batch(snap_ctx* ctx, int nconf, const int* natoms, const double
                        const double* pos, double* energy, double* forces, double* virial,
                        int use_graph, void* stream);
 
+/* snap_bispectrum_deriv for a batch of independent configurations (layout
+ * as snap_compute_batch): dB[i][l] = sum_k g_k . dB_l(i)/dr_k for every atom
+ * of every configuration (Sec. II-A, Eqs. z and dbidrk), one launch per
+ * stage over all of them.  g: device [sum natoms][3]; dB: device
+ * [sum natoms][N_B].  Asynchronous like snap_compute_batch (device-side
+ * status from snap_sync).  The force-matching gradient of configuration k
+ * is d(sum g . F)/d(beta_l) = -sum of dB over its atoms. */
+int snap_bispectrum_deriv_batch(snap_ctx* ctx, int nconf, const int* natoms, const double* boxes,
+                                const double* pos, const double* g, double* dB, void* stream);
+
 /* Launch-shape tunables:
  *  col_warps (2, 4 or 8): warps per CTA of the register column-chain kernels
  *    (compute_U takes half of it, at least 2); each warp computes one atom,

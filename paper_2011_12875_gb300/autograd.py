@@ -7,7 +7,10 @@ evaluation gathered with the upstream per-atom weights
 
 force_matching_grad() returns the loss sum_k |F_k - F_ref,k|^2 and its
 gradient with respect to beta from the bispectrum derivative along
-g = 2 (F - F_ref) (snap_bispectrum_deriv): dL/dbeta_l = -sum_i dB_g[i, l].
+g = 2 (F - F_ref) (snap_bispectrum_deriv): dL/dbeta_l = -sum_i dB_g[i, l];
+force_matching_grad_batch() does the same for a batch of configurations with
+one batched evaluation and one batched derivative (snap_compute_batch,
+snap_bispectrum_deriv_batch).
 """
 from __future__ import annotations
 
@@ -57,6 +60,20 @@ def force_matching_grad(model: "_snap.Snap", pos, box, f_ref):
     loss = (r * r).sum()
     g = (2.0 * r).contiguous()
     dB = model.bispectrum_deriv(pos, box, g)
+    grad = torch.zeros(dB.shape[1] + 1, dtype=torch.float64, device=pos.device)
+    grad[1:] = -dB.sum(dim=0)
+    return loss, grad
+
+
+def force_matching_grad_batch(model: "_snap.Snap", pos, natoms, boxes, f_ref):
+    """(L, dL/dbeta) for L = sum over all configurations and atoms of
+    |F_k - F_ref,k|^2, the configurations concatenated as in
+    Snap.compute_batch: one batched force evaluation and one batched
+    bispectrum derivative along g = 2 (F - F_ref)."""
+    _, F, _ = model.compute_batch(pos, natoms, boxes)
+    r = F - f_ref
+    loss = (r * r).sum()
+    dB = model.bispectrum_deriv_batch(pos, natoms, boxes, (2.0 * r).contiguous())
     grad = torch.zeros(dB.shape[1] + 1, dtype=torch.float64, device=pos.device)
     grad[1:] = -dB.sum(dim=0)
     return loss, grad

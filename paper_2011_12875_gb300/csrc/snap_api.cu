@@ -61,6 +61,12 @@ struct snap_ctx {
   int* d_bout = nullptr;
   int* d_bfirst = nullptr;
   int* d_bgfirst = nullptr;
+  int* d_bchunk_term = nullptr;
+  int* d_bchunk_group = nullptr;
+  int* d_bcomp_chunk = nullptr;
+  // bispectrum component runs by run count: device table and most chunks a run
+  std::map<int, std::pair<int*, int>> bpart_cache;
+  int nbparts = 0;
   void* d_root = nullptr;
   void* d_hscale = nullptr;
   int* d_yslice = nullptr;
@@ -321,6 +327,27 @@ int ensure_flags(snap_ctx* c) {
   return SNAP_OK;
 }
 
+// Component runs of the bispectrum kernels for n atoms: enough CTAs (32-atom
+// blocks x runs) for about three per SM, at most one run per component.
+int ensure_bparts(snap_ctx* c, long n) {
+  const long nblk = (n + 31) / 32;
+  int parts = (int)std::min<long>(16, std::max<long>(1, (3L * c->nsm + nblk - 1) / std::max(1L, nblk)));
+  parts = std::min(parts, c->tab.ncoeff);
+  if (parts == c->nbparts) return SNAP_OK;
+  auto it = c->bpart_cache.find(parts);
+  if (it == c->bpart_cache.end()) {
+    int mx = 0;
+    const std::vector<int> b = c->tab.bparts(parts, &mx);
+    int* d = nullptr;
+    int rc = upload(c, &d, b);
+    if (rc) return rc;
+    it = c->bpart_cache.emplace(parts, std::make_pair(d, mx)).first;
+  }
+  c->nbparts = parts;
+  c->ws_gen += 1;
+  return SNAP_OK;
+}
+
 bool box_ok(const double* box) {
   if (!box) return false;
   for (int d = 0; d < 3; ++d)
@@ -400,6 +427,15 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.bout = c->d_bout;
   a.bfirst = c->d_bfirst;
   a.bgfirst = c->d_bgfirst;
+  a.bchunk_term = c->d_bchunk_term;
+  a.bchunk_group = c->d_bchunk_group;
+  a.bcomp_chunk = c->d_bcomp_chunk;
+  a.nbparts = c->nbparts;
+  if (c->nbparts > 0) {
+    const auto& bp = c->bpart_cache.at(c->nbparts);
+    a.bpart = bp.first;
+    a.bmaxchunks = bp.second;
+  }
   a.rootpq = c->d_root;
   a.hscale = c->d_hscale;
   return a;
@@ -422,6 +458,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   if (!rc) rc = ensure_flags(c);
   if (rc) return rc;
   rc = ensure_slices(c, n);
+  if (!rc && mode != 0) rc = ensure_bparts(c, n);
   if (rc) return rc;
   SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 8 * sizeof(int), s));
   std::vector<cudaEvent_t> ev;
@@ -650,6 +687,50 @@ int launch_batch(snap_ctx* c, const double* pos, double* energy, double* forces,
   return SNAP_OK;
 }
 
+// The derivative of the bispectrum of a prepared batch along g (mode 2 of
+// enqueue over the concatenated configurations): asynchronous, allocates
+// nothing.
+int launch_batch_deriv(snap_ctx* c, const double* pos, const double* g, double* dB, cudaStream_t s) {
+  const int n = c->bat_total;
+  SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 8 * sizeof(int), s));
+  snap::NeighArgs na;
+  std::memset(&na, 0, sizeof(na));
+  na.n = n;
+  na.K = c->K;
+  na.confs = c->d_confs;
+  na.cta_map = c->d_ctamap;
+  na.pos = pos;
+  na.pos4 = c->d_pos4;
+  na.rcut = c->rcut;
+  na.cnt = c->d_cnt;
+  na.nbr = c->d_nbr;
+  na.img = c->d_img;
+  na.rij = c->d_rij;
+  na.key = c->d_key;
+  na.flags = c->d_flags;
+  snap::WorkArgs a = make_args(c, n, c->K);
+  const bool mixed = c->precision == SNAP_MIXED;
+  const bool colk = c->twojmax >= 1 && (mixed || c->twojmax <= 8);
+  SNAP_CUDA(c, snap::launch_pos4(n, pos, c->d_pos4, s));
+  int nl = 1;
+  if (colk) {
+    SNAP_CUDA(c, mixed ? snap::launch_neigh_u<float>(na, a, c->bat_ncta, s)
+                       : snap::launch_neigh_u<double>(na, a, c->bat_ncta, s));
+    nl += 1;
+  } else {
+    SNAP_CUDA(c, snap::launch_neigh_build_batch(na, c->bat_ncta, s));
+    SNAP_CUDA(c, mixed ? snap::launch_ui<float>(a, s) : snap::launch_ui<double>(a, s));
+    nl += 2;
+  }
+  SNAP_CUDA(c, mixed ? snap::launch_tan_col<float>(a, g, c->d_dU, s) : snap::launch_tan_col<double>(a, g, c->d_dU, s));
+  SNAP_CUDA(c, mixed ? snap::launch_dbi<float>(a, c->d_dU, dB, s) : snap::launch_dbi<double>(a, c->d_dU, dB, s));
+  SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  c->launches = nl + 2;
+  c->generation += 1;
+  c->have_last = false;
+  return SNAP_OK;
+}
+
 int check_flags(snap_ctx* c) {
   c->last_nmax = c->h_flags[0];
   c->seen_nmax = std::max(c->seen_nmax, c->last_nmax);
@@ -861,6 +942,9 @@ int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switch
   if (!rc) rc = upload(c, &c->d_bout, c->tab.bout);
   if (!rc) rc = upload(c, &c->d_bfirst, c->tab.bcomp_first);
   if (!rc) rc = upload(c, &c->d_bgfirst, c->tab.bgroup_first);
+  if (!rc) rc = upload(c, &c->d_bchunk_term, c->tab.bchunk_term);
+  if (!rc) rc = upload(c, &c->d_bchunk_group, c->tab.bchunk_group);
+  if (!rc) rc = upload(c, &c->d_bcomp_chunk, c->tab.bcomp_chunk);
   if (rc) {
     g_create_error = c->err;
     snap_destroy(c);
@@ -1066,6 +1150,25 @@ int snap_compute_batch(snap_ctx* c, int nconf, const int* natoms, const double* 
   SNAP_CUDA(c, cudaGraphLaunch(c->gexec, s));
   c->generation += 1;
   return SNAP_OK;
+}
+
+int snap_bispectrum_deriv_batch(snap_ctx* c, int nconf, const int* natoms, const double* boxes,
+                                const double* pos, const double* g, double* dB, void* stream) {
+  if (!c) return SNAP_ERR_ARG;
+  if (nconf < 0 || (nconf > 0 && (!natoms || !boxes))) return fail(c, SNAP_ERR_ARG, "bad batch description");
+  long total = 0;
+  for (int k = 0; k < nconf; ++k) {
+    if (natoms[k] < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
+    if (int rb = check_box(c, boxes + 3 * k)) return rb;
+    total += natoms[k];
+  }
+  if (total > (1L << 30)) return fail(c, SNAP_ERR_ARG, "batch too large");
+  if (total == 0) return SNAP_OK;
+  if (!pos || !g || !dB) return fail(c, SNAP_ERR_ARG, "pos, g and dB are required");
+  int rc = prepare_batch(c, nconf, natoms, boxes);
+  if (!rc) rc = ensure_bparts(c, c->bat_total);
+  if (rc) return rc;
+  return launch_batch_deriv(c, pos, g, dB, (cudaStream_t)stream);
 }
 
 int snap_set_tuning(snap_ctx* c, int col_warps, int yi_waves, int yi_layout) {
@@ -1326,6 +1429,11 @@ int snap_destroy(snap_ctx* c) {
   dfree(c->d_bout);
   dfree(c->d_bfirst);
   dfree(c->d_bgfirst);
+  dfree(c->d_bchunk_term);
+  dfree(c->d_bchunk_group);
+  dfree(c->d_bcomp_chunk);
+  for (auto& kv : c->bpart_cache) cudaFree(kv.second.first);
+  c->bpart_cache.clear();
   dfree(c->d_root);
   dfree(c->d_hscale);
   for (auto& kv : c->yslice_cache) cudaFree(kv.second);

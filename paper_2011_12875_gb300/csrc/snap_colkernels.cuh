@@ -400,45 +400,119 @@ __global__ void __launch_bounds__(NuShape<BATCH>::NW * 32) neigh_u_kernel(NeighA
 // atoms: the pair (i, k) moves by delta = g_k - g_i, so
 //   dU_t = sum_k d/de [ f_c(r_ik + e delta) u_t(r_ik + e delta) ] at e = 0
 //        = sum_k (grad f_c . delta) u_t + f_c (du_t/dr . delta).
-// One tangent chain rides along the layer recursion (the recursion is linear
-// in u, so the tangent obeys the differentiated recursion with conj(da) and
-// conj(db) along delta).  Layout and accumulation as ui_col_kernel; no w_self.
+// In the scaled form w = f_c v (u = S v): w_t = conj(a) w_{t-1}[ma] -
+// conj(b) w_{t-1}[ma-1] from w_0 = f_c, and its tangent
+//   dw_t = conj(da) w[ma] + conj(a) dw[ma] - conj(db) w[ma-1] - conj(b) dw[ma-1]
+// from dw_0 = grad f_c . delta, so dU_t = S sum_k dw_t (no w_self).  Launch
+// shape, reduction and order of the sums as compute_U (UiPlan).
 template <typename R, int J2>
-__global__ void __launch_bounds__(256) tan_col_kernel(WorkArgs a, const double* __restrict__ gd,
-                                                          void* dUout) {
+__device__ __forceinline__ void du_passes(const R* __restrict__ tg, int cnt, int wq, int lane,
+                                          c2<R>* __restrict__ scr) {
   using S = Shape<J2>;
-  constexpr int NC = S::NC, P = S::P;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int H = a.H;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long i = (long)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (i >= a.n) return;  // whole warp
-  c2<R>* acc = reinterpret_cast<c2<R>*>(smem) + (size_t)warp * P * H;  // [P][H]
+  using UP = UiPlan<R, J2>;
+  constexpr int NC = S::NC, P = S::P, LV = UP::LV, CPW = UP::CPW, Q = UP::Q, H = UP::HH;
+  c2<R>* run = scr + (size_t)CPW * H;
+  for (int e = lane; e < H; e += 32) run[e] = mk<R>(0, 0);
   const int g = lane / NC, mb = lane - g * NC;
   const bool grp = g < P;
-  for (int e = lane; e < P * H; e += 32) acc[e] = mk<R>(0, 0);
-  __syncwarp();
-  c2<R>* my = acc + (grp ? g : 0) * H;
-  R rs[J2 + 1];
-#pragma unroll
-  for (int t = 0; t <= J2; ++t) rs[t] = (t > mb) ? R(1) / sqrt(R(t - mb)) : R(0);
-  const int cnt = a.cnt[i];
-  for (int s0 = 0; s0 < cnt; s0 += P) {
-    const int s = s0 + g;
+  const bool writer = grp && (g & ((1 << LV) - 1)) == 0;
+  c2<R>* my = scr + (size_t)(writer ? (g >> LV) : 0) * H;
+  const int npass = (cnt + P - 1) / P;
+  for (int pass = wq; pass < npass; pass += Q) {
+    const int s = pass * P + g;
     const bool ok = grp && s < cnt;
     c2<R> ca = mk<R>(1, 0), cb = mk<R>(0, 0), cda = mk<R>(0, 0), cdb = mk<R>(0, 0);
     R fc = 0, dfc = 0;
-    if (ok) {
-      const long slot = (long)i * a.K + s;
+    if (ok) {  // [10]: a, b, f_c, d f_c, da, db along delta
+      const R* t = tg + 10 * s;
+      ca = mk<R>(t[0], -t[1]);
+      cb = mk<R>(t[2], -t[3]);
+      fc = t[4];
+      dfc = t[5];
+      cda = mk<R>(t[6], -t[7]);
+      cdb = mk<R>(t[8], -t[9]);
+    }
+    c2<R> w[J2 + 1], dw[J2 + 1];
+#pragma unroll
+    for (int k = 0; k <= J2; ++k) w[k] = dw[k] = mk<R>(0, 0);
+    if (mb == 0) {
+      w[0] = mk<R>(fc, 0);
+      dw[0] = mk<R>(dfc, 0);
+    }
+    {
+      const R v0 = group_sum<LV, NC>(dw[0].re, lane);
+      if (writer && mb == 0) my[0] = mk<R>(v0, 0);
+    }
+    static_for<1, J2>([&](auto tc) {
+      constexpr int t = decltype(tc)::value;
+      if constexpr ((t & 1) == 0) {
+        v_seed<R, t>(w, mb == t / 2);
+        v_seed<R, t>(dw, mb == t / 2);
+      }
+      // dw first (it reads the old w), then w
+#pragma unroll
+      for (int ma = t; ma >= 0; --ma) {
+        c2<R> y = mk<R>(0, 0);
+        if (ma < t) {
+          const c2<R> p = w[ma], q = dw[ma];
+          y.re += cda.re * p.re - cda.im * p.im + ca.re * q.re - ca.im * q.im;
+          y.im += cda.re * p.im + cda.im * p.re + ca.re * q.im + ca.im * q.re;
+        }
+        if (ma > 0) {
+          const c2<R> p = w[ma - 1], q = dw[ma - 1];
+          y.re -= cdb.re * p.re - cdb.im * p.im + cb.re * q.re - cb.im * q.im;
+          y.im -= cdb.re * p.im + cdb.im * p.re + cb.re * q.im + cb.im * q.re;
+        }
+        dw[ma] = y;
+      }
+      v_layer<R, t>(w, ca, cb);
+      c2<R>* dst = my + half_base(t) + mb * (t + 1);
+#pragma unroll
+      for (int ma = 0; ma <= t; ++ma) {
+        const R vr = group_sum<LV, NC>(dw[ma].re, lane);
+        const R vi = group_sum<LV, NC>(dw[ma].im, lane);
+        if (writer && 2 * mb <= t) dst[ma] = mk<R>(vr, vi);
+      }
+    });
+    __syncwarp();
+    for (int e = lane; e < H; e += 32) {
+      c2<R> v = run[e];
+#pragma unroll
+      for (int c = 0; c < CPW; ++c) {
+        const c2<R> q = scr[(size_t)c * H + e];
+        v.re += q.re;
+        v.im += q.im;
+      }
+      run[e] = v;
+    }
+    __syncwarp();
+  }
+}
+
+template <typename R, int J2>
+__global__ void __launch_bounds__(64, ui_min_ctas<R, J2>()) tan_col_kernel(WorkArgs a, const double* __restrict__ gd,
+                                                                         void* dUout) {
+  using UP = UiPlan<R, J2>;
+  constexpr int Q = UP::Q, A = UP::A, CPW = UP::CPW, H = UP::HH;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = a.K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int al = warp / Q, wq = warp - al * Q;
+  const long i0 = (long)blockIdx.x * A;
+  const long i = i0 + al;
+  const bool have = i < a.n;  // warp-uniform
+  c2<R>* scr = reinterpret_cast<c2<R>*>(smem) + (size_t)warp * (CPW + 1) * H;
+  R* tg = reinterpret_cast<R*>(smem + (size_t)A * Q * UP::warp_bytes) + (size_t)al * K * 10;
+  const int cnt = have ? a.cnt[i] : 0;
+  if (have && wq == 0)  // the pair data along delta = g_k - g_i, a lane per slot
+    for (int s = lane; s < cnt; s += 32) {
+      const long slot = i * K + s;
       const R* gm = reinterpret_cast<const R*>(a.geom) + slot * kGeomStride;
       const int k = a.nbr[slot];
       R dl[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) dl[d] = (R)(gd[3 * (long)k + d] - gd[3 * (long)i + d]);
-      ca = mk<R>(gm[0], -gm[1]);
-      cb = mk<R>(gm[2], -gm[3]);
-      fc = gm[4];
-      R ar = 0, ai = 0, br = 0, bi = 0;
+      for (int d = 0; d < 3; ++d) dl[d] = (R)(gd[3 * (long)k + d] - gd[3 * i + d]);
+      R dfc = 0, ar = 0, ai = 0, br = 0, bi = 0;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         dfc += dl[d] * gm[5 + d];
@@ -447,67 +521,37 @@ __global__ void __launch_bounds__(256) tan_col_kernel(WorkArgs a, const double* 
         br += dl[d] * gm[14 + 2 * d];
         bi += dl[d] * gm[15 + 2 * d];
       }
-      cda = mk<R>(ar, -ai);  // conj(da along delta)
-      cdb = mk<R>(br, -bi);
+      R* t = tg + 10 * s;
+      t[0] = gm[0];
+      t[1] = gm[1];
+      t[2] = gm[2];
+      t[3] = gm[3];
+      t[4] = gm[4];
+      t[5] = dfc;
+      t[6] = ar;
+      t[7] = ai;
+      t[8] = br;
+      t[9] = bi;
     }
-    c2<R> u[J2 + 1], du[J2 + 1];
-#pragma unroll
-    for (int k = 0; k <= J2; ++k) u[k] = du[k] = mk<R>(0, 0);
-    if (mb == 0) u[0] = mk<R>(1, 0);
-    if (ok && mb == 0) my[0].re += dfc;
-    static_for<1, J2>([&](auto tc) {
-      constexpr int t = decltype(tc)::value;
-      if constexpr ((t & 1) == 0) {
-        seed_column<R, t>(u, mb == t / 2);
-        seed_column<R, t>(du, mb == t / 2);
-      }
-      const R r = rs[t];
-      const c2<R> A = mk<R>(r * ca.re, r * ca.im), B = mk<R>(r * cb.re, r * cb.im);
-      const c2<R> dA = mk<R>(r * cda.re, r * cda.im), dB = mk<R>(r * cdb.re, r * cdb.im);
-#pragma unroll
-      for (int ma = t; ma >= 0; --ma) {
-        c2<R> v = mk<R>(0, 0), dv = mk<R>(0, 0);
-        if (ma < t) {
-          const R c = sqrt_int<R>(t - ma);
-          const c2<R> p = u[ma], q = du[ma];
-          v.re = c * (A.re * p.re - A.im * p.im);
-          v.im = c * (A.re * p.im + A.im * p.re);
-          dv.re = c * (dA.re * p.re - dA.im * p.im + A.re * q.re - A.im * q.im);
-          dv.im = c * (dA.re * p.im + dA.im * p.re + A.re * q.im + A.im * q.re);
-        }
-        if (ma > 0) {
-          const R c = sqrt_int<R>(ma);
-          const c2<R> p = u[ma - 1], q = du[ma - 1];
-          v.re -= c * (B.re * p.re - B.im * p.im);
-          v.im -= c * (B.re * p.im + B.im * p.re);
-          dv.re -= c * (dB.re * p.re - dB.im * p.im + B.re * q.re - B.im * q.im);
-          dv.im -= c * (dB.re * p.im + dB.im * p.re + B.re * q.im + B.im * q.re);
-        }
-        u[ma] = v;
-        du[ma] = dv;
-      }
-      if (ok && 2 * mb <= t) {
-        c2<R>* dst = my + half_base(t) + mb * (t + 1);
-#pragma unroll
-        for (int ma = 0; ma <= t; ++ma) {
-          dst[ma].re += dfc * u[ma].re + fc * du[ma].re;
-          dst[ma].im += dfc * u[ma].im + fc * du[ma].im;
-        }
-      }
-    });
-  }
-  __syncwarp();
+  __syncthreads();
+  if (have) du_passes<R, J2>(tg, cnt, wq, lane, scr);
+  __syncthreads();
   c2<R>* Ug = reinterpret_cast<c2<R>*>(dUout);
-  const long blk = i >> 5;
-  const int li = (int)(i & 31);
-  for (int e = lane; e < H; e += 32) {
-    R sr = 0, si = 0;
+  for (int a2 = 0; a2 < A; ++a2) {
+    const long ii = i0 + a2;
+    if (ii >= a.n) break;
+    const c2<R>* rr = reinterpret_cast<const c2<R>*>(smem) + (size_t)a2 * Q * (CPW + 1) * H + (size_t)CPW * H;
+    for (int e = threadIdx.x; e < H; e += blockDim.x) {
+      R sr = 0, si = 0;
 #pragma unroll
-    for (int c = 0; c < P; ++c) {
-      sr += acc[c * H + e].re;
-      si += acc[c * H + e].im;
+      for (int q = 0; q < Q; ++q) {
+        const c2<R> v = rr[(size_t)q * (CPW + 1) * H + e];
+        sr += v.re;
+        si += v.im;
+      }
+      const R sc = reinterpret_cast<const R*>(a.hscale)[e];
+      Ug[((ii >> 5) * H + e) * 32 + (ii & 31)] = mk<R>(sr * sc, si * sc);
     }
-    Ug[(blk * H + e) * 32 + li] = mk<R>(sr, si);
   }
 }
 
@@ -782,11 +826,13 @@ cudaError_t launch_neigh_u_t(const NeighArgs& na, const WorkArgs& a, int ncta, c
 template <typename R, int J2>
 cudaError_t launch_tan_col_t(const WorkArgs& a, const double* g, void* dU, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const size_t per = sizeof(c2<R>) * (size_t)Shape<J2>::P * a.H;
-  const int nw = col_fit_warps(a.col_warps, per);
-  cudaError_t e = col_allow_smem(tan_col_kernel<R, J2>, per * nw);
+  using UP = UiPlan<R, J2>;
+  if (a.H != UP::HH) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)UP::A * (UP::Q * UP::warp_bytes + sizeof(R) * 10 * (size_t)a.K);
+  cudaError_t e = col_allow_smem(tan_col_kernel<R, J2>, smem);
   if (e != cudaSuccess) return e;
-  return launch_k(tan_col_kernel<R, J2>, dim3((a.n + nw - 1) / nw), dim3(nw * 32), per * nw, s, a, g, dU);
+  return launch_k(tan_col_kernel<R, J2>, dim3((unsigned)((a.n + UP::A - 1) / UP::A)), dim3(UP::A * UP::Q * 32),
+                  smem, s, a, g, dU);
 }
 
 // Launch plan of the fused dE kernel: warps per CTA (NW) and atoms per CTA

@@ -21,6 +21,7 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
 
 constexpr int kMaxTwoJ = 14;
 constexpr int kYGroupMax = 8;  // longest compute_Y term group (longer ones are cut)
+constexpr int kBChunk = 192;   // bispectrum terms a warp takes at a time (whole groups)
 constexpr int kYRecPad = 256;  // zero records after the compute_Y term list (read-ahead)
 constexpr int kYRecPrefetch = 64;  // compute_Y's L1 prefetch distance without the record ring
 constexpr int kMaxNeighCap = 64;
@@ -180,6 +181,11 @@ struct WorkArgs {
   const int* bout;        // U element of every output group
   const int* bfirst;      // [ncoeff+1] first term of each component
   const int* bgfirst;     // [ncoeff+1] first output group of each component
+  const int* bchunk_term;   // chunks of the bispectrum term list (snap_tables.h)
+  const int* bchunk_group;
+  const int* bcomp_chunk;
+  const int* bpart;         // [nbparts+1] first component of each CTA's run
+  int nbparts, bmaxchunks;
   double* B;              // [N][ncoeff]
   const void* rootpq;
   const void* hscale;  // R [H]: S_t(ma, mb) of the scaled recursion (u = S v)

@@ -231,14 +231,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase,
 // CTA's shared memory).  skip_copy registers the bytes without issuing the
 // copy: a test hook under which the wait runs out with nothing in flight.
 // `overlap()` runs on every thread while the copy is in flight.
+// With src2 given, a second block of `bytes` from src2 lands right after the
+// first (dst + bytes) on the same barrier.
 template <typename F>
 __device__ bool stage_bulk(void* dst, const void* src, unsigned bytes, uint64_t* bar, int* flags,
-                           bool skip_copy, F&& overlap) {
+                           bool skip_copy, F&& overlap, const void* src2 = nullptr) {
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
-    mbar_expect_tx(bar, bytes);
-    if (!skip_copy) bulk_g2s(dst, src, bytes, bar);
+    mbar_expect_tx(bar, src2 ? 2 * bytes : bytes);
+    if (!skip_copy) {
+      bulk_g2s(dst, src, bytes, bar);
+      if (src2) bulk_g2s(static_cast<char*>(dst) + bytes, src2, bytes, bar);
+    }
   }
   overlap();
   const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0, kWaitNs));
@@ -599,100 +604,84 @@ __global__ void __launch_bounds__(kYaWarps * 32) yi_atom_kernel(WorkArgs a) {
 
 // ------------------------------------------------------- bispectrum B_l
 // Descriptor output (Sec. II-A, Eq. z): B_l = Re Z^t_{t1t2} : conj(U_t) for
-// every canonical component l, for 32 atoms per warp (lanes = atoms, U staged
-// in shared memory as in compute_Y).  One warp per component: its terms are
-// summed per output element and each output is dotted with conj(U_t).
-template <typename R, bool STAGED>
-__global__ void __launch_bounds__(256) bi_kernel(WorkArgs a) {
+// every canonical component l, 32 atoms a CTA (lanes = atoms; the block's U
+// staged in shared memory by a TMA bulk copy, as in compute_Y), and, with
+// DERIV, its directional derivative along the tangent dU of Ulisttot
+// (Eqs. z and dbidrk): B_l is trilinear in (U_t1, U_t2, conj U_t), so
+//   dB_l = Re [ (Z(dU_t1, U_t2) + Z(U_t1, dU_t2)) : conj(U_t) + Z : conj(dU_t) ]
+// (dU has the inversion symmetry of U, so the records' conjugation flags hold
+// for it too; its block is staged beside U).
+// The term list is cut into chunks of whole output groups (about kBChunk
+// terms, never across a component).  CTA (block, part) takes the components
+// of its part; its warps take the part's chunks in turn, each leaving one
+// partial sum per atom in shared memory, and the partials of a component are
+// added in chunk order: a fixed order, whatever the launch shape, and no warp
+// waits on the largest component.
+template <typename R, bool STAGED, bool DERIV>
+__global__ void __launch_bounds__(256) bi_kernel(WorkArgs a, const cx<R>* __restrict__ dUg, double* __restrict__ out) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const long blk = blockIdx.x;
   const int H = a.H;
   const cx<R>* us = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
+  const cx<R>* ds = DERIV ? dUg + blk * H * 32 : nullptr;
+  const size_t plane = (size_t)H * 32 * sizeof(cx<R>);
+  R* part = reinterpret_cast<R*>(smem + (STAGED ? (DERIV ? 2 : 1) * plane + 16 : 0));  // [maxchunks][32]
   if (STAGED) {
     cx<R>* su = reinterpret_cast<cx<R>*>(smem);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(su + H * 32);
-    const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
-    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0, [] {})) return;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (DERIV ? 2 : 1) * plane);
+    if (!stage_bulk(su, us, (unsigned)plane, bar, a.flags, a.test_skip_stage != 0, [] {},
+                    DERIV ? reinterpret_cast<const void*>(ds) : nullptr))
+      return;
     us = su;
+    if (DERIV) ds = su + H * 32;
   }
-  const int l = blockIdx.y * (blockDim.x >> 5) + warp;
-  if (l >= a.ncoeff) return;
+  const int l0 = a.bpart[blockIdx.y], l1 = a.bpart[blockIdx.y + 1];
+  const int c0 = a.bcomp_chunk[l0], c1 = a.bcomp_chunk[l1];
   const YRec<R>* __restrict__ rec = reinterpret_cast<const YRec<R>*>(a.brec);
-  int g = a.bgfirst[l];
-  R zr = R(0), zi = R(0), acc = R(0);
-  for (int q = a.bfirst[l]; q < a.bfirst[l + 1]; ++q) {
-    const unsigned w = rec[q].w;
-    const R c = rec[q].c;
-    const cx<R> u1 = us[(int)(w & 1023u) * 32 + lane];
-    const cx<R> u2 = us[(int)((w >> 10) & 1023u) * 32 + lane];
-    const R b = flip_if(u1.im, (w >> 20) & 1u);
-    const R d = flip_if(u2.im, (w >> 21) & 1u);
-    zr += c * (u1.re * u2.re - b * d);
-    zi += c * (u1.re * d + b * u2.re);
-    if (w & (1u << 22)) {
-      const cx<R> u = us[a.bout[g] * 32 + lane];
-      acc += u.re * zr + u.im * zi;
-      zr = R(0);
-      zi = R(0);
-      ++g;
+  for (int ch = c0 + warp; ch < c1; ch += nw) {
+    int g = a.bchunk_group[ch];
+    R zr = R(0), zi = R(0), dzr = R(0), dzi = R(0), acc = R(0);
+    const int q1 = a.bchunk_term[ch + 1];
+    for (int q = a.bchunk_term[ch]; q < q1; ++q) {
+      const unsigned w = rec[q].w;
+      const R c = rec[q].c;
+      const int e1 = (int)(w & 1023u), e2 = (int)((w >> 10) & 1023u);
+      const unsigned f1 = (w >> 20) & 1u, f2 = (w >> 21) & 1u;
+      const cx<R> u1 = us[e1 * 32 + lane], u2 = us[e2 * 32 + lane];
+      const R b = flip_if(u1.im, f1), d = flip_if(u2.im, f2);
+      zr += c * (u1.re * u2.re - b * d);
+      zi += c * (u1.re * d + b * u2.re);
+      if (DERIV) {
+        const cx<R> d1 = ds[e1 * 32 + lane], d2 = ds[e2 * 32 + lane];
+        const R db1 = flip_if(d1.im, f1), db2 = flip_if(d2.im, f2);
+        // d(u1 u2) = du1 u2 + u1 du2
+        dzr += c * (d1.re * u2.re - db1 * d + u1.re * d2.re - b * db2);
+        dzi += c * (d1.re * d + db1 * u2.re + u1.re * db2 + b * d2.re);
+      }
+      if (w & (1u << 22)) {
+        const int o = a.bout[g];
+        const cx<R> u = us[o * 32 + lane];
+        if (DERIV) {
+          const cx<R> du = ds[o * 32 + lane];
+          acc += u.re * dzr + u.im * dzi + du.re * zr + du.im * zi;
+          dzr = dzi = R(0);
+        } else {
+          acc += u.re * zr + u.im * zi;
+        }
+        zr = zi = R(0);
+        ++g;
+      }
     }
+    part[(ch - c0) * 32 + lane] = acc;
   }
+  __syncthreads();
   const long i = blk * 32 + lane;
-  if (i < a.n) a.B[i * a.ncoeff + l] = (double)acc;
-}
-
-// ------------------------------------------- d B_l along a displacement
-// Directional derivative of the bispectrum (Eq. z) along the tangent dU of
-// Ulisttot: B_l is trilinear in (U_t1, U_t2, conj U_t), so
-//   dB_l = Re [ (Z(dU_t1, U_t2) + Z(U_t1, dU_t2)) : conj(U_t) + Z : conj(dU_t) ],
-// the same term list as bi_kernel (dU has the inversion symmetry of U, so
-// the conjugation flags apply to both).  U is staged as in bi_kernel; dU is
-// read from global memory.
-template <typename R, bool STAGED>
-__global__ void __launch_bounds__(256) dbi_kernel(WorkArgs a, const cx<R>* __restrict__ dUg, double* dB) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long blk = blockIdx.x;
-  const int H = a.H;
-  const cx<R>* us = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
-  const cx<R>* ds = dUg + blk * H * 32;
-  if (STAGED) {
-    cx<R>* su = reinterpret_cast<cx<R>*>(smem);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(su + H * 32);
-    const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
-    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0, [] {})) return;
-    us = su;
+  for (int l = l0 + warp; l < l1; l += nw) {
+    R v = R(0);
+    for (int ch = a.bcomp_chunk[l]; ch < a.bcomp_chunk[l + 1]; ++ch) v += part[(ch - c0) * 32 + lane];
+    if (i < a.n) out[i * a.ncoeff + l] = (double)v;
   }
-  const int l = blockIdx.y * (blockDim.x >> 5) + warp;
-  if (l >= a.ncoeff) return;
-  const YRec<R>* __restrict__ rec = reinterpret_cast<const YRec<R>*>(a.brec);
-  int g = a.bgfirst[l];
-  R zr = R(0), zi = R(0), dzr = R(0), dzi = R(0), acc = R(0);
-  for (int q = a.bfirst[l]; q < a.bfirst[l + 1]; ++q) {
-    const unsigned w = rec[q].w;
-    const R c = rec[q].c;
-    const int e1 = (int)(w & 1023u), e2 = (int)((w >> 10) & 1023u);
-    const unsigned f1 = (w >> 20) & 1u, f2 = (w >> 21) & 1u;
-    const cx<R> u1 = us[e1 * 32 + lane], u2 = us[e2 * 32 + lane];
-    const cx<R> d1 = ds[e1 * 32 + lane], d2 = ds[e2 * 32 + lane];
-    const R b = flip_if(u1.im, f1), d = flip_if(u2.im, f2);
-    const R db1 = flip_if(d1.im, f1), db2 = flip_if(d2.im, f2);
-    zr += c * (u1.re * u2.re - b * d);
-    zi += c * (u1.re * d + b * u2.re);
-    // d(u1 u2) = du1 u2 + u1 du2
-    dzr += c * (d1.re * u2.re - db1 * d + u1.re * d2.re - b * db2);
-    dzi += c * (d1.re * d + db1 * u2.re + u1.re * db2 + b * d2.re);
-    if (w & (1u << 22)) {
-      const int o = a.bout[g];
-      const cx<R> u = us[o * 32 + lane], du = ds[o * 32 + lane];
-      acc += u.re * dzr + u.im * dzi + du.re * zr + du.im * zi;
-      zr = zi = dzr = dzi = R(0);
-      ++g;
-    }
-  }
-  const long i = blk * 32 + lane;
-  if (i < a.n) dB[i * a.ncoeff + l] = (double)acc;
 }
 
 // ------------------------------------------- weighted force (autograd)
@@ -1233,35 +1222,39 @@ cudaError_t launch_force(const WorkArgs& a, cudaStream_t s) {
   return launch_k(force_kernel<R>, dim3((unsigned)((a.n + kFAtoms - 1) / kFAtoms)), dim3(kFThreads), sm, s, a);
 }
 
+// Bispectrum (dU == nullptr) or its derivative along dU into out [N][N_B]:
+// grid (32-atom blocks, component runs a.nbparts), 8 warps a CTA.
+template <typename R, bool DERIV>
+cudaError_t launch_bi_t(const WorkArgs& a, const void* dU, double* out, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const long nblk = (a.n + 31) / 32;
+  const size_t plane = (size_t)a.H * 32 * sizeof(cx<R>);
+  const size_t stage = (DERIV ? 2 : 1) * plane + 16;
+  const size_t parts = (size_t)a.bmaxchunks * 32 * sizeof(R);
+  const bool staged = stage + parts <= 200 * 1024;
+  const size_t sm = (staged ? stage : 0) + parts;
+  const dim3 grid((unsigned)nblk, (unsigned)a.nbparts);
+  const cx<R>* d = reinterpret_cast<const cx<R>*>(dU);
+  if (staged) {
+    cudaError_t e = allow_smem(bi_kernel<R, true, DERIV>, sm);
+    if (e != cudaSuccess) return e;
+    return launch_k(bi_kernel<R, true, DERIV>, grid, dim3(256), sm, s, a, d, out);
+  }
+  cudaError_t e = allow_smem(bi_kernel<R, false, DERIV>, sm);
+  if (e != cudaSuccess) return e;
+  return launch_k(bi_kernel<R, false, DERIV>, grid, dim3(256), sm, s, a, d, out);
+}
+
 template <typename R>
 cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s) {
-  if (a.n <= 0) return cudaSuccess;
-  const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm, 2);
-  dim3 grid(g.nblk, (a.ncoeff + 7) / 8);
-  const size_t sm = (size_t)2 * a.H * 32 * sizeof(R) + 16;
-  if (g.staged) {
-    cudaError_t e = allow_smem(bi_kernel<R, true>, sm);
-    if (e != cudaSuccess) return e;
-    return launch_k(bi_kernel<R, true>, dim3(grid), dim3(256), sm, s, a);
-  }
-  return launch_k(bi_kernel<R, false>, dim3(grid), dim3(256), 0, s, a);
+  return launch_bi_t<R, false>(a, nullptr, a.B, s);
 }
 template cudaError_t launch_bi<float>(const WorkArgs&, cudaStream_t);
 template cudaError_t launch_bi<double>(const WorkArgs&, cudaStream_t);
 
 template <typename R>
 cudaError_t launch_dbi(const WorkArgs& a, const void* dU, double* dB, cudaStream_t s) {
-  if (a.n <= 0) return cudaSuccess;
-  const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm, 2);
-  dim3 grid(g.nblk, (a.ncoeff + 7) / 8);
-  const cx<R>* d = reinterpret_cast<const cx<R>*>(dU);
-  const size_t sm = (size_t)2 * a.H * 32 * sizeof(R) + 16;
-  if (g.staged) {
-    cudaError_t e = allow_smem(dbi_kernel<R, true>, sm);
-    if (e != cudaSuccess) return e;
-    return launch_k(dbi_kernel<R, true>, dim3(grid), dim3(256), sm, s, a, d, dB);
-  }
-  return launch_k(dbi_kernel<R, false>, dim3(grid), dim3(256), 0, s, a, d, dB);
+  return launch_bi_t<R, true>(a, dU, dB, s);
 }
 template cudaError_t launch_dbi<float>(const WorkArgs&, const void*, double*, cudaStream_t);
 template cudaError_t launch_dbi<double>(const WorkArgs&, const void*, double*, cudaStream_t);

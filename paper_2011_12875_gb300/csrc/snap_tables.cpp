@@ -392,6 +392,31 @@ void HostTables::build(int J2, bool size_runs) {
   }
   bcomp_first.push_back((int)bterms.size());
   bgroup_first.push_back((int)bout.size());
+  // chunks of whole groups, about kBChunk terms, within components
+  bchunk_term.clear();
+  bchunk_group.clear();
+  bcomp_chunk.clear();
+  for (int l = 0; l < ncoeff; ++l) {
+    bcomp_chunk.push_back((int)bchunk_term.size());
+    int q = bcomp_first[l], gq = bgroup_first[l];
+    bchunk_term.push_back(q);
+    bchunk_group.push_back(gq);
+    int inchunk = 0;
+    for (; q < bcomp_first[l + 1]; ++q) {
+      ++inchunk;
+      if (bterms[q] & (1u << 22)) {  // a group ends here
+        ++gq;
+        if (inchunk >= kBChunk && q + 1 < bcomp_first[l + 1]) {
+          bchunk_term.push_back(q + 1);
+          bchunk_group.push_back(gq);
+          inchunk = 0;
+        }
+      }
+    }
+  }
+  bcomp_chunk.push_back((int)bchunk_term.size());
+  bchunk_term.push_back((int)bterms.size());
+  bchunk_group.push_back((int)bout.size());
 
   half_scale.assign(H, 0.0);
   for (int e = 0; e < H; ++e) {
@@ -433,6 +458,14 @@ std::vector<int> HostTables::bslices(int nslices) const {
   }
   while ((int)b.size() < nslices + 1) b.push_back(ncoeff);
   b[nslices] = ncoeff;
+  return b;
+}
+
+std::vector<int> HostTables::bparts(int nparts, int* maxchunks) const {
+  const std::vector<int> b = bslices(nparts);
+  int mx = 0;
+  for (int k = 0; k < nparts; ++k) mx = std::max(mx, bcomp_chunk[b[k + 1]] - bcomp_chunk[b[k]]);
+  *maxchunks = mx;
   return b;
 }
 

@@ -33,6 +33,10 @@ struct HostTables {
   std::vector<int> bout;
   std::vector<int> bcomp_first;
   std::vector<int> bgroup_first;  // [ncoeff+1] first output group of each component
+  // the bispectrum term list cut into chunks of whole output groups (about
+  // kBChunk terms, never across a component): first term and first group of
+  // every chunk (+1 end entry each) and the first chunk of every component
+  std::vector<int> bchunk_term, bchunk_group, bcomp_chunk;
   std::vector<double> rootpq;
   // [H]: S_t(ma, mb) = sqrt((t - ma)! ma! / (t - mb)!) of every half-layout
   // element, the factor between the scaled recursion's v and u
@@ -48,6 +52,10 @@ struct HostTables {
   // [lanes][m] output indices, -1 past a lane's last; m returned in *m
   std::vector<int> lane_outputs(int lanes, int* m) const;
   std::vector<int> bslices(int nslices) const;
+  // nparts contiguous runs of components with about equal term counts (entry
+  // k = first component of run k, entry nparts = ncoeff); *maxchunks = the
+  // most chunks of one run
+  std::vector<int> bparts(int nparts, int* maxchunks) const;
 };
 
 double clebsch_gordan(int tj1, int tm1, int tj2, int tm2, int tj, int tm);

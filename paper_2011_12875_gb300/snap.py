@@ -44,7 +44,7 @@ EXPORTS = ("snap_num_coeff", "snap_create", "snap_set_beta", "snap_set_neigh_cap
            "snap_bispectrum_deriv", "snap_force_weighted", "snap_generation",
            "snap_compute_batch", "snap_set_tuning", "snap_get_tuning", "snap_autotune",
            "snap_neighbors_noalloc", "snap_yi_host", "snap_test_stage_timeout",
-           "snap_probe_fma")
+           "snap_probe_fma", "snap_bispectrum_deriv_batch")
 NSTAGES = 5
 
 _lib = None
@@ -100,6 +100,8 @@ def load(path: str | None = None):
     L.snap_generation.restype = ctypes.c_longlong
     L.snap_compute_batch.argtypes = [p, i, p, p, p, p, p, p, i, p]
     L.snap_compute_batch.restype = i
+    L.snap_bispectrum_deriv_batch.argtypes = [p, i, p, p, p, p, p, p]
+    L.snap_bispectrum_deriv_batch.restype = i
     L.snap_set_tuning.argtypes = [p, i, i, i]
     L.snap_set_tuning.restype = i
     L.snap_test_stage_timeout.argtypes = [p, i]
@@ -345,6 +347,26 @@ class Snap:
             self.sync(stream)
         self._batch_keep = (na, bx)
         return energy, forces, virial
+
+    def bispectrum_deriv_batch(self, pos, natoms, boxes, g, out=None, stream=None, wait=True):
+        """snap_bispectrum_deriv over a batch of configurations (see
+        compute_batch for the layout): dB [sum natoms, N_B]."""
+        import torch
+        na, bx, _, _, _ = self._batch_args(pos, natoms, boxes, None, None, None)
+        if g.dtype != torch.float64 or not g.is_cuda or not g.is_contiguous() or g.shape != pos.shape:
+            raise ValueError("g must be a contiguous float64 CUDA tensor shaped like pos")
+        nc = self._lib.snap_num_coeff(self.twojmax)
+        if out is None:
+            out = torch.empty((pos.shape[0], nc), dtype=torch.float64, device=pos.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(pos.device).cuda_stream
+        self._check(self._lib.snap_bispectrum_deriv_batch(
+            self._h, len(na), _np_ptr(na), _np_ptr(bx), _t_ptr(pos), _t_ptr(g), _t_ptr(out),
+            ctypes.c_void_p(stream)))
+        self._batch_keep = (na, bx)
+        if wait:
+            self.sync(stream)
+        return out
 
     def set_tuning(self, col_warps: int, yi_waves: int, yi_layout: int = 0):
         """Launch-shape tunables (see snap_set_tuning); yi_layout 0 = warp of

@@ -377,3 +377,38 @@ def test_force_matching_gradient_vs_oracle(snapmod, twojmax, prec):
         proj_o = float((2.0 * r_o * Fv).sum())
         proj = float(grad[1:] @ v[1:])
         assert abs(proj - proj_o) <= tol * np.abs(v[1:]).sum() * np.abs(grad[1:]).max(), (k, proj, proj_o)
+
+
+@pytest.mark.parametrize("prec,twojmax", [(0, 8), (1, 8), (1, 14)])
+def test_bispectrum_derivative_batch_equals_per_configuration(snapmod, prec, twojmax):
+    """snap_bispectrum_deriv_batch over uneven configurations (boxes below
+    2 rcut included) gives, bit for bit, the derivative of one
+    snap_bispectrum_deriv per configuration, and the batched force-matching
+    gradient is the sum of the per-configuration gradients."""
+    from paper_2011_12875_gb300 import autograd as AG
+    cfgs, pos, natoms, boxes = batch_of([3, 2, 4, 3], seed=71)
+    s = snapmod.Snap(twojmax, inputs.beta(twojmax), precision=prec)
+    rng = np.random.Generator(np.random.PCG64(72))
+    g = rng.normal(size=pos.shape)
+    P = torch.tensor(pos, device="cuda:0")
+    G = torch.tensor(g, device="cuda:0")
+    dB = s.bispectrum_deriv_batch(P, natoms, boxes, G).cpu().numpy().copy()
+    start = 0
+    for c in cfgs:
+        sl = slice(start, start + c.natoms)
+        one = s.bispectrum_deriv(torch.tensor(c.pos, device="cuda:0"), c.box,
+                                 torch.tensor(g[sl], device="cuda:0")).cpu().numpy()
+        assert np.array_equal(dB[sl], one)
+        start += c.natoms
+    f_ref = torch.tensor(rng.normal(size=pos.shape), device="cuda:0")
+    loss, grad = AG.force_matching_grad_batch(s, P, natoms, boxes, f_ref)
+    lsum, gsum, start = 0.0, np.zeros(len(grad)), 0
+    for c in cfgs:
+        sl = slice(start, start + c.natoms)
+        l1, g1 = AG.force_matching_grad(s, torch.tensor(c.pos, device="cuda:0"), c.box, f_ref[sl].contiguous())
+        lsum += float(l1)
+        gsum += g1.cpu().numpy()
+        start += c.natoms
+    s.close()
+    assert float(loss) == pytest.approx(lsum, rel=1e-12)
+    np.testing.assert_allclose(grad.cpu().numpy(), gsum, rtol=1e-10, atol=1e-12 * np.abs(gsum).max())
