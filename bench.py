@@ -365,11 +365,20 @@ def next_rows(torch, snap, inputs, flush, dev, args):
                                                             wait=False), steps, flush, dev)
     best_ms = s.autotune(pos, natoms, boxes, reps=5)
     tuned = s.get_tuning()
+    tuned_persist = s.get_knob(snap.KNOB_PERSIST)
     s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=True)
     t_graph = _events_time(torch, lambda: s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=True,
                                                           wait=False), steps, flush, dev)
     t_nograph = _events_time(torch, lambda: s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=False,
                                                             wait=False), steps, flush, dev)
+    # the persistent work-queue launches at the tuned shape, graph replay
+    per_persist = {}
+    for p_ in (0, 1, 2, 3):
+        s.set_knob(snap.KNOB_PERSIST, p_)
+        s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=True)
+        per_persist[p_] = _events_time(torch, lambda: s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=True,
+                                                                      wait=False), steps, flush, dev)
+    s.set_knob(snap.KNOB_PERSIST, tuned_persist)
     s.sync()
     singles = [torch.tensor(c.pos, device=dev) for c in cfgs]
     outs = [(torch.empty(c.natoms, dtype=torch.float64, device=dev),
@@ -390,10 +399,11 @@ def next_rows(torch, snap, inputs, flush, dev, args):
         "batched_no_graph_ms": t_nograph, "per_config_loop_ms": t_loop,
         "per_config_loop_atom_steps_per_s": total / (t_loop * 1e-3),
         "speedup_vs_loop": t_loop / t_graph,
+        "graph_ms_by_persist": per_persist,
         "default_tuning": {"col_warps": default_tuning[0], "yi_waves": default_tuning[1],
                            "yi_layout": default_tuning[2], "graph_ms": t_default},
         "autotuned": {"col_warps": tuned[0], "yi_waves": tuned[1], "yi_layout": tuned[2],
-                      "autotune_median_ms": best_ms}}
+                      "persist": tuned_persist, "autotune_median_ms": best_ms}}
     # --- compute_Y layouts on the headline workload: warp of 32 atoms (AoSoA)
     # vs warp per atom, stage time and whole step
     w = inputs.WORKLOADS["bcc10_2j8"]

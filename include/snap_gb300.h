@@ -225,9 +225,30 @@ int snap_bispectrum_deriv_batch(snap_ctx* ctx, int nconf, const int* natoms, con
  * compute_Y kernel and may change rounding.  snap_autotune times every
  * combination of col_warps in {2, 4, 8} with yi_waves in {1, 2, 4} (layout 0)
  * or layout 1 on the given batch (reps timed calls each, CUDA events on
- * `stream`), keeps the fastest, and reports its median time in *best_ms.
- * Synchronous. */
+ * `stream`), then the persistent launches (SNAP_KNOB_PERSIST 1..3) at the
+ * fastest shape, keeps the fastest setting, and reports its median time in
+ * *best_ms.  Synchronous. */
 int snap_set_tuning(snap_ctx* ctx, int col_warps, int yi_waves, int yi_layout);
+
+/* The same tunables one at a time, plus SNAP_KNOB_PERSIST (0..3, default
+ * 0): bit 0 runs compute_Y, bit 1 the fused dE kernel, as a persistent
+ * launch over a work queue -- a grid of as many CTAs as stay resident, each
+ * taking items (a 32-atom block and output slice for compute_Y, a CTA's
+ * atoms for the fused dE) from a device counter until none are left, across
+ * all configurations of a batch (spec batching pattern; the paper's
+ * stage-per-kernel refactor, Listing 2, with one launch per stage).  No CTA
+ * waits on another, and an item computes what the CTA it replaces would, so
+ * the knob changes no result bit.  snap_autotune also searches it (after the
+ * launch shapes, at the best shape).  SNAP_ERR_ARG for an unknown knob or
+ * value. */
+enum snap_knob {
+  SNAP_KNOB_COL_WARPS = 0,
+  SNAP_KNOB_YI_WAVES = 1,
+  SNAP_KNOB_YI_LAYOUT = 2,
+  SNAP_KNOB_PERSIST = 3
+};
+int snap_set_knob(snap_ctx* ctx, int knob, int value);
+int snap_get_knob(const snap_ctx* ctx, int knob, int* value);
 int snap_get_tuning(const snap_ctx* ctx, int* col_warps, int* yi_waves, int* yi_layout);
 int snap_autotune(snap_ctx* ctx, int nconf, const int* natoms, const double* boxes,
                   const double* pos, double* energy, double* forces, double* virial, int reps,

@@ -47,6 +47,7 @@ struct snap_ctx {
   int yi_waves = 2;
   int yi_layout = 0;
   int test_skip_stage = 0;  // snap_test_stage_timeout
+  int persist = 0;          // SNAP_KNOB_PERSIST
   int last_nmax = 0;
   int seen_nmax = 0;  // largest neighbour count seen: the fused dE launch is planned for it
   int last_n = 0, last_K = 0;
@@ -422,6 +423,7 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.de_maxcnt = de_maxcnt(c, K);
   a.yi_waves = c->yi_waves;
   a.test_skip_stage = c->test_skip_stage;
+  a.persist = c->persist;
   a.ncoeff = c->tab.ncoeff;
   a.brec = c->d_brec;
   a.bout = c->d_bout;
@@ -827,8 +829,8 @@ int compute_dev(snap_ctx* c, int n, const double* pos, const double* box, const 
   const std::vector<unsigned long long> key = {
       1, (unsigned long long)c->ws_gen, (unsigned long long)n, (unsigned long long)K,
       (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves,
-      (unsigned long long)c->yi_layout, key_bits(box[0]), key_bits(box[1]), key_bits(box[2]),
-      key_ptr(pos), key_ptr(energy), key_ptr(forces),
+      (unsigned long long)c->yi_layout | ((unsigned long long)c->persist << 8), key_bits(box[0]),
+      key_bits(box[1]), key_bits(box[2]), key_ptr(pos), key_ptr(energy), key_ptr(forces),
       key_ptr(virial), key_ptr(ucnt), key_ptr(uidx), key_ptr(uimg), (unsigned long long)ucap,
       (unsigned long long)de_maxcnt(c, K)};
   return graph_run(c, c->gdev, key, s, run);
@@ -1189,6 +1191,39 @@ int snap_set_tuning(snap_ctx* c, int col_warps, int yi_waves, int yi_layout) {
   return SNAP_OK;
 }
 
+int snap_set_knob(snap_ctx* c, int knob, int value) {
+  if (!c) return SNAP_ERR_ARG;
+  switch (knob) {
+    case SNAP_KNOB_COL_WARPS: return snap_set_tuning(c, value, c->yi_waves, c->yi_layout);
+    case SNAP_KNOB_YI_WAVES: return snap_set_tuning(c, c->col_warps, value, c->yi_layout);
+    case SNAP_KNOB_YI_LAYOUT: return snap_set_tuning(c, c->col_warps, c->yi_waves, value);
+    case SNAP_KNOB_PERSIST:
+      if (value < 0 || value > 3) return fail(c, SNAP_ERR_ARG, "persist must be in 0..3");
+      if (c->persist != value) {
+        c->persist = value;
+        c->gdev.reset();
+        c->ghost.reset();
+        if (c->gexec) {
+          cudaGraphExecDestroy(c->gexec);
+          c->gexec = nullptr;
+        }
+      }
+      return SNAP_OK;
+    default: return fail(c, SNAP_ERR_ARG, "unknown knob");
+  }
+}
+
+int snap_get_knob(const snap_ctx* c, int knob, int* value) {
+  if (!c || !value) return SNAP_ERR_ARG;
+  switch (knob) {
+    case SNAP_KNOB_COL_WARPS: *value = c->col_warps; return SNAP_OK;
+    case SNAP_KNOB_YI_WAVES: *value = c->yi_waves; return SNAP_OK;
+    case SNAP_KNOB_YI_LAYOUT: *value = c->yi_layout; return SNAP_OK;
+    case SNAP_KNOB_PERSIST: *value = c->persist; return SNAP_OK;
+    default: return SNAP_ERR_ARG;
+  }
+}
+
 int snap_test_stage_timeout(snap_ctx* c, int on) {
   if (!c) return SNAP_ERR_ARG;
   if (on != 0 && on != 1) return fail(c, SNAP_ERR_ARG, "on must be 0 or 1");
@@ -1219,47 +1254,65 @@ int snap_autotune(snap_ctx* c, int nconf, const int* natoms, const double* boxes
   if (!c) return SNAP_ERR_ARG;
   if (reps < 1) reps = 5;
   cudaStream_t s = (cudaStream_t)stream;
-  const int cw[3] = {2, 4, 8};
-  const int yw[3] = {1, 2, 4};
-  double best = 1e300;
-  int bc = c->col_warps, by = c->yi_waves, bl = c->yi_layout;
   cudaEvent_t e0, e1;
   SNAP_CUDA(c, cudaEventCreate(&e0));
   SNAP_CUDA(c, cudaEventCreate(&e1));
-  int rc = SNAP_OK;
-  // combinations: col_warps x (yi_waves of the warp-of-atoms compute_Y, or
-  // the warp-per-atom compute_Y, which has no split)
+  // median milliseconds of the batch at the context's current knobs
+  auto measure = [&](double* out) -> int {
+    std::vector<float> ms;
+    for (int it = 0; it < reps + 2; ++it) {
+      cudaEventRecord(e0, s);
+      const int r = snap_compute_batch(c, nconf, natoms, boxes, pos, energy, forces, virial, 0, stream);
+      cudaEventRecord(e1, s);
+      if (r) return r;
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (it >= 2) ms.push_back(t);
+    }
+    std::sort(ms.begin(), ms.end());
+    *out = ms[ms.size() / 2];
+    return SNAP_OK;
+  };
+  const int cw[3] = {2, 4, 8};
+  const int yw[3] = {1, 2, 4};
+  double best = 1e300;
+  int bc = c->col_warps, by = c->yi_waves, bl = c->yi_layout, bp = c->persist;
+  int rc = snap_set_knob(c, SNAP_KNOB_PERSIST, 0);
+  // 1. launch shapes: col_warps x (yi_waves of the warp-of-atoms compute_Y,
+  //    or the warp-per-atom compute_Y, which has no split), one-shot grids
   for (int a = 0; a < 3 && !rc; ++a)
     for (int b = 0; b < 4 && !rc; ++b) {
       const int lay = b == 3 ? 1 : 0;
       const int wav = b == 3 ? c->yi_waves : yw[b];
       rc = snap_set_tuning(c, cw[a], wav, lay);
-      if (rc) break;
-      std::vector<float> ms;
-      for (int it = 0; it < reps + 2 && !rc; ++it) {
-        cudaEventRecord(e0, s);
-        rc = snap_compute_batch(c, nconf, natoms, boxes, pos, energy, forces, virial, 0, stream);
-        cudaEventRecord(e1, s);
-        if (rc) break;
-        cudaEventSynchronize(e1);
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        if (it >= 2) ms.push_back(t);
-      }
-      if (rc) break;
-      std::sort(ms.begin(), ms.end());
-      const double med = ms[ms.size() / 2];
-      if (med < best) {
+      double med = 0.0;
+      if (!rc) rc = measure(&med);
+      if (!rc && med < best) {
         best = med;
         bc = cw[a];
         by = wav;
         bl = lay;
+        bp = 0;
       }
     }
+  // 2. at the best shape, the persistent work-queue launches of compute_Y
+  //    and the fused dE (alone and together)
+  if (!rc) rc = snap_set_tuning(c, bc, by, bl);
+  for (int p = 1; p <= 3 && !rc; ++p) {
+    rc = snap_set_knob(c, SNAP_KNOB_PERSIST, p);
+    double med = 0.0;
+    if (!rc) rc = measure(&med);
+    if (!rc && med < best) {
+      best = med;
+      bp = p;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
   rc = snap_set_tuning(c, bc, by, bl);
+  if (!rc) rc = snap_set_knob(c, SNAP_KNOB_PERSIST, bp);
   if (best_ms) *best_ms = best;
   SNAP_CUDA(c, cudaStreamSynchronize(s));
   return rc ? rc : check_flags(c);
@@ -1332,8 +1385,8 @@ int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const dou
     const std::vector<unsigned long long> key = {
         2, (unsigned long long)c->ws_gen, (unsigned long long)natoms, (unsigned long long)c->K,
         (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves,
-        (unsigned long long)c->yi_layout, key_bits(box[0]), key_bits(box[1]), key_bits(box[2]),
-        key_ptr(pos_host), key_ptr(energy_host),
+        (unsigned long long)c->yi_layout | ((unsigned long long)c->persist << 8), key_bits(box[0]),
+        key_bits(box[1]), key_bits(box[2]), key_ptr(pos_host), key_ptr(energy_host),
         key_ptr(forces_host), key_ptr(virial_host), key_ptr(c->d_hpos),
         (unsigned long long)de_maxcnt(c, c->K)};
     // pageable host memory is neither mapped nor capturable: plain copies (a

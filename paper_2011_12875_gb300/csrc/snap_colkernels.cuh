@@ -588,15 +588,29 @@ __device__ __forceinline__ R shfl_down(R v) {
 // (passes per warp) x P / (pairs per atom) no warp takes more passes than
 // planned (the time of a CTA is that of its longest chain of passes).  A
 // pair's arithmetic does not depend on its pass or its warp.
-template <typename R, int J2>
+//
+// QUEUE: a persistent launch over a work queue -- a grid of resident CTAs,
+// each taking CTA-sized items (A consecutive atoms) from a device counter
+// (flags[6], zeroed with the flags by every evaluation) until they run out;
+// an item's arithmetic is that of the CTA it would have been.
+template <typename R, int J2, bool QUEUE>
 __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(WorkArgs a, int A) {
   using S_ = Shape<J2>;
   constexpr int NC = S_::NC, P = S_::P;
   const int NW = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long item_s;
   const int H = a.H;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long i0 = (long)blockIdx.x * A;  // the CTA's atoms i0 .. i0 + na - 1
+  const long nitems = (a.n + A - 1) / A;
+  for (long item = blockIdx.x;;) {
+  if (QUEUE) {
+    if (threadIdx.x == 0) item_s = atomicAdd(&a.flags[6], 1);
+    __syncthreads();
+    item = item_s;
+    if (item >= nitems) break;
+  }
+  const long i0 = item * A;  // the CTA's atoms i0 .. i0 + na - 1
   const int na = (int)min((long)A, a.n - i0);
   c2<R>* Ywa = reinterpret_cast<c2<R>*>(smem);                    // [A][H] weighted Y
   c2<R>* ust = Ywa + (size_t)A * H;                              // [NW*P][H] forward columns
@@ -772,6 +786,9 @@ __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(W
     }
     __syncwarp();
   }
+  if (!QUEUE) break;
+  __syncthreads();  // the item's shared memory is reused by the next item
+  }
 }
 
 template <typename K>
@@ -917,7 +934,7 @@ cudaError_t launch_de_rev_col_t(const WorkArgs& a, cudaStream_t s) {
     std::lock_guard<std::mutex> lock(mu);
     if (regs == 0) {
       cudaFuncAttributes fa;
-      cudaError_t e = cudaFuncGetAttributes(&fa, de_rev_col_kernel<R, J2>);
+      cudaError_t e = cudaFuncGetAttributes(&fa, de_rev_col_kernel<R, J2, false>);
       if (e != cudaSuccess) return e;
       regs = fa.numRegs;
     }
@@ -931,10 +948,21 @@ cudaError_t launch_de_rev_col_t(const WorkArgs& a, cudaStream_t s) {
     }
   }
   if (p.smem == 0) return cudaErrorInvalidConfiguration;  // no plan fits (not reached for 2J <= 14)
-  cudaError_t e = col_allow_smem(de_rev_col_kernel<R, J2>, p.smem);
+  const long nitems = (a.n + p.A - 1) / p.A;
+  if (a.persist & 2) {
+    // persistent: as many CTAs as stay resident, items from the queue
+    auto kq = de_rev_col_kernel<R, J2, true>;
+    cudaError_t e = col_allow_smem(kq, p.smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kq, p.nw * 32, p.smem);
+    if (e != cudaSuccess) return e;
+    const long grid = std::min<long>(nitems, (long)nsm * std::max(1, occ));
+    return launch_k(kq, dim3((unsigned)grid), dim3(p.nw * 32), p.smem, s, a, p.A);
+  }
+  cudaError_t e = col_allow_smem(de_rev_col_kernel<R, J2, false>, p.smem);
   if (e != cudaSuccess) return e;
-  return launch_k(de_rev_col_kernel<R, J2>, dim3((unsigned)((a.n + p.A - 1) / p.A)), dim3(p.nw * 32), p.smem, s,
-                  a, p.A);
+  return launch_k(de_rev_col_kernel<R, J2, false>, dim3((unsigned)nitems), dim3(p.nw * 32), p.smem, s, a, p.A);
 }
 
 }  // namespace col

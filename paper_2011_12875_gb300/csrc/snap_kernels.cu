@@ -477,34 +477,16 @@ __device__ __forceinline__ void y_outputs(Src& src, const uint4* __restrict__ ru
   }
 }
 
-// CTA = one 32-atom block x one ysplit-th of the outputs; U of the block
-// staged by a TMA bulk copy.
+// One warp's outputs of slice `slice` for the 32-atom block blk, with the
+// block's U at `us` (staged in shared memory or in global memory).
 template <typename R, bool STAGED, bool CP>
-__global__ void __launch_bounds__(STAGED ? 1024 : 256, 1) yi_kernel(WorkArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long blk0 = blockIdx.x;
-  const int H = a.H;
-  const cx<R>* us = reinterpret_cast<const cx<R>*>(a.U) + blk0 * H * 32;
-  if (STAGED) {
-    cx<R>* su = reinterpret_cast<cx<R>*>(smem);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(su + (CP ? 2 : 1) * H * 32);
-    const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
-    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0, [] {})) return;
-    if (CP) {
-      for (int e = threadIdx.x; e < H * 32; e += blockDim.x) {
-        const cx<R> v = su[e];
-        su[H * 32 + e] = mk<R>(v.re, -v.im);
-      }
-      __syncthreads();
-    }
-    us = su;
-  }
-  const int slice = blockIdx.y * (blockDim.x >> 5) + warp;
+__device__ __forceinline__ void yi_slice(const WorkArgs& a, unsigned char* smem, const cx<R>* us, long blk,
+                                         int slice, int warp, int lane) {
   if (slice >= a.nslices) return;
+  const int H = a.H;
   const int o0 = a.yslice[slice], o1 = a.yslice[slice + 1];
   if (o0 >= o1) return;
-  cx<R>* Yg = reinterpret_cast<cx<R>*>(a.Y) + blk0 * H * 32;
+  cx<R>* Yg = reinterpret_cast<cx<R>*>(a.Y) + blk * H * 32;
   const YRec<R>* __restrict__ rec = reinterpret_cast<const YRec<R>*>(a.yrec);
   const char* ul = reinterpret_cast<const char*>(us + lane);
   if constexpr (sizeof(R) == 8) {
@@ -538,11 +520,86 @@ __global__ void __launch_bounds__(STAGED ? 1024 : 256, 1) yi_kernel(WorkArgs a) 
       YRecRing src;
       src.init(rec, q0, lane, rb);
       y_outputs<R, CP>(src, runs, q0, o0, o1, ul, Yg, lane);
-      cp_async_wait<0>();  // no copy outlives the warp
+      cp_async_wait<0>();  // no copy outlives the warp's slice
     } else {
       YRecGlobal<R> src{rec};
       y_outputs<R, CP>(src, runs, q0, o0, o1, ul, Yg, lane);
     }
+  }
+}
+
+// CTA = one 32-atom block x one ysplit-th of the outputs; U of the block
+// staged by a TMA bulk copy.
+template <typename R, bool STAGED, bool CP>
+__global__ void __launch_bounds__(STAGED ? 1024 : 256, 1) yi_kernel(WorkArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long blk0 = blockIdx.x;
+  const int H = a.H;
+  const cx<R>* us = reinterpret_cast<const cx<R>*>(a.U) + blk0 * H * 32;
+  if (STAGED) {
+    cx<R>* su = reinterpret_cast<cx<R>*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(su + (CP ? 2 : 1) * H * 32);
+    const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
+    if (!stage_bulk(su, us, bytes, bar, a.flags, a.test_skip_stage != 0, [] {})) return;
+    if (CP) {
+      for (int e = threadIdx.x; e < H * 32; e += blockDim.x) {
+        const cx<R> v = su[e];
+        su[H * 32 + e] = mk<R>(v.re, -v.im);
+      }
+      __syncthreads();
+    }
+    us = su;
+  }
+  yi_slice<R, STAGED, CP>(a, smem, us, blk0, blockIdx.y * (blockDim.x >> 5) + warp, warp, lane);
+}
+
+// The same work as a persistent launch over a work queue: a grid of resident
+// CTAs, each taking (block, split) items from a device counter (flags[5],
+// zeroed with the flags by every evaluation) until the items run out, across
+// all configurations of a batch.  No CTA waits on another (the counter is the
+// only shared state), and an item's arithmetic is that of the CTA it would
+// have been, so the results are bit for bit those of yi_kernel.  The staging
+// barrier is reused item after item (its phase flips per completed copy).
+template <typename R, bool CP>
+__global__ void __launch_bounds__(1024, 1) yi_queue_kernel(WorkArgs a, int ysplit) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int item_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int H = a.H;
+  const long nitems = (long)((a.n + 31) / 32) * ysplit;
+  cx<R>* su = reinterpret_cast<cx<R>*>(smem);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(su + (CP ? 2 : 1) * H * 32);
+  const unsigned bytes = (unsigned)(H * 32 * sizeof(cx<R>));
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  unsigned phase = 0;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(&a.flags[5], 1);
+    __syncthreads();  // also: every warp is done with the previous block
+    const long item = item_s;
+    if (item >= nitems) break;
+    const long blk = item / ysplit;
+    const int part = (int)(item - blk * ysplit);
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, bytes);
+      if (!a.test_skip_stage) bulk_g2s(su, reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32, bytes, bar);
+    }
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, phase, kWaitNs));
+    if (!ok) {
+      if (threadIdx.x == 0) atomicMax(&a.flags[3], 1);
+      mbar_wait_bounded(bar, phase, kWaitNs / 4);
+      return;
+    }
+    phase ^= 1u;
+    if (CP) {
+      for (int e = threadIdx.x; e < H * 32; e += blockDim.x) {
+        const cx<R> v = su[e];
+        su[H * 32 + e] = mk<R>(v.re, -v.im);
+      }
+      __syncthreads();
+    }
+    yi_slice<R, true, CP>(a, smem, su, blk, part * (blockDim.x >> 5) + warp, warp, lane);
+    __syncthreads();  // item_s is rewritten next
   }
 }
 
@@ -1190,6 +1247,18 @@ cudaError_t launch_yi(const WorkArgs& a, cudaStream_t s) {
   }
   const YiGeometry g = yi_geometry(sizeof(R), a.H, a.n, a.nsm, a.yi_waves);
   if (g.nslices != a.nslices) return cudaErrorInvalidValue;
+  if ((a.persist & 1) && g.staged) {
+    // persistent: as many CTAs as stay resident, (block, split) items from the queue
+    auto kq = g.conjplane ? yi_queue_kernel<R, true> : yi_queue_kernel<R, false>;
+    cudaError_t e = allow_smem(kq, g.smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kq, g.threads, g.smem);
+    if (e != cudaSuccess) return e;
+    const long nitems = (long)g.nblk * g.ysplit;
+    const long grid = std::min<long>(nitems, (long)a.nsm * std::max(1, occ));
+    return launch_k(kq, dim3((unsigned)grid), dim3(g.threads), g.smem, s, a, g.ysplit);
+  }
   dim3 grid(g.nblk, g.ysplit);
   if (g.staged && g.conjplane) {
     cudaError_t e = allow_smem(yi_kernel<R, true, true>, g.smem);

@@ -27,6 +27,11 @@ ERR_TIMEOUT = -5
 ERR_NOMEM = -6
 ERR_NEIGH_ASYM = -7
 
+KNOB_COL_WARPS = 0
+KNOB_YI_WAVES = 1
+KNOB_YI_LAYOUT = 2
+KNOB_PERSIST = 3
+
 BUF_NBR_CNT = 0
 BUF_NBR_IDX = 1
 BUF_NBR_IMG = 2
@@ -44,7 +49,7 @@ EXPORTS = ("snap_num_coeff", "snap_create", "snap_set_beta", "snap_set_neigh_cap
            "snap_bispectrum_deriv", "snap_force_weighted", "snap_generation",
            "snap_compute_batch", "snap_set_tuning", "snap_get_tuning", "snap_autotune",
            "snap_neighbors_noalloc", "snap_yi_host", "snap_test_stage_timeout",
-           "snap_probe_fma", "snap_bispectrum_deriv_batch")
+           "snap_probe_fma", "snap_bispectrum_deriv_batch", "snap_set_knob", "snap_get_knob")
 NSTAGES = 5
 
 _lib = None
@@ -102,6 +107,10 @@ def load(path: str | None = None):
     L.snap_compute_batch.restype = i
     L.snap_bispectrum_deriv_batch.argtypes = [p, i, p, p, p, p, p, p]
     L.snap_bispectrum_deriv_batch.restype = i
+    L.snap_set_knob.argtypes = [p, i, i]
+    L.snap_set_knob.restype = i
+    L.snap_get_knob.argtypes = [p, i, p]
+    L.snap_get_knob.restype = i
     L.snap_set_tuning.argtypes = [p, i, i, i]
     L.snap_set_tuning.restype = i
     L.snap_test_stage_timeout.argtypes = [p, i]
@@ -372,6 +381,15 @@ class Snap:
         """Launch-shape tunables (see snap_set_tuning); yi_layout 0 = warp of
         32 atoms, 1 = warp per atom."""
         self._check(self._lib.snap_set_tuning(self._h, col_warps, yi_waves, yi_layout))
+
+    def set_knob(self, knob: int, value: int):
+        """One tunable (KNOB_*; see snap_set_knob)."""
+        self._check(self._lib.snap_set_knob(self._h, knob, value))
+
+    def get_knob(self, knob: int) -> int:
+        v = ctypes.c_int()
+        self._check(self._lib.snap_get_knob(self._h, knob, ctypes.byref(v)))
+        return v.value
 
     def test_stage_timeout(self, on: bool):
         """Test hook (snap_test_stage_timeout): staging copies are not issued,

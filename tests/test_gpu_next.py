@@ -247,6 +247,7 @@ def test_autotune_keeps_results(snapmod):
     ms = s.autotune(P, natoms, boxes, reps=3)
     cw, yw, yl = s.get_tuning()
     assert ms > 0 and cw in (2, 4, 8) and yw in (1, 2, 4) and yl in (0, 1)
+    assert s.get_knob(snapmod.KNOB_PERSIST) in (0, 1, 2, 3)
     E1, F1, _ = [x.cpu().numpy() for x in s.compute_batch(P, natoms, boxes, use_graph=True)]
     if yl == 0:
         # launch shapes only: the same per-atom arithmetic in the same order,
@@ -412,3 +413,31 @@ def test_bispectrum_derivative_batch_equals_per_configuration(snapmod, prec, two
     s.close()
     assert float(loss) == pytest.approx(lsum, rel=1e-12)
     np.testing.assert_allclose(grad.cpu().numpy(), gsum, rtol=1e-10, atol=1e-12 * np.abs(gsum).max())
+
+
+@pytest.mark.parametrize("prec,twojmax", [(1, 8), (1, 14), (0, 8)])
+def test_persistent_work_queue_changes_no_bit(snapmod, prec, twojmax):
+    """SNAP_KNOB_PERSIST 1..3 (compute_Y and/or the fused dE as persistent
+    launches over device work queues): the same bits as the one-shot grids,
+    for one configuration and for a batch, direct and as a replayed graph."""
+    cfgs, pos, natoms, boxes = batch_of([3, 2, 5, 4], seed=81)
+    s = snapmod.Snap(twojmax, inputs.beta(twojmax), precision=prec)
+    P = torch.tensor(pos, device="cuda:0")
+    one = torch.tensor(cfgs[2].pos, device="cuda:0")
+
+    def run():
+        single = [x.cpu().numpy().copy() for x in s.compute(one, cfgs[2].box)]
+        batch = [x.cpu().numpy().copy() for x in s.compute_batch(P, natoms, boxes, use_graph=True)]
+        return single + batch
+
+    ref = run()
+    for p in (1, 2, 3):
+        s.set_knob(snapmod.KNOB_PERSIST, p)
+        assert s.get_knob(snapmod.KNOB_PERSIST) == p
+        for _ in range(2):  # capture, then replay
+            for x, y in zip(run(), ref):
+                assert np.array_equal(x, y), p
+    s.set_knob(snapmod.KNOB_PERSIST, 0)
+    with pytest.raises(snapmod.SnapError):
+        s.set_knob(snapmod.KNOB_PERSIST, 4)
+    s.close()
