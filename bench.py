@@ -607,6 +607,15 @@ def main():
             line["cpu_baseline"] = cpu_baseline(head)
             acc = accuracy_vs_oracle(torch, snap, inputs, dev)
             detail["accuracy_vs_oracle"] = acc
+            # the unreduced method's flops (counted in the oracle's loops)
+            # beside the library's reduced algorithm (flops.py), per unit
+            from oracle import snap_oracle as O
+            detail["flops_per_unit"] = {}
+            for J in (8, 14):
+                o = O.flops(J)
+                detail["flops_per_unit"][f"2j{J}"] = {
+                    "oracle": o, "library": {"compute_u_pair": flops.ui_pair(J), "y_atom": flops.yi_atom(J),
+                                             "de_pair": flops.de_pair(J)}}
         # the detail first (its own line, no "metric" key), then the bench
         # line itself, short, with the variants and the per-2J force error
         # last so that a short tail of the output still holds them

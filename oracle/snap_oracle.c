@@ -528,3 +528,57 @@ double orc_energy_from_u(int twojmax, const double* beta, const double* Uin,
   free(p.triples);
   return E;
 }
+
+/* ------------------------------------------------------------------ */
+/* Floating-point work of the oracle's own (unreduced) evaluation of one
+ * step, counted by walking the loops of ulist_one, ulisttot_atom,
+ * triple_product and dedr_pair with the same bounds and the same
+ * zero-coefficient skips, without their arithmetic.  Convention: a real add
+ * or multiply is 1, a real-by-complex scale 2, a complex add 2, a complex
+ * multiply 6; a square root or a division is 1; sign changes and
+ * conjugations are free.
+ *   out[0]: compute_U of one neighbour pair (recursion, f_c u added to U)
+ *   out[1]: B and the product-rule Y of one atom (every canonical triple)
+ *   out[2]: dU and dE/dr of one neighbour pair (recursion with its three
+ *           Cartesian derivatives, then the contraction with Y)
+ * The per-atom energy, forces and virial sums are not counted.        */
+void orc_flops(int twojmax, double* out) {
+  double u_pair = 0.0, y_atom = 0.0, de_pair = 0.0;
+  /* ulist_one: a term is sqrt of a ratio (2), its scale of conj(a) (2),
+   * the complex product (6) and the accumulation (2); with du, per
+   * direction two complex products and their sum (14), the scale (2) and
+   * the accumulation (2) */
+  double terms = 0.0;
+  for (int t = 1; t <= twojmax; ++t)
+    for (int mb = 0; mb < t; ++mb)
+      for (int ma = 0; ma <= t; ++ma) terms += (ma < t) + (ma > 0);
+  const int nfull = orc_full_size(twojmax);
+  u_pair = 12.0 * terms + 4.0 * nfull;             /* + f_c u added to U_tot */
+  de_pair = 12.0 * terms + 3.0 * 18.0 * terms +     /* u and du */
+            3.0 * 10.0 * nfull;                     /* dU (6) and Re conj(Y) dU (4) */
+  /* triple_product: per nonzero term c = ca cb (1), c u1 (2), (c u1) u2
+   * (6), times conj(u3) (6), real part added (1); the Y update of u3:
+   * beta c (1), its scale of u1 u2 (2 + 6), accumulation (2); of u1 and of
+   * u2: a complex product (6), the scale (2), accumulation (2) each */
+  for (int t1 = 0; t1 <= twojmax; ++t1)
+    for (int t2 = 0; t2 <= t1; ++t2)
+      for (int t = t1 - t2; t <= t1 + t2 && t <= twojmax; t += 2) {
+        if (t < t1) continue;
+        for (int ma1 = 0; ma1 <= t1; ++ma1)
+          for (int ma2 = 0; ma2 <= t2; ++ma2) {
+            const int m = (2 * ma1 - t1) + (2 * ma2 - t2);
+            if (m < -t || m > t) continue;
+            if (orc_cg(t1, 2 * ma1 - t1, t2, 2 * ma2 - t2, t, m) == 0.0) continue;
+            for (int mb1 = 0; mb1 <= t1; ++mb1)
+              for (int mb2 = 0; mb2 <= t2; ++mb2) {
+                const int nn = (2 * mb1 - t1) + (2 * mb2 - t2);
+                if (nn < -t || nn > t) continue;
+                if (orc_cg(t1, 2 * mb1 - t1, t2, 2 * mb2 - t2, t, nn) == 0.0) continue;
+                y_atom += 16.0 + 11.0 + 2.0 * 10.0;
+              }
+          }
+      }
+  out[0] = u_pair;
+  out[1] = y_atom;
+  out[2] = de_pair;
+}

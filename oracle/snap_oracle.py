@@ -43,6 +43,8 @@ def lib():
         L.orc_compute.restype = i
         L.orc_energy_from_u.argtypes = [i, p, p, p]
         L.orc_energy_from_u.restype = d
+        L.orc_flops.argtypes = [i, p]
+        L.orc_flops.restype = None
         _lib = L
     return _lib
 
@@ -222,3 +224,12 @@ def threads() -> int:
     """OpenMP threads the oracle will use (OMP_NUM_THREADS or all cores)."""
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v else (os.cpu_count() or 1)
+
+
+def flops(twojmax: int) -> dict:
+    """Floating-point work of the oracle's own unreduced evaluation (counted
+    by walking its loops): compute_U per pair, B + product-rule Y per atom,
+    dU + dE/dr per pair."""
+    out = np.zeros(3)
+    lib().orc_flops(twojmax, _ptr(out))
+    return {"compute_u_pair": float(out[0]), "y_b_atom": float(out[1]), "du_de_pair": float(out[2])}

@@ -353,3 +353,36 @@ def test_neighbor_list_brute_force():
                 if np.linalg.norm(cfg.pos[k] + s * cfg.box - cfg.pos[i]) < inputs.RCUT:
                     want.add((i, k, *s))
     assert got == want
+
+
+def test_oracle_flop_counter_walks_the_nonzero_cg_terms():
+    """orc_flops counts 47 flops per nonzero term of the oracle's triple
+    products: the number of terms with both Clebsch-Gordan factors nonzero,
+    counted here with sympy's CG (an independent routine), for 2J up to 4;
+    and the recursion's terms (two per element but the edges) for U and dU."""
+    sympy = pytest.importorskip("sympy")
+    from sympy.physics.quantum.cg import CG
+    from sympy import Rational as Q
+    for J in range(0, 5):
+        nterm = 0
+        for t1 in range(J + 1):
+            for t2 in range(t1 + 1):
+                for t in range(t1 - t2, min(J, t1 + t2) + 1, 2):
+                    if t < t1:
+                        continue
+                    nz = {}
+                    for x1 in range(t1 + 1):
+                        for x2 in range(t2 + 1):
+                            m = (2 * x1 - t1) + (2 * x2 - t2)
+                            if abs(m) > t:
+                                continue
+                            v = CG(Q(t1, 2), Q(2 * x1 - t1, 2), Q(t2, 2), Q(2 * x2 - t2, 2), Q(t, 2), Q(m, 2)).doit()
+                            nz[(x1, x2)] = v != 0
+                    good = [k for k, v in nz.items() if v]
+                    nterm += len(good) ** 2
+        rec = sum((ma < t) + (ma > 0) for t in range(1, J + 1) for mb in range(t) for ma in range(t + 1))
+        nfull = sum((t + 1) ** 2 for t in range(J + 1))
+        f = O.flops(J)
+        assert f["y_b_atom"] == 47 * nterm, J
+        assert f["compute_u_pair"] == 12 * rec + 4 * nfull
+        assert f["du_de_pair"] == 12 * rec + 54 * rec + 30 * nfull
