@@ -126,16 +126,17 @@ def job_throughput(world: int, natoms: int, ms: float) -> float:
     return world * natoms / (ms * 1e-3)
 
 
-def read_traffic(kernel: str, workload: str):
+def read_traffic(kernel: str, workload: str, precision: str):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
-    summary (a line 'traffic <kernel> <workload> <bytes>'), else None."""
+    summary (a line 'traffic <kernel> <workload> <precision> <bytes>'), else
+    None."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         p = line.split()
-        if len(p) == 4 and p[0] == "traffic" and p[1] == kernel and p[2] == workload:
-            return float(p[3])
+        if len(p) == 5 and p[0] == "traffic" and p[1] == kernel and p[2] == workload and p[3] == precision:
+            return float(p[4])
     return None
 
 
@@ -556,7 +557,7 @@ def main():
         "roofline": {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(hpeak, 2), "unit": "TFLOP/s", "frac": round(achieved / hpeak, 4),
                      "peak_measured": round(measured_peak, 2) if measured_peak else None,
-                     "traffic": read_traffic(dom, head.name)},
+                     "traffic": read_traffic(dom, head.name, args.precision)},
         "clocks": clocks,
     }
     detail = {"ms_per_step_median": ms_med, "neighbors": r["npairs"] / r["natoms"],
