@@ -298,7 +298,8 @@ int ensure_workspace(snap_ctx* c, int n, int K) {
   SNAP_CUDA(c, cudaMalloc(&c->d_dU, uy));
   // lanes past the last atom read zeros in compute_Y
   SNAP_CUDA(c, cudaMemset(c->d_U, 0, uy));
-  SNAP_CUDA(c, cudaMalloc(&c->d_vpart, sizeof(double) * 6 * (4 * nblk + 1)));
+  // one virial partial per force CTA (at least one atom each)
+  SNAP_CUDA(c, cudaMalloc(&c->d_vpart, sizeof(double) * 6 * (ncap + 1)));
   c->cap_n = ncap;
   c->cap_nk = nkcap;
   c->ws_gen += 1;
