@@ -367,6 +367,7 @@ def next_rows(torch, snap, inputs, flush, dev, args):
     best_ms = s.autotune(pos, natoms, boxes, reps=5)
     tuned = s.get_tuning()
     tuned_persist = s.get_knob(snap.KNOB_PERSIST)
+    tuned_de_atoms = s.get_knob(snap.KNOB_DE_ATOMS)
     s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=True)
     t_graph = _events_time(torch, lambda: s.compute_batch(pos, natoms, boxes, E, F, W, use_graph=True,
                                                           wait=False), steps, flush, dev)
@@ -404,7 +405,7 @@ def next_rows(torch, snap, inputs, flush, dev, args):
         "default_tuning": {"col_warps": default_tuning[0], "yi_waves": default_tuning[1],
                            "yi_layout": default_tuning[2], "graph_ms": t_default},
         "autotuned": {"col_warps": tuned[0], "yi_waves": tuned[1], "yi_layout": tuned[2],
-                      "persist": tuned_persist, "autotune_median_ms": best_ms}}
+                      "persist": tuned_persist, "de_atoms": tuned_de_atoms, "autotune_median_ms": best_ms}}
     # --- compute_Y layouts on the headline workload: warp of 32 atoms (AoSoA)
     # vs warp per atom, stage time and whole step
     w = inputs.WORKLOADS["bcc10_2j8"]

@@ -226,7 +226,8 @@ int snap_bispectrum_deriv_batch(snap_ctx* ctx, int nconf, const int* natoms, con
  * combination of col_warps in {2, 4, 8} with yi_waves in {1, 2, 4} (layout 0)
  * or layout 1 on the given batch (reps timed calls each, CUDA events on
  * `stream`), then the persistent launches (SNAP_KNOB_PERSIST 1..3) at the
- * fastest shape, keeps the fastest setting, and reports its median time in
+ * fastest shape, then the fused dE kernel's atoms per CTA (SNAP_KNOB_DE_ATOMS
+ * 2, 4, ..., 32), keeps the fastest setting, and reports its median time in
  * *best_ms.  Synchronous. */
 int snap_set_tuning(snap_ctx* ctx, int col_warps, int yi_waves, int yi_layout);
 
@@ -245,7 +246,12 @@ enum snap_knob {
   SNAP_KNOB_COL_WARPS = 0,
   SNAP_KNOB_YI_WAVES = 1,
   SNAP_KNOB_YI_LAYOUT = 2,
-  SNAP_KNOB_PERSIST = 3
+  SNAP_KNOB_PERSIST = 3,
+  /* atoms per CTA of the fused dE kernel (0..256, default 0 = planned from
+   * the system size and the largest neighbour count seen); with a value the
+   * warp count is the best one for it.  A warp's pass count (neighbours per
+   * warp) follows.  Changes no result bit. */
+  SNAP_KNOB_DE_ATOMS = 4
 };
 int snap_set_knob(snap_ctx* ctx, int knob, int value);
 int snap_get_knob(const snap_ctx* ctx, int knob, int* value);

@@ -48,6 +48,7 @@ struct snap_ctx {
   int yi_layout = 0;
   int test_skip_stage = 0;  // snap_test_stage_timeout
   int persist = 0;          // SNAP_KNOB_PERSIST
+  int de_atoms = 0;         // SNAP_KNOB_DE_ATOMS
   int last_nmax = 0;
   int seen_nmax = 0;  // largest neighbour count seen: the fused dE launch is planned for it
   int last_n = 0, last_K = 0;
@@ -425,6 +426,7 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.yi_waves = c->yi_waves;
   a.test_skip_stage = c->test_skip_stage;
   a.persist = c->persist;
+  a.de_atoms = c->de_atoms;
   a.ncoeff = c->tab.ncoeff;
   a.brec = c->d_brec;
   a.bout = c->d_bout;
@@ -830,8 +832,9 @@ int compute_dev(snap_ctx* c, int n, const double* pos, const double* box, const 
   const std::vector<unsigned long long> key = {
       1, (unsigned long long)c->ws_gen, (unsigned long long)n, (unsigned long long)K,
       (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves,
-      (unsigned long long)c->yi_layout | ((unsigned long long)c->persist << 8), key_bits(box[0]),
-      key_bits(box[1]), key_bits(box[2]), key_ptr(pos), key_ptr(energy), key_ptr(forces),
+      (unsigned long long)c->yi_layout | ((unsigned long long)c->persist << 8) |
+          ((unsigned long long)c->de_atoms << 16),
+      key_bits(box[0]), key_bits(box[1]), key_bits(box[2]), key_ptr(pos), key_ptr(energy), key_ptr(forces),
       key_ptr(virial), key_ptr(ucnt), key_ptr(uidx), key_ptr(uimg), (unsigned long long)ucap,
       (unsigned long long)de_maxcnt(c, K)};
   return graph_run(c, c->gdev, key, s, run);
@@ -1199,9 +1202,14 @@ int snap_set_knob(snap_ctx* c, int knob, int value) {
     case SNAP_KNOB_YI_WAVES: return snap_set_tuning(c, c->col_warps, value, c->yi_layout);
     case SNAP_KNOB_YI_LAYOUT: return snap_set_tuning(c, c->col_warps, c->yi_waves, value);
     case SNAP_KNOB_PERSIST:
-      if (value < 0 || value > 3) return fail(c, SNAP_ERR_ARG, "persist must be in 0..3");
-      if (c->persist != value) {
-        c->persist = value;
+    case SNAP_KNOB_DE_ATOMS: {
+      int& slot = knob == SNAP_KNOB_PERSIST ? c->persist : c->de_atoms;
+      if (knob == SNAP_KNOB_PERSIST && (value < 0 || value > 3))
+        return fail(c, SNAP_ERR_ARG, "persist must be in 0..3");
+      if (knob == SNAP_KNOB_DE_ATOMS && (value < 0 || value > 256))
+        return fail(c, SNAP_ERR_ARG, "de_atoms must be in 0..256");
+      if (slot != value) {
+        slot = value;
         c->gdev.reset();
         c->ghost.reset();
         if (c->gexec) {
@@ -1210,6 +1218,7 @@ int snap_set_knob(snap_ctx* c, int knob, int value) {
         }
       }
       return SNAP_OK;
+    }
     default: return fail(c, SNAP_ERR_ARG, "unknown knob");
   }
 }
@@ -1221,6 +1230,7 @@ int snap_get_knob(const snap_ctx* c, int knob, int* value) {
     case SNAP_KNOB_YI_WAVES: *value = c->yi_waves; return SNAP_OK;
     case SNAP_KNOB_YI_LAYOUT: *value = c->yi_layout; return SNAP_OK;
     case SNAP_KNOB_PERSIST: *value = c->persist; return SNAP_OK;
+    case SNAP_KNOB_DE_ATOMS: *value = c->de_atoms; return SNAP_OK;
     default: return SNAP_ERR_ARG;
   }
 }
@@ -1309,11 +1319,25 @@ int snap_autotune(snap_ctx* c, int nconf, const int* natoms, const double* boxes
       bp = p;
     }
   }
+  // 3. at the best of those, the fused dE kernel's atoms per CTA (the pass
+  //    count of a warp follows from it): planned, or 2, 4, ... 32
+  int bd = 0;
+  if (!rc) rc = snap_set_knob(c, SNAP_KNOB_PERSIST, bp);
+  for (int d = 2; d <= 32 && !rc; d *= 2) {
+    rc = snap_set_knob(c, SNAP_KNOB_DE_ATOMS, d);
+    double med = 0.0;
+    if (!rc) rc = measure(&med);
+    if (!rc && med < best) {
+      best = med;
+      bd = d;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
   rc = snap_set_tuning(c, bc, by, bl);
   if (!rc) rc = snap_set_knob(c, SNAP_KNOB_PERSIST, bp);
+  if (!rc) rc = snap_set_knob(c, SNAP_KNOB_DE_ATOMS, bd);
   if (best_ms) *best_ms = best;
   SNAP_CUDA(c, cudaStreamSynchronize(s));
   return rc ? rc : check_flags(c);
@@ -1386,8 +1410,9 @@ int snap_compute_host(snap_ctx* c, int natoms, const double* pos_host, const dou
     const std::vector<unsigned long long> key = {
         2, (unsigned long long)c->ws_gen, (unsigned long long)natoms, (unsigned long long)c->K,
         (unsigned long long)c->col_warps, (unsigned long long)c->yi_waves,
-        (unsigned long long)c->yi_layout | ((unsigned long long)c->persist << 8), key_bits(box[0]),
-        key_bits(box[1]), key_bits(box[2]), key_ptr(pos_host), key_ptr(energy_host),
+        (unsigned long long)c->yi_layout | ((unsigned long long)c->persist << 8) |
+            ((unsigned long long)c->de_atoms << 16),
+        key_bits(box[0]), key_bits(box[1]), key_bits(box[2]), key_ptr(pos_host), key_ptr(energy_host),
         key_ptr(forces_host), key_ptr(virial_host), key_ptr(c->d_hpos),
         (unsigned long long)de_maxcnt(c, c->K)};
     // pageable host memory is neither mapped nor capturable: plain copies (a

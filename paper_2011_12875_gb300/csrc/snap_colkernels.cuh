@@ -867,8 +867,10 @@ struct DePlan {
   int nw, A;
   size_t smem;
 };
+// force_A > 0 (the SNAP_KNOB_DE_ATOMS tunable) restricts the search to CTAs
+// of force_A atoms (the best warp count for it) and skips the reference.
 inline DePlan de_plan(int n, int maxcnt, int P, size_t per_warp, size_t per_atom, int regs, int nsm,
-                      int max_warps, int nw0) {
+                      int max_warps, int nw0, int force_A = 0) {
   const int ralloc = (regs + 7) / 8 * 8;
   auto shape = [&](int nw, int A, size_t* smem, long* waves, long* ppw) -> bool {
     *smem = (size_t)A * per_atom + (size_t)nw * per_warp + sizeof(int) * (A + 1);
@@ -898,7 +900,7 @@ inline DePlan de_plan(int n, int maxcnt, int P, size_t per_warp, size_t per_atom
   DePlan best{0, 0, 0};
   long best_cost = -1, best_warps = 0;
   for (int nw = 2; nw <= max_warps; nw *= 2) {
-    for (int A = 1; A <= 256; ++A) {
+    for (int A = force_A > 0 ? force_A : 1; A <= (force_A > 0 ? force_A : 256); ++A) {
       long waves, ppw;
       size_t smem;
       if (!shape(nw, A, &smem, &waves, &ppw)) break;
@@ -911,6 +913,7 @@ inline DePlan de_plan(int n, int maxcnt, int P, size_t per_warp, size_t per_atom
       }
     }
   }
+  if (force_A > 0 && best_cost >= 0) return best;
   if (best_cost < 0 || (ref.smem != 0 && (double)best_cost > 0.97 * ref_cost)) return ref;
   return best;
 }
@@ -938,11 +941,11 @@ cudaError_t launch_de_rev_col_t(const WorkArgs& a, cudaStream_t s) {
       if (e != cudaSuccess) return e;
       regs = fa.numRegs;
     }
-    const long long key[4] = {a.n, maxcnt, ((long long)nsm << 32) | nw0, a.H};
+    const long long key[4] = {a.n, ((long long)a.de_atoms << 32) | maxcnt, ((long long)nsm << 32) | nw0, a.H};
     if (std::equal(key, key + 4, last_key)) {
       p = last_plan;
     } else {
-      p = de_plan(a.n, maxcnt, Shape<J2>::P, per_warp, per_atom, regs, nsm, de_max_warps<R>(), nw0);
+      p = de_plan(a.n, maxcnt, Shape<J2>::P, per_warp, per_atom, regs, nsm, de_max_warps<R>(), nw0, a.de_atoms);
       std::copy(key, key + 4, last_key);
       last_plan = p;
     }

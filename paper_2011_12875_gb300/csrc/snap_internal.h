@@ -175,6 +175,7 @@ struct WorkArgs {
   int de_maxcnt;  // neighbour count the fused dE launch is planned for (last seen maximum, else K)
   int yi_waves;   // compute_Y waves per SM (tunable)
   int persist;    // tunable: bit 0 persistent compute_Y, bit 1 persistent fused dE (work queues)
+  int de_atoms;   // tunable: atoms per fused dE CTA (0: planned)
   int test_skip_stage;  // test hook: TMA staging registers its bytes but issues no copy
   // bispectrum output
   int ncoeff;

@@ -31,6 +31,7 @@ KNOB_COL_WARPS = 0
 KNOB_YI_WAVES = 1
 KNOB_YI_LAYOUT = 2
 KNOB_PERSIST = 3
+KNOB_DE_ATOMS = 4
 
 BUF_NBR_CNT = 0
 BUF_NBR_IDX = 1

@@ -248,6 +248,7 @@ def test_autotune_keeps_results(snapmod):
     cw, yw, yl = s.get_tuning()
     assert ms > 0 and cw in (2, 4, 8) and yw in (1, 2, 4) and yl in (0, 1)
     assert s.get_knob(snapmod.KNOB_PERSIST) in (0, 1, 2, 3)
+    assert s.get_knob(snapmod.KNOB_DE_ATOMS) in (0, 2, 4, 8, 16, 32)
     E1, F1, _ = [x.cpu().numpy() for x in s.compute_batch(P, natoms, boxes, use_graph=True)]
     if yl == 0:
         # launch shapes only: the same per-atom arithmetic in the same order,
@@ -418,8 +419,9 @@ def test_bispectrum_derivative_batch_equals_per_configuration(snapmod, prec, two
 @pytest.mark.parametrize("prec,twojmax", [(1, 8), (1, 14), (0, 8)])
 def test_persistent_work_queue_changes_no_bit(snapmod, prec, twojmax):
     """SNAP_KNOB_PERSIST 1..3 (compute_Y and/or the fused dE as persistent
-    launches over device work queues): the same bits as the one-shot grids,
-    for one configuration and for a batch, direct and as a replayed graph."""
+    launches over device work queues) and SNAP_KNOB_DE_ATOMS: the same bits as
+    the default launches, for one configuration and for a batch, direct and as
+    a replayed graph."""
     cfgs, pos, natoms, boxes = batch_of([3, 2, 5, 4], seed=81)
     s = snapmod.Snap(twojmax, inputs.beta(twojmax), precision=prec)
     P = torch.tensor(pos, device="cuda:0")
@@ -440,4 +442,9 @@ def test_persistent_work_queue_changes_no_bit(snapmod, prec, twojmax):
     s.set_knob(snapmod.KNOB_PERSIST, 0)
     with pytest.raises(snapmod.SnapError):
         s.set_knob(snapmod.KNOB_PERSIST, 4)
+    # the fused dE kernel's atoms per CTA (neighbours per warp follow)
+    for d in (2, 5, 16, 0):
+        s.set_knob(snapmod.KNOB_DE_ATOMS, d)
+        for x, y in zip(run(), ref):
+            assert np.array_equal(x, y), d
     s.close()
