@@ -434,8 +434,11 @@ def next_rows(torch, snap, inputs, flush, dev, args):
         p_ = torch.tensor(cfg.pos, device=dev)
         Bout = torch.empty((cfg.natoms, snap.num_coeff(8)), dtype=torch.float64, device=dev)
         s.bispectrum(p_, cfg.box, out=Bout)
-        t = _events_time(torch, lambda: s.bispectrum(p_, cfg.box, out=Bout), 10, flush, dev)
+        t = _events_time(torch, lambda: s.bispectrum(p_, cfg.box, out=Bout, wait=False), 10, flush, dev)
+        s.sync()
+        t_sync = _events_time(torch, lambda: s.bispectrum(p_, cfg.box, out=Bout), 10, flush, dev)
         out[f"bispectrum_2000_2j8_{tag}"] = {"atom_steps_per_s": cfg.natoms / (t * 1e-3), "ms": t,
+                                             "ms_with_host_wait": t_sync,
                                              "includes": "neighbour list, geometry, compute_U, B"}
         s.close()
     # --- force matching: loss + d loss / d beta over 32 configurations (+-0.2 A)

@@ -158,6 +158,13 @@ int snap_compute_bispectrum(snap_ctx* ctx, int natoms, const double* pos, const 
                             const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
                             int nbr_cap, double* B, void* stream);
 
+/* snap_compute_bispectrum without the final wait, as snap_compute_async:
+ * argument errors at once, device-side errors from the next snap_sync; the
+ * first call for a given N and capacity allocates (not inside a capture). */
+int snap_compute_bispectrum_async(snap_ctx* ctx, int natoms, const double* pos, const double* box,
+                                  const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
+                                  int nbr_cap, double* B, void* stream);
+
 /* Derivative of every atom's bispectrum along a displacement field g of the
  * atoms (forward mode, dB/dr is never stored):
  *   dB[i][l] = sum_k g_k . dB_l(i)/dr_k      (Sec. II-A, Eqs. z and dbidrk)
@@ -236,8 +243,8 @@ int snap_set_tuning(snap_ctx* ctx, int col_warps, int yi_waves, int yi_layout);
  * launch over a work queue -- a grid of as many CTAs as stay resident, each
  * taking items (a 32-atom block and output slice for compute_Y, a CTA's
  * atoms for the fused dE) from a device counter until none are left, across
- * all configurations of a batch (spec batching pattern; the paper's
- * stage-per-kernel refactor, Listing 2, with one launch per stage).  No CTA
+ * all configurations of a batch (the paper's stage-per-kernel refactor,
+ * Listing 2, with one launch per stage over many configurations).  No CTA
  * waits on another, and an item computes what the CTA it replaces would, so
  * the knob changes no result bit.  snap_autotune also searches it (after the
  * launch shapes, at the best shape).  SNAP_ERR_ARG for an unknown knob or
@@ -251,7 +258,13 @@ enum snap_knob {
    * the system size and the largest neighbour count seen); with a value the
    * warp count is the best one for it.  A warp's pass count (neighbours per
    * warp) follows.  Changes no result bit. */
-  SNAP_KNOB_DE_ATOMS = 4
+  SNAP_KNOB_DE_ATOMS = 4,
+  /* word layout of the bispectrum kernels (B and dB): 0 (default) planned,
+   * 1 sign flips on a single staged plane, 2 the conjugate plane staged
+   * beside U where it fits (else as 1).  Not searched by snap_autotune (it
+   * times the energy path).  The conjugate is the same value either way, so
+   * the knob changes no result bit. */
+  SNAP_KNOB_BI_LAYOUT = 5
 };
 int snap_set_knob(snap_ctx* ctx, int knob, int value);
 int snap_get_knob(const snap_ctx* ctx, int knob, int* value);
@@ -326,6 +339,20 @@ int snap_test_stage_timeout(snap_ctx* ctx, int on);
  * Returns SNAP_OK, or SNAP_ERR_ARG for a twojmax outside 0..14, an unknown
  * precision or a NULL pointer. */
 int snap_yi_host(int twojmax, int precision, const double* beta, const double* u, double* y);
+
+/* The bispectrum kernels' term records for one atom, walked on the host in
+ * FP64 exactly as the device walks them (Sec. II-A, Eq. z: B_l = Re of the
+ * triple product Z^t_{t1t2} : conj(U_t), each output element's terms summed
+ * and contracted with conj(U_t) at the element, over the half layout with
+ * the mirrored elements' weights folded into the coefficients, chunk
+ * partials added in chunk order).  No GPU work: a check of the record words.
+ *   layout: 0 the sign-flip words, 1 the conjugate-plane words
+ *   u:      double [H][2] (re, im), Ulisttot of the atom in half layout (it
+ *           must have the inversion symmetry of a physical Ulisttot)
+ *   b:      double [snap_num_coeff(twojmax)] out
+ * Returns SNAP_OK, or SNAP_ERR_ARG for a twojmax outside 0..14, a layout
+ * other than 0 or 1 or a NULL pointer. */
+int snap_bi_host(int twojmax, int layout, const double* u, double* b);
 
 /* Neighbour list for callers that cannot call cudaMalloc.  Such callers
  * include host programs that hand the GPU's memory to their own allocator or

@@ -60,14 +60,20 @@ struct snap_ctx {
   int* d_yfirst = nullptr;
   unsigned short* d_yruns = nullptr;
   void* d_brec = nullptr;
-  int* d_bout = nullptr;
-  int* d_bfirst = nullptr;
-  int* d_bgfirst = nullptr;
+  void* d_brec_cp = nullptr;
+  void* d_bscratch = nullptr;  // chunk partials of the bispectrum kernels (when shared memory is short)
+  size_t bscratch_cap = 0;
+  int bi_layout = 0;           // knob: 0 planned, 1 sign flips, 2 conjugate plane
   int* d_bchunk_term = nullptr;
-  int* d_bchunk_group = nullptr;
+  unsigned short* d_bchunk_runs = nullptr;
   int* d_bcomp_chunk = nullptr;
   // bispectrum component runs by run count: device table and most chunks a run
-  std::map<int, std::pair<int*, int>> bpart_cache;
+  struct BPart {
+    int* d;         // [runs + 1] first component of each run
+    int maxchunks;  // most chunks of one run
+    int maxterms;   // most terms of one run
+  };
+  std::map<int, BPart> bpart_cache;
   int nbparts = 0;
   void* d_root = nullptr;
   void* d_hscale = nullptr;
@@ -236,24 +242,33 @@ int upload_yrec(snap_ctx* c) {
   return upload_inplace(c, reinterpret_cast<snap::YRec<double>**>(&c->d_yrec), r);
 }
 
-// bispectrum term records (coefficients do not depend on beta)
+// bispectrum term records (coefficients do not depend on beta), in both
+// word layouts; the conjugate-plane records only where the doubled plane of
+// one 32-atom block can be staged (snap_kernels.cu decides per launch)
+template <typename R>
+int upload_brec_t(snap_ctx* c, const std::vector<unsigned>& w, void** dst) {
+  // two zero records of padding: a run's staged copy may round its end up to
+  // 16 bytes
+  std::vector<snap::YRec<R>> r(w.size() + 2);
+  std::memset(r.data(), 0, r.size() * sizeof(r[0]));
+  for (size_t k = 0; k < w.size(); ++k) {
+    r[k].w = w[k];
+    r[k].c = (R)c->tab.bdev_coef[k];
+  }
+  return upload(c, reinterpret_cast<snap::YRec<R>**>(dst), r);
+}
+
 int upload_brec(snap_ctx* c) {
-  const size_t n = c->tab.bterms.size();
-  if (c->precision == SNAP_MIXED) {
-    std::vector<snap::YRec<float>> r(n);
-    for (size_t k = 0; k < n; ++k) {
-      r[k].w = c->tab.bterms[k];
-      r[k].c = (float)c->tab.bterm_coef[k];
-    }
-    return upload(c, reinterpret_cast<snap::YRec<float>**>(&c->d_brec), r);
+  const bool mixed = c->precision == SNAP_MIXED;
+  for (int cp = 0; cp < 2; ++cp) {
+    if (cp && !snap::bi_plane_fits((int)c->rsize(), c->tab.H)) break;
+    const std::vector<unsigned> w = c->tab.bwords(cp != 0);
+    if (w.size() != c->tab.bdev.size()) return fail(c, SNAP_ERR_ARG, "bispectrum tables: element out of range");
+    void** dst = cp ? &c->d_brec_cp : &c->d_brec;
+    const int rc = mixed ? upload_brec_t<float>(c, w, dst) : upload_brec_t<double>(c, w, dst);
+    if (rc) return rc;
   }
-  std::vector<snap::YRec<double>> r(n);
-  for (size_t k = 0; k < n; ++k) {
-    r[k].w = c->tab.bterms[k];
-    r[k].pad = 0;
-    r[k].c = c->tab.bterm_coef[k];
-  }
-  return upload(c, reinterpret_cast<snap::YRec<double>**>(&c->d_brec), r);
+  return SNAP_OK;
 }
 
 void free_workspace(snap_ctx* c) {
@@ -330,24 +345,55 @@ int ensure_flags(snap_ctx* c) {
   return SNAP_OK;
 }
 
-// Component runs of the bispectrum kernels for n atoms: enough CTAs (32-atom
-// blocks x runs) for about three per SM, at most one run per component.
-int ensure_bparts(snap_ctx* c, long n) {
-  const long nblk = (n + 31) / 32;
-  int parts = (int)std::min<long>(16, std::max<long>(1, (3L * c->nsm + nblk - 1) / std::max(1L, nblk)));
-  parts = std::min(parts, c->tab.ncoeff);
-  if (parts == c->nbparts) return SNAP_OK;
-  auto it = c->bpart_cache.find(parts);
-  if (it == c->bpart_cache.end()) {
-    int mx = 0;
-    const std::vector<int> b = c->tab.bparts(parts, &mx);
-    int* d = nullptr;
-    int rc = upload(c, &d, b);
-    if (rc) return rc;
-    it = c->bpart_cache.emplace(parts, std::make_pair(d, mx)).first;
+// Component runs of the bispectrum kernels (B, or dB with deriv) for n
+// atoms, and the global scratch of the chunk partials when a run has more
+// than shared memory holds.  CTAs = 32-atom blocks x runs; the CTAs an SM
+// runs share its issue slots, so the time goes as the most CTAs an SM takes
+// times a CTA's share of a block (1/runs) plus its fixed cost (staging the
+// block, about kBiCtaCost of a block's work): the run count minimises
+// ceil(blocks x runs / SMs) x (1 / runs + kBiCtaCost), at most one run per
+// component.
+int ensure_bparts(snap_ctx* c, long n, bool deriv) {
+  const long nblk = std::max(1L, (n + 31) / 32);
+  const int rs = (int)c->rsize();
+  const bool have_cp = c->d_brec_cp != nullptr;
+  constexpr double kBiCtaCost = 0.02;
+  int parts = 1;
+  double best = 1e300;
+  for (int p = 1; p <= std::min(64, c->tab.ncoeff); ++p) {
+    const double cost = (double)((nblk * p + c->nsm - 1) / c->nsm) * (1.0 / p + kBiCtaCost);
+    if (cost < best * (1.0 - 1e-9)) {
+      best = cost;
+      parts = p;
+    }
   }
-  c->nbparts = parts;
-  c->ws_gen += 1;
+  if (parts != c->nbparts) {
+    auto it = c->bpart_cache.find(parts);
+    if (it == c->bpart_cache.end()) {
+      int mx = 0, mt = 0;
+      const std::vector<int> b = c->tab.bparts(parts, &mx, &mt);
+      int* d = nullptr;
+      int rc = upload(c, &d, b);
+      if (rc) return rc;
+      it = c->bpart_cache.emplace(parts, snap_ctx::BPart{d, mx, mt}).first;
+    }
+    c->nbparts = parts;
+    c->ws_gen += 1;
+  }
+  const snap_ctx::BPart& bp = c->bpart_cache.at(parts);
+  const int mx = bp.maxchunks;
+  const snap::BiPlan p = snap::bi_plan(rs, c->tab.H, deriv, mx, bp.maxterms, c->bi_layout, have_cp);
+  if (p.gpart) {
+    const size_t bytes = (size_t)nblk * parts * mx * 32 * rs;
+    if (bytes > c->bscratch_cap) {
+      cudaDeviceSynchronize();
+      dfree(c->d_bscratch);
+      c->bscratch_cap = 0;
+      SNAP_CUDA(c, cudaMalloc(&c->d_bscratch, bytes));
+      c->bscratch_cap = bytes;
+      c->ws_gen += 1;
+    }
+  }
   return SNAP_OK;
 }
 
@@ -429,17 +475,18 @@ snap::WorkArgs make_args(snap_ctx* c, int n, int K) {
   a.de_atoms = c->de_atoms;
   a.ncoeff = c->tab.ncoeff;
   a.brec = c->d_brec;
-  a.bout = c->d_bout;
-  a.bfirst = c->d_bfirst;
-  a.bgfirst = c->d_bgfirst;
+  a.brec_cp = c->d_brec_cp;
   a.bchunk_term = c->d_bchunk_term;
-  a.bchunk_group = c->d_bchunk_group;
+  a.bchunk_runs = c->d_bchunk_runs;
   a.bcomp_chunk = c->d_bcomp_chunk;
+  a.bi_layout = c->bi_layout;
+  a.bscratch = c->d_bscratch;
   a.nbparts = c->nbparts;
   if (c->nbparts > 0) {
     const auto& bp = c->bpart_cache.at(c->nbparts);
-    a.bpart = bp.first;
-    a.bmaxchunks = bp.second;
+    a.bpart = bp.d;
+    a.bmaxchunks = bp.maxchunks;
+    a.bmaxterms = bp.maxterms;
   }
   a.rootpq = c->d_root;
   a.hscale = c->d_hscale;
@@ -463,7 +510,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   if (!rc) rc = ensure_flags(c);
   if (rc) return rc;
   rc = ensure_slices(c, n);
-  if (!rc && mode != 0) rc = ensure_bparts(c, n);
+  if (!rc && mode != 0) rc = ensure_bparts(c, n, mode == 2);
   if (rc) return rc;
   SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 8 * sizeof(int), s));
   std::vector<cudaEvent_t> ev;
@@ -526,7 +573,6 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
     na.nbr = c->d_nbr;
     na.img = c->d_img;
     na.rij = c->d_rij;
-  na.key = c->d_key;
     na.key = c->d_key;
     na.flags = c->d_flags;
     SNAP_CUDA(c, snap::launch_pos4(n, pos, c->d_pos4, s, c->d_tiles, pos_stage));
@@ -885,6 +931,56 @@ int snap_yi_host(int twojmax, int precision, const double* beta, const double* u
   return SNAP_OK;
 }
 
+int snap_bi_host(int twojmax, int layout, const double* u, double* b) {
+  if (twojmax < 0 || twojmax > snap::kMaxTwoJ || (layout != 0 && layout != 1) || !u || !b) return SNAP_ERR_ARG;
+  snap::HostTables tab;
+  tab.build(twojmax);
+  const bool cp = layout == 1;
+  const std::vector<unsigned> words = tab.bwords(cp);
+  if (words.size() != tab.bdev.size()) return SNAP_ERR_ARG;
+  const int H = tab.H;
+  // factor x of the word: an element, conjugated past H (cp) or by its flag
+  auto fac = [&](unsigned x, unsigned conj, double& re, double& im) {
+    if (cp && x >= (unsigned)H) {
+      x -= (unsigned)H;
+      conj = 1;
+    }
+    re = u[2 * x];
+    im = conj ? -u[2 * x + 1] : u[2 * x + 1];
+  };
+  for (int l = 0; l < tab.ncoeff; ++l) {
+    double v = 0.0;
+    for (int ch = tab.bcomp_chunk[l]; ch < tab.bcomp_chunk[l + 1]; ++ch) {
+      // the chunk's runs of pieces of 1, 2, ... kBGroupMax terms, in order
+      int q = tab.bchunk_term[ch];
+      double acc = 0.0;
+      for (int len = 1; len <= snap::kBGroupMax; ++len) {
+        for (int n = tab.bchunk_runs[(size_t)ch * snap::kBGroupMax + len - 1]; n > 0; --n) {
+          const unsigned w0 = words[q];
+          const unsigned o = (w0 & 0xFFu) | (((w0 >> (cp ? 30 : 28)) & 3u) << 8);
+          double zr = 0.0, zi = 0.0;
+          for (int k = 0; k < len; ++k, ++q) {
+            const unsigned w = words[q];
+            const unsigned x1 = cp ? (w >> 19) & 0x7FFu : (w >> 18) & 0x3FFu;
+            const unsigned x2 = cp ? (w >> 8) & 0x7FFu : (w >> 8) & 0x3FFu;
+            double ar, ai, br, bi;
+            fac(x1, cp ? 0u : (w >> 30) & 1u, ar, ai);
+            fac(x2, cp ? 0u : (w >> 31) & 1u, br, bi);
+            const double c = tab.bdev_coef[q];
+            zr += c * (ar * br - ai * bi);
+            zi += c * (ar * bi + ai * br);
+          }
+          acc += u[2 * o] * zr + u[2 * o + 1] * zi;  // Re(Z conj U_o)
+        }
+      }
+      if (q != tab.bchunk_term[ch + 1]) return SNAP_ERR_ARG;  // runs must cover the chunk
+      v += acc;
+    }
+    b[l] = v;
+  }
+  return SNAP_OK;
+}
+
 int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switchflag,
                 const double* beta, int precision, snap_ctx** out) {
   if (!out) {
@@ -945,11 +1041,8 @@ int snap_create(int twojmax, double rcut, double rfac0, double rmin0, int switch
   if (!rc) rc = upload_r(c, &c->d_hscale, c->tab.half_scale);
   if (!rc) rc = upload_yrec(c);
   if (!rc) rc = upload_brec(c);
-  if (!rc) rc = upload(c, &c->d_bout, c->tab.bout);
-  if (!rc) rc = upload(c, &c->d_bfirst, c->tab.bcomp_first);
-  if (!rc) rc = upload(c, &c->d_bgfirst, c->tab.bgroup_first);
   if (!rc) rc = upload(c, &c->d_bchunk_term, c->tab.bchunk_term);
-  if (!rc) rc = upload(c, &c->d_bchunk_group, c->tab.bchunk_group);
+  if (!rc) rc = upload(c, &c->d_bchunk_runs, c->tab.bchunk_runs);
   if (!rc) rc = upload(c, &c->d_bcomp_chunk, c->tab.bcomp_chunk);
   if (rc) {
     g_create_error = c->err;
@@ -1064,20 +1157,32 @@ const char* snap_stage_name(int stage) {
 
 int snap_launches_per_call(const snap_ctx* c) { return c ? c->launches : -1; }
 
-int snap_compute_bispectrum(snap_ctx* c, int natoms, const double* pos, const double* box,
-                            const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
-                            int nbr_cap, double* B, void* stream) {
+namespace {
+int bispectrum_enqueue(snap_ctx* c, int natoms, const double* pos, const double* box, const int* nbr_cnt,
+                       const int* nbr_idx, const signed char* nbr_img, int nbr_cap, double* B, cudaStream_t s) {
   if (!c) return SNAP_ERR_ARG;
   if (natoms < 0) return fail(c, SNAP_ERR_ARG, "natoms < 0");
   if (int rb = check_box(c, box)) return rb;
   if (natoms == 0) return SNAP_OK;
   if (!pos || !B) return fail(c, SNAP_ERR_ARG, "pos and B are required");
+  return enqueue(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, nullptr, nullptr, nullptr, s, 1, B);
+}
+}  // namespace
+
+int snap_compute_bispectrum(snap_ctx* c, int natoms, const double* pos, const double* box,
+                            const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
+                            int nbr_cap, double* B, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = enqueue(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, nullptr, nullptr, nullptr, s,
-                   1, B);
-  if (rc) return rc;
+  int rc = bispectrum_enqueue(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, B, s);
+  if (rc || natoms == 0) return rc;
   SNAP_CUDA(c, cudaStreamSynchronize(s));
   return check_flags(c);
+}
+
+int snap_compute_bispectrum_async(snap_ctx* c, int natoms, const double* pos, const double* box,
+                                  const int* nbr_cnt, const int* nbr_idx, const signed char* nbr_img,
+                                  int nbr_cap, double* B, void* stream) {
+  return bispectrum_enqueue(c, natoms, pos, box, nbr_cnt, nbr_idx, nbr_img, nbr_cap, B, (cudaStream_t)stream);
 }
 
 int snap_bispectrum_deriv(snap_ctx* c, int natoms, const double* pos, const double* box,
@@ -1172,7 +1277,7 @@ int snap_bispectrum_deriv_batch(snap_ctx* c, int nconf, const int* natoms, const
   if (total == 0) return SNAP_OK;
   if (!pos || !g || !dB) return fail(c, SNAP_ERR_ARG, "pos, g and dB are required");
   int rc = prepare_batch(c, nconf, natoms, boxes);
-  if (!rc) rc = ensure_bparts(c, c->bat_total);
+  if (!rc) rc = ensure_bparts(c, c->bat_total, true);
   if (rc) return rc;
   return launch_batch_deriv(c, pos, g, dB, (cudaStream_t)stream);
 }
@@ -1219,6 +1324,13 @@ int snap_set_knob(snap_ctx* c, int knob, int value) {
       }
       return SNAP_OK;
     }
+    case SNAP_KNOB_BI_LAYOUT:
+      if (value < 0 || value > 2) return fail(c, SNAP_ERR_ARG, "bi_layout must be in 0..2");
+      if (c->bi_layout != value) {
+        c->bi_layout = value;
+        c->nbparts = 0;  // re-plan the runs and the scratch
+      }
+      return SNAP_OK;
     default: return fail(c, SNAP_ERR_ARG, "unknown knob");
   }
 }
@@ -1231,6 +1343,7 @@ int snap_get_knob(const snap_ctx* c, int knob, int* value) {
     case SNAP_KNOB_YI_LAYOUT: *value = c->yi_layout; return SNAP_OK;
     case SNAP_KNOB_PERSIST: *value = c->persist; return SNAP_OK;
     case SNAP_KNOB_DE_ATOMS: *value = c->de_atoms; return SNAP_OK;
+    case SNAP_KNOB_BI_LAYOUT: *value = c->bi_layout; return SNAP_OK;
     default: return SNAP_ERR_ARG;
   }
 }
@@ -1505,13 +1618,12 @@ int snap_destroy(snap_ctx* c) {
   dfree(c->d_yruns);
   dfree(c->d_ysched);
   dfree(c->d_brec);
-  dfree(c->d_bout);
-  dfree(c->d_bfirst);
-  dfree(c->d_bgfirst);
+  dfree(c->d_brec_cp);
+  dfree(c->d_bscratch);
   dfree(c->d_bchunk_term);
-  dfree(c->d_bchunk_group);
+  dfree(c->d_bchunk_runs);
   dfree(c->d_bcomp_chunk);
-  for (auto& kv : c->bpart_cache) cudaFree(kv.second.first);
+  for (auto& kv : c->bpart_cache) cudaFree(kv.second.d);
   c->bpart_cache.clear();
   dfree(c->d_root);
   dfree(c->d_hscale);

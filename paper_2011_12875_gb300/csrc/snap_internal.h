@@ -21,7 +21,9 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
 
 constexpr int kMaxTwoJ = 14;
 constexpr int kYGroupMax = 8;  // longest compute_Y term group (longer ones are cut)
-constexpr int kBChunk = 192;   // bispectrum terms a warp takes at a time (whole groups)
+constexpr int kBChunk = 96;    // bispectrum terms a warp takes at a time (whole groups)
+constexpr int kBMaxChunks = 1024;  // chunks are lengthened past this count
+constexpr int kBGroupMax = 8;      // longest bispectrum term piece (longer groups are cut)
 constexpr int kYRecPad = 256;  // zero records after the compute_Y term list (read-ahead)
 constexpr int kYRecPrefetch = 64;  // compute_Y's L1 prefetch distance without the record ring
 constexpr int kMaxNeighCap = 64;
@@ -179,15 +181,15 @@ struct WorkArgs {
   int test_skip_stage;  // test hook: TMA staging registers its bytes but issues no copy
   // bispectrum output
   int ncoeff;
-  const void* brec;       // YRec<R> records of the bispectrum terms
-  const int* bout;        // U element of every output group
-  const int* bfirst;      // [ncoeff+1] first term of each component
-  const int* bgfirst;     // [ncoeff+1] first output group of each component
+  const void* brec;       // YRec<R> records of the bispectrum terms (sign-flip words)
+  const void* brec_cp;    // the same records in the conjugate-plane words (null: unused)
   const int* bchunk_term;   // chunks of the bispectrum term list (snap_tables.h)
-  const int* bchunk_group;
+  const void* bchunk_runs;  // [nchunks][kBGroupMax] u16: pieces of 1, 2, ... terms of every chunk
   const int* bcomp_chunk;
+  int bi_layout;            // tunable: 0 planned, 1 sign flips, 2 conjugate plane
+  void* bscratch;           // partial sums of the bispectrum chunks when shared memory is short
   const int* bpart;         // [nbparts+1] first component of each CTA's run
-  int nbparts, bmaxchunks;
+  int nbparts, bmaxchunks, bmaxterms;  // runs, most chunks and most terms of one run
   double* B;              // [N][ncoeff]
   const void* rootpq;
   const void* hscale;  // R [H]: S_t(ma, mb) of the scaled recursion (u = S v)
@@ -239,6 +241,25 @@ cudaError_t launch_virial_conf(const double* vatom, const NeighConf* confs, int 
 template <typename R> cudaError_t launch_de(const WorkArgs& a, cudaStream_t s);
 template <typename R> cudaError_t launch_force(const WorkArgs& a, cudaStream_t s);
 template <typename R> cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s);
+
+// Launch plan of the bispectrum kernels (B and dB) for the precision's size
+// (4 or 8 bytes), H, and the most chunks and terms of a CTA's run: the
+// block's planes staged or read from global memory, the conjugate plane or
+// sign flips, the run's term records staged or read through L1 (rs), the
+// partial sums in shared memory or in the global scratch (gpart, then CTAs x
+// maxchunks x 32 x rsize bytes), and the dynamic shared memory.  Layout:
+// [planes][barrier, 16 B][records, rec_bytes][partials].
+constexpr int kBiThreads = 512;
+constexpr int kBiCtasPerSm = 2;  // register budget of the kernels (64 a thread)
+constexpr size_t kBiSmemMax = 200 * 1024;   // one CTA an SM
+constexpr size_t kBiSmemPair = 112 * 1024;  // two CTAs an SM
+struct BiPlan {
+  bool staged, cp, rs, gpart;
+  size_t smem, rec_bytes;
+};
+BiPlan bi_plan(int rsize, int H, bool deriv, int maxchunks, int maxterms, int layout, bool have_cp);
+// whether the conjugate-plane records can ever be used for this size and H
+bool bi_plane_fits(int rsize, int H);
 
 // Register column-chain kernels (snap_col_*.cu), for 1 <= twojmax <= 14;
 // cudaErrorInvalidValue when no instance exists for the precision/2J.

@@ -231,18 +231,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase,
 // CTA's shared memory).  skip_copy registers the bytes without issuing the
 // copy: a test hook under which the wait runs out with nothing in flight.
 // `overlap()` runs on every thread while the copy is in flight.
-// With src2 given, a second block of `bytes` from src2 lands right after the
-// first (dst + bytes) on the same barrier.
+// With src2 given, a second block of `bytes` from src2 lands at dst + off2
+// (right after the first when off2 is 0) on the same barrier.
+// With src3 given, bytes3 from src3 land at dst + off3, on the same barrier.
 template <typename F>
 __device__ bool stage_bulk(void* dst, const void* src, unsigned bytes, uint64_t* bar, int* flags,
-                           bool skip_copy, F&& overlap, const void* src2 = nullptr) {
+                           bool skip_copy, F&& overlap, const void* src2 = nullptr, unsigned off2 = 0,
+                           const void* src3 = nullptr, unsigned bytes3 = 0, unsigned off3 = 0) {
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
-    mbar_expect_tx(bar, src2 ? 2 * bytes : bytes);
+    mbar_expect_tx(bar, (src2 ? 2 * bytes : bytes) + (src3 ? bytes3 : 0u));
     if (!skip_copy) {
       bulk_g2s(dst, src, bytes, bar);
-      if (src2) bulk_g2s(static_cast<char*>(dst) + bytes, src2, bytes, bar);
+      if (src2) bulk_g2s(static_cast<char*>(dst) + (off2 ? off2 : bytes), src2, bytes, bar);
+      if (src3) bulk_g2s(static_cast<char*>(dst) + off3, src3, bytes3, bar);
     }
   }
   overlap();
@@ -667,69 +670,218 @@ __global__ void __launch_bounds__(kYaWarps * 32) yi_atom_kernel(WorkArgs a) {
 // (Eqs. z and dbidrk): B_l is trilinear in (U_t1, U_t2, conj U_t), so
 //   dB_l = Re [ (Z(dU_t1, U_t2) + Z(U_t1, dU_t2)) : conj(U_t) + Z : conj(dU_t) ]
 // (dU has the inversion symmetry of U, so the records' conjugation flags hold
-// for it too; its block is staged beside U).
-// The term list is cut into chunks of whole output groups (about kBChunk
-// terms, never across a component).  CTA (block, part) takes the components
-// of its part; its warps take the part's chunks in turn, each leaving one
-// partial sum per atom in shared memory, and the partials of a component are
-// added in chunk order: a fixed order, whatever the launch shape, and no warp
-// waits on the largest component.
-template <typename R, bool STAGED, bool DERIV>
-__global__ void __launch_bounds__(256) bi_kernel(WorkArgs a, const cx<R>* __restrict__ dUg, double* __restrict__ out) {
+// for it too).
+// The term list is cut into chunks of whole output groups (never across a
+// component).  CTA (block, part) takes the components of its part; its
+// warps take the part's chunks in turn, each leaving one partial sum per atom
+// (in shared memory, or in a global scratch where the part has too many
+// chunks), and the partials of a component are added in chunk order: a fixed
+// order, whatever the launch shape, and no warp waits on the largest
+// component.
+//
+// Records (snap_tables.h, bwords): the factors' byte offsets sit in the word
+// already scaled to the plane's element stride (one mask each).  Each output
+// group is cut into pieces of at most kBGroupMax terms, and a chunk's pieces
+// are stored by length, so a chunk is runs of equal-length pieces walked by
+// branch-free bodies (records, factors and output elements loaded ahead of
+// the arithmetic); a piece's first word holds its output element.  The
+// contraction is linear in Z, so each piece is contracted on its own.  CP:
+// the staged block is [2][H][32] with the conjugates in its second half (no
+// sign flips); with DERIV the tangent's planes follow, [U | conj U | dU |
+// conj dU].
+template <typename R, bool CP>
+__device__ __forceinline__ unsigned b_off1(unsigned w) {
+  const unsigned o = CP ? ((w >> 11) & 0x7FF00u) : ((w >> 10) & 0x3FF00u);
+  return sizeof(R) == 4 ? o : o << 1;
+}
+template <typename R, bool CP>
+__device__ __forceinline__ unsigned b_off2(unsigned w) {
+  const unsigned o = CP ? (w & 0x7FF00u) : (w & 0x3FF00u);
+  return sizeof(R) == 4 ? o : o << 1;
+}
+template <typename R>
+__device__ __forceinline__ R fmr(R x, R y, R z) {
+  if constexpr (sizeof(R) == 4) return fmaf(x, y, z);
+  else return fma(x, y, z);
+}
+// byte offset of a piece's output element, from the piece's first word
+template <typename R, bool CP>
+__device__ __forceinline__ unsigned b_out(unsigned w) {
+  const unsigned o = (w & 0xFFu) | (((w >> (CP ? 30 : 28)) & 3u) << 8);
+  return o * (unsigned)(32 * sizeof(cx<R>));
+}
+
+// one record: from the CTA's staged copy (RS) or through the read-only path
+template <typename R, bool RS>
+__device__ __forceinline__ void b_load(const YRec<R>* __restrict__ rec, int q, unsigned& w, R& c) {
+  if constexpr (RS) {
+    if constexpr (sizeof(R) == 4) {
+      const uint2 r = *reinterpret_cast<const uint2*>(rec + q);
+      w = r.x;
+      c = __uint_as_float(r.y);
+    } else {
+      const uint4 r = *reinterpret_cast<const uint4*>(rec + q);
+      w = r.x;
+      c = (R)__hiloint2double((int)r.w, (int)r.z);
+    }
+  } else if constexpr (sizeof(R) == 4) {
+    const uint2 r = __ldg(reinterpret_cast<const uint2*>(rec + q));
+    w = r.x;
+    c = __uint_as_float(r.y);
+  } else {
+    const uint4 r = __ldg(reinterpret_cast<const uint4*>(rec + q));
+    w = r.x;
+    c = (R)__hiloint2double((int)r.w, (int)r.z);
+  }
+}
+
+// G pieces of K terms from record q: per piece Z = sum c u1 u2 (and dZ),
+// then acc += Re(Z conj U_o) (DERIV: Re(dZ conj U_o + Z conj dU_o)).
+template <typename R, bool CP, bool DERIV, bool RS, int K, int G>
+__device__ __forceinline__ void b_pieces(const YRec<R>* __restrict__ rec, int q, const char* __restrict__ ul,
+                                         const char* __restrict__ dl, R& acc) {
+  constexpr int N = G * K;
+  unsigned w[N];
+  R c[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) b_load<R, RS>(rec, q + j, w[j], c[j]);
+  cx<R> u1[N], u2[N], d1[DERIV ? N : 1], d2[DERIV ? N : 1], uo[G], duo[DERIV ? G : 1];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    u1[j] = *reinterpret_cast<const cx<R>*>(ul + b_off1<R, CP>(w[j]));
+    u2[j] = *reinterpret_cast<const cx<R>*>(ul + b_off2<R, CP>(w[j]));
+    if constexpr (DERIV) {
+      d1[j] = *reinterpret_cast<const cx<R>*>(dl + b_off1<R, CP>(w[j]));
+      d2[j] = *reinterpret_cast<const cx<R>*>(dl + b_off2<R, CP>(w[j]));
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const unsigned ob = b_out<R, CP>(w[g * K]);
+    uo[g] = *reinterpret_cast<const cx<R>*>(ul + ob);
+    if constexpr (DERIV) duo[g] = *reinterpret_cast<const cx<R>*>(dl + ob);
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    R zr, zi, dzr = R(0), dzi = R(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int j = g * K + k;
+      const unsigned m1 = (w[j] << 1) & 0x80000000u, m2 = w[j] & 0x80000000u;
+      const R b1 = CP ? u1[j].im : flip_sign(u1[j].im, m1), b2 = CP ? u2[j].im : flip_sign(u2[j].im, m2);
+      // c u1 u2 = (p + i q)(u2.re + i b2), p + i q = c u1
+      const R p = c[j] * u1[j].re, qq = c[j] * b1;
+      if (k == 0) {
+        zr = p * u2[j].re;
+        zi = p * b2;
+      } else {
+        zr = fmr(p, u2[j].re, zr);
+        zi = fmr(p, b2, zi);
+      }
+      zr = fmr(-qq, b2, zr);
+      zi = fmr(qq, u2[j].re, zi);
+      if constexpr (DERIV) {
+        // d(c u1 u2) = c du1 u2 + c u1 du2
+        const R db1 = CP ? d1[j].im : flip_sign(d1[j].im, m1), db2 = CP ? d2[j].im : flip_sign(d2[j].im, m2);
+        const R dp = c[j] * d1[j].re, dq = c[j] * db1;
+        dzr = fmr(dp, u2[j].re, dzr);
+        dzr = fmr(-dq, b2, dzr);
+        dzr = fmr(p, d2[j].re, dzr);
+        dzr = fmr(-qq, db2, dzr);
+        dzi = fmr(dp, b2, dzi);
+        dzi = fmr(dq, u2[j].re, dzi);
+        dzi = fmr(p, db2, dzi);
+        dzi = fmr(qq, d2[j].re, dzi);
+      }
+    }
+    if constexpr (DERIV) {
+      acc = fmr(uo[g].re, dzr, acc);
+      acc = fmr(uo[g].im, dzi, acc);
+      acc = fmr(duo[g].re, zr, acc);
+      acc = fmr(duo[g].im, zi, acc);
+    } else {
+      acc = fmr(uo[g].re, zr, acc);
+      acc = fmr(uo[g].im, zi, acc);
+    }
+  }
+}
+
+// All ng pieces of K terms from record q (advanced past them): about kStep
+// records a body.
+template <typename R, bool CP, bool DERIV, bool RS, int K>
+__device__ __forceinline__ void b_run(const YRec<R>* __restrict__ rec, int& q, int ng, const char* __restrict__ ul,
+                                      const char* __restrict__ dl, R& acc) {
+  constexpr int kStep = DERIV ? 4 : 8;
+  constexpr int G = K >= kStep ? 1 : kStep / K;
+  for (; ng >= G; ng -= G, q += G * K) b_pieces<R, CP, DERIV, RS, K, G>(rec, q, ul, dl, acc);
+  for (; ng > 0; --ng, q += K) b_pieces<R, CP, DERIV, RS, K, 1>(rec, q, ul, dl, acc);
+}
+
+// gpart: the partial sums' scratch in global memory ([CTA][maxchunks][32]),
+// or null for shared memory.  RS: the run's records staged beside the planes
+// (rec_bytes of shared memory) by the same bulk copy.
+template <typename R, bool STAGED, bool CP, bool DERIV, bool RS>
+__global__ void __launch_bounds__(kBiThreads, kBiCtasPerSm)
+    bi_kernel(WorkArgs a, const cx<R>* __restrict__ dUg, double* __restrict__ out, R* __restrict__ gpart,
+              unsigned rec_bytes) {
   extern __shared__ __align__(128) unsigned char smem[];
+  static_assert(STAGED || (!CP && !RS), "the conjugate plane and the records are staged");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const long blk = blockIdx.x;
   const int H = a.H;
-  const cx<R>* us = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
-  const cx<R>* ds = DERIV ? dUg + blk * H * 32 : nullptr;
   const size_t plane = (size_t)H * 32 * sizeof(cx<R>);
-  R* part = reinterpret_cast<R*>(smem + (STAGED ? (DERIV ? 2 : 1) * plane + 16 : 0));  // [maxchunks][32]
-  if (STAGED) {
-    cx<R>* su = reinterpret_cast<cx<R>*>(smem);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (DERIV ? 2 : 1) * plane);
-    if (!stage_bulk(su, us, (unsigned)plane, bar, a.flags, a.test_skip_stage != 0, [] {},
-                    DERIV ? reinterpret_cast<const void*>(ds) : nullptr))
-      return;
-    us = su;
-    if (DERIV) ds = su + H * 32;
-  }
+  constexpr int NP = (CP ? 2 : 1) * (DERIV ? 2 : 1);
+  const cx<R>* ug = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
+  const cx<R>* dg = DERIV ? dUg + blk * H * 32 : nullptr;
+  const char* ul = reinterpret_cast<const char*>(ug + lane);
+  const char* dl = DERIV ? reinterpret_cast<const char*>(dg + lane) : nullptr;
+  const size_t roff = STAGED ? NP * plane + 16 : 0;  // records, then partials
+  R* part = gpart ? gpart + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * a.bmaxchunks * 32
+                  : reinterpret_cast<R*>(smem + roff + (RS ? rec_bytes : 0u));  // [maxchunks][32]
   const int l0 = a.bpart[blockIdx.y], l1 = a.bpart[blockIdx.y + 1];
   const int c0 = a.bcomp_chunk[l0], c1 = a.bcomp_chunk[l1];
-  const YRec<R>* __restrict__ rec = reinterpret_cast<const YRec<R>*>(a.brec);
-  for (int ch = c0 + warp; ch < c1; ch += nw) {
-    int g = a.bchunk_group[ch];
-    R zr = R(0), zi = R(0), dzr = R(0), dzi = R(0), acc = R(0);
-    const int q1 = a.bchunk_term[ch + 1];
-    for (int q = a.bchunk_term[ch]; q < q1; ++q) {
-      const unsigned w = rec[q].w;
-      const R c = rec[q].c;
-      const int e1 = (int)(w & 1023u), e2 = (int)((w >> 10) & 1023u);
-      const unsigned f1 = (w >> 20) & 1u, f2 = (w >> 21) & 1u;
-      const cx<R> u1 = us[e1 * 32 + lane], u2 = us[e2 * 32 + lane];
-      const R b = flip_if(u1.im, f1), d = flip_if(u2.im, f2);
-      zr += c * (u1.re * u2.re - b * d);
-      zi += c * (u1.re * d + b * u2.re);
-      if (DERIV) {
-        const cx<R> d1 = ds[e1 * 32 + lane], d2 = ds[e2 * 32 + lane];
-        const R db1 = flip_if(d1.im, f1), db2 = flip_if(d2.im, f2);
-        // d(u1 u2) = du1 u2 + u1 du2
-        dzr += c * (d1.re * u2.re - db1 * d + u1.re * d2.re - b * db2);
-        dzi += c * (d1.re * d + db1 * u2.re + u1.re * db2 + b * d2.re);
-      }
-      if (w & (1u << 22)) {
-        const int o = a.bout[g];
-        const cx<R> u = us[o * 32 + lane];
+  const YRec<R>* __restrict__ grec = reinterpret_cast<const YRec<R>*>(CP ? a.brec_cp : a.brec);
+  // records [qb, q1) of the run; FP32 records start on a 16-byte boundary
+  const int qb = RS ? (sizeof(R) == 4 ? a.bchunk_term[c0] & ~1 : a.bchunk_term[c0]) : 0;
+  const unsigned rbytes =
+      RS ? (unsigned)(((a.bchunk_term[c1] - qb) * sizeof(YRec<R>) + 15) / 16 * 16) : 0u;
+  if (STAGED) {
+    cx<R>* su = reinterpret_cast<cx<R>*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NP * plane);
+    if (!stage_bulk(su, ug, (unsigned)plane, bar, a.flags, a.test_skip_stage != 0, [] {},
+                    DERIV ? reinterpret_cast<const void*>(dg) : nullptr, (unsigned)((CP ? 2 : 1) * plane),
+                    RS ? reinterpret_cast<const void*>(grec + qb) : nullptr, rbytes, (unsigned)roff))
+      return;
+    if (CP) {
+      const int he = H * 32;
+      for (int e = threadIdx.x; e < he; e += blockDim.x) {
+        const cx<R> v = su[e];
+        su[he + e] = mk<R>(v.re, -v.im);
         if (DERIV) {
-          const cx<R> du = ds[o * 32 + lane];
-          acc += u.re * dzr + u.im * dzi + du.re * zr + du.im * zi;
-          dzr = dzi = R(0);
-        } else {
-          acc += u.re * zr + u.im * zi;
+          const cx<R> d = su[2 * he + e];
+          su[3 * he + e] = mk<R>(d.re, -d.im);
         }
-        zr = zi = R(0);
-        ++g;
       }
+      __syncthreads();
     }
+    ul = reinterpret_cast<const char*>(su + lane);
+    if (DERIV) dl = ul + (CP ? 2 : 1) * plane;
+  }
+  const YRec<R>* __restrict__ rec = RS ? reinterpret_cast<const YRec<R>*>(smem + roff) : grec;
+  static_assert(kBGroupMax == 8, "one 16-byte run header per chunk");
+  const uint4* __restrict__ runs = reinterpret_cast<const uint4*>(a.bchunk_runs);
+  for (int ch = c0 + warp; ch < c1; ch += nw) {
+    const uint4 h = __ldg(runs + ch);
+    int q = a.bchunk_term[ch] - qb;
+    R acc = R(0);
+    b_run<R, CP, DERIV, RS, 1>(rec, q, (int)(h.x & 0xffffu), ul, dl, acc);
+    b_run<R, CP, DERIV, RS, 2>(rec, q, (int)(h.x >> 16), ul, dl, acc);
+    b_run<R, CP, DERIV, RS, 3>(rec, q, (int)(h.y & 0xffffu), ul, dl, acc);
+    b_run<R, CP, DERIV, RS, 4>(rec, q, (int)(h.y >> 16), ul, dl, acc);
+    b_run<R, CP, DERIV, RS, 5>(rec, q, (int)(h.z & 0xffffu), ul, dl, acc);
+    b_run<R, CP, DERIV, RS, 6>(rec, q, (int)(h.z >> 16), ul, dl, acc);
+    b_run<R, CP, DERIV, RS, 7>(rec, q, (int)(h.w & 0xffffu), ul, dl, acc);
+    b_run<R, CP, DERIV, RS, 8>(rec, q, (int)(h.w >> 16), ul, dl, acc);
     part[(ch - c0) * 32 + lane] = acc;
   }
   __syncthreads();
@@ -1293,25 +1445,47 @@ cudaError_t launch_force(const WorkArgs& a, cudaStream_t s) {
 
 // Bispectrum (dU == nullptr) or its derivative along dU into out [N][N_B]:
 // grid (32-atom blocks, component runs a.nbparts), 8 warps a CTA.
+BiPlan bi_plan(int rsize, int H, bool deriv, int maxchunks, int maxterms, int layout, bool have_cp) {
+  BiPlan p;
+  const size_t plane = (size_t)H * 32 * 2 * rsize;
+  const size_t np = deriv ? 2 : 1;
+  const size_t part = (size_t)maxchunks * 32 * rsize;
+  p.staged = np * plane + 16 <= kBiSmemMax;
+  // the conjugate plane when asked for, or (planned) when two CTAs still fit an SM
+  p.cp = p.staged && have_cp && layout != 1 && 2 * np * plane + 16 <= kBiSmemMax &&
+         (layout == 2 || 2 * np * plane + 16 + part <= kBiSmemPair);
+  const size_t planes = p.staged ? (p.cp ? 2 : 1) * np * plane + 16 : 0;
+  p.gpart = planes + part > kBiSmemMax;
+  const size_t base = planes + (p.gpart ? 0 : part);
+  // a run's records (one more for the 16-byte-aligned start of FP32 records)
+  // when they fit without losing the second CTA of an SM
+  const size_t rec = (((size_t)maxterms + 1) * (rsize == 4 ? 8 : 16) + 15) / 16 * 16;
+  p.rs = p.staged && base + rec <= (base <= kBiSmemPair ? kBiSmemPair : kBiSmemMax);
+  p.rec_bytes = p.rs ? rec : 0;
+  p.smem = base + p.rec_bytes;
+  return p;
+}
+
+bool bi_plane_fits(int rsize, int H) { return 2 * (size_t)H * 32 * 2 * rsize + 16 <= kBiSmemMax; }
+
 template <typename R, bool DERIV>
 cudaError_t launch_bi_t(const WorkArgs& a, const void* dU, double* out, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const long nblk = (a.n + 31) / 32;
-  const size_t plane = (size_t)a.H * 32 * sizeof(cx<R>);
-  const size_t stage = (DERIV ? 2 : 1) * plane + 16;
-  const size_t parts = (size_t)a.bmaxchunks * 32 * sizeof(R);
-  const bool staged = stage + parts <= 200 * 1024;
-  const size_t sm = (staged ? stage : 0) + parts;
+  const BiPlan p = bi_plan((int)sizeof(R), a.H, DERIV, a.bmaxchunks, a.bmaxterms, a.bi_layout, a.brec_cp != nullptr);
+  R* gpart = p.gpart ? reinterpret_cast<R*>(a.bscratch) : nullptr;
+  if (p.gpart && !gpart) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)nblk, (unsigned)a.nbparts);
   const cx<R>* d = reinterpret_cast<const cx<R>*>(dU);
-  if (staged) {
-    cudaError_t e = allow_smem(bi_kernel<R, true, DERIV>, sm);
+  const unsigned rb = (unsigned)p.rec_bytes;
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = allow_smem(kern, p.smem);
     if (e != cudaSuccess) return e;
-    return launch_k(bi_kernel<R, true, DERIV>, grid, dim3(256), sm, s, a, d, out);
-  }
-  cudaError_t e = allow_smem(bi_kernel<R, false, DERIV>, sm);
-  if (e != cudaSuccess) return e;
-  return launch_k(bi_kernel<R, false, DERIV>, grid, dim3(256), sm, s, a, d, out);
+    return launch_k(kern, grid, dim3(kBiThreads), p.smem, s, a, d, out, gpart, rb);
+  };
+  if (!p.staged) return go(bi_kernel<R, false, false, DERIV, false>);
+  if (p.cp) return p.rs ? go(bi_kernel<R, true, true, DERIV, true>) : go(bi_kernel<R, true, true, DERIV, false>);
+  return p.rs ? go(bi_kernel<R, true, false, DERIV, true>) : go(bi_kernel<R, true, false, DERIV, false>);
 }
 
 template <typename R>

@@ -392,7 +392,9 @@ void HostTables::build(int J2, bool size_runs) {
   }
   bcomp_first.push_back((int)bterms.size());
   bgroup_first.push_back((int)bout.size());
-  // chunks of whole groups, about kBChunk terms, within components
+  // chunks of whole groups, about kBChunk terms (more at large 2J, so that
+  // there are at most about kBMaxChunks), within components
+  const int chunk_len = std::max<int>(kBChunk, (int)((bterms.size() + kBMaxChunks - 1) / kBMaxChunks));
   bchunk_term.clear();
   bchunk_group.clear();
   bcomp_chunk.clear();
@@ -406,7 +408,7 @@ void HostTables::build(int J2, bool size_runs) {
       ++inchunk;
       if (bterms[q] & (1u << 22)) {  // a group ends here
         ++gq;
-        if (inchunk >= kBChunk && q + 1 < bcomp_first[l + 1]) {
+        if (inchunk >= chunk_len && q + 1 < bcomp_first[l + 1]) {
           bchunk_term.push_back(q + 1);
           bchunk_group.push_back(gq);
           inchunk = 0;
@@ -417,6 +419,43 @@ void HostTables::build(int J2, bool size_runs) {
   bcomp_chunk.push_back((int)bchunk_term.size());
   bchunk_term.push_back((int)bterms.size());
   bchunk_group.push_back((int)bout.size());
+  // device order: every chunk's groups cut into pieces of at most kBGroupMax
+  // terms (a group of n terms into ceil(n / kBGroupMax) pieces whose lengths
+  // differ by at most one), pieces ordered by length, stably
+  const int nchunks = (int)bchunk_term.size() - 1;
+  bdev.assign(bterms.size(), 0u);
+  bdev_coef.assign(bterms.size(), 0.0);
+  bdev_o.assign(bterms.size(), -1);
+  bchunk_runs.assign((size_t)nchunks * kBGroupMax, 0);
+  struct Piece {
+    int first, len, o;
+  };
+  std::vector<Piece> pieces;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    pieces.clear();
+    int g = bchunk_group[ch], gfirst = bchunk_term[ch];
+    for (int q = bchunk_term[ch]; q < bchunk_term[ch + 1]; ++q) {
+      if (!(bterms[q] & (1u << 22))) continue;
+      const int n = q + 1 - gfirst, np = (n + kBGroupMax - 1) / kBGroupMax;
+      for (int k = 0, at = gfirst; k < np; ++k) {
+        const int len = n / np + (k < n % np ? 1 : 0);
+        pieces.push_back({at, len, bout[g]});
+        at += len;
+      }
+      gfirst = q + 1;
+      ++g;
+    }
+    std::stable_sort(pieces.begin(), pieces.end(), [](const Piece& x, const Piece& y) { return x.len < y.len; });
+    int at = bchunk_term[ch];
+    for (const Piece& pc : pieces) {
+      bchunk_runs[(size_t)ch * kBGroupMax + pc.len - 1] += 1;
+      for (int k = 0; k < pc.len; ++k, ++at) {
+        bdev[at] = bterms[pc.first + k] & 0x3FFFFFu;
+        bdev_coef[at] = bterm_coef[pc.first + k];
+        bdev_o[at] = k == 0 ? pc.o : -1;
+      }
+    }
+  }
 
   half_scale.assign(H, 0.0);
   for (int e = 0; e < H; ++e) {
@@ -461,11 +500,16 @@ std::vector<int> HostTables::bslices(int nslices) const {
   return b;
 }
 
-std::vector<int> HostTables::bparts(int nparts, int* maxchunks) const {
+std::vector<int> HostTables::bparts(int nparts, int* maxchunks, int* maxterms) const {
   const std::vector<int> b = bslices(nparts);
-  int mx = 0;
-  for (int k = 0; k < nparts; ++k) mx = std::max(mx, bcomp_chunk[b[k + 1]] - bcomp_chunk[b[k]]);
+  int mx = 0, mt = 0;
+  for (int k = 0; k < nparts; ++k) {
+    const int c0 = bcomp_chunk[b[k]], c1 = bcomp_chunk[b[k + 1]];
+    mx = std::max(mx, c1 - c0);
+    mt = std::max(mt, bchunk_term[c1] - bchunk_term[c0]);
+  }
   *maxchunks = mx;
+  *maxterms = mt;
   return b;
 }
 
@@ -501,6 +545,23 @@ std::vector<int> HostTables::slices(int nslices) const {
   while ((int)b.size() < nslices + 1) b.push_back(H);
   b[nslices] = H;
   return b;
+}
+
+std::vector<unsigned> HostTables::bwords(bool cp) const {
+  std::vector<unsigned> w(bdev.size(), 0u);
+  for (size_t q = 0; q < bdev.size(); ++q) {
+    const unsigned t = bdev[q];
+    const unsigned i1 = t & 1023u, i2 = (t >> 10) & 1023u, c1 = (t >> 20) & 1u, c2 = (t >> 21) & 1u;
+    unsigned x = cp ? (((i2 + c2 * (unsigned)H) << 8) | ((i1 + c1 * (unsigned)H) << 19))
+                    : ((i2 << 8) | (i1 << 18) | (c1 << 30) | (c2 << 31));
+    if (bdev_o[q] >= 0) {
+      const unsigned o = (unsigned)bdev_o[q];
+      if (o > 1023u) return {};  // not reached for 2J <= 14 (H = 652)
+      x |= (o & 0xFFu) | ((o >> 8) << (cp ? 30 : 28));
+    }
+    w[q] = x;
+  }
+  return w;
 }
 
 }  // namespace snap

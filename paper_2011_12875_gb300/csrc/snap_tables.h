@@ -37,6 +37,18 @@ struct HostTables {
   // kBChunk terms, never across a component): first term and first group of
   // every chunk (+1 end entry each) and the first chunk of every component
   std::vector<int> bchunk_term, bchunk_group, bcomp_chunk;
+  // The device order of the bispectrum terms: within every chunk each output
+  // group cut into pieces of at most kBGroupMax terms (near-equal lengths),
+  // the pieces ordered by length (stably), so that the device walks runs of
+  // equal-length pieces with branch-free bodies.  Chunks keep their term
+  // ranges.  bdev: the table words (as bterms, without the end bits);
+  // bdev_coef: their coefficients; bdev_o: the U element of each term's
+  // piece, -1 on all but a piece's first term; bchunk_runs [nchunks]
+  // [kBGroupMax]: the number of pieces of 1, 2, ... terms of every chunk.
+  std::vector<unsigned> bdev;
+  std::vector<double> bdev_coef;
+  std::vector<int> bdev_o;
+  std::vector<unsigned short> bchunk_runs;
   std::vector<double> rootpq;
   // [H]: S_t(ma, mb) = sqrt((t - ma)! ma! / (t - mb)!) of every half-layout
   // element, the factor between the scaled recursion's v and u
@@ -55,7 +67,19 @@ struct HostTables {
   // nparts contiguous runs of components with about equal term counts (entry
   // k = first component of run k, entry nparts = ncoeff); *maxchunks = the
   // most chunks of one run
-  std::vector<int> bparts(int nparts, int* maxchunks) const;
+  // and *maxterms = the most terms of one run
+  std::vector<int> bparts(int nparts, int* maxchunks, int* maxterms) const;
+  // The bispectrum records' words as the device reads them (one per term of
+  // the device order):
+  //   cp = false (factors' stored elements, imaginary parts flipped by flag):
+  //     bits 8-17 second factor, 18-27 first factor, 30 conjugate the first
+  //     factor, 31 conjugate the second; a piece's U element in bits 0-7
+  //     (low) and 28-29 (high) of its first word
+  //   cp = true (factors in a [2][H] plane, conjugates in the second half):
+  //     bits 8-18 second factor, 19-29 first factor; the piece's U element in
+  //     bits 0-7 and 30-31 of its first word
+  // Empty if an element does not fit in 10 bits.
+  std::vector<unsigned> bwords(bool cp) const;
 };
 
 double clebsch_gordan(int tj1, int tm1, int tj2, int tm2, int tj, int tm);

@@ -32,6 +32,7 @@ KNOB_YI_WAVES = 1
 KNOB_YI_LAYOUT = 2
 KNOB_PERSIST = 3
 KNOB_DE_ATOMS = 4
+KNOB_BI_LAYOUT = 5
 
 BUF_NBR_CNT = 0
 BUF_NBR_IDX = 1
@@ -47,9 +48,10 @@ EXPORTS = ("snap_num_coeff", "snap_create", "snap_set_beta", "snap_set_neigh_cap
            "snap_compute_host", "snap_get_buffer", "snap_half_index", "snap_half_size",
            "snap_destroy", "snap_last_error", "snap_profile", "snap_profile_read",
            "snap_stage_name", "snap_launches_per_call", "snap_compute_bispectrum",
+           "snap_compute_bispectrum_async",
            "snap_bispectrum_deriv", "snap_force_weighted", "snap_generation",
            "snap_compute_batch", "snap_set_tuning", "snap_get_tuning", "snap_autotune",
-           "snap_neighbors_noalloc", "snap_yi_host", "snap_test_stage_timeout",
+           "snap_neighbors_noalloc", "snap_yi_host", "snap_bi_host", "snap_test_stage_timeout",
            "snap_probe_fma", "snap_bispectrum_deriv_batch", "snap_set_knob", "snap_get_knob")
 NSTAGES = 5
 
@@ -98,6 +100,8 @@ def load(path: str | None = None):
     L.snap_launches_per_call.restype = i
     L.snap_compute_bispectrum.argtypes = [p, i, p, p, p, p, p, i, p, p]
     L.snap_compute_bispectrum.restype = i
+    L.snap_compute_bispectrum_async.argtypes = [p, i, p, p, p, p, p, i, p, p]
+    L.snap_compute_bispectrum_async.restype = i
     L.snap_bispectrum_deriv.argtypes = [p, i, p, p, p, p, p, i, p, p, p]
     L.snap_bispectrum_deriv.restype = i
     L.snap_force_weighted.argtypes = [p, p, p, p]
@@ -130,6 +134,8 @@ def load(path: str | None = None):
     L.snap_half_size.restype = i
     L.snap_yi_host.argtypes = [i, i, p, p, p]
     L.snap_yi_host.restype = i
+    L.snap_bi_host.argtypes = [i, i, p, p]
+    L.snap_bi_host.restype = i
     L.snap_probe_fma.argtypes = [i, i, p, p]
     L.snap_probe_fma.restype = i
     L.snap_destroy.argtypes = [p]
@@ -175,6 +181,19 @@ def yi_host(twojmax: int, beta, u_half, precision: int = MIXED) -> np.ndarray:
     if rc != 0:
         raise SnapError(rc, "snap_yi_host: invalid argument")
     return y
+
+
+def bi_host(twojmax: int, u_half, layout: int = 0) -> np.ndarray:
+    """The bispectrum kernels' record words for one atom walked on the host in
+    FP64 (snap_bi_host): u_half [H][2] -> B [ncoeff].  layout 0: sign-flip
+    words, 1: conjugate-plane words.  No GPU work."""
+    H = half_size(twojmax)
+    u = np.ascontiguousarray(u_half, dtype=np.float64).reshape(H, 2)
+    b = np.zeros(num_coeff(twojmax))
+    rc = load().snap_bi_host(twojmax, layout, _np_ptr(u), _np_ptr(b))
+    if rc != 0:
+        raise SnapError(rc, "snap_bi_host: invalid argument")
+    return b
 
 
 def _np_ptr(a: np.ndarray):
@@ -263,8 +282,10 @@ class Snap:
                        ctypes.c_void_p(stream)))
         return energy, forces, virial
 
-    def bispectrum(self, pos, box, out=None, neighbors=None, stream=None):
-        """Bispectrum components B [N, N_B] (float64 device tensor)."""
+    def bispectrum(self, pos, box, out=None, neighbors=None, stream=None, wait=True):
+        """Bispectrum components B [N, N_B] (float64 device tensor).  With
+        wait=False the call returns once enqueued; device-side errors come
+        from the next sync()."""
         import torch
         if pos.dtype != torch.float64 or not pos.is_cuda or not pos.is_contiguous():
             raise ValueError("pos must be a contiguous float64 CUDA tensor")
@@ -280,7 +301,8 @@ class Snap:
         if neighbors is not None:
             cnt, idx, img = neighbors
             cap = idx.shape[1]
-        self._check(self._lib.snap_compute_bispectrum(
+        fn = self._lib.snap_compute_bispectrum if wait else self._lib.snap_compute_bispectrum_async
+        self._check(fn(
             self._h, n, _t_ptr(pos), _np_ptr(boxa), _t_ptr(cnt), _t_ptr(idx), _t_ptr(img), cap,
             _t_ptr(out), ctypes.c_void_p(stream)))
         return out

@@ -448,3 +448,50 @@ def test_persistent_work_queue_changes_no_bit(snapmod, prec, twojmax):
         for x, y in zip(run(), ref):
             assert np.array_equal(x, y), d
     s.close()
+
+
+@pytest.mark.parametrize("prec,twojmax", [(1, 8), (0, 8), (1, 14)])
+def test_bispectrum_layouts_and_async_change_no_bit(snapmod, prec, twojmax):
+    """The word layouts of the bispectrum kernels (sign flips or the staged
+    conjugate plane: the same conjugate either way) and the asynchronous entry
+    point give B and dB bit for bit equal to the planned synchronous call."""
+    cfg = inputs.bcc(4, disp=0.15, seed=41)
+    s = snapmod.Snap(twojmax, inputs.beta(twojmax), precision=prec)
+    pos = torch.tensor(cfg.pos, device="cuda:0")
+    g = torch.tensor(np.random.Generator(np.random.PCG64(42)).normal(size=cfg.pos.shape), device="cuda:0")
+    B0 = s.bispectrum(pos, cfg.box).cpu().numpy().copy()
+    D0 = s.bispectrum_deriv(pos, cfg.box, g).cpu().numpy().copy()
+    for lay in (1, 2):
+        s.set_knob(snapmod.KNOB_BI_LAYOUT, lay)
+        assert s.get_knob(snapmod.KNOB_BI_LAYOUT) == lay
+        assert np.array_equal(s.bispectrum(pos, cfg.box).cpu().numpy(), B0)
+        assert np.array_equal(s.bispectrum_deriv(pos, cfg.box, g).cpu().numpy(), D0)
+    s.set_knob(snapmod.KNOB_BI_LAYOUT, 0)
+    out = torch.empty_like(torch.tensor(B0, device="cuda:0"))
+    s.bispectrum(pos, cfg.box, out=out, wait=False)
+    s.sync()
+    assert np.array_equal(out.cpu().numpy(), B0)
+    with pytest.raises(snapmod.SnapError):
+        s.set_knob(snapmod.KNOB_BI_LAYOUT, 3)
+    s.close()
+
+
+def test_bispectrum_partials_in_global_scratch(snapmod):
+    """2J = 14, mixed, 4394 atoms: one component run a CTA, whose chunk
+    partials do not fit beside the staged plane and go to the global scratch.
+    B against the oracle on sampled atoms (all components), at the mixed
+    bispectrum tolerance."""
+    cfg = inputs.bcc(13, disp=0.1, seed=44)
+    beta = inputs.beta(14)
+    s = snapmod.Snap(14, beta, precision=1)
+    B = s.bispectrum(torch.tensor(cfg.pos, device="cuda:0"), cfg.box).cpu().numpy()
+    s.close()
+    rng = np.random.Generator(np.random.PCG64(45))
+    atoms = np.sort(rng.choice(cfg.natoms, size=24, replace=False))
+    need = np.zeros(cfg.natoms, dtype=bool)
+    need[atoms] = True
+    pairs = O.build_neighbors(cfg.pos, cfg.box, inputs.RCUT)
+    ref = O.compute(O.Params(14), beta, cfg.natoms, pairs, need=need, want_B=True)
+    err = rel_err(B[atoms], ref.B[atoms])
+    print(f"ERRS-B-SCRATCH {err:.3e}")
+    assert err <= MIXED_B_TOL

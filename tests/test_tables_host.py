@@ -86,3 +86,32 @@ def test_oracle_y_has_the_mirror_the_export_fills_in(twojmax):
                 s = -1.0 if (ma + mb) & 1 else 1.0
                 want = s * np.conj(Y[full_pos(t, t - ma, mb)])
                 assert abs(Y[full_pos(t, ma, mb)] - want) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("twojmax", [2, 5, 8, 10])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_bispectrum_words_give_the_oracle_b(snapmod, twojmax, layout):
+    """The bispectrum kernels' record words (factor offsets, conjugation by
+    flag or by the conjugate plane, the step to each group's output element,
+    chunks of whole groups), walked on the host, give the oracle's B_l (Eq. z
+    with every triple product of the full matrices multiplied out) for a U
+    with the inversion symmetry.  The oracle's B_l is its energy with beta the
+    l-th unit vector (E is linear in beta, beta_0 = 0)."""
+    rng = np.random.default_rng(900 + twojmax)
+    h = symmetric_u(snapmod, twojmax, rng)
+    U = half_to_full(h[None], twojmax, snapmod.half_index)[0]
+    nc = O.ncoeff(twojmax)
+    want = np.empty(nc)
+    for l in range(nc):
+        beta = np.zeros(nc + 1)
+        beta[1 + l] = 1.0
+        want[l] = O.energy_from_u(twojmax, beta, U)
+    got = snapmod.bi_host(twojmax, h, layout=layout)
+    scale = np.abs(want).max()
+    assert np.abs(got - want).max() <= 1e-12 * scale, np.abs(got - want).max() / scale
+
+
+def test_bispectrum_words_reject_bad_arguments(snapmod):
+    h = np.zeros((snapmod.half_size(4), 2))
+    with pytest.raises(snapmod.SnapError):
+        snapmod.bi_host(4, h, layout=2)
