@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--workload", default="bcc10_2j8",
                     help="headline workload (bcc4_2j8, bcc10_2j8, bcc10_2j14, bcc20_2j14)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--row", choices=["batch", "bispectrum", "force_matching"],
+                    help="only this widened row (one JSON line, no headline)")
     ap.add_argument("--probe-peaks", action="store_true",
                     help="only measure the FP32 and FP64 FMA peaks (snap_probe_fma) with clocks")
     return ap.parse_args()
@@ -342,10 +344,10 @@ def _events_time(torch, fn, steps, flush, dev):
     return statistics.mean(a.elapsed_time(b) for a, b in evs)
 
 
-def next_rows(torch, snap, inputs, flush, dev, args):
-    """Measurements of the widened rows: batched evaluation of 64 uneven
-    configurations (graph replay vs a per-configuration loop, after the
-    autotuner), bispectrum output, and the force-matching loss + gradient."""
+def row_batch(torch, snap, inputs, flush, dev, args):
+    """Batched evaluation of 64 uneven configurations (graph replay vs a
+    per-configuration loop, after the autotuner), and compute_Y's two
+    layouts on the headline workload."""
     import numpy as np
     out = {}
     # --- batch: 64 configurations, 54..2000 atoms, +-2% strain, 2J = 8, mixed
@@ -426,7 +428,12 @@ def next_rows(torch, snap, inputs, flush, dev, args):
         s.close()
         lay[tag] = {"step_ms": t, "compute_yi_ms": pr["compute_yi"][0] / max(pr["compute_yi"][1], 1)}
     out["compute_y_layout_2000_2j8_mixed"] = lay
-    # --- bispectrum output, 2000 atoms, 2J = 8
+    return out
+
+
+def row_bispectrum(torch, snap, inputs, flush, dev, args):
+    """Bispectrum output, 2000 atoms, 2J = 8, both precisions."""
+    out = {}
     w = inputs.WORKLOADS["bcc10_2j8"]
     cfg = w.config()
     for prec, tag in ((snap.MIXED, "mixed"), (snap.FP64, "fp64")):
@@ -434,14 +441,20 @@ def next_rows(torch, snap, inputs, flush, dev, args):
         p_ = torch.tensor(cfg.pos, device=dev)
         Bout = torch.empty((cfg.natoms, snap.num_coeff(8)), dtype=torch.float64, device=dev)
         s.bispectrum(p_, cfg.box, out=Bout)
-        t = _events_time(torch, lambda: s.bispectrum(p_, cfg.box, out=Bout, wait=False), 10, flush, dev)
+        t = _events_time(torch, lambda: s.bispectrum(p_, cfg.box, out=Bout, wait=False), 30, flush, dev)
         s.sync()
-        t_sync = _events_time(torch, lambda: s.bispectrum(p_, cfg.box, out=Bout), 10, flush, dev)
+        t_sync = _events_time(torch, lambda: s.bispectrum(p_, cfg.box, out=Bout), 30, flush, dev)
         out[f"bispectrum_2000_2j8_{tag}"] = {"atom_steps_per_s": cfg.natoms / (t * 1e-3), "ms": t,
                                              "ms_with_host_wait": t_sync,
                                              "includes": "neighbour list, geometry, compute_U, B"}
         s.close()
-    # --- force matching: loss + d loss / d beta over 32 configurations (+-0.2 A)
+    return out
+
+
+def row_force_matching(torch, snap, inputs, flush, dev, args):
+    """Force-matching loss + gradient over 32 configurations, 2J = 8 and 14."""
+    import numpy as np
+    out = {}
     from paper_2011_12875_gb300 import autograd as AG
     fit = inputs.fitting_set(32)
     rng = np.random.Generator(np.random.PCG64(99))
@@ -469,6 +482,18 @@ def next_rows(torch, snap, inputs, flush, dev, args):
             "step": "all 32 configurations batched: E, F (snap_compute_batch); loss sum|F-F_ref|^2; "
                     "dL/dbeta via snap_bispectrum_deriv_batch"}
         s.close()
+    return out
+
+
+ROWS = {"batch": row_batch, "bispectrum": row_bispectrum, "force_matching": row_force_matching}
+
+
+def next_rows(torch, snap, inputs, flush, dev, args):
+    """Measurements of the widened rows: batched evaluation, bispectrum
+    output, and the force-matching loss + gradient."""
+    out = {}
+    for fn in ROWS.values():
+        out.update(fn(torch, snap, inputs, flush, dev, args))
     return out
 
 
@@ -516,6 +541,13 @@ def main():
     build.build()
     snap.load()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    if args.row:
+        if rank == 0:
+            print(json.dumps({"row": args.row, **ROWS[args.row](torch, snap, inputs, flush, dev, args)}), flush=True)
+        if pg:
+            pg.barrier()
+            pg.destroy_process_group()
+        return
 
     head = inputs.WORKLOADS[args.workload]
     hprec = snap.MIXED if args.precision == "mixed" else snap.FP64
