@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--workload", default="bcc10_2j8",
                     help="headline workload (bcc4_2j8, bcc10_2j8, bcc10_2j14, bcc20_2j14)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--neighbors", default="built", choices=["built", "supplied"],
+                    help="supplied: the headline takes the neighbour list from the caller")
     ap.add_argument("--row", choices=["batch", "bispectrum", "force_matching"],
                     help="only this widened row (one JSON line, no headline)")
     ap.add_argument("--probe-peaks", action="store_true",
@@ -254,9 +256,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def time_variant(torch, snap, w, precision, steps, warmup, flush, dev, profile=False):
+def time_variant(torch, snap, w, precision, steps, warmup, flush, dev, profile=False, supplied=False):
     """Device time of `steps` evaluations (CUDA events on the compute stream,
-    L2 flushed between steps outside the events)."""
+    L2 flushed between steps outside the events).  supplied: the neighbour
+    list is the caller's (the library's own list of the configuration, read
+    back once and passed in, as an MD code passes its list), so a step is
+    compute_U from the stored separations instead of the build."""
     import numpy as np
     cfg, beta = w.config(), w.beta()
     s = snap.Snap(w.twojmax, beta, precision=precision)
@@ -266,8 +271,16 @@ def time_variant(torch, snap, w, precision, steps, warmup, flush, dev, profile=F
     F = torch.empty((n, 3), dtype=torch.float64, device=dev)
     W = torch.empty(6, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
+    nb = {}
+    if supplied:
+        s.compute(pos, cfg.box, E, F, W)
+        idx = s.get_buffer(snap.BUF_NBR_IDX)
+        K = idx.size // n
+        nb = {"neighbors": (torch.tensor(s.get_buffer(snap.BUF_NBR_CNT), device=dev),
+                            torch.tensor(idx.reshape(n, K), device=dev),
+                            torch.tensor(s.get_buffer(snap.BUF_NBR_IMG).reshape(n, K, 3), device=dev))}
     for _ in range(warmup):
-        s.compute(pos, cfg.box, E, F, W, wait=False)
+        s.compute(pos, cfg.box, E, F, W, wait=False, **nb)
     s.sync()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(steps)]
@@ -276,7 +289,7 @@ def time_variant(torch, snap, w, precision, steps, warmup, flush, dev, profile=F
     for k in range(steps):
         flush.fill_(k & 0xff)
         evs[k][0].record(stream)
-        s.compute(pos, cfg.box, E, F, W, wait=False)
+        s.compute(pos, cfg.box, E, F, W, wait=False, **nb)
         evs[k][1].record(stream)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
@@ -289,7 +302,7 @@ def time_variant(torch, snap, w, precision, steps, warmup, flush, dev, profile=F
         s.profile(True)
         for k in range(min(steps, 20)):
             flush.fill_(k & 0xff)
-            s.compute(pos, cfg.box, E, F, W, wait=False)
+            s.compute(pos, cfg.box, E, F, W, wait=False, **nb)
         s.sync()
         prof = s.profile_read()
         s.profile(False)
@@ -564,7 +577,7 @@ def main():
         pg.barrier()
     sampler.start()
     r = time_variant(torch, snap, head, hprec, args.steps, args.warmup, flush, dev,
-                     profile=True)
+                     profile=True, supplied=args.neighbors == "supplied")
     clocks = sampler.stop()
     ms_mean = statistics.mean(r["ms"])
     ms_med = statistics.median(r["ms"])
@@ -588,7 +601,7 @@ def main():
         "data": "synthetic BCC, +-0.1 A, seeded beta",
         "config": {"workload": head.name, "natoms": r["natoms"], "twojmax": head.twojmax,
                    "precision": args.precision, "l2": "flushed between steps",
-                   "parallelism": f"replicas x{world}"},
+                   "neighbors": args.neighbors, "parallelism": f"replicas x{world}"},
         "gpu_launches": r["launches"] * args.steps,
         "roofline": {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(hpeak, 2), "unit": "TFLOP/s", "frac": round(achieved / hpeak, 4),
@@ -636,6 +649,15 @@ def main():
                     "steps": k, "dominant_share": vp[vdom][0] / sum(x[0] for x in vp.values()),
                     "achieved_tflops": ach, "peak_tflops": peak,
                     "stages_ms": {x: vp[x][0] / max(vp[x][1], 1) for x in vp}}
+            # the headline workload with the caller's neighbour list (an MD
+            # code's list): compute_U from stored separations, no build
+            w = inputs.WORKLOADS["bcc10_2j8"]
+            v = time_variant(torch, snap, w, snap.MIXED, max(3, min(args.steps, 300)), 3, flush, dev,
+                             profile=True, supplied=True)
+            vm = statistics.mean(v["ms"])
+            detail["supplied_list_2j8_2000_mixed"] = {
+                "value": round(v["natoms"] / (vm * 1e-3)), "ms": round(vm, 4),
+                "stages_ms": {x: v["prof"][x][0] / max(v["prof"][x][1], 1) for x in v["prof"]}}
             detail["next"] = next_rows(torch, snap, inputs, flush, dev, args)
         variants["mixed_2j8_2000"] = {"value": round(value / world), "ms": round(ms_mean, 4),
                                       "kernel": dom, "frac": round(achieved / hpeak, 4)}
