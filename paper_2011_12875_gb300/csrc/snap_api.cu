@@ -103,8 +103,13 @@ struct snap_ctx {
   snap::WorkArgs last_args;   // arguments of the last evaluation (weighted gather)
   bool have_last = false;
   double* d_vpart = nullptr;
+  // device status words and counters, zeroed at the end of every evaluation
+  // (flags_out_kernel), which also writes the status words to h_flags,
+  // pinned and mapped (d_hflags: its device address)
   int* d_flags = nullptr;
   int* h_flags = nullptr;
+  int* d_hflags = nullptr;
+  bool flags_dirty = false;  // an evaluation was begun and not closed: zero before the next
 
   // per-stage profiling
   bool prof_on = false;
@@ -341,8 +346,31 @@ int ensure_slices(snap_ctx* c, int n) {
 int ensure_flags(snap_ctx* c) {
   if (c->d_flags) return SNAP_OK;
   SNAP_CUDA(c, cudaMalloc(&c->d_flags, 8 * sizeof(int)));
-  SNAP_CUDA(c, cudaMallocHost(&c->h_flags, 8 * sizeof(int)));
+  SNAP_CUDA(c, cudaMemset(c->d_flags, 0, 8 * sizeof(int)));
+  SNAP_CUDA(c, cudaHostAlloc(reinterpret_cast<void**>(&c->h_flags), 8 * sizeof(int), cudaHostAllocMapped));
+  std::memset(c->h_flags, 0, 8 * sizeof(int));
+  SNAP_CUDA(c, cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_hflags), c->h_flags, 0));
   return SNAP_OK;
+}
+
+// Begin an evaluation on stream s: the flags are zero unless the previous
+// evaluation did not reach its end (a launch failed), then they are zeroed.
+cudaError_t open_flags(snap_ctx* c, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (c->flags_dirty) e = cudaMemsetAsync(c->d_flags, 0, 8 * sizeof(int), s);
+  c->flags_dirty = true;
+  return e;
+}
+// End it: the status words to the host (read after the stream's work), the
+// flags zeroed, by one small kernel rather than a copy and a memset (each a
+// copy-engine operation on the step's critical path).
+cudaError_t close_flags(snap_ctx* c, cudaStream_t s) {
+  cudaError_t e = snap::launch_flags_out(c->d_flags, c->d_hflags, s);
+  if (e == cudaSuccess) {
+    c->flags_dirty = false;
+    c->launches += 1;
+  }
+  return e;
 }
 
 // Component runs of the bispectrum kernels (B, or dB with deriv) for n
@@ -512,7 +540,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   rc = ensure_slices(c, n);
   if (!rc && mode != 0) rc = ensure_bparts(c, n, mode == 2);
   if (rc) return rc;
-  SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 8 * sizeof(int), s));
+  SNAP_CUDA(c, open_flags(c, s));
   std::vector<cudaEvent_t> ev;
   if (c->prof_on && mode == 0) {
     if (!c->prof_free.empty()) {
@@ -604,7 +632,7 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
                          : snap::launch_dbi<double>(a, c->d_dU, B, s));
       c->launches += 2;
     }
-    SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SNAP_CUDA(c, close_flags(c, s));
     c->last_n = n;
     c->last_K = K;
     return SNAP_OK;
@@ -614,11 +642,12 @@ int enqueue(snap_ctx* c, int n, const double* pos, const double* box, const int*
   SNAP_CUDA(c, colk ? (mixed ? snap::launch_de_col<float>(a, s) : snap::launch_de_col<double>(a, s))
                     : (mixed ? snap::launch_de<float>(a, s) : snap::launch_de<double>(a, s)));
   SNAP_CUDA(c, mark());
+  a.hflags = c->d_hflags;  // the force kernel ends the evaluation
   SNAP_CUDA(c, mixed ? snap::launch_force<float>(a, s) : snap::launch_force<double>(a, s));
+  c->flags_dirty = false;
   SNAP_CUDA(c, mark());
   c->launches += 3;
   if (!ev.empty()) c->prof_pending.push_back(ev);
-  SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
   c->last_n = n;
   c->last_K = K;
   return SNAP_OK;
@@ -691,7 +720,7 @@ int prepare_batch(snap_ctx* c, int nconf, const int* natoms, const double* boxes
 int launch_batch(snap_ctx* c, const double* pos, double* energy, double* forces, double* virial,
                  cudaStream_t s) {
   const int n = c->bat_total;
-  SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 8 * sizeof(int), s));
+  SNAP_CUDA(c, open_flags(c, s));
   snap::NeighArgs na;
   std::memset(&na, 0, sizeof(na));
   na.n = n;
@@ -728,9 +757,11 @@ int launch_batch(snap_ctx* c, const double* pos, double* energy, double* forces,
   SNAP_CUDA(c, mixed ? snap::launch_yi<float>(a, s) : snap::launch_yi<double>(a, s));
   SNAP_CUDA(c, colk ? (mixed ? snap::launch_de_col<float>(a, s) : snap::launch_de_col<double>(a, s))
                     : (mixed ? snap::launch_de<float>(a, s) : snap::launch_de<double>(a, s)));
+  a.hflags = c->d_hflags;  // the force kernel ends the evaluation (the virial sums use no flag)
   SNAP_CUDA(c, mixed ? snap::launch_force<float>(a, s) : snap::launch_force<double>(a, s));
+  c->flags_dirty = false;
+  a.hflags = nullptr;
   if (virial) SNAP_CUDA(c, snap::launch_virial_conf(c->d_vatom, c->d_confs, c->bat_nconf, virial, s));
-  SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
   c->launches = nl + 3 + (virial ? 1 : 0);
   c->generation += 1;
   c->last_args = a;
@@ -743,7 +774,7 @@ int launch_batch(snap_ctx* c, const double* pos, double* energy, double* forces,
 // nothing.
 int launch_batch_deriv(snap_ctx* c, const double* pos, const double* g, double* dB, cudaStream_t s) {
   const int n = c->bat_total;
-  SNAP_CUDA(c, cudaMemsetAsync(c->d_flags, 0, 8 * sizeof(int), s));
+  SNAP_CUDA(c, open_flags(c, s));
   snap::NeighArgs na;
   std::memset(&na, 0, sizeof(na));
   na.n = n;
@@ -775,8 +806,8 @@ int launch_batch_deriv(snap_ctx* c, const double* pos, const double* g, double* 
   }
   SNAP_CUDA(c, mixed ? snap::launch_tan_col<float>(a, g, c->d_dU, s) : snap::launch_tan_col<double>(a, g, c->d_dU, s));
   SNAP_CUDA(c, mixed ? snap::launch_dbi<float>(a, c->d_dU, dB, s) : snap::launch_dbi<double>(a, c->d_dU, dB, s));
-  SNAP_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  c->launches = nl + 2;
+  SNAP_CUDA(c, close_flags(c, s));
+  c->launches = nl + 2 + 1;  // + the flags kernel
   c->generation += 1;
   c->have_last = false;
   return SNAP_OK;

@@ -163,6 +163,9 @@ struct WorkArgs {
   double* vpart;
   double* virial;
   int* flags;
+  // non-null on the kernel that ends an evaluation (the force kernel): its
+  // last CTA writes flags[0..3] to this host-mapped copy and zeroes the flags
+  int* hflags;
   const int* half_tmm;
   const void* yrec;       // compute_Y term records (see snap_tables.cpp)
   const int* yfirst;      // [H+1] first term of each output element
@@ -234,6 +237,10 @@ __host__ __device__ inline bool yrec_plane_format(int rsize, int H) {
   return rsize == 4 && yi_conjplane(rsize, H);
 }
 YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves);
+
+// End of an evaluation: flags[0..3] into the host-mapped status words
+// (device pointer hflags), all eight flags zeroed.
+cudaError_t launch_flags_out(int* flags, int* hflags, cudaStream_t s);
 
 // Per-configuration virial: sum of vatom over each configuration's atoms.
 cudaError_t launch_virial_conf(const double* vatom, const NeighConf* confs, int nconf, double* virial,

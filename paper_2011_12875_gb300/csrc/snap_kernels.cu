@@ -1247,20 +1247,34 @@ __global__ void __launch_bounds__(kFThreads) force_kernel(WorkArgs a) {
     const double e = (ew[0][tid] + ew[1][tid]) + (ew[2][tid] + ew[3][tid]);
     a.energy[i0 + tid] = a.beta0 + e * (1.0 / 3.0);
   }
-  if (a.vatom || !a.virial) return;
+  const bool vir = !a.vatom && a.virial;
+  if (!vir && !a.hflags) return;
   const int cta = blockIdx.x, ncta = gridDim.x;
-  if (tid < 6) {
-    a.vpart[6 * cta + tid] = (wv[0][tid] + wv[1][tid]) + (wv[2][tid] + wv[3][tid]);
+  if (vir && tid < 6) a.vpart[6 * cta + tid] = (wv[0][tid] + wv[1][tid]) + (wv[2][tid] + wv[3][tid]);
+  __syncthreads();
+  // the fence after the barrier makes every write and flag update of this
+  // CTA (the reverse-slot check's included) visible before its count
+  if (tid == 0) {
     __threadfence();
+    last = (atomicAdd(&a.flags[4], 1) == ncta - 1);
   }
   __syncthreads();
-  if (tid == 0) last = (atomicAdd(&a.flags[4], 1) == ncta - 1);
-  __syncthreads();
   if (!last) return;
+  __threadfence();
+  if (a.hflags) {
+    // the evaluation's end: the status words to the host-mapped copy and all
+    // flags zeroed for the next evaluation (no other CTA touches them now)
+    __syncthreads();  // every thread of this CTA is past its own flag reads
+    if (tid < 8) {
+      const int v = __ldcg(a.flags + tid);
+      if (tid < 4) a.hflags[tid] = v;
+      a.flags[tid] = 0;
+    }
+  }
+  if (!vir) return;
   // last CTA: thread t adds the CTA partials t, t + kFThreads, ... in order
   // (loads issued four at a time), then the same trees: a fixed order, so
   // the virial is deterministic
-  __threadfence();
   double x[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int b0 = tid; b0 < ncta; b0 += 4 * kFThreads) {
     double y[4][6];
@@ -1505,6 +1519,22 @@ template cudaError_t launch_dbi<double>(const WorkArgs&, const void*, double*, c
 cudaError_t launch_force_weighted(const WorkArgs& a, const double* w, double* grad, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   return launch_k(force_weighted_kernel, dim3((a.n + 7) / 8), dim3(256), 0, s, a, w, grad);
+}
+
+// End of an evaluation: the status words (flags 0-3) go to the host-mapped
+// copy, and every flag, counters included, is zeroed for the next
+// evaluation (the kernels before it in the stream have completed).
+__global__ void flags_out_kernel(int* __restrict__ flags, int* __restrict__ hflags) {
+  const int t = threadIdx.x;
+  if (t < 8) {
+    const int v = flags[t];
+    if (t < 4) hflags[t] = v;
+    flags[t] = 0;
+  }
+}
+
+cudaError_t launch_flags_out(int* flags, int* hflags, cudaStream_t s) {
+  return launch_k(flags_out_kernel, dim3(1), dim3(32), 0, s, flags, hflags);
 }
 
 // Per-configuration virial: one CTA per configuration sums its atoms in a
