@@ -863,6 +863,14 @@ cudaError_t launch_tan_col_t(const WorkArgs& a, const double* g, void* dU, cudaS
 //  * The searched plan is taken when it costs 3% less than the reference
 //    (measured at 2J8 and 2J14 on 2000 atoms, a 64-configuration batch, and
 //    16000 atoms at 2J14, where the reference stays ahead).
+//  * pipe_bound (FP64, whose pipe runs at 1/64 of the FP32 rate and is busy
+//    all the time): the CTAs an SM holds share its pipe, so A is chosen first
+//    by ceil(ctas / SMs) x ceil(A x maxcnt / P), the most CTAs an SM takes
+//    times a CTA's passes, among the A whose best warp count (the search
+//    above) keeps at least 8 warps an SM resident; then the warp count for
+//    that A as above.  Measured at 2J8, 2000 atoms: A = 2 1.067 ms, 3 1.138,
+//    16 1.151, 8 1.166, 4 1.182, 1 1.194, 6 1.365, 12 1.704 (the model: 63,
+//    65, 70, 70, 72, 70, 78, 104).
 struct DePlan {
   int nw, A;
   size_t smem;
@@ -870,7 +878,34 @@ struct DePlan {
 // force_A > 0 (the SNAP_KNOB_DE_ATOMS tunable) restricts the search to CTAs
 // of force_A atoms (the best warp count for it) and skips the reference.
 inline DePlan de_plan(int n, int maxcnt, int P, size_t per_warp, size_t per_atom, int regs, int nsm,
-                      int max_warps, int nw0, int force_A = 0) {
+                      int max_warps, int nw0, int force_A = 0, bool pipe_bound = false);
+
+// The pipe-bound choice of A (see de_plan), then the plan for it.
+inline DePlan de_plan_pipe(int n, int maxcnt, int P, size_t per_warp, size_t per_atom, int regs, int nsm,
+                           int max_warps, int nw0) {
+  const int ralloc = (regs + 7) / 8 * 8;
+  DePlan best{0, 0, 0};
+  long best_cost = -1;
+  for (int A = 1; A <= 64; ++A) {
+    const DePlan p = de_plan(n, maxcnt, P, per_warp, per_atom, regs, nsm, max_warps, nw0, A);
+    if (p.smem == 0) break;
+    const long ctas = (n + A - 1) / A;
+    const int cps = std::min({65536 / (ralloc * p.nw * 32), (int)((228 * 1024) / (p.smem + 1024)), 64 / p.nw, 32});
+    const long per_sm = (ctas + nsm - 1) / nsm;
+    if (std::min<long>(per_sm, cps) * p.nw < 8) continue;  // too few warps to keep the pipe busy
+    const long cost = per_sm * (((long)A * maxcnt + P - 1) / P);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = p;
+    }
+  }
+  if (best_cost < 0) return de_plan(n, maxcnt, P, per_warp, per_atom, regs, nsm, max_warps, nw0);
+  return best;
+}
+
+inline DePlan de_plan(int n, int maxcnt, int P, size_t per_warp, size_t per_atom, int regs, int nsm,
+                      int max_warps, int nw0, int force_A, bool pipe_bound) {
+  if (pipe_bound && force_A <= 0) return de_plan_pipe(n, maxcnt, P, per_warp, per_atom, regs, nsm, max_warps, nw0);
   const int ralloc = (regs + 7) / 8 * 8;
   auto shape = [&](int nw, int A, size_t* smem, long* waves, long* ppw) -> bool {
     *smem = (size_t)A * per_atom + (size_t)nw * per_warp + sizeof(int) * (A + 1);
@@ -945,7 +980,8 @@ cudaError_t launch_de_rev_col_t(const WorkArgs& a, cudaStream_t s) {
     if (std::equal(key, key + 4, last_key)) {
       p = last_plan;
     } else {
-      p = de_plan(a.n, maxcnt, Shape<J2>::P, per_warp, per_atom, regs, nsm, de_max_warps<R>(), nw0, a.de_atoms);
+      p = de_plan(a.n, maxcnt, Shape<J2>::P, per_warp, per_atom, regs, nsm, de_max_warps<R>(), nw0, a.de_atoms,
+                  sizeof(R) == 8);
       std::copy(key, key + 4, last_key);
       last_plan = p;
     }
