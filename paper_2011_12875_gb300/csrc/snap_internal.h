@@ -251,7 +251,7 @@ template <typename R> cudaError_t launch_bi(const WorkArgs& a, cudaStream_t s);
 
 // Launch plan of the bispectrum kernels (B and dB) for the precision's size
 // (4 or 8 bytes), H, and the most chunks and terms of a CTA's run: the
-// block's planes staged or read from global memory, the conjugate plane or
+// block's planes staged (U's, and dU's when both fit) or read from global memory, the conjugate plane or
 // sign flips, the run's term records staged or read through L1 (rs), the
 // partial sums in shared memory or in the global scratch (gpart, then CTAs x
 // maxchunks x 32 x rsize bytes), and the dynamic shared memory.  Layout:
@@ -261,7 +261,7 @@ constexpr int kBiCtasPerSm = 2;  // register budget of the kernels (64 a thread)
 constexpr size_t kBiSmemMax = 200 * 1024;   // one CTA an SM
 constexpr size_t kBiSmemPair = 112 * 1024;  // two CTAs an SM
 struct BiPlan {
-  bool staged, cp, rs, gpart;
+  bool staged, ds, cp, rs, gpart;  // ds: the tangent's block staged beside U (dB)
   size_t smem, rec_bytes;
 };
 BiPlan bi_plan(int rsize, int H, bool deriv, int maxchunks, int maxterms, int layout, bool have_cp);

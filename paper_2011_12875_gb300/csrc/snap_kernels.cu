@@ -820,17 +820,21 @@ __device__ __forceinline__ void b_run(const YRec<R>* __restrict__ rec, int& q, i
 // gpart: the partial sums' scratch in global memory ([CTA][maxchunks][32]),
 // or null for shared memory.  RS: the run's records staged beside the planes
 // (rec_bytes of shared memory) by the same bulk copy.
-template <typename R, bool STAGED, bool CP, bool DERIV, bool RS>
+// DS (DERIV): the tangent's block is staged too; without it (two blocks do not
+// fit, 2J = 14) U alone is staged and dU is read through L1.
+template <typename R, bool STAGED, bool CP, bool DERIV, bool RS, bool DS>
 __global__ void __launch_bounds__(kBiThreads, kBiCtasPerSm)
     bi_kernel(WorkArgs a, const cx<R>* __restrict__ dUg, double* __restrict__ out, R* __restrict__ gpart,
               unsigned rec_bytes) {
   extern __shared__ __align__(128) unsigned char smem[];
   static_assert(STAGED || (!CP && !RS), "the conjugate plane and the records are staged");
+  static_assert(!DS || (STAGED && DERIV), "the tangent is staged with U");
+  static_assert(!(CP && DERIV && !DS), "the conjugate plane of dU needs dU staged");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const long blk = blockIdx.x;
   const int H = a.H;
   const size_t plane = (size_t)H * 32 * sizeof(cx<R>);
-  constexpr int NP = (CP ? 2 : 1) * (DERIV ? 2 : 1);
+  constexpr int NP = (CP ? 2 : 1) * (DS ? 2 : 1);
   const cx<R>* ug = reinterpret_cast<const cx<R>*>(a.U) + blk * H * 32;
   const cx<R>* dg = DERIV ? dUg + blk * H * 32 : nullptr;
   const char* ul = reinterpret_cast<const char*>(ug + lane);
@@ -849,7 +853,7 @@ __global__ void __launch_bounds__(kBiThreads, kBiCtasPerSm)
     cx<R>* su = reinterpret_cast<cx<R>*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NP * plane);
     if (!stage_bulk(su, ug, (unsigned)plane, bar, a.flags, a.test_skip_stage != 0, [] {},
-                    DERIV ? reinterpret_cast<const void*>(dg) : nullptr, (unsigned)((CP ? 2 : 1) * plane),
+                    DS ? reinterpret_cast<const void*>(dg) : nullptr, (unsigned)((CP ? 2 : 1) * plane),
                     RS ? reinterpret_cast<const void*>(grec + qb) : nullptr, rbytes, (unsigned)roff))
       return;
     if (CP) {
@@ -857,7 +861,7 @@ __global__ void __launch_bounds__(kBiThreads, kBiCtasPerSm)
       for (int e = threadIdx.x; e < he; e += blockDim.x) {
         const cx<R> v = su[e];
         su[he + e] = mk<R>(v.re, -v.im);
-        if (DERIV) {
+        if (DS) {
           const cx<R> d = su[2 * he + e];
           su[3 * he + e] = mk<R>(d.re, -d.im);
         }
@@ -865,7 +869,7 @@ __global__ void __launch_bounds__(kBiThreads, kBiCtasPerSm)
       __syncthreads();
     }
     ul = reinterpret_cast<const char*>(su + lane);
-    if (DERIV) dl = ul + (CP ? 2 : 1) * plane;
+    if (DS) dl = ul + (CP ? 2 : 1) * plane;
   }
   const YRec<R>* __restrict__ rec = RS ? reinterpret_cast<const YRec<R>*>(smem + roff) : grec;
   static_assert(kBGroupMax == 8, "one 16-byte run header per chunk");
@@ -1464,11 +1468,13 @@ BiPlan bi_plan(int rsize, int H, bool deriv, int maxchunks, int maxterms, int la
   const size_t plane = (size_t)H * 32 * 2 * rsize;
   const size_t np = deriv ? 2 : 1;
   const size_t part = (size_t)maxchunks * 32 * rsize;
-  p.staged = np * plane + 16 <= kBiSmemMax;
+  p.staged = plane + 16 <= kBiSmemMax;              // U's block
+  p.ds = deriv && np * plane + 16 <= kBiSmemMax;    // and the tangent's beside it
+  const size_t ns = p.ds ? 2 : 1;                    // staged blocks
   // the conjugate plane when asked for, or (planned) when two CTAs still fit an SM
-  p.cp = p.staged && have_cp && layout != 1 && 2 * np * plane + 16 <= kBiSmemMax &&
-         (layout == 2 || 2 * np * plane + 16 + part <= kBiSmemPair);
-  const size_t planes = p.staged ? (p.cp ? 2 : 1) * np * plane + 16 : 0;
+  p.cp = p.staged && (!deriv || p.ds) && have_cp && layout != 1 && 2 * ns * plane + 16 <= kBiSmemMax &&
+         (layout == 2 || 2 * ns * plane + 16 + part <= kBiSmemPair);
+  const size_t planes = p.staged ? (p.cp ? 2 : 1) * ns * plane + 16 : 0;
   p.gpart = planes + part > kBiSmemMax;
   const size_t base = planes + (p.gpart ? 0 : part);
   // a run's records (one more for the 16-byte-aligned start of FP32 records)
@@ -1497,9 +1503,12 @@ cudaError_t launch_bi_t(const WorkArgs& a, const void* dU, double* out, cudaStre
     if (e != cudaSuccess) return e;
     return launch_k(kern, grid, dim3(kBiThreads), p.smem, s, a, d, out, gpart, rb);
   };
-  if (!p.staged) return go(bi_kernel<R, false, false, DERIV, false>);
-  if (p.cp) return p.rs ? go(bi_kernel<R, true, true, DERIV, true>) : go(bi_kernel<R, true, true, DERIV, false>);
-  return p.rs ? go(bi_kernel<R, true, false, DERIV, true>) : go(bi_kernel<R, true, false, DERIV, false>);
+  if (!p.staged) return go(bi_kernel<R, false, false, DERIV, false, false>);
+  if (DERIV && !p.ds)  // U staged, dU through L1
+    return p.rs ? go(bi_kernel<R, true, false, DERIV, true, false>) : go(bi_kernel<R, true, false, DERIV, false, false>);
+  if (p.cp)
+    return p.rs ? go(bi_kernel<R, true, true, DERIV, true, DERIV>) : go(bi_kernel<R, true, true, DERIV, false, DERIV>);
+  return p.rs ? go(bi_kernel<R, true, false, DERIV, true, DERIV>) : go(bi_kernel<R, true, false, DERIV, false, DERIV>);
 }
 
 template <typename R>
