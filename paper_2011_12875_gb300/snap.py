@@ -213,6 +213,8 @@ class Snap:
         self._lib = load()
         self.twojmax = twojmax
         self.precision = precision
+        self._hp = {}      # host-array addresses (compute_host)
+        self._boxes = {}   # boxes as float64 arrays (compute_host)
         b = np.ascontiguousarray(beta, dtype=np.float64)
         nc = self._lib.snap_num_coeff(twojmax)
         if nc < 0 or b.shape != (nc + 1,):
@@ -464,10 +466,27 @@ class Snap:
     def launches_per_call(self) -> int:
         return self._lib.snap_launches_per_call(self._h)
 
+    def _host_ptr(self, a):
+        """Address of a host array's data.  Arrays passed again (the usual loop
+        over steps with the same buffers) take it from a cache that holds a
+        reference to each array, so its buffer cannot move or be freed while
+        cached (numpy cannot resize an array that has other references)."""
+        if a is None:
+            return None
+        hit = self._hp.get(id(a))
+        if hit is not None and hit[0] is a:
+            return hit[1]
+        if len(self._hp) >= 16:
+            self._hp.clear()
+        p = a.ctypes.data
+        self._hp[id(a)] = (a, p)
+        return p
+
     def compute_host(self, pos: np.ndarray, box, stream=None, want_energy=True, want_virial=True,
                      out=None):
         """Evaluate from HOST numpy arrays (copies in and out inside the call)."""
-        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        if not (isinstance(pos, np.ndarray) and pos.dtype == np.float64 and pos.flags.c_contiguous):
+            pos = np.ascontiguousarray(pos, dtype=np.float64)
         n = pos.shape[0]
         if out is None:
             E = np.empty(n) if want_energy else None
@@ -475,10 +494,15 @@ class Snap:
             W = np.empty(6) if want_virial else None
         else:
             E, F, W = out
-        boxa = np.ascontiguousarray(box, dtype=np.float64)
+        key = tuple(float(x) for x in box)
+        boxa = self._boxes.get(key)
+        if boxa is None:
+            if len(self._boxes) >= 16:
+                self._boxes.clear()
+            boxa = self._boxes[key] = np.array(key, dtype=np.float64)
+        hp = self._host_ptr
         self._check(self._lib.snap_compute_host(
-            self._h, n, _np_ptr(pos), _np_ptr(boxa), None if E is None else _np_ptr(E), _np_ptr(F),
-            None if W is None else _np_ptr(W), ctypes.c_void_p(stream or 0)))
+            self._h, n, hp(pos), hp(boxa), hp(E), hp(F), hp(W), stream or 0))
         return E, F, W
 
     def get_buffer(self, which: int) -> np.ndarray:
