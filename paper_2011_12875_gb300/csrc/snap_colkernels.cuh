@@ -130,20 +130,31 @@ __host__ __device__ constexpr double c_sqrt(double x) { return x <= 1.0 ? 1.0 : 
 template <int T, int MA>
 __host__ __device__ constexpr double v_scale() { return c_sqrt(c_fact(T - MA) * c_fact(MA)); }
 
+// x * y + z, one rounding (the sums below are written as chains of these:
+// a component of a complex multiply-add is two fused operations, where
+// x += a*b + c*d would round a product, a fused sum and an addition)
+template <typename R>
+__device__ __forceinline__ R fm(R x, R y, R z) {
+  if constexpr (sizeof(R) == 4) return fmaf(x, y, z);
+  else return fma(x, y, z);
+}
+
 // One layer of the scaled recursion on a lane's column, in place, ma
-// descending; A = conj(a), B = conj(b).
+// descending; A = conj(a), B = conj(b).  An element is four fused
+// multiply-adds a component.
 template <typename R, int T, int N>
 __device__ __forceinline__ void v_layer(c2<R> (&v)[N], const c2<R> A, const c2<R> B) {
   static_assert(T < N, "column too short");
-  c2<R> w = mk<R>(-(B.re * v[T - 1].re - B.im * v[T - 1].im), -(B.re * v[T - 1].im + B.im * v[T - 1].re));
+  c2<R> w = mk<R>(fm(B.im, v[T - 1].im, -(B.re * v[T - 1].re)), fm(-B.im, v[T - 1].re, -(B.re * v[T - 1].im)));
   v[T] = w;
 #pragma unroll
   for (int ma = T - 1; ma >= 1; --ma) {
-    w.re = (A.re * v[ma].re - A.im * v[ma].im) - (B.re * v[ma - 1].re - B.im * v[ma - 1].im);
-    w.im = (A.re * v[ma].im + A.im * v[ma].re) - (B.re * v[ma - 1].im + B.im * v[ma - 1].re);
+    const c2<R> x = v[ma], y = v[ma - 1];
+    w.re = fm(B.im, y.im, fm(-B.re, y.re, fm(-A.im, x.im, A.re * x.re)));
+    w.im = fm(-B.im, y.re, fm(-B.re, y.im, fm(A.im, x.re, A.re * x.im)));
     v[ma] = w;
   }
-  v[0] = mk<R>(A.re * v[0].re - A.im * v[0].im, A.re * v[0].im + A.im * v[0].re);
+  v[0] = mk<R>(fm(-A.im, v[0].im, A.re * v[0].re), fm(A.im, v[0].re, A.re * v[0].im));
 }
 
 // Seed of column T / 2 (lanes with take) for layer T - 1 in the scaled form:
@@ -455,13 +466,13 @@ __device__ __forceinline__ void du_passes(const R* __restrict__ tg, int cnt, int
         c2<R> y = mk<R>(0, 0);
         if (ma < t) {
           const c2<R> p = w[ma], q = dw[ma];
-          y.re += cda.re * p.re - cda.im * p.im + ca.re * q.re - ca.im * q.im;
-          y.im += cda.re * p.im + cda.im * p.re + ca.re * q.im + ca.im * q.re;
+          y.re = fm(-ca.im, q.im, fm(ca.re, q.re, fm(-cda.im, p.im, fm(cda.re, p.re, y.re))));
+          y.im = fm(ca.im, q.re, fm(ca.re, q.im, fm(cda.im, p.re, fm(cda.re, p.im, y.im))));
         }
         if (ma > 0) {
           const c2<R> p = w[ma - 1], q = dw[ma - 1];
-          y.re -= cdb.re * p.re - cdb.im * p.im + cb.re * q.re - cb.im * q.im;
-          y.im -= cdb.re * p.im + cdb.im * p.re + cb.re * q.im + cb.im * q.re;
+          y.re = fm(cb.im, q.im, fm(-cb.re, q.re, fm(cdb.im, p.im, fm(-cdb.re, p.re, y.re))));
+          y.im = fm(-cb.im, q.re, fm(-cb.re, q.im, fm(-cdb.im, p.re, fm(-cdb.re, p.im, y.im))));
         }
         dw[ma] = y;
       }
@@ -692,7 +703,7 @@ __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(W
 #pragma unroll
         for (int ma = 0; ma <= t; ++ma) {
           dst[ma] = u[ma];
-          Ssum += yr[ma].re * u[ma].re + yr[ma].im * u[ma].im;
+          Ssum = fm(yr[ma].im, u[ma].im, fm(yr[ma].re, u[ma].re, Ssum));
         }
       }
     });
@@ -733,15 +744,15 @@ __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(W
         const c2<R> Av = lam[m];
         const c2<R> Bv = lam[m + 1];
         // g_a += conj(A) u ; g_b -= conj(B) u
-        ga.re += Av.re * uu.re + Av.im * uu.im;
-        ga.im += Av.re * uu.im - Av.im * uu.re;
-        gb.re -= Bv.re * uu.re + Bv.im * uu.im;
-        gb.im -= Bv.re * uu.im - Bv.im * uu.re;
+        ga.re = fm(Av.im, uu.im, fm(Av.re, uu.re, ga.re));
+        ga.im = fm(-Av.im, uu.re, fm(Av.re, uu.im, ga.im));
+        gb.re = fm(-Bv.im, uu.im, fm(-Bv.re, uu.re, gb.re));
+        gb.im = fm(Bv.im, uu.re, fm(-Bv.re, uu.im, gb.im));
         // new adjoint: Yw + a A - b B
         const c2<R> y = act ? yr[m] : mk<R>(0, 0);
         c2<R> nl;
-        nl.re = y.re + ka.re * Av.re - ka.im * Av.im - (kb.re * Bv.re - kb.im * Bv.im);
-        nl.im = y.im + ka.re * Av.im + ka.im * Av.re - (kb.re * Bv.im + kb.im * Bv.re);
+        nl.re = fm(kb.im, Bv.im, fm(-kb.re, Bv.re, fm(-ka.im, Av.im, fm(ka.re, Av.re, y.re))));
+        nl.im = fm(-kb.im, Bv.re, fm(-kb.re, Bv.im, fm(ka.im, Av.re, fm(ka.re, Av.im, y.im))));
         if constexpr (even) {
           if (mir) {
             const int mp = tp - m;
@@ -749,14 +760,14 @@ __global__ void __launch_bounds__(de_max_warps<R>() * 32, 1) de_rev_col_kernel(W
             const c2<R> v = mk<R>(sg * uu.re, -sg * uu.im);
             const c2<R> A2 = recv[mp];
             const c2<R> B2 = recv[mp + 1];
-            ga.re += A2.re * v.re + A2.im * v.im;
-            ga.im += A2.re * v.im - A2.im * v.re;
-            gb.re -= B2.re * v.re + B2.im * v.im;
-            gb.im -= B2.re * v.im - B2.im * v.re;
-            const R lr = ka.re * A2.re - ka.im * A2.im - (kb.re * B2.re - kb.im * B2.im);
-            const R li = ka.re * A2.im + ka.im * A2.re - (kb.re * B2.im + kb.im * B2.re);
-            nl.re += sg * lr;
-            nl.im -= sg * li;
+            ga.re = fm(A2.im, v.im, fm(A2.re, v.re, ga.re));
+            ga.im = fm(-A2.im, v.re, fm(A2.re, v.im, ga.im));
+            gb.re = fm(-B2.im, v.im, fm(-B2.re, v.re, gb.re));
+            gb.im = fm(B2.im, v.re, fm(-B2.re, v.im, gb.im));
+            const R lr = fm(kb.im, B2.im, fm(-kb.re, B2.re, fm(-ka.im, A2.im, ka.re * A2.re)));
+            const R li = fm(-kb.im, B2.re, fm(-kb.re, B2.im, fm(ka.im, A2.re, ka.re * A2.im)));
+            nl.re = fm(sg, lr, nl.re);
+            nl.im = fm(-sg, li, nl.im);
           }
         }
         lam[m] = nl;

@@ -264,6 +264,14 @@ __device__ __forceinline__ double flip_if(double v, unsigned bit) {
   return bit ? -v : v;
 }
 
+// x * y + z with one rounding (complex multiply-adds are written as chains
+// of these, two a component)
+template <typename R>
+__device__ __forceinline__ R fmr(R x, R y, R z) {
+  if constexpr (sizeof(R) == 4) return fmaf(x, y, z);
+  else return fma(x, y, z);
+}
+
 // v with its sign bit XORed with bit 31 of m
 __device__ __forceinline__ float flip_sign(float v, unsigned m) {
   return __int_as_float(__float_as_int(v) ^ (int)m);
@@ -416,8 +424,8 @@ __device__ __forceinline__ void y_groups(Src& src, int q, const char* __restrict
       ai += c[j] * (CP ? u2[j].im : flip_sign(u2[j].im, w[j] & 0x80000000u));
     }
     const R i1 = CP ? u1[b].im : flip_sign(u1[b].im, (w[b * K] << 1) & 0x80000000u);
-    yre += u1[b].re * ar - i1 * ai;
-    yim += u1[b].re * ai + i1 * ar;
+    yre = fmr(-i1, ai, fmr(u1[b].re, ar, yre));
+    yim = fmr(i1, ar, fmr(u1[b].re, ai, yim));
   }
 }
 
@@ -433,8 +441,8 @@ __device__ __forceinline__ void y_term(unsigned w, R c, cx<R> u2, const char* __
   if (w & (1u << 28)) {
     const cx<R> u1 = *reinterpret_cast<const cx<R>*>(ul + y_off1<R, false>(w));
     const R i1 = CP ? u1.im : flip_sign(u1.im, (w << 1) & 0x80000000u);
-    y.re += u1.re * y.ar - i1 * y.ai;
-    y.im += u1.re * y.ai + i1 * y.ar;
+    y.re = fmr(-i1, y.ai, fmr(u1.re, y.ar, y.re));
+    y.im = fmr(i1, y.ar, fmr(u1.re, y.ai, y.im));
     y.ar = R(0);
     y.ai = R(0);
     if (w & (1u << 29)) {
@@ -652,8 +660,8 @@ __global__ void __launch_bounds__(kYaWarps * 32) yi_atom_kernel(WorkArgs a) {
       if (w & (pf ? (1u << 12) : (1u << 28))) {
         const int e1 = pf ? (int)(w & 1023u) : (int)((w >> 18) & 1023u) + (int)((w >> 30) & 1u) * H;
         const cx<R> u1 = ua[e1];
-        y.re += u1.re * y.ar - u1.im * y.ai;
-        y.im += u1.re * y.ai + u1.im * y.ar;
+        y.re = fmr(-u1.im, y.ai, fmr(u1.re, y.ar, y.re));
+        y.im = fmr(u1.im, y.ar, fmr(u1.re, y.ai, y.im));
         y.ar = R(0);
         y.ai = R(0);
       }
@@ -698,11 +706,6 @@ template <typename R, bool CP>
 __device__ __forceinline__ unsigned b_off2(unsigned w) {
   const unsigned o = CP ? (w & 0x7FF00u) : (w & 0x3FF00u);
   return sizeof(R) == 4 ? o : o << 1;
-}
-template <typename R>
-__device__ __forceinline__ R fmr(R x, R y, R z) {
-  if constexpr (sizeof(R) == 4) return fmaf(x, y, z);
-  else return fma(x, y, z);
 }
 // byte offset of a piece's output element, from the piece's first word
 template <typename R, bool CP>
@@ -993,7 +996,7 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
         }
         ust[hb + e] = v;
         const cx<R> yw = Yw[hb + e];
-        S += yw.re * v.re + yw.im * v.im;
+        S = fmr(yw.im, v.im, fmr(yw.re, v.re, S));
       }
       __syncwarp();
     }
@@ -1021,15 +1024,15 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
         const cx<R> l2 = lt[mb * (t + 1) + m + 1];
         const cx<R> A = mk<R>(c1 * l1.re, c1 * l1.im);
         const cx<R> B = mk<R>(c2 * l2.re, c2 * l2.im);
-        cx<R> r1 = conj_mul(A, u);
-        cx<R> r2 = conj_mul(B, u);
-        ga.re += r1.re;
-        ga.im += r1.im;
-        gb.re -= r2.re;
-        gb.im -= r2.im;
-        const cx<R> aA = mul(ca, A), bB = mul(cb, B);
+        // g_a += conj(A) u ; g_b -= conj(B) u ; new adjoint Yw + a A - b B
+        ga.re = fmr(A.im, u.im, fmr(A.re, u.re, ga.re));
+        ga.im = fmr(-A.im, u.re, fmr(A.re, u.im, ga.im));
+        gb.re = fmr(-B.im, u.im, fmr(-B.re, u.re, gb.re));
+        gb.im = fmr(B.im, u.re, fmr(-B.re, u.im, gb.im));
         const cx<R> yw = Yw[hbp + e];
-        cx<R> nl = mk<R>(yw.re + aA.re - bB.re, yw.im + aA.im - bB.im);
+        cx<R> nl;
+        nl.re = fmr(cb.im, B.im, fmr(-cb.re, B.re, fmr(-ca.im, A.im, fmr(ca.re, A.re, yw.re))));
+        nl.im = fmr(-cb.im, B.re, fmr(-cb.re, B.im, fmr(ca.im, A.re, fmr(ca.re, A.im, yw.im))));
         if (mirror && mb == mc - 1) {
           // u_t column mc reads v(mp) = sig conj(u_{t-1}[m][mc-1]), mp = tp - m
           const int mp = tp - m;
@@ -1041,16 +1044,14 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
           const cx<R> k2 = lt[mc * (t + 1) + mp + 1];
           const cx<R> A2 = mk<R>(d1 * k1.re, d1 * k1.im);
           const cx<R> B2 = mk<R>(d2 * k2.re, d2 * k2.im);
-          r1 = conj_mul(A2, v);
-          r2 = conj_mul(B2, v);
-          ga.re += r1.re;
-          ga.im += r1.im;
-          gb.re -= r2.re;
-          gb.im -= r2.im;
-          const cx<R> aA2 = mul(ca, A2), bB2 = mul(cb, B2);
-          const cx<R> lv = mk<R>(aA2.re - bB2.re, aA2.im - bB2.im);
-          nl.re += sig * lv.re;
-          nl.im -= sig * lv.im;
+          ga.re = fmr(A2.im, v.im, fmr(A2.re, v.re, ga.re));
+          ga.im = fmr(-A2.im, v.re, fmr(A2.re, v.im, ga.im));
+          gb.re = fmr(-B2.im, v.im, fmr(-B2.re, v.re, gb.re));
+          gb.im = fmr(B2.im, v.re, fmr(-B2.re, v.im, gb.im));
+          const R lr = fmr(cb.im, B2.im, fmr(-cb.re, B2.re, fmr(-ca.im, A2.im, ca.re * A2.re)));
+          const R li = fmr(-cb.im, B2.re, fmr(-cb.re, B2.im, fmr(ca.im, A2.re, ca.re * A2.im)));
+          nl.re = fmr(sig, lr, nl.re);
+          nl.im = fmr(-sig, li, nl.im);
         }
         ln[e] = nl;
       }
