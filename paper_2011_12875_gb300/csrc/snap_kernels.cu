@@ -1389,13 +1389,18 @@ YiGeometry yi_geometry(int rsize, int H, int n, int nsm, int waves) {
   //   ceil(nblk ysplit / resident) (1 / ysplit + c),
   // c = the fixed per-CTA cost (staging U) relative to a whole block's terms,
   // taken as 0.02 / waves (the tunable: more waves, finer splits), and a
-  // tenth of that without staging.
+  // tenth of that without staging.  Staged FP64 keeps its pipe busy all the
+  // time, so the CTAs an SM holds share it: there the count is the most CTAs
+  // an SM takes, ceil(nblk ysplit / SMs), instead of the waves (2J8, 2000
+  // atoms: 405 against 426 us).  Unstaged (2J14) it reads U through L1 and
+  // wants the warps of the finer split (11.06 against 9.33 ms by the SM count).
   const long resident = (long)nsm * cps;
+  const long per = (rsize == 8 && g.staged) ? (long)nsm : resident;
   const double c = (g.staged ? 0.02 : 0.002) / std::max(1, waves);
   double best = 1e300;
   g.ysplit = 1;
   for (int ys = 1; ys <= 64; ++ys) {
-    const long w = ((long)g.nblk * ys + resident - 1) / resident;
+    const long w = ((long)g.nblk * ys + per - 1) / per;
     const double t = (double)w * (1.0 / ys + c);
     if (t < best - 1e-12) {
       best = t;
