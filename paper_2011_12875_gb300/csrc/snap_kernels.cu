@@ -38,6 +38,14 @@ template <typename R>
 __device__ __forceinline__ cx<R> conj_mul(cx<R> a, cx<R> b) {
   return mk<R>(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
 }
+// x * y + z with one rounding (complex multiply-adds are written as chains
+// of these, two a component)
+template <typename R>
+__device__ __forceinline__ R fmr(R x, R y, R z) {
+  if constexpr (sizeof(R) == 4) return fmaf(x, y, z);
+  else return fma(x, y, z);
+}
+
 // a * b
 template <typename R>
 __device__ __forceinline__ cx<R> mul(cx<R> a, cx<R> b) {
@@ -70,6 +78,17 @@ __device__ __forceinline__ cx<R> prev_elem(const cx<R>* lay, int tp, int m, int 
   return mk<R>(s * v.re, -s * v.im);
 }
 
+// The same in the scaled form v = u / S_t(ma, mb) (S_t = sqrt((t-ma)! ma! /
+// (t-mb)!)): the mirrored element of the new middle column mb = (tp+1)/2
+// also picks up S's ratio between the two columns, 1 / sqrt(mb) (qm).
+template <typename R>
+__device__ __forceinline__ cx<R> prev_elem_v(const cx<R>* lay, int tp, int m, int mb, R qm) {
+  if (2 * mb <= tp) return lay[mb * (tp + 1) + m];
+  const cx<R> v = lay[(tp - mb) * (tp + 1) + (tp - m)];
+  const R s = ((m + mb) & 1) ? -qm : qm;
+  return mk<R>(s * v.re, -s * v.im);
+}
+
 // ------------------------------------------------------------- compute_U
 // First the atom's slot geometry (snap_geom.cuh), then the recursion.  One
 // CTA per atom i, one warp per neighbour pair (lanes over the elements of
@@ -77,9 +96,11 @@ __device__ __forceinline__ cx<R> prev_elem(const cx<R>* lay, int tp, int m, int 
 // (Eq. hysphrecur): for mb <= t/2,
 //   u_t[ma][mb] = sqrt((t-ma)/(t-mb)) conj(a) u_{t-1}[ma][mb]
 //               - sqrt(ma/(t-mb))     conj(b) u_{t-1}[ma-1][mb],
-// with only the previous layer kept (double buffer, shared memory).  f_c u_t
-// is summed per warp in shared memory, the warps are summed in a fixed order
-// and w_self is added on the diagonal (Eq. u).
+// with only the previous layer kept (double buffer, shared memory), run in the
+// scaled form u = S v, v_t[ma] = conj(a) v_{t-1}[ma] - conj(b) v_{t-1}[ma-1]
+// (S absorbs both root factors; four fused multiply-adds a component).  f_c v
+// is summed per warp in shared memory, the warps are summed in a fixed order,
+// multiplied by S once, and w_self is added on the diagonal (Eq. u).
 template <typename R, int NW>
 __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -113,26 +134,23 @@ __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
     __syncwarp();
     for (int t = 1; t <= J2; ++t) {
       const int size = half_layer_size(t), hb = half_base(t);
+      const R qm = (t & 1) ? R(0) : root[kRootDim + t / 2];  // 1 / sqrt(t/2): the mirror's ratio
       for (int e = lane; e < size; e += 32) {
         const int mb = e / (t + 1), ma = e - mb * (t + 1);
         cx<R> v = mk<R>(0, 0);
-        if (ma < t) {
-          const cx<R> p = prev_elem(cur, t - 1, ma, mb);
-          const cx<R> w = conj_mul(ca, p);
-          const R c = root[(t - ma) * kRootDim + (t - mb)];
-          v.re += c * w.re;
-          v.im += c * w.im;
+        if (ma < t) {  // + conj(a) v_{t-1}[ma]
+          const cx<R> p = prev_elem_v(cur, t - 1, ma, mb, qm);
+          v.re = fmr(ca.im, p.im, ca.re * p.re);
+          v.im = fmr(-ca.im, p.re, ca.re * p.im);
         }
-        if (ma > 0) {
-          const cx<R> p = prev_elem(cur, t - 1, ma - 1, mb);
-          const cx<R> w = conj_mul(cb, p);
-          const R c = root[ma * kRootDim + (t - mb)];
-          v.re -= c * w.re;
-          v.im -= c * w.im;
+        if (ma > 0) {  // - conj(b) v_{t-1}[ma-1]
+          const cx<R> p = prev_elem_v(cur, t - 1, ma - 1, mb, qm);
+          v.re = fmr(-cb.im, p.im, fmr(-cb.re, p.re, v.re));
+          v.im = fmr(cb.im, p.re, fmr(-cb.re, p.im, v.im));
         }
         nxt[e] = v;
-        myacc[hb + e].re += fc * v.re;
-        myacc[hb + e].im += fc * v.im;
+        myacc[hb + e].re = fmr(fc, v.re, myacc[hb + e].re);
+        myacc[hb + e].im = fmr(fc, v.im, myacc[hb + e].im);
       }
       __syncwarp();
       cx<R>* tmp = cur;
@@ -151,6 +169,9 @@ __global__ void __launch_bounds__(NW * 32) ui_kernel(WorkArgs a) {
       s.re += acc[w * H + e].re;
       s.im += acc[w * H + e].im;
     }
+    const R sc = reinterpret_cast<const R*>(a.hscale)[e];  // u = S v
+    s.re *= sc;
+    s.im *= sc;
     const int p = a.half_tmm[e];
     if (tmm_ma(p) == tmm_mb(p)) s.re += (R)a.wself;
     Ug[(blk * H + e) * 32 + li] = s;
@@ -262,14 +283,6 @@ __device__ __forceinline__ float flip_if(float v, unsigned bit) {
 }
 __device__ __forceinline__ double flip_if(double v, unsigned bit) {
   return bit ? -v : v;
-}
-
-// x * y + z with one rounding (complex multiply-adds are written as chains
-// of these, two a component)
-template <typename R>
-__device__ __forceinline__ R fmr(R x, R y, R z) {
-  if constexpr (sizeof(R) == 4) return fmaf(x, y, z);
-  else return fma(x, y, z);
 }
 
 // v with its sign bit XORed with bit 31 of m
@@ -955,8 +968,10 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
     for (int e = threadIdx.x; e < H; e += blockDim.x) {
       const int p = a.half_tmm[e];
       const R w = (R)half_weight(tmm_t(p), tmm_ma(p), tmm_mb(p));
+      // the contraction weight times S of the scaled recursion (u = S v)
+      const R ws = w * reinterpret_cast<const R*>(a.hscale)[e];
       const cx<R> y = Yg[(blk * H + e) * 32 + li];
-      Yw[e] = mk<R>(w * y.re, w * y.im);
+      Yw[e] = mk<R>(ws * y.re, ws * y.im);
     }
   }
   __syncthreads();
@@ -979,20 +994,19 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
     for (int t = 1; t <= J2; ++t) {
       const int size = half_layer_size(t), hb = half_base(t);
       const cx<R>* pl = ust + half_base(t - 1);
+      const R qm = (t & 1) ? R(0) : root[kRootDim + t / 2];  // 1 / sqrt(t/2): the mirror's ratio
       for (int e = lane; e < size; e += 32) {
         const int mb = e / (t + 1), ma = e - mb * (t + 1);
         cx<R> v = mk<R>(0, 0);
-        if (ma < t) {
-          const cx<R> w = conj_mul(ca, prev_elem(pl, t - 1, ma, mb));
-          const R c = root[(t - ma) * kRootDim + (t - mb)];
-          v.re += c * w.re;
-          v.im += c * w.im;
+        if (ma < t) {  // + conj(a) v_{t-1}[ma]
+          const cx<R> p = prev_elem_v(pl, t - 1, ma, mb, qm);
+          v.re = fmr(ca.im, p.im, ca.re * p.re);
+          v.im = fmr(-ca.im, p.re, ca.re * p.im);
         }
-        if (ma > 0) {
-          const cx<R> w = conj_mul(cb, prev_elem(pl, t - 1, ma - 1, mb));
-          const R c = root[ma * kRootDim + (t - mb)];
-          v.re -= c * w.re;
-          v.im -= c * w.im;
+        if (ma > 0) {  // - conj(b) v_{t-1}[ma-1]
+          const cx<R> p = prev_elem_v(pl, t - 1, ma - 1, mb, qm);
+          v.re = fmr(-cb.im, p.im, fmr(-cb.re, p.re, v.re));
+          v.im = fmr(cb.im, p.re, fmr(-cb.re, p.im, v.im));
         }
         ust[hb + e] = v;
         const cx<R> yw = Yw[hb + e];
@@ -1014,16 +1028,13 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
       const int sizep = half_layer_size(tp), hbp = half_base(tp);
       const bool mirror = ((t & 1) == 0);
       const int mc = t >> 1;  // the column of layer t that reads a mirrored column
+      const R qmc = mirror ? root[kRootDim + mc] : R(0);  // 1 / sqrt(mc)
       for (int e = lane; e < sizep; e += 32) {
         const int mb = e / (tp + 1), m = e - mb * (tp + 1);
         const cx<R> u = ust[hbp + e];
-        // u_{t-1}[m][mb] feeds u_t[m][mb] (a-term) and u_t[m+1][mb] (b-term)
-        const R c1 = root[(t - m) * kRootDim + (t - mb)];
-        const R c2 = root[(m + 1) * kRootDim + (t - mb)];
-        const cx<R> l1 = lt[mb * (t + 1) + m];
-        const cx<R> l2 = lt[mb * (t + 1) + m + 1];
-        const cx<R> A = mk<R>(c1 * l1.re, c1 * l1.im);
-        const cx<R> B = mk<R>(c2 * l2.re, c2 * l2.im);
+        // v_{t-1}[m][mb] feeds v_t[m][mb] (a-term) and v_t[m+1][mb] (b-term)
+        const cx<R> A = lt[mb * (t + 1) + m];
+        const cx<R> B = lt[mb * (t + 1) + m + 1];
         // g_a += conj(A) u ; g_b -= conj(B) u ; new adjoint Yw + a A - b B
         ga.re = fmr(A.im, u.im, fmr(A.re, u.re, ga.re));
         ga.im = fmr(-A.im, u.re, fmr(A.re, u.im, ga.im));
@@ -1034,16 +1045,12 @@ __global__ void __launch_bounds__(NW * 32) de_kernel(WorkArgs a) {
         nl.re = fmr(cb.im, B.im, fmr(-cb.re, B.re, fmr(-ca.im, A.im, fmr(ca.re, A.re, yw.re))));
         nl.im = fmr(-cb.im, B.re, fmr(-cb.re, B.im, fmr(ca.im, A.re, fmr(ca.re, A.im, yw.im))));
         if (mirror && mb == mc - 1) {
-          // u_t column mc reads v(mp) = sig conj(u_{t-1}[m][mc-1]), mp = tp - m
+          // v_t column mc reads sig qm conj(v_{t-1}[m][mc-1]) at row mp = tp - m
           const int mp = tp - m;
-          const R sig = ((m + mc - 1) & 1) ? R(-1) : R(1);
+          const R sig = ((m + mc - 1) & 1) ? -qmc : qmc;
           const cx<R> v = mk<R>(sig * u.re, -sig * u.im);
-          const R d1 = root[(t - mp) * kRootDim + (t - mc)];
-          const R d2 = root[(mp + 1) * kRootDim + (t - mc)];
-          const cx<R> k1 = lt[mc * (t + 1) + mp];
-          const cx<R> k2 = lt[mc * (t + 1) + mp + 1];
-          const cx<R> A2 = mk<R>(d1 * k1.re, d1 * k1.im);
-          const cx<R> B2 = mk<R>(d2 * k2.re, d2 * k2.im);
+          const cx<R> A2 = lt[mc * (t + 1) + mp];
+          const cx<R> B2 = lt[mc * (t + 1) + mp + 1];
           ga.re = fmr(A2.im, v.im, fmr(A2.re, v.re, ga.re));
           ga.im = fmr(-A2.im, v.re, fmr(A2.re, v.im, ga.im));
           gb.re = fmr(-B2.im, v.im, fmr(-B2.re, v.re, gb.re));
