@@ -116,3 +116,49 @@ def test_noalloc_reports_overflow_and_rejects_oversized_input(lib):
                                       None) == 0
     again = noalloc_lists(lib, cfg, 32)
     assert again[4] == 26
+
+
+def test_noalloc_call_captured_in_a_cuda_graph_replays_on_new_positions(lib):
+    """The entry point's reason to exist is use inside a stream capture: one
+    call (counter reset, positions, build, max-count copy) is captured once
+    and replayed on two configurations of the same box copied into the
+    captured position buffer.  Each replay matches the existing entry point,
+    max_count included, so the scratch counters are cleared on every replay."""
+    cap = 32
+    a = inputs.bcc(4, disp=0.1, seed=11)
+    b = inputs.bcc(4, disp=0.2, seed=12)
+    assert np.array_equal(a.box, b.box)
+    n = a.natoms
+    dev = "cuda:0"
+    pos = torch.tensor(a.pos, dtype=torch.float64, device=dev)
+    cnt = torch.full((n,), -1, dtype=torch.int32, device=dev)
+    nbr = torch.full((n, cap), -1, dtype=torch.int32, device=dev)
+    img = torch.zeros((n, cap, 3), dtype=torch.int8, device=dev)
+    rij = torch.zeros((n, cap, 3), dtype=torch.float64, device=dev)
+    mx = torch.zeros(1, dtype=torch.int32, device=dev)
+    box = np.ascontiguousarray(a.box, dtype=np.float64)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+
+    def call(stream):
+        return lib.snap_neighbors_noalloc(n, ptr(pos), box.ctypes.data_as(ctypes.c_void_p),
+                                          inputs.RCUT, cap, ptr(cnt), ptr(nbr), ptr(img),
+                                          ptr(rij), ptr(mx), ctypes.c_void_p(stream))
+
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        assert call(side.cuda_stream) == 0  # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        assert call(torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    for cfg in (a, b, a):
+        want = existing_lists(cfg, cap)
+        pos.copy_(torch.tensor(cfg.pos, dtype=torch.float64, device=dev))
+        cnt.fill_(-1)
+        mx.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        got = (cnt.cpu().numpy(), nbr.cpu().numpy(), img.cpu().numpy(), rij.cpu().numpy())
+        same(got, want)
+        assert int(mx.item()) == want[0].max()
