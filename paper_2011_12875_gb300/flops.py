@@ -34,20 +34,23 @@ def ui_pair(twojmax: int) -> int:
 
 @lru_cache(maxsize=None)
 def de_pair(twojmax: int) -> int:
-    """Fused dU + dE, one pair: forward recursion (as compute_U, with the
-    Re(Y conj u) accumulation, 4) and the reverse pass: per element of layer
-    t-1 two root scalings (4), two conj(lambda) u products accumulated into
-    g_a, g_b (16), a*A and b*B (12), the new adjoint (4); the mirrored column
-    of even layers repeats the same work; final combination 3 x 10 (FP64)."""
+    """Fused dU + dE, one pair, in the scaled form (S folded into the
+    weighted Y, so neither pass scales by roots).  Forward: the recursion as
+    in compute_U and the Re(Yw conj v) accumulation (4) per element.
+    Reverse, per element of layer t-1: conj(A) v and conj(B) v accumulated
+    into g_a, g_b (8 + 8) and the new adjoint Yw + a A - b B (16); an element
+    that also seeds the mirrored column of an even layer t adds the seed's
+    scaling of v (2), the same two accumulations (16), a A2 - b B2 (14) and
+    its scaled addition to the adjoint (4).  Final combination 3 x 10."""
     f = 2
     for t in range(1, twojmax + 1):
         for ma, mb in half_layer(t):
             nterm = (ma < t) + (ma > 0)
-            f += 10 * nterm + 4
+            f += 6 * nterm + 2 * (nterm - 1) + 4
     for t in range(twojmax, 0, -1):
         tp = t - 1
         for m, mb in half_layer(tp):
-            f += 36
+            f += 32
             if t % 2 == 0 and mb == t // 2 - 1:
                 f += 36
     return f + 30
