@@ -23,9 +23,14 @@ def ui_pair(twojmax: int) -> int:
     (u = S v, v_t[ma] = conj(a) v_{t-1}[ma] - conj(b) v_{t-1}[ma-1], with f_c
     carried in v from layer 0): a complex multiply (6) per term and the
     subtraction of the two terms (2), and the element added to the pair sum
-    (2); S and w_self are applied once per atom, not per pair."""
+    (2); before an even layer t, the seed of its middle column (layer t-1's
+    column t/2: the mirror of column t/2 - 1 scaled by 1/sqrt(t/2), 2 for
+    each of its t elements); S and w_self are applied once per atom, not
+    per pair."""
     f = 2  # layer 0: f_c added to the sum
     for t in range(1, twojmax + 1):
+        if t % 2 == 0:
+            f += 2 * t
         for ma, mb in half_layer(t):
             nterm = (ma < t) + (ma > 0)
             f += 6 * nterm + 2 * (nterm - 1) + 2
@@ -35,15 +40,18 @@ def ui_pair(twojmax: int) -> int:
 @lru_cache(maxsize=None)
 def de_pair(twojmax: int) -> int:
     """Fused dU + dE, one pair, in the scaled form (S folded into the
-    weighted Y, so neither pass scales by roots).  Forward: the recursion as
-    in compute_U and the Re(Yw conj v) accumulation (4) per element.
+    weighted Y, so neither pass scales by roots).  Forward: the recursion and
+    the seeds as in compute_U (layer 0 is v = 1, S = Re Yw_0: no arithmetic)
+    and the Re(Yw conj v) accumulation (4) per element.
     Reverse, per element of layer t-1: conj(A) v and conj(B) v accumulated
     into g_a, g_b (8 + 8) and the new adjoint Yw + a A - b B (16); an element
     that also seeds the mirrored column of an even layer t adds the seed's
     scaling of v (2), the same two accumulations (16), a A2 - b B2 (14) and
     its scaled addition to the adjoint (4).  Final combination 3 x 10."""
-    f = 2
+    f = 0
     for t in range(1, twojmax + 1):
+        if t % 2 == 0:
+            f += 2 * t
         for ma, mb in half_layer(t):
             nterm = (ma < t) + (ma > 0)
             f += 6 * nterm + 2 * (nterm - 1) + 4
