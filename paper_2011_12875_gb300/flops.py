@@ -9,7 +9,9 @@ of the benchmark; the derivation is written out in the design notes.
 from __future__ import annotations
 
 import heapq
+from fractions import Fraction
 from functools import lru_cache
+from math import factorial
 
 
 def half_layer(t: int):
@@ -109,6 +111,25 @@ def _cover_size(edges) -> int:
 
 
 @lru_cache(maxsize=None)
+def _cg_nonzero(t1: int, x1: int, t2: int, x2: int, t: int) -> bool:
+    """Whether <j1 m1 j2 m2 | j m1+m2> is nonzero, decided exactly: with
+    doubled ranks (t = 2j) and m1 = x1 - t1/2, m2 = x2 - t2/2, for a triangle
+    (t1, t2, t) and |m1 + m2| <= j the coefficient is a nonzero factor times
+    Racah's alternating sum of inverse factorial products, here summed in
+    rationals."""
+    a = (t1 + t2 - t) // 2          # j1 + j2 - j
+    b = t1 - x1                     # j1 - m1
+    c = x2                          # j2 + m2
+    d = (t - t1 - t2) // 2 + x1     # j - j2 + m1
+    e = (t - t1 + t2) // 2 - x2     # j - j1 - m2
+    s = Fraction(0)
+    for k in range(max(0, -d, -e), min(a, b, c) + 1):
+        s += Fraction((-1) ** k, factorial(k) * factorial(a - k) * factorial(b - k) *
+                      factorial(c - k) * factorial(d + k) * factorial(e + k))
+    return s != 0
+
+
+@lru_cache(maxsize=None)
 def yi_atom(twojmax: int) -> int:
     """compute_Y, one atom.  For each half element (t, ma, mb) of Y, the terms
     beta~ C(ma1,ma2) C(mb1,mb2) U_t1[ma1][mb1] U_t2[ma2][mb2] of every triple
@@ -118,9 +139,9 @@ def yi_atom(twojmax: int) -> int:
     contraction reads, and are not computed.  The terms of an output are
     grouped by a shared factor, Y += U[e] * sum_k coef_k U[e_k], the factors
     chosen by a greedy vertex cover.  Per term a real-by-complex
-    scale-accumulate (4), per group a complex multiply-accumulate (8).  Terms
-    are counted structurally (a Clebsch-Gordan product that happens to vanish
-    is still counted)."""
+    scale-accumulate (4), per group a complex multiply-accumulate (8).  A
+    term whose Clebsch-Gordan product vanishes (a selection rule or an
+    accidental zero of Racah's sum) is no work and is not counted."""
     f = 0
     for t in range(twojmax + 1):
         for ma, mb in half_layer(t):
@@ -133,7 +154,11 @@ def yi_atom(twojmax: int) -> int:
                         continue
                     dl = (t1 + t2 - t) // 2
                     for mb1 in range(max(0, mb + dl - t2), min(t1, mb + dl) + 1):
+                        if not _cg_nonzero(t1, mb1, t2, mb + dl - mb1, t):
+                            continue
                         for ma1 in range(max(0, ma + dl - t2), min(t1, ma + dl) + 1):
+                            if not _cg_nonzero(t1, ma1, t2, ma + dl - ma1, t):
+                                continue
                             x1 = _half_elem(t1, ma1, mb1)
                             x2 = _half_elem(t2, ma + dl - ma1, mb + dl - mb1)
                             pairs.add((min(x1, x2), max(x1, x2)) if t1 == t2 else (x1, x2))

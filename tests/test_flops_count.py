@@ -12,6 +12,8 @@ The run is pinned to the oracle before its tally is trusted:
   * reverse: dE/dr of E = f_c Re sum conj(Yw) v equals central differences
     of the same E through the oracle's Cayley-Klein geometry (Sec. II).
 A count in ``flops.py`` that drops or adds a term then fails the equality.
+compute_Y's count (``flops.yi_atom``) leaves out terms whose Clebsch-Gordan
+product vanishes; its exact zero test is pinned to the oracle's CG values.
 """
 import math
 
@@ -196,3 +198,27 @@ def test_counted_reverse_is_the_gradient(J):
         e[d] = h
         fd = (energy(r + e) - energy(r - e)) / (2 * h)
         assert abs(fd - dedr[d]) < 1e-7 * max(1.0, abs(fd)), (d, fd, dedr[d])
+
+
+def test_y_count_zero_decision_matches_the_oracle_cg():
+    """compute_Y's count leaves out terms whose Clebsch-Gordan product
+    vanishes; its exact zero test agrees with the oracle's Racah CG (in
+    FP64: an accidental zero comes out below 1e-12) on every coefficient
+    the 2J <= 14 term lists use."""
+    J = 14
+    nz = zero = 0
+    for t in range(J + 1):
+        for t1 in range(J + 1):
+            for t2 in range(t1 + 1):
+                if not (t1 - t2 <= t <= min(J, t1 + t2)) or (t1 + t2 - t) % 2:
+                    continue
+                for x1 in range(t1 + 1):
+                    for x2 in range(t2 + 1):
+                        m = (2 * x1 - t1) + (2 * x2 - t2)
+                        if abs(m) > t:
+                            continue
+                        want = abs(O.cg(t1, 2 * x1 - t1, t2, 2 * x2 - t2, t, m)) > 1e-12
+                        assert flops._cg_nonzero(t1, x1, t2, x2, t) == want, (t1, x1, t2, x2, t)
+                        nz += want
+                        zero += not want
+    assert nz > 0 and zero > 0
