@@ -942,12 +942,14 @@ __global__ void __launch_bounds__(256) force_weighted_kernel(WorkArgs a, const d
 }
 
 // ------------------------------------------------------ fused dU + dE/dr
-// One CTA per atom i with Y_i (weighted by half_weight) staged in shared
-// memory; one warp per pair.  For a pair, S(a, b) = sum_t Re Y_t : conj(u_t)
+// One CTA per atom i with Y_i (weighted by half_weight and by S of the
+// scaled recursion u = S v) staged in shared memory; one warp per pair.  For
+// a pair, S(a, b) = sum_t Re Y_t : conj(u_t) = sum_t Re (S Y_t) : conj(v_t)
 // is a real function of the Cayley-Klein parameters.  Its gradient follows
-// from one forward pass of the layer recursion (all layers kept in shared
-// memory) and one reverse (adjoint) pass through the same recursion, so
-// neither dU nor its three Cartesian components is ever formed.  Then
+// from one forward pass of the scaled layer recursion (all layers of v kept
+// in shared memory) and one reverse (adjoint) pass through the same
+// recursion, so neither dU nor its three Cartesian components is ever
+// formed, and neither pass applies a root factor.  Then
 //   dE_i/dr_ik = S df_c/dr + f_c (<g_a, da/dr> + <g_b, db/dr>),
 // <x, y> = Re(conj(x) y), which is Eq. (snapforce2) for this pair.
 template <typename R, int NW>
