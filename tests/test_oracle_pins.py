@@ -386,3 +386,67 @@ def test_oracle_flop_counter_walks_the_nonzero_cg_terms():
         assert f["y_b_atom"] == 47 * nterm, J
         assert f["compute_u_pair"] == 12 * rec + 4 * nfull
         assert f["du_de_pair"] == 12 * rec + 54 * rec + 30 * nfull
+
+
+def z_full(t1, t2, t, Ua, Ub):
+    """Z^t_{t1 t2}[ma][mb] = sum CG CG Ua_t1[ma1][mb1] Ub_t2[ma2][mb2]
+    (Eq. z), full matrices, written out here on its own."""
+    dl = (t1 + t2 - t) // 2
+    A, Bm = O.block(Ua, t1), O.block(Ub, t2)
+    Z = np.zeros((t + 1, t + 1), dtype=complex)
+    for ma in range(t + 1):
+        for mb in range(t + 1):
+            s = 0j
+            for ma1 in range(max(0, ma + dl - t2), min(t1, ma + dl) + 1):
+                ma2 = ma + dl - ma1
+                ca = O.cg(t1, 2 * ma1 - t1, t2, 2 * ma2 - t2, t, 2 * ma - t)
+                for mb1 in range(max(0, mb + dl - t2), min(t1, mb + dl) + 1):
+                    mb2 = mb + dl - mb1
+                    cb = O.cg(t1, 2 * mb1 - t1, t2, 2 * mb2 - t2, t, 2 * mb - t)
+                    s += ca * cb * A[ma1, mb1] * Bm[ma2, mb2]
+            Z[ma, mb] = s
+    return Z
+
+
+@pytest.mark.parametrize("twojmax", [2, 4])
+def test_direct_db_route_gives_the_adjoint_forces(twojmax):
+    """The second route of the forces (Eq. dbidrk): dB_l^i/dr_ik by the
+    product rule on B_l = Re Z : conj(U) with dU of the one pair, then
+    dE_i/dr_ik = sum_l beta_l dB_l^i/dr_ik.  It equals the oracle's adjoint
+    dE_i/dr_ik (Eq. snapforce2, through Y) pair by pair, and dB agrees with
+    central differences of the oracle's B in the pair's separation."""
+    p = O.Params(twojmax)
+    cfg = inputs.bcc(2, disp=0.15, seed=31)
+    beta = inputs.beta(twojmax)
+    pairs = O.build_neighbors(cfg.pos, cfg.box, p.rcut)
+    n = cfg.natoms
+    res = O.compute(p, beta, n, pairs, want_UY=True, want_B=True)
+    tr = O.triples(twojmax)
+    i = 3
+    Ui = res.U[i]
+    for q in np.flatnonzero(pairs.i == i)[:6]:
+        u, du, g = O.ulist_pair(p, pairs.rij[q], with_du=True)
+        dB = np.zeros((len(tr), 3))
+        for d in range(3):
+            dU = g["dfc"][d] * u + g["fc"] * du[d]
+            for l, (t1, t2, t) in enumerate(tr):
+                Z = z_full(t1, t2, t, Ui, Ui)
+                dZ = z_full(t1, t2, t, dU, Ui) + z_full(t1, t2, t, Ui, dU)
+                dB[l, d] = np.real(np.sum(dZ * np.conj(O.block(Ui, t))) +
+                                   np.sum(Z * np.conj(O.block(dU, t))))
+        dE = beta[1:] @ dB
+        scale = max(1.0, np.abs(res.dedr).max())
+        np.testing.assert_allclose(dE, res.dedr[q], rtol=0, atol=1e-11 * scale)
+        # dB against central differences of the oracle's B_l^i
+        need = np.zeros(n, dtype=bool)
+        need[i] = True
+        h = 1e-5
+        for d in range(3):
+            Bpm = []
+            for sgn in (1.0, -1.0):
+                rij = pairs.rij.copy()
+                rij[q, d] += sgn * h
+                moved = O.Pairs(pairs.i, pairs.k, pairs.img, rij)
+                Bpm.append(O.compute(p, beta, n, moved, need=need, want_B=True).B[i])
+            fd = (Bpm[0] - Bpm[1]) / (2 * h)
+            np.testing.assert_allclose(dB[:, d], fd, rtol=0, atol=1e-7 * max(1.0, np.abs(fd).max()))
