@@ -450,3 +450,18 @@ def test_direct_db_route_gives_the_adjoint_forces(twojmax):
                 Bpm.append(O.compute(p, beta, n, moved, need=need, want_B=True).B[i])
             fd = (Bpm[0] - Bpm[1]) / (2 * h)
             np.testing.assert_allclose(dB[:, d], fd, rtol=0, atol=1e-7 * max(1.0, np.abs(fd).max()))
+
+
+@pytest.mark.parametrize("twojmax", [3, 8])
+def test_isolated_cluster_has_no_net_force_or_torque(twojmax):
+    """The energy of an isolated cluster is invariant under translation and
+    rotation, so the forces sum to zero and so do their torques r x F."""
+    p = O.Params(twojmax)
+    pos, box = cluster()
+    _, r = O.evaluate(p, inputs.beta(twojmax), pos, box)
+    scale = np.abs(r.F).max() * len(pos)
+    assert scale > 0
+    np.testing.assert_allclose(r.F.sum(0), 0.0, atol=1e-12 * scale)
+    c = pos - pos.mean(0)
+    torque = np.cross(c, r.F).sum(0)
+    np.testing.assert_allclose(torque, 0.0, atol=1e-12 * scale * np.abs(c).max())
