@@ -98,7 +98,8 @@ __device__ __forceinline__ cx<R> prev_elem_v(const cx<R>* lay, int tp, int m, in
 //               - sqrt(ma/(t-mb))     conj(b) u_{t-1}[ma-1][mb],
 // with only the previous layer kept (double buffer, shared memory), run in the
 // scaled form u = S v, v_t[ma] = conj(a) v_{t-1}[ma] - conj(b) v_{t-1}[ma-1]
-// (S absorbs both root factors; four fused multiply-adds a component).  f_c v
+// (S absorbs both root factors; a multiply and three fused multiply-adds a
+// component, with S_t(ma, mb) = sqrt((t-ma)! ma! / (t-mb)!)).  f_c v
 // is summed per warp in shared memory, the warps are summed in a fixed order,
 // multiplied by S once, and w_self is added on the diagonal (Eq. u).
 template <typename R, int NW>
